@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the float64 modal DG solver (2D Euler, SSP-RK3).
+
+Metric: DOF-updates/s per RK stage = N * N_p * 4 * 3 * steps / time, on the
+256 x 256 jittered periodic mesh (131,072 triangles) at p = 3 with the isentropic
+vortex.  One benchmark step = one SSP-RK3 time step (three right-hand sides and
+stage updates) followed by the conserved-totals reduction, i.e. every row of the
+hot path, on inputs already resident in HBM.  L2 is flushed (256 MiB write)
+between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on
+its own GPU (the path is replicated, not sharded): value = all ranks' DOF
+updates / the slowest rank's time.  --impl reference times the CPU oracle on
+the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s per RK stage, FP64 vs mixed at stated err; adjoint/forward ratio"
+UNIT = "DOF-updates/s"
+WORKLOAD = dict(name="isentropic vortex, 256x256 jittered periodic triangle mesh "
+                     "(131072 elements), p=3, 4-point Gauss edges, SSP-RK3, CFL 0.3",
+                n=256, p=3, ne=0, cfl=0.3)
+
+
+def flops_element_per_elem(p: int, ne: int) -> float:
+    """Algorithmic float64 flops of one element-kernel launch per element (stage
+    update with next traces), counting an FMA as 2 flops:
+      interpolation 2*NQ*NP*4, flux + J^tau transform 40 per point,
+      projection 2*2NQ*NP*4, lift 2*3NE*NP*4, stage update 5*NP*4,
+      next traces 2*3NE*NP*4."""
+    NP = (p + 1) * (p + 2) // 2
+    NQ = (p + 1) ** 2
+    NF = 3 * ne
+    return 2 * NQ * NP * 4 + 40 * NQ + 4 * NQ * NP * 4 + 2 * NF * NP * 4 + 5 * NP * 4 + 2 * NF * NP * 4
+
+
+def _src_hash(*names) -> str:
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1601_07944_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per launch of the element kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) from one ncu capture, keyed by the hash of the kernel
+# source it was taken on; a source change voids the entry.
+TRAFFIC = {}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_id_for_smi(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _dof_per_step(N: int, p: int) -> int:
+    return N * (p + 1) * (p + 2) // 2 * 4 * 3
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_1601_07944_gb300 import inputs as I
+    oracle.build()
+    p = WORKLOAD["p"]
+    # calibrate on a 64x64 mesh of the same structure and order, then size the
+    # sample so that warm-up + timed steps take about a minute
+    n = 64
+    mesh = I.periodic_mesh(n)
+    o = oracle.OracleDG.from_mesh(mesh, p, n_edge_pts=WORKLOAD["ne"])
+    c = o.project_ic(I.vortex)
+    dt = I.fixed_dt(I.periodic_mesh(WORKLOAD["n"]), I.vortex, p, WORKLOAD["cfl"])
+    t = time.perf_counter(); o.ssp_rk3(c, dt, 1); t1 = time.perf_counter() - t
+    budget = 60.0
+    per_elem_step = t1 / mesh.n_elem
+    steps = args.steps + args.warmup
+    while n < WORKLOAD["n"] and 4 * (2 * n * n) * per_elem_step * steps < budget:
+        n *= 2
+    mesh = I.periodic_mesh(n)
+    o = oracle.OracleDG.from_mesh(mesh, p, n_edge_pts=WORKLOAD["ne"])
+    c = o.project_ic(I.vortex)
+    for _ in range(args.warmup):
+        c = o.ssp_rk3(c, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c = o.ssp_rk3(c, dt, 1)
+    el = time.perf_counter() - t0
+    value = _dof_per_step(mesh.n_elem, p) * args.steps / el
+    sample = ("oracle SSP-RK3 steps of the same vortex at p=3 on a %dx%d mesh (%d elements) of "
+              "the same construction, 1 thread" % (n, n, mesh.n_elem))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded jittered periodic mesh, isentropic vortex)",
+        "config": {"workload": WORKLOAD["name"], "sample": sample, "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """The oracle on the full workload mesh for as many whole steps as fit in about
+    `seconds` (at least one), single-threaded."""
+    import oracle
+    from paper_1601_07944_gb300 import inputs as I
+    oracle.build()
+    mesh = I.periodic_mesh(WORKLOAD["n"])
+    p = WORKLOAD["p"]
+    o = oracle.OracleDG.from_mesh(mesh, p, n_edge_pts=WORKLOAD["ne"])
+    c = o.project_ic(I.vortex)
+    dt = I.fixed_dt(mesh, I.vortex, p, WORKLOAD["cfl"])
+    steps, el = 0, 0.0
+    while el < seconds or steps == 0:
+        t = time.perf_counter()
+        c = o.ssp_rk3(c, dt, 1)
+        el += time.perf_counter() - t
+        steps += 1
+    return {"value": _dof_per_step(mesh.n_elem, p) * steps / el, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": "%d full SSP-RK3 step(s) of the 256x256 p=3 workload on 1 host thread "
+                      "(%.1f s)" % (steps, el)}
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1601_07944_gb300 import _build, dg, inputs as I
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    dg.load()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    p, ne = WORKLOAD["p"], WORKLOAD["ne"]
+    mesh = I.periodic_mesh(WORKLOAD["n"])
+    m = dg.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    ne = m.ne
+    c = m.project_function(I.vortex)
+    dt = I.fixed_dt(mesh, I.vortex, p, WORKLOAD["cfl"])
+    dof_step = _dof_per_step(m.N, p)
+    stream = torch.cuda.current_stream()
+
+    fp64_peak, fp32_peak = dg.probe_fma_rate()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        m.rk_step(c, dt, 1)
+        m.conserved_totals(c)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(_gpu_id_for_smi(local))
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    m.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    totals = None
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        m.rk_step(c, dt, 1)
+        totals = m.conserved_totals(c)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    ktimes = m.kernel_times()
+    m.set_timing(False)
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+    t_max = dev_ms
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * dof_step * args.steps / (t_max * 1e-3)
+
+    # end to end through the host-buffer entry point: H2D, step, D2H every step
+    e2e_steps = max(1, min(args.steps, 20))
+    h = torch.empty(m.coef_shape, dtype=torch.float64).pin_memory()
+    h.copy_(c.cpu())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        m.rk_step_host(h, dt, 1)
+    e2e_s = time.perf_counter() - t0
+    state_bytes = m.N * 4 * m.np * 8
+
+    line = None
+    if rank == 0:
+        launches = sum(n for n, _ in ktimes.values())
+        el_n, el_ms = ktimes.get("element", (0, 0.0))
+        avg_el_ms = el_ms / max(1, el_n)
+        flops = flops_element_per_elem(p, ne) * m.N
+        achieved = flops / (avg_el_ms * 1e-3) / 1e12
+        khash = _src_hash("dg_kernels.cu")
+        traffic = TRAFFIC.get(khash)
+        share = {k: round(ms / max(1e-12, sum(x for _, x in ktimes.values())), 4)
+                 for k, (_, ms) in ktimes.items()}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded jittered periodic mesh, isentropic vortex)",
+            "config": {"workload": WORKLOAD["name"], "n_elem": m.N, "p": p, "n_edge_pts": ne,
+                       "n_vol_pts": m.nq, "precision": "fp64", "dt": dt,
+                       "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_element (float64 FMA pipe)",
+                         "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak if fp64_peak else None, "traffic": traffic,
+                         "peak_source": "measured live: dg_probe_fma_rate float64 FMA chain",
+                         "flops_per_launch": flops, "avg_launch_ms": avg_el_ms},
+            "kernel_share": share,
+            "kernel_times_ms": {k: {"launches": n, "total_ms": ms} for k, (n, ms) in ktimes.items()},
+            "fp32_fma_tflops": fp32_peak,
+            "e2e": {"value": dof_step * e2e_steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                    "entry": "dg_rk_step_host"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s_timed_region": wall,
+            "totals_last_step": [float(x) for x in totals] if totals is not None else None,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) modal discontinuous Galerkin solver for
+ * the 2D compressible Euler equations on unstructured triangle meshes.
+ *
+ * The method is the one of Fuhry, Giuliani and Krivodonova, "Discontinuous
+ * Galerkin methods on graphics processing units for nonlinear hyperbolic
+ * conservation laws" (arXiv:1601.07944):
+ *   - weak form on each triangle mapped to the reference triangle
+ *     {(0,0),(1,0),(0,1)} (Section 2, Eqs. 2ddg, weak2dsys, 2dmap);
+ *   - orthonormal modal basis with N_p = (p+1)(p+2)/2 functions (Eq. np), so
+ *     the mass matrix is the identity and dc/dt = (volume - surface)/det J
+ *     (Eq. 2ddg0);
+ *   - volume integral against the basis gradients (Eq. volume, Algorithm 1);
+ *   - edge integral of a numerical flux computed once per edge from the traces
+ *     of both elements, the right element's points taken in reverse order
+ *     (Eqs. surface, edgeint, Algorithm 2), combined per element (Algorithm 3);
+ *   - Euler flux with p = (gamma-1)(E - rho|v|^2/2) (Eq. euler, Section 5).
+ * Choices this library fixes where the paper leaves them open: the Dubiner
+ * basis (collapsed coordinates, ordered by total degree then by the second
+ * index), a collapsed Gauss-Jacobi volume rule with p+1 points per direction,
+ * Gauss-Legendre edge rules with n_edge_pts points (default p+1, as in the
+ * paper's Section 4.3.3), the local Lax-Friedrichs flux and the three-stage
+ * SSP Runge-Kutta method.
+ *
+ * Conventions for every call:
+ *   - Coefficient arrays are element-major, c[e][m][j]: element e, conserved
+ *     variable m in (rho, rho u, rho v, E), mode j; float64, contiguous,
+ *     N * 4 * N_p values.  They are DEVICE pointers owned by the caller unless a
+ *     call says otherwise.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     asynchronous on it unless stated; a caller must not reuse an output before
+ *     the stream has reached the call.
+ *   - The mesh handle owns its geometry, basis tables and work buffers; calls on
+ *     one handle must not overlap in time on different streams.
+ *   - No call aborts.  Every call returns a dg_status; on failure
+ *     dg_last_error() returns a message for the calling thread.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mesh dg_mesh;     /* opaque, library-owned */
+
+typedef enum {
+    DG_OK = 0,
+    DG_EINVAL = 1,      /* bad argument (null pointer, size, order out of range) */
+    DG_ENOMEM = 2,      /* host or device allocation failed */
+    DG_ECUDA = 3,       /* a CUDA runtime call failed (message says which) */
+    DG_EMESH = 4,       /* mesh fails validation (orientation, neighbours, edges) */
+    DG_ENONPHYS = 5,    /* non-physical state met (rho <= 0 or p <= 0) */
+    DG_ETIMEOUT = 6,    /* a bounded device wait expired */
+    DG_ENOTIMPL = 7     /* valid request this build does not implement */
+} dg_status;
+
+/* Arithmetic of the contractions (interpolation to quadrature points, projection
+ * onto the basis and lifting of edge fluxes).  The Riemann flux, the Runge-Kutta
+ * accumulation and the conserved totals are float64 in every mode. */
+typedef enum {
+    DG_FP64 = 0,        /* every operation in float64 */
+    DG_TF32X1 = 1,      /* contractions on the tensor cores, one TF32 product, FP32 accumulate */
+    DG_TF32X3 = 2       /* contractions as split 3xTF32 products, FP32 accumulate */
+} dg_precision;
+
+/* Host description of a mesh; dg_mesh_create copies everything it needs. */
+typedef struct {
+    int64_t n_elem;             /* N >= 1 */
+    const double *elem_xy;      /* HOST [N][3][2]: vertices, counter-clockwise (det J > 0).
+                                   Periodic meshes store each element's coordinates
+                                   unwrapped; the two copies of a shared edge must be
+                                   translates of each other. */
+    const int64_t *nbr;         /* HOST [N][3]: element across local face q, where local
+                                   face q runs from vertex q to vertex (q+1) mod 3 */
+    const int8_t *nbr_face;     /* HOST [N][3]: that neighbour's local face index */
+    int p;                      /* polynomial degree, 1 <= p <= 5 */
+    int n_edge_pts;             /* Gauss-Legendre points per edge; 0 = p+1 (the paper's rule).
+                                   Supported: p+1, and p for p = 3 */
+    double gamma;               /* ratio of specific heats (1.4 for air) */
+} dg_mesh_desc;
+
+typedef struct {
+    int64_t n_elem;             /* N */
+    int64_t n_face;             /* number of distinct edges */
+    int p, n_modes, n_vol_pts, n_edge_pts;
+    double gamma;
+} dg_mesh_info_t;
+
+/* Validates the mesh (det J > 0; nbr[nbr[e][q]][nbr_face[e][q]] == e and the face
+ * index maps back; the shared edge's endpoints are translates), builds the edge
+ * list, geometry and basis tables on the host and copies them to the current
+ * CUDA device.  Synchronous.  *out receives a handle to free with dg_mesh_destroy.
+ * Errors: DG_EINVAL (null pointers, p or n_edge_pts unsupported), DG_EMESH,
+ * DG_ENOMEM, DG_ECUDA. */
+dg_status dg_mesh_create(const dg_mesh_desc *desc, dg_mesh **out);
+
+/* Frees the handle and its device memory (synchronises the device first).
+ * A NULL handle is accepted. */
+dg_status dg_mesh_destroy(dg_mesh *mesh);
+
+/* Sizes of the discretisation. */
+dg_status dg_mesh_info(const dg_mesh *mesh, dg_mesh_info_t *info);
+
+/* Physical coordinates of the volume quadrature points (Eq. 2dmap applied to the
+ * reference rule): xy[N][n_vol_pts][2], DEVICE.  Asynchronous. */
+dg_status dg_volume_points(const dg_mesh *mesh, double *xy, void *stream);
+
+/* L2 projection of point values onto the orthonormal basis (Section 2, the
+ * initial data u_0):  c[e][m][j] = sum_k w_k u[e][k][m] phi_j(r_k), with u the
+ * conserved state at the points returned by dg_volume_points.
+ * u: DEVICE [N][n_vol_pts][4]; c: DEVICE [N][4][N_p].  Asynchronous. */
+dg_status dg_project_ic(dg_mesh *mesh, const double *u, double *c, void *stream);
+
+/* Right-hand side of Eq. 2ddg0: r = (volume integral - surface integral)/det J for
+ * every element, mode and variable, with the local Lax-Friedrichs flux
+ *   F_hat = (F(U_l).n + F(U_r).n)/2 - alpha (U_r - U_l)/2,
+ *   alpha = max(|v_l.n| + c_l, |v_r.n| + c_r),
+ * evaluated once per edge.  c, r: DEVICE [N][4][N_p], must not alias.
+ * Asynchronous. */
+dg_status dg_rhs(dg_mesh *mesh, const double *c, double *r, dg_precision prec, void *stream);
+
+/* nsteps steps of the three-stage SSP Runge-Kutta method (Shu-Osher form),
+ *   u1 = u + dt L(u),  u2 = 3/4 u + 1/4 (u1 + dt L(u1)),
+ *   u <- 1/3 u + 2/3 (u2 + dt L(u2)),
+ * in place on c (DEVICE [N][4][N_p]).  The stage accumulation is float64 in every
+ * precision mode.  Asynchronous. */
+dg_status dg_rk_step(dg_mesh *mesh, double *c, double dt, int nsteps, dg_precision prec,
+                     void *stream);
+
+/* Same as dg_rk_step with c in HOST memory (pinned memory gives the fastest
+ * copies): copies c to the device, takes nsteps steps and copies the result back
+ * into c.  Synchronous. */
+dg_status dg_rk_step_host(dg_mesh *mesh, double *c_host, double dt, int nsteps,
+                          dg_precision prec, void *stream);
+
+/* Discrete adjoint of one SSP-RK3 step (float64): given the state c_n at the start
+ * of the step and lam_np1 = dJ/dc_{n+1}, writes lam_n = dJ/dc_n = (d c_{n+1}/d c_n)^T
+ * lam_np1.  The stages are recomputed from c_n.  At a tie of the two wave speeds in
+ * alpha the derivative follows the left trace, and d|x|/dx at x = 0 is taken as 0.
+ * All arrays DEVICE [N][4][N_p]; lam_n must not alias the others.  Asynchronous. */
+dg_status dg_adjoint_step(dg_mesh *mesh, const double *c_n, double dt, const double *lam_np1,
+                          double *lam_n, void *stream);
+
+/* Domain integrals of the conserved variables,
+ *   T_m = sum_e int_{Omega_e} U_m = sum_e det J_e c[e][m][0] / sqrt(2)
+ * (only the constant mode has a non-zero mean), as a fixed-order float64
+ * reduction, so repeated calls give bitwise equal results.  c: DEVICE.
+ * out: HOST double[4].  Synchronous on stream. */
+dg_status dg_conserved_totals(dg_mesh *mesh, const double *c, double out[4], void *stream);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+
+/* Kernel kinds reported by dg_kernel_times. */
+enum {
+    DG_K_TRACES = 0,    /* edge traces of a coefficient array */
+    DG_K_FACE = 1,      /* Lax-Friedrichs flux, one thread per edge point */
+    DG_K_ELEMENT = 2,   /* volume + lift + 1/det J + stage update (+ next traces) */
+    DG_K_PROJECT = 3,   /* L2 projection of point data */
+    DG_K_TOTALS = 4,    /* conserved totals reduction */
+    DG_K_ADJOINT = 5,   /* adjoint kernels */
+    DG_K_OTHER = 6,
+    DG_NKINDS = 8
+};
+
+/* When enable != 0, every kernel this library launches for the mesh is
+ * bracketed by a pair of CUDA events recorded on the launch's own stream.
+ * Enabling or disabling clears the accumulated times. */
+dg_status dg_set_timing(dg_mesh *mesh, int enable);
+
+/* Waits for the recorded events and adds their durations, per kernel kind, to
+ * ms[DG_NKINDS] and launches[DG_NKINDS] (HOST arrays, overwritten with the
+ * totals since timing was enabled).  Synchronous. */
+dg_status dg_kernel_times(dg_mesh *mesh, double ms[8], int64_t launches[8]);
+
+/* Measures the device's sustained fused multiply-add rate in float64 and
+ * float32 (TFLOP/s, 2 flops per FMA) with a register-resident FMA chain over
+ * every SM, timed with CUDA events on stream.  Either output may be NULL.
+ * Synchronous; allocates a small scratch buffer. */
+dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *dg_last_error(void);
+
+/* Host-only (needs no GPU): the reference rules and basis tables this library
+ * uses for degree p with ne edge points.  Any pointer may be NULL.
+ *   vol_r, vol_s, vol_w [nq] with nq = (p+1)^2;  edge_x, edge_w [ne];
+ *   phi, dphi_r, dphi_s [nq][N_p] at the volume points;  phi_face [3][ne][N_p]
+ *   at the edge points of local faces 0, 1, 2 (edge point order: xi ascending,
+ *   face q running from reference vertex q to vertex q+1). */
+dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s, double *vol_w,
+                         double *edge_x, double *edge_w, double *phi, double *dphi_r,
+                         double *dphi_s, double *phi_face);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

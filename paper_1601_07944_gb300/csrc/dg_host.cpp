@@ -1,0 +1,619 @@
+/*
+ * dg_host.cpp -- host side of the DG library: reference rules, basis tables,
+ * mesh validation, edge list and geometry, device upload and the C ABI entry
+ * points (include/dg.h).
+ *
+ * Quadrature here is computed by the Golub-Welsch method: the nodes of an
+ * n-point Gauss rule for a Jacobi weight are the eigenvalues of the symmetric
+ * tridiagonal Jacobi matrix of the orthonormal recurrence, and the weights are
+ * mu_0 times the squared first components of the normalised eigenvectors.  The
+ * small symmetric eigenproblem is solved with cyclic Jacobi rotations.
+ *
+ * The basis is the orthonormal Dubiner basis on the reference triangle
+ * {(0,0),(1,0),(0,1)} (the paper's Eq. np asks for an orthonormal basis of
+ * degree <= p; this library fixes the Dubiner one):
+ *   phi_ab(r, s) = N_ab P_a(alpha) (1-s)^a P_b^{(2a+1,0)}(beta),
+ *   alpha = 2r/(1-s) - 1, beta = 2s - 1, N_ab = sqrt(2 (2a+1) (a+b+1)),
+ * with Jacobi polynomials in their standard normalisation (three-term
+ * recurrence), ordered by total degree a+b and then by b.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+dg_status fail(dg_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+dg_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(DG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define DG_CUDA(call, what)                      \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Gauss rules by Golub-Welsch
+// ---------------------------------------------------------------------------
+
+// Eigen-decomposition of a small symmetric matrix A (n x n, row-major) by cyclic
+// Jacobi rotations.  On return A's diagonal holds the eigenvalues and the
+// columns of V the orthonormal eigenvectors.
+void sym_eigen(int n, std::vector<double> &A, std::vector<double> &V) {
+  V.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag += A[i * n + i] * A[i * n + i];
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    }
+    if (off <= 1e-36 * (diag + 1e-300)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {          // A <- A R  (columns p, q)
+          double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {          // A <- R^T A (rows p, q)
+          double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {          // V <- V R
+          double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+// n-point Gauss rule for the weight (1-x)^a (1+x)^b on [-1, 1], ascending nodes.
+void gauss_rule(int n, double a, double b, std::vector<double> &x, std::vector<double> &w) {
+  std::vector<double> J(n * n, 0.0), V;
+  for (int k = 0; k < n; ++k) {
+    double s = 2.0 * k + a + b;
+    J[k * n + k] = (k == 0) ? (b - a) / (a + b + 2.0) : (b * b - a * a) / (s * (s + 2.0));
+    if (k >= 1) {
+      double kk = k;
+      double num = 4.0 * kk * (kk + a) * (kk + b) * (kk + a + b);
+      double den = s * s * (s + 1.0) * (s - 1.0);
+      double off = std::sqrt(num / den);
+      J[(k - 1) * n + k] = off;
+      J[k * n + (k - 1)] = off;
+    }
+  }
+  sym_eigen(n, J, V);
+  double mu0 = std::pow(2.0, a + b + 1.0) * std::exp(std::lgamma(a + 1.0) + std::lgamma(b + 1.0) -
+                                                      std::lgamma(a + b + 2.0));
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int i, int j) { return J[i * n + i] < J[j * n + j]; });
+  x.resize(n);
+  w.resize(n);
+  for (int t = 0; t < n; ++t) {
+    int i = idx[t];
+    x[t] = J[i * n + i];
+    w[t] = mu0 * V[0 * n + i] * V[0 * n + i];
+  }
+}
+
+// Collapsed rule on the reference triangle: Gauss-Legendre in alpha, Gauss-Jacobi
+// (1,0) in beta; r = (1+alpha)(1-beta)/4, s = (1+beta)/2, weight wa*wb/8.
+// Point index = ib*n + ia.
+void collapsed_rule(int n, std::vector<double> &r, std::vector<double> &s, std::vector<double> &w) {
+  std::vector<double> xa, wa, xb, wb;
+  gauss_rule(n, 0.0, 0.0, xa, wa);
+  gauss_rule(n, 1.0, 0.0, xb, wb);
+  r.resize(n * n); s.resize(n * n); w.resize(n * n);
+  for (int ib = 0; ib < n; ++ib)
+    for (int ia = 0; ia < n; ++ia) {
+      int k = ib * n + ia;
+      r[k] = 0.25 * (1.0 + xa[ia]) * (1.0 - xb[ib]);
+      s[k] = 0.5 * (1.0 + xb[ib]);
+      w[k] = 0.125 * wa[ia] * wb[ib];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dubiner basis from Jacobi recurrences
+// ---------------------------------------------------------------------------
+
+double jacobi_p(int n, double a, double b, double x) {
+  if (n == 0) return 1.0;
+  double pm = 1.0, pc = 0.5 * (a - b + (a + b + 2.0) * x);
+  for (int k = 1; k < n; ++k) {
+    // P_{k+1} from P_k, P_{k-1}
+    double kk = k;
+    double s = 2.0 * kk + a + b;
+    double A = 2.0 * (kk + 1.0) * (kk + a + b + 1.0) * s;
+    double B = (s + 1.0) * (a * a - b * b);
+    double C = s * (s + 1.0) * (s + 2.0);
+    double D = 2.0 * (kk + a) * (kk + b) * (s + 2.0);
+    double pn = ((B + C * x) * pc - D * pm) / A;
+    pm = pc;
+    pc = pn;
+  }
+  return pc;
+}
+
+double jacobi_dp(int n, double a, double b, double x) {
+  if (n == 0) return 0.0;
+  return 0.5 * (n + a + b + 1.0) * jacobi_p(n - 1, a + 1.0, b + 1.0, x);
+}
+
+void mode_ab(int j, int *a, int *b) {
+  int k = 0;
+  for (int d = 0;; ++d)
+    for (int bb = 0; bb <= d; ++bb, ++k)
+      if (k == j) { *a = d - bb; *b = bb; return; }
+}
+
+void dubiner(int p, double r, double s, double *phi, double *dr, double *ds) {
+  int np = (p + 1) * (p + 2) / 2;
+  double oms = 1.0 - s;
+  double al = 2.0 * r / oms - 1.0, be = 2.0 * s - 1.0;
+  for (int j = 0; j < np; ++j) {
+    int a, b;
+    mode_ab(j, &a, &b);
+    double N = std::sqrt(2.0 * (2 * a + 1) * (a + b + 1));
+    double Pa = jacobi_p(a, 0, 0, al), dPa = jacobi_dp(a, 0, 0, al);
+    double Pb = jacobi_p(b, 2 * a + 1, 0, be), dPb = jacobi_dp(b, 2 * a + 1, 0, be);
+    double oa = std::pow(oms, a);
+    double oa1 = a > 0 ? std::pow(oms, a - 1) : 0.0;
+    if (phi) phi[j] = N * Pa * oa * Pb;
+    // d/dr: d alpha/dr = 2/(1-s)
+    if (dr) dr[j] = N * 2.0 * dPa * oa1 * Pb;
+    // d/ds: d alpha/ds = (1+alpha)/(1-s), d beta/ds = 2
+    if (ds) ds[j] = N * (oa1 * (dPa * (1.0 + al) - a * Pa) * Pb + 2.0 * Pa * oa * dPb);
+  }
+}
+
+void face_point(int q, double xi, double *r, double *s) {
+  static const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+  int q1 = (q + 1) % 3;
+  *r = 0.5 * (1.0 - xi) * V[q][0] + 0.5 * (1.0 + xi) * V[q1][0];
+  *s = 0.5 * (1.0 - xi) * V[q][1] + 0.5 * (1.0 + xi) * V[q1][1];
+}
+
+bool supported(int p, int ne) {
+  if (p < 1 || p > dg::PMAX) return false;
+  return ne == p + 1 || (p == 3 && ne == 3);
+}
+
+void free_mesh(dg_mesh *m) {
+  if (!m) return;
+  cudaFree(m->geo); cudaFree(m->xy); cudaFree(m->elem_face); cudaFree(m->face_conn);
+  cudaFree(m->face_geo); cudaFree(m->table_block); cudaFree(m->trace); cudaFree(m->fhat);
+  cudaFree(m->stage); cudaFree(m->host_state); cudaFree(m->partial); cudaFree(m->totals_dev);
+  cudaFree(m->adj_buf);
+  if (m->timing) {
+    for (auto &r : m->timing->pool) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    delete m->timing;
+  }
+  delete m;
+}
+
+// Runs one launcher; with timing on, brackets it with an event pair on `stream`.
+template <class F>
+int timed(dg_mesh *m, int kind, void *stream, F &&launch) {
+  dg::Timing *t = m->timing;
+  if (!t || !t->on) return launch();
+  if (t->used == t->pool.size()) {
+    dg::Timing::Rec r{};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return launch();
+    }
+    t->pool.push_back(r);
+  }
+  dg::Timing::Rec &r = t->pool[t->used];
+  cudaEventRecord(r.a, (cudaStream_t)stream);
+  int e = launch();
+  cudaEventRecord(r.b, (cudaStream_t)stream);
+  r.kind = kind;
+  ++t->used;
+  return e;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" const char *dg_last_error(void) { return g_err.c_str(); }
+
+extern "C" dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s, double *vol_w,
+                                    double *edge_x, double *edge_w, double *phi, double *dphi_r,
+                                    double *dphi_s, double *phi_face) {
+  if (ne == 0) ne = p + 1;
+  if (p < 0 || p > 8 || ne < 1 || ne > 16) return fail(DG_EINVAL, "dg_host_tables: p=%d ne=%d", p, ne);
+  int np = (p + 1) * (p + 2) / 2, nd = p + 1, nq = nd * nd;
+  std::vector<double> r, s, w, ex, ew;
+  collapsed_rule(nd, r, s, w);
+  gauss_rule(ne, 0.0, 0.0, ex, ew);
+  for (int k = 0; k < nq; ++k) {
+    if (vol_r) vol_r[k] = r[k];
+    if (vol_s) vol_s[k] = s[k];
+    if (vol_w) vol_w[k] = w[k];
+    dubiner(p, r[k], s[k], phi ? phi + k * np : nullptr, dphi_r ? dphi_r + k * np : nullptr,
+            dphi_s ? dphi_s + k * np : nullptr);
+  }
+  for (int k = 0; k < ne; ++k) {
+    if (edge_x) edge_x[k] = ex[k];
+    if (edge_w) edge_w[k] = ew[k];
+  }
+  if (phi_face)
+    for (int q = 0; q < 3; ++q)
+      for (int k = 0; k < ne; ++k) {
+        double rr, ss;
+        face_point(q, ex[k], &rr, &ss);
+        dubiner(p, rr, ss, phi_face + (q * ne + k) * np, nullptr, nullptr);
+      }
+  g_err.clear();
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
+  using namespace dg;
+  if (!d || !out) return fail(DG_EINVAL, "dg_mesh_create: null argument");
+  *out = nullptr;
+  if (!d->elem_xy || !d->nbr || !d->nbr_face) return fail(DG_EINVAL, "dg_mesh_create: null mesh array");
+  const int64_t N = d->n_elem;
+  if (N < 1 || N > (int64_t)INT32_MAX / 3) return fail(DG_EINVAL, "dg_mesh_create: n_elem=%lld", (long long)N);
+  const int p = d->p;
+  const int ne = d->n_edge_pts ? d->n_edge_pts : p + 1;
+  if (!supported(p, ne)) return fail(DG_EINVAL, "dg_mesh_create: unsupported p=%d n_edge_pts=%d", p, ne);
+  if (!(d->gamma > 1.0)) return fail(DG_EINVAL, "dg_mesh_create: gamma must exceed 1");
+
+  const double *xy = d->elem_xy;
+  // --- validation and edge list ------------------------------------------
+  std::vector<double> geo(N * GEO);
+  for (int64_t e = 0; e < N; ++e) {
+    const double *v = xy + 6 * e;
+    double a = v[2] - v[0], b = v[4] - v[0], c = v[3] - v[1], dd = v[5] - v[1];
+    double det = a * dd - b * c;
+    if (!(det > 0.0) || !std::isfinite(det))
+      return fail(DG_EMESH, "element %lld is not counter-clockwise (det J = %g)", (long long)e, det);
+    double *g = &geo[e * GEO];
+    g[0] = dd; g[1] = -b; g[2] = -c; g[3] = a;      // det J * J^{-1}
+    g[4] = 1.0 / det; g[5] = det; g[6] = 0.0; g[7] = 0.0;
+  }
+  std::vector<int32_t> elem_face(N * 3, -1);
+  std::vector<FaceConn> conn;
+  std::vector<FaceGeo> fgeo;
+  conn.reserve(N * 3 / 2 + 1);
+  fgeo.reserve(N * 3 / 2 + 1);
+  for (int64_t e = 0; e < N; ++e)
+    for (int q = 0; q < 3; ++q) {
+      int64_t f = d->nbr[3 * e + q];
+      int qf = d->nbr_face[3 * e + q];
+      if (f < 0 || f >= N || qf < 0 || qf > 2)
+        return fail(DG_EMESH, "element %lld face %d: neighbour (%lld, %d) out of range (boundary edges "
+                    "are not supported)", (long long)e, q, (long long)f, qf);
+      if (d->nbr[3 * f + qf] != e || d->nbr_face[3 * f + qf] != q)
+        return fail(DG_EMESH, "element %lld face %d: neighbour relation is not symmetric", (long long)e, q);
+      if (f == e && qf == q) return fail(DG_EMESH, "element %lld face %d is its own neighbour", (long long)e, q);
+      const double *v = xy + 6 * e, *w = xy + 6 * f;
+      int q1 = (q + 1) % 3, qf1 = (qf + 1) % 3;
+      double dx = v[2 * q1] - v[2 * q], dy = v[2 * q1 + 1] - v[2 * q + 1];
+      double len = std::sqrt(dx * dx + dy * dy);
+      // the neighbour traverses the edge backwards: v_q ~ w_{qf+1}, v_{q+1} ~ w_qf
+      double t0x = v[2 * q] - w[2 * qf1], t0y = v[2 * q + 1] - w[2 * qf1 + 1];
+      double t1x = v[2 * q1] - w[2 * qf], t1y = v[2 * q1 + 1] - w[2 * qf + 1];
+      if (std::fabs(t0x - t1x) > 1e-9 * len || std::fabs(t0y - t1y) > 1e-9 * len)
+        return fail(DG_EMESH, "element %lld face %d: the neighbour's edge is not a translate", (long long)e, q);
+      if (!(e < f || (e == f && q < qf))) continue;
+      int32_t fi = (int32_t)conn.size();
+      conn.push_back(FaceConn{(int32_t)e, q, (int32_t)f, qf});
+      fgeo.push_back(FaceGeo{dy / len, -dx / len, 0.5 * len, 0.0});
+      elem_face[3 * e + q] = 2 * fi + 0;
+      elem_face[3 * f + qf] = 2 * fi + 1;
+    }
+  const int64_t F = (int64_t)conn.size();
+
+  // --- tables ----------------------------------------------------------------
+  const int np = (p + 1) * (p + 2) / 2, nd = p + 1, nq = nd * nd, nf = 3 * ne;
+  std::vector<double> r, s, w, ex, ew;
+  collapsed_rule(nd, r, s, w);
+  gauss_rule(ne, 0.0, 0.0, ex, ew);
+  std::vector<double> phi(nq * np), dr(nq * np), ds(nq * np), phif(nf * np);
+  for (int k = 0; k < nq; ++k) dubiner(p, r[k], s[k], &phi[k * np], &dr[k * np], &ds[k * np]);
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < ne; ++k) {
+      double rr, ss;
+      face_point(q, ex[k], &rr, &ss);
+      dubiner(p, rr, ss, &phif[(q * ne + k) * np], nullptr, nullptr);
+    }
+  size_t off = 0;
+  auto take = [&](size_t n) { size_t o = off; off += (n + 3) & ~size_t(3); return o; };
+  size_t oBvT = take(np * nq), oDr = take(nq * np), oDs = take(nq * np), oLf = take(nf * np),
+         oBfT = take(np * nf), oPw = take(nq * np), oVr = take(nq), oVs = take(nq);
+  std::vector<double> tb(off, 0.0);
+  for (int k = 0; k < nq; ++k)
+    for (int j = 0; j < np; ++j) {
+      tb[oBvT + j * nq + k] = phi[k * np + j];
+      tb[oDr + k * np + j] = w[k] * dr[k * np + j];
+      tb[oDs + k * np + j] = w[k] * ds[k * np + j];
+      tb[oPw + k * np + j] = w[k] * phi[k * np + j];
+    }
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < ne; ++k)
+      for (int j = 0; j < np; ++j) {
+        int qk = q * ne + k;
+        tb[oLf + qk * np + j] = ew[k] * phif[qk * np + j];
+        tb[oBfT + j * nf + qk] = phif[qk * np + j];
+      }
+  for (int k = 0; k < nq; ++k) { tb[oVr + k] = r[k]; tb[oVs + k] = s[k]; }
+
+  // --- device upload ---------------------------------------------------------
+  dg_mesh *m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ENOMEM, "dg_mesh_create: host allocation");
+  m->timing = new (std::nothrow) dg::Timing();
+  if (!m->timing) { delete m; return fail(DG_ENOMEM, "dg_mesh_create: host allocation"); }
+  m->p = p; m->np = np; m->nq = nq; m->nd = nd; m->ne = ne; m->gamma = d->gamma;
+  m->N = N; m->F = F;
+  cudaGetDevice(&m->device);
+  if (cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess || m->num_sms < 1) {
+    cudaGetLastError();
+    m->num_sms = 1;
+  }
+  auto dalloc = [&](void **ptr, size_t bytes, const char *what) -> dg_status {
+    cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DG_ENOMEM, "cudaMalloc(%s, %zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    }
+    return DG_OK;
+  };
+  dg_status st;
+#define DG_ALLOC(ptr, bytes, what) \
+  if ((st = dalloc((void **)&(ptr), (bytes), (what))) != DG_OK) { free_mesh(m); return st; }
+  DG_ALLOC(m->geo, sizeof(double) * N * GEO, "geometry");
+  DG_ALLOC(m->xy, sizeof(double) * N * 6, "vertices");
+  DG_ALLOC(m->elem_face, sizeof(int32_t) * N * 3, "element faces");
+  DG_ALLOC(m->face_conn, sizeof(FaceConn) * F, "face connectivity");
+  DG_ALLOC(m->face_geo, sizeof(FaceGeo) * F, "face geometry");
+  DG_ALLOC(m->table_block, sizeof(double) * off, "tables");
+  DG_ALLOC(m->trace, sizeof(double) * N * nf * M, "traces");
+  DG_ALLOC(m->fhat, sizeof(double) * F * ne * M, "edge fluxes");
+  DG_ALLOC(m->stage, sizeof(double) * N * M * np, "stage buffer");
+  m->totals_blocks = 256;
+  DG_ALLOC(m->partial, sizeof(double) * m->totals_blocks * M, "totals partials");
+  DG_ALLOC(m->totals_dev, sizeof(double) * M, "totals");
+#undef DG_ALLOC
+  m->table_doubles = off;
+  double *T = m->table_block;
+  m->tab.BvT = T + oBvT; m->tab.Dr = T + oDr; m->tab.Ds = T + oDs; m->tab.Lf = T + oLf;
+  m->tab.BfT = T + oBfT; m->tab.Pw = T + oPw; m->tab.vr = T + oVr; m->tab.vs = T + oVs;
+  cudaError_t ce;
+  if ((ce = cudaMemcpy(m->geo, geo.data(), sizeof(double) * N * GEO, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemcpy(m->xy, xy, sizeof(double) * N * 6, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemcpy(m->elem_face, elem_face.data(), sizeof(int32_t) * N * 3, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemcpy(m->face_conn, conn.data(), sizeof(FaceConn) * F, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemcpy(m->face_geo, fgeo.data(), sizeof(FaceGeo) * F, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemcpy(m->table_block, tb.data(), sizeof(double) * off, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    free_mesh(m);
+    return cuda_fail(ce, "dg_mesh_create: upload");
+  }
+  *out = m;
+  g_err.clear();
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mesh_destroy(dg_mesh *m) {
+  if (!m) return DG_OK;
+  cudaDeviceSynchronize();
+  free_mesh(m);
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mesh_info(const dg_mesh *m, dg_mesh_info_t *info) {
+  if (!m || !info) return fail(DG_EINVAL, "dg_mesh_info: null argument");
+  info->n_elem = m->N; info->n_face = m->F; info->p = m->p; info->n_modes = m->np;
+  info->n_vol_pts = m->nq; info->n_edge_pts = m->ne; info->gamma = m->gamma;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_volume_points(const dg_mesh *m, double *xy, void *stream) {
+  if (!m || !xy) return fail(DG_EINVAL, "dg_volume_points: null argument");
+  DG_CUDA((cudaError_t)dg::launch_volume_points(m, xy, stream), "dg_volume_points");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_project_ic(dg_mesh *m, const double *u, double *c, void *stream) {
+  if (!m || !u || !c) return fail(DG_EINVAL, "dg_project_ic: null argument");
+  DG_CUDA((cudaError_t)timed(m, DG_K_PROJECT, stream, [&] { return dg::launch_project(m, u, c, stream); }),
+          "dg_project_ic");
+  return DG_OK;
+}
+
+static dg_status check_prec(dg_precision prec, const char *who) {
+  if (prec == DG_FP64) return DG_OK;
+  if (prec == DG_TF32X1 || prec == DG_TF32X3)
+    return fail(DG_ENOTIMPL, "%s: precision %d is not built yet", who, (int)prec);
+  return fail(DG_EINVAL, "%s: unknown precision %d", who, (int)prec);
+}
+
+extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision prec, void *stream) {
+  if (!m || !c || !r) return fail(DG_EINVAL, "dg_rhs: null argument");
+  if (c == r) return fail(DG_EINVAL, "dg_rhs: c and r alias");
+  dg_status st = check_prec(prec, "dg_rhs");
+  if (st != DG_OK) return st;
+  DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return dg::launch_traces(m, c, m->trace, stream); }),
+          "dg_rhs traces");
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return dg::launch_face_flux(m, m->trace, m->fhat, stream); }),
+          "dg_rhs edge flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+            return dg::launch_element(m, c, nullptr, r, nullptr, m->fhat, 0.0, 0.0, 0.0, 0, stream);
+          }), "dg_rhs element");
+  return DG_OK;
+}
+
+// One SSP-RK3 step; on entry m->trace holds the traces of c when traces_valid.
+static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, void *stream) {
+  using namespace dg;
+  auto face = [&](const char *what) -> dg_status {
+    DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
+            what);
+    return DG_OK;
+  };
+  auto elem = [&](const double *cin, const double *u0, double *out, double a0, double b0,
+                  const char *what) -> dg_status {
+    DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+              return launch_element(m, cin, u0, out, m->trace, m->fhat, dt, a0, b0, 1, stream);
+            }), what);
+    return DG_OK;
+  };
+  dg_status st;
+  if (!traces_valid)
+    DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces(m, c, m->trace, stream); }),
+            "rk traces");
+  // stage 1: u1 = c + dt L(c)
+  if ((st = face("rk stage 1 flux")) != DG_OK) return st;
+  if ((st = elem(c, nullptr, m->stage, 0.0, 1.0, "rk stage 1")) != DG_OK) return st;
+  // stage 2: u2 = 3/4 c + 1/4 (u1 + dt L(u1)), written over u1
+  if ((st = face("rk stage 2 flux")) != DG_OK) return st;
+  if ((st = elem(m->stage, c, m->stage, 0.75, 0.25, "rk stage 2")) != DG_OK) return st;
+  // stage 3: c <- 1/3 c + 2/3 (u2 + dt L(u2))
+  if ((st = face("rk stage 3 flux")) != DG_OK) return st;
+  if ((st = elem(m->stage, c, c, 1.0 / 3.0, 2.0 / 3.0, "rk stage 3")) != DG_OK) return st;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg_precision prec,
+                                void *stream) {
+  if (!m || !c) return fail(DG_EINVAL, "dg_rk_step: null argument");
+  if (nsteps < 0) return fail(DG_EINVAL, "dg_rk_step: nsteps < 0");
+  if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_rk_step: dt is not finite");
+  dg_status st = check_prec(prec, "dg_rk_step");
+  if (st != DG_OK) return st;
+  for (int it = 0; it < nsteps; ++it)
+    if ((st = rk3_step(m, c, dt, it > 0, stream)) != DG_OK) return st;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int nsteps,
+                                     dg_precision prec, void *stream) {
+  if (!m || !c_host) return fail(DG_EINVAL, "dg_rk_step_host: null argument");
+  size_t bytes = sizeof(double) * m->N * dg::M * m->np;
+  if (!m->host_state) {
+    cudaError_t e = cudaMalloc(&m->host_state, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); m->host_state = nullptr; return fail(DG_ENOMEM, "dg_rk_step_host: cudaMalloc"); }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaMemcpyAsync(m->host_state, c_host, bytes, cudaMemcpyHostToDevice, s), "dg_rk_step_host H2D");
+  dg_status st = dg_rk_step(m, m->host_state, dt, nsteps, prec, stream);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemcpyAsync(c_host, m->host_state, bytes, cudaMemcpyDeviceToHost, s), "dg_rk_step_host D2H");
+  DG_CUDA(cudaStreamSynchronize(s), "dg_rk_step_host sync");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_conserved_totals(dg_mesh *m, const double *c, double out[4], void *stream) {
+  if (!m || !c || !out) return fail(DG_EINVAL, "dg_conserved_totals: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA((cudaError_t)timed(m, DG_K_TOTALS, stream, [&] { return dg::launch_totals(m, c, m->totals_dev, stream); }),
+          "dg_conserved_totals");
+  DG_CUDA(cudaMemcpyAsync(out, m->totals_dev, sizeof(double) * dg::M, cudaMemcpyDeviceToHost, s),
+          "dg_conserved_totals D2H");
+  DG_CUDA(cudaStreamSynchronize(s), "dg_conserved_totals sync");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, const double *lam_np1,
+                                     double *lam_n, void *stream) {
+  (void)dt; (void)stream;
+  if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "dg_adjoint_step: null argument");
+  return fail(DG_ENOTIMPL, "dg_adjoint_step: not built yet");
+}
+
+extern "C" dg_status dg_set_timing(dg_mesh *m, int enable) {
+  if (!m || !m->timing) return fail(DG_EINVAL, "dg_set_timing: null mesh");
+  dg::Timing *t = m->timing;
+  if (t->used) cudaDeviceSynchronize();
+  t->on = enable != 0;
+  t->used = 0;
+  for (int k = 0; k < DG_NKINDS; ++k) { t->ms[k] = 0.0; t->launches[k] = 0; }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_kernel_times(dg_mesh *m, double ms[8], int64_t launches[8]) {
+  if (!m || !m->timing || !ms || !launches) return fail(DG_EINVAL, "dg_kernel_times: null argument");
+  dg::Timing *t = m->timing;
+  for (size_t i = 0; i < t->used; ++i) {
+    dg::Timing::Rec &r = t->pool[i];
+    DG_CUDA(cudaEventSynchronize(r.b), "dg_kernel_times sync");
+    float e = 0.f;
+    DG_CUDA(cudaEventElapsedTime(&e, r.a, r.b), "dg_kernel_times elapsed");
+    t->ms[r.kind] += (double)e;
+    t->launches[r.kind] += 1;
+  }
+  t->used = 0;
+  for (int k = 0; k < DG_NKINDS; ++k) { ms[k] = t->ms[k]; launches[k] = t->launches[k]; }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stream) {
+  int dev = 0, sms = 0;
+  DG_CUDA(cudaGetDevice(&dev), "probe");
+  DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "probe");
+  const int threads = 256, blocks = sms * 8;
+  double *buf = nullptr;
+  DG_CUDA(cudaMalloc(&buf, sizeof(double) * blocks * threads), "probe alloc");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  dg_status st = DG_OK;
+  for (int fp64 = 1; fp64 >= 0 && st == DG_OK; --fp64) {
+    double *dst = fp64 ? fp64_tflops : fp32_tflops;
+    if (!dst) continue;
+    const int iters = fp64 ? 4096 : 65536;
+    cudaError_t e = (cudaError_t)dg::launch_fma_probe(fp64, blocks, threads, iters / 8, buf, stream);  // warm-up
+    if (e == cudaSuccess) {
+      cudaEventRecord(a, s);
+      e = (cudaError_t)dg::launch_fma_probe(fp64, blocks, threads, iters, buf, stream);
+      cudaEventRecord(b, s);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) { st = cuda_fail(e, "dg_probe_fma_rate"); break; }
+    // 8 chains x iters FMAs x 2 flops per thread
+    *dst = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(buf);
+  return st;
+}

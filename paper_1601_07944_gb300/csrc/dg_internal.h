@@ -1,0 +1,98 @@
+/*
+ * dg_internal.h -- internal state of the DG library shared by the host setup
+ * (dg_host.cpp) and the CUDA kernels (dg_kernels.cu).  Not part of the ABI.
+ */
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int M = 4;          // conserved variables (rho, rho u, rho v, E)
+constexpr int PMAX = 5;
+
+// Geometry record of one element (8 doubles, 64 bytes):
+//   jt[0..3] = J^tau = det J * J^{-1} in row-major order, so that the reference
+//   flux is G_r = jt0 F1 + jt1 F2, G_s = jt2 F1 + jt3 F2; then 1/det J, det J.
+constexpr int GEO = 8;
+
+// Face record: left element, its local face, right element, its local face.
+struct FaceConn { int32_t l, L, r, R; };
+// Face geometry: unit normal (left -> right) and half length l_f (Eq. len).
+struct FaceGeo { double nx, ny, hl, pad; };
+
+struct DevTables {
+  // All float64, device.  NP modes, NQ volume points, NF = 3*NE face points.
+  double *BvT;   // [NP][NQ]   phi_j(r_k)                    (interpolation)
+  double *Dr;    // [NQ][NP]   w_k d phi_j/dr (r_k)           (projection)
+  double *Ds;    // [NQ][NP]   w_k d phi_j/ds (r_k)
+  double *Lf;    // [NF][NP]   omega_k phi_j(r_{q,k})         (lifting)
+  double *BfT;   // [NP][NF]   phi_j(r_{q,k})                 (edge traces)
+  double *Pw;    // [NQ][NP]   w_k phi_j(r_k)                 (L2 projection of data)
+  double *vr, *vs;   // [NQ] reference volume points
+};
+
+// Per-kernel CUDA-event timing (dg_set_timing / dg_kernel_times).
+struct Timing {
+  bool on = false;
+  struct Rec { cudaEvent_t a, b; int kind; };
+  std::vector<Rec> pool;        // event pairs, reused
+  size_t used = 0;              // pairs recorded since the last harvest
+  double ms[DG_NKINDS] = {};
+  int64_t launches[DG_NKINDS] = {};
+};
+
+}  // namespace dg
+
+struct dg_mesh {
+  int p, np, nq, nd, ne;
+  double gamma;
+  int64_t N, F;
+  int device;
+  int num_sms;
+  // device arrays
+  double *geo;                 // [N][GEO]
+  double *xy;                  // [N][6]
+  int32_t *elem_face;          // [N][3]: f*2 + side (0 = left, 1 = right)
+  dg::FaceConn *face_conn;     // [F]
+  dg::FaceGeo *face_geo;       // [F]
+  dg::DevTables tab;
+  double *table_block;         // one allocation holding every table
+  size_t table_doubles;
+  // work buffers
+  double *trace;               // [N][3*ne][M]
+  double *fhat;                // [F][ne][M]
+  double *stage;               // [N][M][np]
+  double *host_state;          // [N][M][np] device copy used by dg_rk_step_host
+  double *partial;             // [nblk][M] totals partials
+  double *totals_dev;          // [M]
+  int totals_blocks;
+  // scratch for the adjoint (allocated on first use)
+  double *adj_buf;
+  size_t adj_doubles;
+  dg::Timing *timing;
+};
+
+namespace dg {
+
+// Kernel launchers (dg_kernels.cu).  All return a cudaError_t cast to int.
+int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream);
+int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream);
+// out = mode==0 ? R(c) : a0*u0 + b0*(c + dt*R(c));  trace_out may be null.
+int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
+                   double *trace_out, const double *fhat, double dt, double a0, double b0,
+                   int mode, void *stream);
+int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
+int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
+int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);
+int element_smem_bytes(int p, int ne);
+// FMA-rate probe: runs `iters` iterations of 8 independent FMA chains per thread.
+int launch_fma_probe(int fp64, int blocks, int threads, int iters, double *out, void *stream);
+
+}  // namespace dg

@@ -1,0 +1,523 @@
+/*
+ * dg_kernels.cu -- float64 kernels of the DG right-hand side and SSP-RK3 stage
+ * on sm_103a.
+ *
+ * One stage of the method (the paper's Section 4.3: volume kernel, edge kernel,
+ * combining kernel) is organised here as two launches:
+ *
+ *   k_face     one thread per (edge, edge point): gathers the two traces, the
+ *              right element's at the reversed point (Eq. edgeint), evaluates the
+ *              local Lax-Friedrichs flux once per edge and stores it scaled by the
+ *              edge Jacobian l = |edge|/2 (Eq. len).
+ *   k_element  one CTA per tile of EB elements, staged through shared memory:
+ *              interpolation to the volume points, Euler flux and the reference
+ *              flux G = J^tau F, projection onto the weighted basis gradients
+ *              (Eq. volume, Algorithm 1), lifting of the three edge fluxes
+ *              (Algorithm 3), scaling by 1/det J (Eq. 2ddg0), the Runge-Kutta
+ *              stage update, and, for the next stage, the edge traces of the new
+ *              state.  Writing the traces from the element that owns the state
+ *              replaces a separate pass over the coefficients.
+ *
+ * The paper's per-edge temporaries (rhs_surface_left/right) become one flux
+ * block per edge; each element gathers its three blocks, so no atomics are used
+ * and every result is deterministic.
+ */
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dg_internal.h"
+
+namespace dg {
+namespace {
+
+template <int P, int NE>
+struct Cfg {
+  static constexpr int NP = (P + 1) * (P + 2) / 2;
+  static constexpr int ND = P + 1;
+  static constexpr int NQ = ND * ND;
+  static constexpr int NF = 3 * NE;
+  static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);   // elements per tile
+  static constexpr int TAB = NP * NQ * 3 + NF * NP * 2;          // table doubles
+  static constexpr int TILE = EB * (M * NP * 2 + NQ * 8 + NF * M);
+  static constexpr int SMEM = (TAB + TILE) * 8;
+};
+
+constexpr int kThreads = 256;
+
+// Euler flux (Eq. euler) contracted with J^tau: the reference flux components
+// G_r, G_s of the four conserved variables at one point.
+__device__ __forceinline__ void ref_flux(const double U[M], const double *jt, double gamma,
+                                         double Gr[M], double Gs[M]) {
+  const double rho = U[0], inv = 1.0 / rho;
+  const double u = U[1] * inv, v = U[2] * inv;
+  const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+  double F1[M], F2[M];
+  F1[0] = U[1];          F2[0] = U[2];
+  F1[1] = U[1] * u + p;  F2[1] = U[1] * v;
+  F1[2] = U[2] * u;      F2[2] = U[2] * v + p;
+  F1[3] = (U[3] + p) * u; F2[3] = (U[3] + p) * v;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    Gr[m] = jt[0] * F1[m] + jt[1] * F2[m];
+    Gs[m] = jt[2] * F1[m] + jt[3] * F2[m];
+  }
+}
+
+// Local Lax-Friedrichs flux F_hat(Ul, Ur, n).  Written so that swapping the two
+// sides and negating n negates the result bit for bit.
+__device__ __forceinline__ void lax_friedrichs(const double ul[M], const double ur[M], double nx,
+                                               double ny, double gamma, double out[M]) {
+  const double il = 1.0 / ul[0], ir = 1.0 / ur[0];
+  const double uL = ul[1] * il, vL = ul[2] * il, uR = ur[1] * ir, vR = ur[2] * ir;
+  const double pL = (gamma - 1.0) * (ul[3] - 0.5 * (ul[1] * uL + ul[2] * vL));
+  const double pR = (gamma - 1.0) * (ur[3] - 0.5 * (ur[1] * uR + ur[2] * vR));
+  const double vnL = uL * nx + vL * ny, vnR = uR * nx + vR * ny;
+  const double sL = fabs(vnL) + sqrt(gamma * pL * il);
+  const double sR = fabs(vnR) + sqrt(gamma * pR * ir);
+  const double a = fmax(sL, sR);
+  double fL[M], fR[M];
+  fL[0] = ul[0] * vnL;              fR[0] = ur[0] * vnR;
+  fL[1] = ul[1] * vnL + pL * nx;    fR[1] = ur[1] * vnR + pR * nx;
+  fL[2] = ul[2] * vnL + pL * ny;    fR[2] = ur[2] * vnR + pR * ny;
+  fL[3] = (ul[3] + pL) * vnL;       fR[3] = (ur[3] + pR) * vnR;
+#pragma unroll
+  for (int m = 0; m < M; ++m) out[m] = 0.5 * (fL[m] + fR[m]) - 0.5 * a * (ur[m] - ul[m]);
+}
+
+// ---------------------------------------------------------------------------
+// edge traces of a coefficient array: trace[e][q*NE+k][m] = sum_j c[e][m][j] phi_j(r_{q,k})
+// ---------------------------------------------------------------------------
+template <int P, int NE>
+__global__ void __launch_bounds__(kThreads)
+k_traces(const double *__restrict__ c, double *__restrict__ trace, const double *__restrict__ BfT,
+         int N) {
+  using C = Cfg<P, NE>;
+  constexpr int NP = C::NP, NF = C::NF, EB = C::EB;
+  __shared__ double sB[NP * NF];
+  __shared__ double sC[EB * M * NP];
+  for (int i = threadIdx.x; i < NP * NF; i += blockDim.x) sB[i] = BfT[i];
+  const int ntiles = (N + EB - 1) / EB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e0 = tile * EB;
+    const int ecount = min(EB, N - e0);
+    __syncthreads();
+    const double *src = c + (size_t)e0 * M * NP;
+    for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x)
+      sC[i] = i < ecount * M * NP ? src[i] : 0.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < ecount * NF; i += blockDim.x) {
+      const int el = i / NF, qk = i - el * NF;
+      double T[M] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const double b = sB[j * NF + qk];
+#pragma unroll
+        for (int m = 0; m < M; ++m) T[m] += sC[(el * M + m) * NP + j] * b;
+      }
+      double *dst = trace + ((size_t)(e0 + el) * NF + qk) * M;
+#pragma unroll
+      for (int m = 0; m < M; ++m) dst[m] = T[m];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// edge flux: fhat[f][k][m] = l_f * F_hat(U_l(r_{L,k}), U_r(r_{R,NE-1-k}), n_f)
+// ---------------------------------------------------------------------------
+template <int NE>
+__global__ void __launch_bounds__(kThreads)
+k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
+       const FaceGeo *__restrict__ fg, int64_t F, double gamma) {
+  constexpr int NF = 3 * NE;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F * NE) return;
+  const int64_t f = i / NE;
+  const int k = (int)(i - f * NE);
+  const FaceConn cn = conn[f];
+  const FaceGeo g = fg[f];
+  const double *pl = trace + ((size_t)cn.l * NF + cn.L * NE + k) * M;
+  const double *pr = trace + ((size_t)cn.r * NF + cn.R * NE + (NE - 1 - k)) * M;
+  double ul[M], ur[M], Fh[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
+  lax_friedrichs(ul, ur, g.nx, g.ny, gamma, Fh);
+  double *dst = fhat + (size_t)i * M;
+#pragma unroll
+  for (int m = 0; m < M; ++m) dst[m] = g.hl * Fh[m];
+}
+
+// ---------------------------------------------------------------------------
+// element kernel: residual, stage update and next traces
+// ---------------------------------------------------------------------------
+template <int P, int NE>
+__global__ void __launch_bounds__(kThreads)
+k_element(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
+          const double *__restrict__ fhat, const double *__restrict__ geo,
+          const int32_t *__restrict__ elem_face, DevTables tab, int N, double dt, double a0,
+          double b0, int mode, double gamma) {
+  using C = Cfg<P, NE>;
+  constexpr int NP = C::NP, NQ = C::NQ, NF = C::NF, EB = C::EB;
+  extern __shared__ double smem[];
+  double *sBvT = smem;                 // [NP][NQ]
+  double *sDr = sBvT + NP * NQ;        // [NQ][NP]
+  double *sDs = sDr + NQ * NP;         // [NQ][NP]
+  double *sLf = sDs + NQ * NP;         // [NF][NP]
+  double *sBfT = sLf + NF * NP;        // [NP][NF]
+  double *sC = sBfT + NP * NF;         // [EB][M][NP]  stage input
+  double *sH = sC + EB * M * NP;       // [EB][NQ][8]  w-free reference fluxes G_r, G_s
+  double *sF = sH + EB * NQ * 8;       // [EB][NF][M]  -F_hat_out * l, element's point order
+  double *sO = sF + EB * NF * M;       // [EB][M][NP]  new state
+
+  for (int i = threadIdx.x; i < NP * NQ; i += blockDim.x) {
+    sBvT[i] = tab.BvT[i];
+    sDr[i] = tab.Dr[i];
+    sDs[i] = tab.Ds[i];
+  }
+  for (int i = threadIdx.x; i < NF * NP; i += blockDim.x) {
+    sLf[i] = tab.Lf[i];
+    sBfT[i] = tab.BfT[i];
+  }
+
+  const int ntiles = (N + EB - 1) / EB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e0 = tile * EB;
+    const int ecount = min(EB, N - e0);
+    __syncthreads();
+    // stage input, coalesced
+    const double *src = c + (size_t)e0 * M * NP;
+    for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x)
+      sC[i] = i < ecount * M * NP ? src[i] : 0.0;
+    // edge fluxes in this element's outward orientation and point order
+    for (int i = threadIdx.x; i < EB * NF; i += blockDim.x) {
+      const int el = i / NF, qk = i - el * NF;
+      double v[M] = {0.0, 0.0, 0.0, 0.0};
+      if (el < ecount) {
+        const int q = qk / NE, k = qk - q * NE;
+        const int ef = elem_face[(size_t)(e0 + el) * 3 + q];
+        const int f = ef >> 1, side = ef & 1;
+        const int kk = side ? NE - 1 - k : k;
+        const double *fp = fhat + ((size_t)f * NE + kk) * M;
+        const double sg = side ? 1.0 : -1.0;    // surface term enters with a minus sign
+#pragma unroll
+        for (int m = 0; m < M; ++m) v[m] = sg * fp[m];
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) sF[i * M + m] = v[m];
+    }
+    __syncthreads();
+
+    // volume points: U = sum_j c_j phi_j(r_k); G = J^tau F(U)
+    for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
+      const int el = i / NQ, k = i - el * NQ;
+      double U[M] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const double b = sBvT[j * NQ + k];
+#pragma unroll
+        for (int m = 0; m < M; ++m) U[m] += sC[(el * M + m) * NP + j] * b;
+      }
+      double Gr[M], Gs[M];
+      if (el < ecount) {
+        const double *g = geo + (size_t)(e0 + el) * GEO;
+        const double jt[4] = {g[0], g[1], g[2], g[3]};
+        ref_flux(U, jt, gamma, Gr, Gs);
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) { Gr[m] = 0.0; Gs[m] = 0.0; }
+      }
+      double *h = sH + (size_t)i * 8;
+#pragma unroll
+      for (int m = 0; m < M; ++m) { h[m] = Gr[m]; h[4 + m] = Gs[m]; }
+    }
+    __syncthreads();
+
+    // modes: volume projection + lifted edge fluxes, 1/det J, stage update
+    for (int i = threadIdx.x; i < EB * NP; i += blockDim.x) {
+      const int el = i / NP, j = i - el * NP;
+      double acc[M] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+      for (int k = 0; k < NQ; ++k) {
+        const double *h = sH + (el * NQ + k) * 8;
+        const double dr = sDr[k * NP + j], ds = sDs[k * NP + j];
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m] += h[m] * dr + h[4 + m] * ds;
+      }
+#pragma unroll
+      for (int qk = 0; qk < NF; ++qk) {
+        const double *fv = sF + (el * NF + qk) * M;
+        const double l = sLf[qk * NP + j];
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m] += fv[m] * l;
+      }
+      if (el < ecount) {
+        const size_t e = (size_t)(e0 + el);
+        const double inv = geo[e * GEO + 4];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const size_t idx = (e * M + m) * NP + j;
+          const double R = acc[m] * inv;
+          double v;
+          if (mode == 0) {
+            v = R;
+          } else {
+            const double cj = sC[(el * M + m) * NP + j];
+            v = b0 * (cj + dt * R);
+            if (a0 != 0.0) v = a0 * u0[idx] + v;
+          }
+          out[idx] = v;
+          sO[(el * M + m) * NP + j] = v;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) sO[(el * M + m) * NP + j] = 0.0;
+      }
+    }
+
+    if (trace_out) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < ecount * NF; i += blockDim.x) {
+        const int el = i / NF, qk = i - el * NF;
+        double T[M] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          const double b = sBfT[j * NF + qk];
+#pragma unroll
+          for (int m = 0; m < M; ++m) T[m] += sO[(el * M + m) * NP + j] * b;
+        }
+        double *dst = trace_out + ((size_t)(e0 + el) * NF + qk) * M;
+#pragma unroll
+        for (int m = 0; m < M; ++m) dst[m] = T[m];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// projection of point data and volume point coordinates
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+k_project(const double *__restrict__ u, double *__restrict__ c, const double *__restrict__ Pw, int N) {
+  constexpr int NP = (P + 1) * (P + 2) / 2, NQ = (P + 1) * (P + 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)N * NP) return;
+  const int64_t e = i / NP;
+  const int j = (int)(i - e * NP);
+  double acc[M] = {0.0, 0.0, 0.0, 0.0};
+  const double *ue = u + (size_t)e * NQ * M;
+  for (int k = 0; k < NQ; ++k) {
+    const double w = Pw[k * NP + j];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += w * ue[k * M + m];
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) c[((size_t)e * M + m) * NP + j] = acc[m];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_volume_points(const double *__restrict__ xy, const double *__restrict__ vr,
+                const double *__restrict__ vs, double *__restrict__ out, int N, int nq) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)N * nq) return;
+  const int64_t e = i / nq;
+  const int k = (int)(i - e * nq);
+  const double *v = xy + e * 6;
+  const double r = vr[k], s = vs[k], l0 = 1.0 - r - s;
+  out[i * 2 + 0] = v[0] * l0 + v[2] * r + v[4] * s;
+  out[i * 2 + 1] = v[1] * l0 + v[3] * r + v[5] * s;
+}
+
+// ---------------------------------------------------------------------------
+// conserved totals: fixed-order two-pass reduction of det J * c[e][m][0]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_totals_partial(const double *__restrict__ c, const double *__restrict__ geo, int N, int np,
+                 double *__restrict__ partial) {
+  __shared__ double red[M][kThreads];
+  double acc[M] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t chunk = ((int64_t)N + gridDim.x - 1) / gridDim.x;
+  const int64_t beg = blockIdx.x * chunk;
+  const int64_t end = min((int64_t)N, beg + chunk);
+  for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const double dj = geo[e * GEO + 5];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += dj * c[(e * M + m) * np];
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) red[m][threadIdx.x] = acc[m];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int m = 0; m < M; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < M) partial[blockIdx.x * M + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_totals_final(const double *__restrict__ partial, int nb, double *__restrict__ out) {
+  __shared__ double red[M][kThreads];
+  double acc[M] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += partial[b * M + m];
+#pragma unroll
+  for (int m = 0; m < M; ++m) red[m][threadIdx.x] = acc[m];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int m = 0; m < M; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + s];
+    __syncthreads();
+  }
+  // int phi_1 over the reference triangle is 1/sqrt(2); the other modes have zero mean
+  if (threadIdx.x < M) out[threadIdx.x] = red[threadIdx.x][0] * 0.70710678118654752440;
+}
+
+// ---------------------------------------------------------------------------
+// FMA-rate probe: 8 independent dependency chains per thread, all in registers
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) {
+  const T x = (T)(1.0 + 1e-7 * threadIdx.x), y = (T)(1e-9 * blockIdx.x);
+  T acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = (T)i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = fma(acc[i], x, y);
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += acc[i];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)s;
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+template <int P, int NE>
+int run_element(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
+                const double *fhat, double dt, double a0, double b0, int mode, cudaStream_t s) {
+  using C = Cfg<P, NE>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_element<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return (int)e;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element<P, NE>, kThreads, C::SMEM);
+  if (e != cudaSuccess) return (int)e;
+  if (per_sm < 1) per_sm = 1;
+  const int ntiles = (int)((m->N + C::EB - 1) / C::EB);
+  const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
+  k_element<P, NE><<<grid, kThreads, C::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
+                                                   (int)m->N, dt, a0, b0, mode, m->gamma);
+  return (int)cudaGetLastError();
+}
+
+template <int P, int NE>
+int run_traces(const dg_mesh *m, const double *c, double *trace, cudaStream_t s) {
+  using C = Cfg<P, NE>;
+  const int ntiles = (int)((m->N + C::EB - 1) / C::EB);
+  const int grid = ntiles < m->num_sms * 4 ? ntiles : m->num_sms * 4;
+  k_traces<P, NE><<<grid, kThreads, 0, s>>>(c, trace, m->tab.BfT, (int)m->N);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int element_smem_bytes(int p, int ne) {
+  if (p == 1 && ne == 2) return Cfg<1, 2>::SMEM;
+  if (p == 2 && ne == 3) return Cfg<2, 3>::SMEM;
+  if (p == 3 && ne == 4) return Cfg<3, 4>::SMEM;
+  if (p == 3 && ne == 3) return Cfg<3, 3>::SMEM;
+  if (p == 4 && ne == 5) return Cfg<4, 5>::SMEM;
+  if (p == 5 && ne == 6) return Cfg<5, 6>::SMEM;
+  return -1;
+}
+
+int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+#define CALL(P, NE) run_traces<P, NE>(m, c, trace, s)
+  if (m->p == 1 && m->ne == 2) return CALL(1, 2);
+  if (m->p == 2 && m->ne == 3) return CALL(2, 3);
+  if (m->p == 3 && m->ne == 4) return CALL(3, 4);
+  if (m->p == 3 && m->ne == 3) return CALL(3, 3);
+  if (m->p == 4 && m->ne == 5) return CALL(4, 5);
+  if (m->p == 5 && m->ne == 6) return CALL(5, 6);
+#undef CALL
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = m->F * m->ne;
+  const int grid = (int)((n + kThreads - 1) / kThreads);
+  switch (m->ne) {
+    case 2: k_face<2><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
+    case 3: k_face<3><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
+    case 4: k_face<4><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
+    case 5: k_face<5><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
+    case 6: k_face<6><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
+                   const double *fhat, double dt, double a0, double b0, int mode, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+#define CALL(P, NE) run_element<P, NE>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s)
+  if (m->p == 1 && m->ne == 2) return CALL(1, 2);
+  if (m->p == 2 && m->ne == 3) return CALL(2, 3);
+  if (m->p == 3 && m->ne == 4) return CALL(3, 4);
+  if (m->p == 3 && m->ne == 3) return CALL(3, 3);
+  if (m->p == 4 && m->ne == 5) return CALL(4, 5);
+  if (m->p == 5 && m->ne == 6) return CALL(5, 6);
+#undef CALL
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_project(const dg_mesh *m, const double *u, double *c, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = m->N * m->np;
+  const int grid = (int)((n + kThreads - 1) / kThreads);
+  switch (m->p) {
+    case 1: k_project<1><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
+    case 2: k_project<2><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
+    case 3: k_project<3><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
+    case 4: k_project<4><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
+    case 5: k_project<5><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_volume_points(const dg_mesh *m, double *xy, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = m->N * m->nq;
+  const int grid = (int)((n + kThreads - 1) / kThreads);
+  k_volume_points<<<grid, kThreads, 0, s>>>(m->xy, m->tab.vr, m->tab.vs, xy, (int)m->N, m->nq);
+  return (int)cudaGetLastError();
+}
+
+int launch_fma_probe(int fp64, int blocks, int threads, int iters, double *out, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (threads != kThreads) return (int)cudaErrorInvalidValue;
+  if (fp64) k_fma_probe<double><<<blocks, threads, 0, s>>>(iters, out);
+  else k_fma_probe<float><<<blocks, threads, 0, s>>>(iters, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  k_totals_partial<<<m->totals_blocks, kThreads, 0, s>>>(c, m->geo, (int)m->N, m->np, m->partial);
+  k_totals_final<<<1, kThreads, 0, s>>>(m->partial, m->totals_blocks, out_dev);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dg

@@ -1,0 +1,255 @@
+"""Thin Python binding of the C ABI in include/dg.h (ctypes).
+
+Argument marshalling only: every step of the solver runs in libdg.so's CUDA
+kernels.  State tensors are torch float64 CUDA tensors of shape [N, 4, N_p]
+(element-major coefficients); calls run on torch's current CUDA stream.
+
+If libdg.so is missing this module raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdg.so")
+
+DG_OK = 0
+STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EMESH",
+          5: "DG_ENONPHYS", 6: "DG_ETIMEOUT", 7: "DG_ENOTIMPL"}
+PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
+
+# every entry point declared in include/dg.h
+EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
+           "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
+           "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
+           "dg_kernel_times", "dg_probe_fma_rate")
+KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
+
+
+class DGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("elem_xy", ctypes.c_void_p), ("nbr", ctypes.c_void_p),
+                ("nbr_face", ctypes.c_void_p), ("p", ctypes.c_int), ("n_edge_pts", ctypes.c_int),
+                ("gamma", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("n_face", ctypes.c_int64), ("p", ctypes.c_int),
+                ("n_modes", ctypes.c_int), ("n_vol_pts", ctypes.c_int), ("n_edge_pts", ctypes.c_int),
+                ("gamma", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdg.so not found at %s: run __graft_entry__.build() (or "
+                           "python -m paper_1601_07944_gb300._build) first" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "dg_mesh_create": [P, P],
+        "dg_mesh_destroy": [P],
+        "dg_mesh_info": [P, P],
+        "dg_volume_points": [P, P, P],
+        "dg_project_ic": [P, P, P, P],
+        "dg_rhs": [P, P, P, I, P],
+        "dg_rk_step": [P, P, D, I, I, P],
+        "dg_rk_step_host": [P, P, D, I, I, P],
+        "dg_adjoint_step": [P, P, D, P, P, P],
+        "dg_conserved_totals": [P, P, P, P],
+        "dg_host_tables": [I, I, P, P, P, P, P, P, P, P, P],
+        "dg_set_timing": [P, I],
+        "dg_kernel_times": [P, P, P],
+        "dg_probe_fma_rate": [P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = I
+    lib.dg_last_error.argtypes = []
+    lib.dg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != DG_OK:
+        raise DGError(st, load().dg_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, name: str, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("%s must be a float64 CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec(precision) -> int:
+    if isinstance(precision, str):
+        return PRECISION[precision]
+    return int(precision)
+
+
+def probe_fma_rate(stream=None):
+    """(fp64, fp32) sustained FMA rates of the current device, TFLOP/s."""
+    a = ctypes.c_double(); b = ctypes.c_double()
+    _check(load().dg_probe_fma_rate(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
+    return a.value, b.value
+
+
+def host_tables(p: int, ne: int = 0):
+    """The library's host-side rules and basis tables (no GPU needed)."""
+    ne = ne or p + 1
+    np_, nq = (p + 1) * (p + 2) // 2, (p + 1) ** 2
+    out = dict(vol_r=np.zeros(nq), vol_s=np.zeros(nq), vol_w=np.zeros(nq), edge_x=np.zeros(ne),
+               edge_w=np.zeros(ne), phi=np.zeros((nq, np_)), dphi_r=np.zeros((nq, np_)),
+               dphi_s=np.zeros((nq, np_)), phi_face=np.zeros((3, ne, np_)))
+    _check(load().dg_host_tables(p, ne, *[_np_ptr(out[k]) for k in (
+        "vol_r", "vol_s", "vol_w", "edge_x", "edge_w", "phi", "dphi_r", "dphi_s", "phi_face")]))
+    return out
+
+
+class Mesh:
+    """A mesh handle (geometry, tables and work buffers on the current GPU)."""
+
+    def __init__(self, elem_xy, nbr, nbr_face, p: int, n_edge_pts: int = 0, gamma: float = 1.4):
+        lib = load()
+        xy = np.ascontiguousarray(elem_xy, dtype=np.float64)
+        nb = np.ascontiguousarray(nbr, dtype=np.int64)
+        nf = np.ascontiguousarray(nbr_face, dtype=np.int8)
+        if xy.ndim != 3 or xy.shape[1:] != (3, 2) or nb.shape != (xy.shape[0], 3) or nf.shape != nb.shape:
+            raise ValueError("mesh arrays must be elem_xy[N,3,2], nbr[N,3], nbr_face[N,3]")
+        desc = _Desc(xy.shape[0], xy.ctypes.data, nb.ctypes.data, nf.ctypes.data, p, n_edge_pts, gamma)
+        h = ctypes.c_void_p()
+        _check(lib.dg_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        info = _Info()
+        _check(lib.dg_mesh_info(h, ctypes.byref(info)))
+        self.N, self.n_face, self.p = info.n_elem, info.n_face, info.p
+        self.np, self.nq, self.ne, self.gamma = info.n_modes, info.n_vol_pts, info.n_edge_pts, info.gamma
+
+    @classmethod
+    def from_mesh(cls, mesh, p: int, **kw):
+        return cls(mesh.elem_xy, mesh.nbr, mesh.nbr_face, p, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def coef_shape(self):
+        return (self.N, 4, self.np)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().dg_mesh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- diagnostics --------------------------------------------------------
+    def set_timing(self, enable: bool):
+        _check(load().dg_set_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """{kind: (launches, total ms)} since timing was enabled (synchronises)."""
+        ms = np.zeros(8); n = np.zeros(8, dtype=np.int64)
+        _check(load().dg_kernel_times(self._h, _np_ptr(ms), _np_ptr(n)))
+        return {KERNEL_KINDS[k]: (int(n[k]), float(ms[k])) for k in range(8) if n[k]}
+
+    # -- calls ------------------------------------------------------------
+    def volume_points(self, stream=None):
+        import torch
+        xy = torch.empty((self.N, self.nq, 2), dtype=torch.float64, device="cuda")
+        _check(load().dg_volume_points(self._h, _dev_ptr(xy, "xy"), _stream_ptr(stream)))
+        return xy
+
+    def project_ic(self, u, out=None, stream=None):
+        import torch
+        c = out if out is not None else torch.empty(self.coef_shape, dtype=torch.float64, device="cuda")
+        _check(load().dg_project_ic(self._h, _dev_ptr(u, "u", (self.N, self.nq, 4)),
+                                    _dev_ptr(c, "c", self.coef_shape), _stream_ptr(stream)))
+        return c
+
+    def rhs(self, c, out=None, precision="fp64", stream=None):
+        import torch
+        r = out if out is not None else torch.empty(self.coef_shape, dtype=torch.float64, device="cuda")
+        _check(load().dg_rhs(self._h, _dev_ptr(c, "c", self.coef_shape), _dev_ptr(r, "r", self.coef_shape),
+                             _prec(precision), _stream_ptr(stream)))
+        return r
+
+    def rk_step(self, c, dt: float, nsteps: int = 1, precision="fp64", stream=None):
+        """nsteps SSP-RK3 steps in place on the device tensor c."""
+        _check(load().dg_rk_step(self._h, _dev_ptr(c, "c", self.coef_shape), float(dt), int(nsteps),
+                                 _prec(precision), _stream_ptr(stream)))
+        return c
+
+    def rk_step_host(self, c_host, dt: float, nsteps: int = 1, precision="fp64", stream=None):
+        """nsteps SSP-RK3 steps on a host array (numpy or CPU tensor, ideally pinned), in place."""
+        import torch
+        if isinstance(c_host, torch.Tensor):
+            if c_host.is_cuda or c_host.dtype != torch.float64 or not c_host.is_contiguous():
+                raise TypeError("c_host must be a contiguous float64 CPU tensor")
+            if tuple(c_host.shape) != self.coef_shape:
+                raise ValueError("c_host has the wrong shape")
+            ptr = ctypes.c_void_p(c_host.data_ptr())
+        else:
+            if c_host.dtype != np.float64 or not c_host.flags.c_contiguous or c_host.shape != self.coef_shape:
+                raise TypeError("c_host must be a contiguous float64 array of shape %s" % (self.coef_shape,))
+            ptr = _np_ptr(c_host)
+        _check(load().dg_rk_step_host(self._h, ptr, float(dt), int(nsteps), _prec(precision),
+                                      _stream_ptr(stream)))
+        return c_host
+
+    def adjoint_step(self, c_n, dt: float, lam_np1, out=None, stream=None):
+        import torch
+        lam = out if out is not None else torch.empty(self.coef_shape, dtype=torch.float64, device="cuda")
+        _check(load().dg_adjoint_step(self._h, _dev_ptr(c_n, "c_n", self.coef_shape), float(dt),
+                                      _dev_ptr(lam_np1, "lam_np1", self.coef_shape),
+                                      _dev_ptr(lam, "lam_n", self.coef_shape), _stream_ptr(stream)))
+        return lam
+
+    def conserved_totals(self, c, stream=None):
+        out = np.zeros(4)
+        _check(load().dg_conserved_totals(self._h, _dev_ptr(c, "c", self.coef_shape), _np_ptr(out),
+                                          _stream_ptr(stream)))
+        return out
+
+    def project_function(self, ic, stream=None):
+        """Projects a function ic(x, y) -> [..., 4] (evaluated on the host) onto the basis."""
+        import torch
+        xy = self.volume_points(stream).cpu().numpy()
+        u = torch.from_numpy(np.ascontiguousarray(ic(xy[..., 0], xy[..., 1]))).cuda()
+        return self.project_ic(u, stream=stream)

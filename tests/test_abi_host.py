@@ -1,0 +1,106 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+entry point include/dg.h declares, its own quadrature and basis tables agree with
+the oracle's independent ones, and mesh validation rejects bad meshes before any
+device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1601_07944_gb300 import _build, dg, inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return dg.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "dg_rhs" in names and "dg_rk_step" in names and "dg_adjoint_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(dg.EXPORTS)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_host_tables_match_oracle(lib, oracle_mod, p):
+    T = dg.host_tables(p)
+    r, s, w = oracle_mod.stroud(p + 1)
+    assert np.abs(T["vol_r"] - r).max() < 1e-15
+    assert np.abs(T["vol_s"] - s).max() < 1e-15
+    assert np.abs(T["vol_w"] - w).max() < 1e-15
+    x, we = oracle_mod.gauss_legendre(p + 1)
+    assert np.abs(T["edge_x"] - x).max() < 1e-15
+    assert np.abs(T["edge_w"] - we).max() < 1e-15
+    phi, dr, ds = oracle_mod.dubiner(p, r, s)
+
+    def rel(a, b):
+        return np.abs(a - b).max() / np.abs(b).max()
+    assert rel(T["phi"], phi) < 1e-14
+    assert rel(T["dphi_r"], dr) < 1e-14
+    assert rel(T["dphi_s"], ds) < 1e-14
+    xi = T["edge_x"]
+    V = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    for q in range(3):
+        pts = 0.5 * (1 - xi)[:, None] * V[q] + 0.5 * (1 + xi)[:, None] * V[(q + 1) % 3]
+        pf, _, _ = oracle_mod.dubiner(p, pts[:, 0], pts[:, 1])
+        assert rel(T["phi_face"][q], pf) < 1e-14
+
+
+def test_host_tables_p3_three_edge_points(lib, oracle_mod):
+    T = dg.host_tables(3, 3)
+    x, w = oracle_mod.gauss_legendre(3)
+    assert np.abs(T["edge_x"] - x).max() < 1e-15 and np.abs(T["edge_w"] - w).max() < 1e-15
+
+
+def _create(lib, xy, nbr, nf, p=2, ne=0):
+    xy = np.ascontiguousarray(xy, np.float64)
+    nbr = np.ascontiguousarray(nbr, np.int64)
+    nf = np.ascontiguousarray(nf, np.int8)
+    desc = dg._Desc(xy.shape[0], xy.ctypes.data, nbr.ctypes.data, nf.ctypes.data, p, ne, 1.4)
+    h = ctypes.c_void_p()
+    st = lib.dg_mesh_create(ctypes.byref(desc), ctypes.byref(h))
+    return st, lib.dg_last_error().decode()
+
+
+def test_mesh_validation_errors(lib):
+    m = I.periodic_mesh(4)
+    xy = m.elem_xy.copy()
+    xy[3] = xy[3][::-1]                           # clockwise element
+    st, msg = _create(lib, xy, m.nbr, m.nbr_face)
+    assert st == 4 and "counter-clockwise" in msg
+    nbr = m.nbr.copy()
+    nbr[5, 1] = (nbr[5, 1] + 1) % m.n_elem          # asymmetric neighbour
+    st, msg = _create(lib, m.elem_xy, nbr, m.nbr_face)
+    assert st == 4 and "symmetric" in msg
+    nbr = m.nbr.copy()
+    nbr[0, 0] = -1                                # boundary code: unsupported
+    st, _ = _create(lib, m.elem_xy, nbr, m.nbr_face)
+    assert st == 4
+    xy = m.elem_xy.copy()
+    xy[7, 1] += 1e-3                              # edge no longer matches its neighbour's
+    xy[7, 1] -= 0.0
+    st, msg = _create(lib, xy, m.nbr, m.nbr_face)
+    assert st == 4
+    st, msg = _create(lib, m.elem_xy, m.nbr, m.nbr_face, p=7)
+    assert st == 1 and "unsupported" in msg
+    st, msg = _create(lib, m.elem_xy, m.nbr, m.nbr_face, p=2, ne=5)
+    assert st == 1
+
+
+def test_null_arguments(lib):
+    assert lib.dg_mesh_create(None, None) == 1
+    assert lib.dg_rhs(None, None, None, 0, None) == 1
+    assert lib.dg_mesh_destroy(None) == 0

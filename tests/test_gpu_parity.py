@@ -1,0 +1,168 @@
+"""GPU (sm_103a) parity of the float64 path against the CPU oracle, through the C ABI.
+
+Tolerance: relative L2 over all coefficients <= 1e-12 (the float64 path differs
+from the oracle only in the order of roundings; a single RHS agrees to ~1e-15).
+Sizes span several element tiles with a ragged last tile (n = 6 gives N = 72,
+n = 16 gives N = 512), and the full 256 x 256 workload is checked on one RHS and
+one time step in the launch configuration the benchmark times.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_07944_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dgmod():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1601_07944_gb300 import _build, dg
+    _build.build()
+    dg.load()
+    return dg
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+CASES = [(1, 0), (2, 0), (3, 0), (3, 3), (4, 0), (5, 0)]
+
+
+def test_volume_points_match(dgmod, oracle_mod):
+    mesh = I.periodic_mesh(6)
+    for p in (1, 4):
+        m = dgmod.Mesh.from_mesh(mesh, p)
+        o = oracle_mod.OracleDG.from_mesh(mesh, p)
+        assert np.abs(_host(m.volume_points()) - o.volume_points()).max() < 1e-14
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_project_ic_parity(dgmod, oracle_mod, p):
+    mesh = I.periodic_mesh(6)
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    got = _host(m.project_function(I.perturbed_vortex))
+    ref = o.project_ic(I.perturbed_vortex)
+    assert rel_l2(got, ref) < 1e-14
+
+
+@pytest.mark.parametrize("n", [6, 16])
+@pytest.mark.parametrize("p,ne", CASES)
+def test_rhs_parity(dgmod, oracle_mod, p, ne, n):
+    mesh = I.periodic_mesh(n)
+    m = dgmod.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p, n_edge_pts=ne)
+    c = o.project_ic(I.perturbed_vortex)
+    ref = o.rhs(c)
+    got = _host(m.rhs(_dev(c)))
+    assert rel_l2(got, ref) < TOL
+    assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("p,ne,n,steps", [(1, 0, 16, 100), (2, 0, 16, 20), (3, 0, 16, 20),
+                                          (3, 3, 16, 10), (4, 0, 8, 10), (5, 0, 8, 5)])
+def test_rk_step_parity(dgmod, oracle_mod, p, ne, n, steps):
+    """Whole runs: each side projects the initial data with its own tables and
+    advances with SSP-RK3 at the same fixed dt.  (p=1, n=16, 100 steps is the
+    512-element vortex workload in full.)"""
+    mesh = I.periodic_mesh(n)
+    ic = I.vortex if p == 1 else I.perturbed_vortex
+    dt = I.fixed_dt(mesh, ic, p)
+    m = dgmod.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p, n_edge_pts=ne)
+    c = m.project_function(ic)
+    m.rk_step(c, dt, steps)
+    ref = o.ssp_rk3(o.project_ic(ic), dt, steps)
+    got = _host(c)
+    assert rel_l2(got, ref) < TOL, rel_l2(got, ref)
+
+
+def test_totals_parity_and_conservation(dgmod, oracle_mod):
+    mesh = I.periodic_mesh(16)
+    p = 2
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    c = m.project_function(I.perturbed_vortex)
+    t0 = m.conserved_totals(c)
+    ref = o.totals(_host(c))
+    assert np.all(np.abs(t0 - ref) <= 1e-14 * np.abs(ref))
+    assert np.array_equal(t0, m.conserved_totals(c))          # fixed-order reduction
+    m.rk_step(c, I.fixed_dt(mesh, I.perturbed_vortex, p), 50)
+    t1 = m.conserved_totals(c)
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * np.abs(t0))
+
+
+def test_deterministic(dgmod):
+    mesh = I.periodic_mesh(16)
+    m = dgmod.Mesh.from_mesh(mesh, 3)
+    c0 = m.project_function(I.perturbed_vortex)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, 3)
+    a = c0.clone(); b = c0.clone()
+    m.rk_step(a, dt, 5)
+    m.rk_step(b, dt, 5)
+    assert np.array_equal(_host(a), _host(b))
+
+
+def test_host_entry_matches_device_entry(dgmod):
+    import torch
+    mesh = I.periodic_mesh(8)
+    m = dgmod.Mesh.from_mesh(mesh, 2)
+    c = m.project_function(I.vortex)
+    dt = I.fixed_dt(mesh, I.vortex, 2)
+    h = torch.empty(c.shape, dtype=torch.float64).pin_memory()
+    h.copy_(c.cpu())
+    m.rk_step(c, dt, 3)
+    m.rk_step_host(h, dt, 3)
+    assert np.array_equal(_host(c), h.numpy())
+
+
+def test_free_stream_full_size(dgmod):
+    """A uniform state is an exact steady solution on the full 1024^2 p=5 mesh."""
+    mesh = I.periodic_mesh(1024)
+    m = dgmod.Mesh.from_mesh(mesh, 5)
+    c = m.project_function(lambda x, y: I.uniform_state(x, y))
+    r = _host(m.rhs(c))
+    assert np.abs(r).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,p", [(256, 3), (512, 4)])
+def test_full_size_parity(dgmod, oracle_mod, n, p):
+    """The 256^2 p=3 and 512^2 p=4 workloads at full size: one RHS and one SSP-RK3
+    step against the oracle, in the benchmark's launch configuration."""
+    mesh = I.periodic_mesh(n)
+    ic = I.vortex if n == 256 else I.perturbed_vortex
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    c = o.project_ic(ic)
+    assert rel_l2(_host(m.rhs(_dev(c))), o.rhs(c)) < TOL
+    dt = I.fixed_dt(mesh, ic, p)
+    cd = _dev(c)
+    m.rk_step(cd, dt, 1)
+    assert rel_l2(_host(cd), o.ssp_rk3(c, dt, 1)) < TOL
+
+
+def test_unbuilt_modes_report_not_implemented(dgmod):
+    mesh = I.periodic_mesh(4)
+    m = dgmod.Mesh.from_mesh(mesh, 1)
+    c = m.project_function(I.vortex)
+    with pytest.raises(dgmod.DGError) as ei:
+        m.adjoint_step(c, 0.01, c.clone())
+    assert ei.value.status == 7
