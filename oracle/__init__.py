@@ -67,6 +67,10 @@ def _load():
             "or_rhs": (I, [P, P, P]),
             "or_ssp_rk3": (I, [P, P, D, I]),
             "or_totals": (I, [P, P, P]),
+            "or_lax_friedrichs_jacobians": (I, [D, P, P, D, D, P, P]),
+            "or_flux_jacobian": (I, [D, P, D, D, P]),
+            "or_rhs_vjp": (I, [P, P, P, P]),
+            "or_ssp_rk3_vjp": (I, [P, P, D, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -151,6 +155,21 @@ def euler_flux(U, gamma=1.4):
     F1 = np.zeros(4); F2 = np.zeros(4)
     _chk(_load().or_euler_flux(gamma, _ptr(U), _ptr(F1), _ptr(F2)))
     return F1, F2
+
+
+def lax_friedrichs_jacobians(Ul, Ur, nx, ny, gamma=1.4):
+    Ul = np.ascontiguousarray(Ul, dtype=np.float64)
+    Ur = np.ascontiguousarray(Ur, dtype=np.float64)
+    Jl = np.zeros((4, 4)); Jr = np.zeros((4, 4))
+    _chk(_load().or_lax_friedrichs_jacobians(gamma, _ptr(Ul), _ptr(Ur), nx, ny, _ptr(Jl), _ptr(Jr)))
+    return Jl, Jr
+
+
+def flux_jacobian(U, nx, ny, gamma=1.4):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    J = np.zeros((4, 4))
+    _chk(_load().or_flux_jacobian(gamma, _ptr(U), nx, ny, _ptr(J)))
+    return J
 
 
 # ---------------------------------------------------------------------------
@@ -254,6 +273,22 @@ class OracleDG:
     def ssp_rk3(self, c, dt: float, nsteps: int):
         out = np.array(c, dtype=np.float64, copy=True, order="C")
         _chk(_lib.or_ssp_rk3(self._h, _ptr(out), dt, nsteps))
+        return out
+
+    def rhs_vjp(self, c, lam):
+        """(dR/dc)^T lam."""
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        out = np.zeros(self.coef_shape())
+        _chk(_lib.or_rhs_vjp(self._h, _ptr(c), _ptr(lam), _ptr(out)))
+        return out
+
+    def ssp_rk3_vjp(self, c_n, dt: float, lam_np1):
+        """(d c_{n+1} / d c_n)^T lam_np1 for one SSP-RK3 step from c_n."""
+        c_n = np.ascontiguousarray(c_n, dtype=np.float64)
+        lam = np.ascontiguousarray(lam_np1, dtype=np.float64)
+        out = np.zeros(self.coef_shape())
+        _chk(_lib.or_ssp_rk3_vjp(self._h, _ptr(c_n), dt, _ptr(lam), _ptr(out)))
         return out
 
     def totals(self, c):

@@ -52,57 +52,68 @@
 /* ------------------------------------------------------------------------- */
 
 /* P_n^{(a,b)}(x) and its derivative, from the standard three-term recurrence
- * (normalisation P_n(1) = binom(n+a, n)). */
-static void jacobi_eval(int n, double a, double b, double x, double *P, double *dP)
+ * (normalisation P_n(1) = binom(n+a, n)), in extended precision. */
+static void jacobi_eval(int n, long double a, long double b, long double x, long double *P, long double *dP)
 {
-    double p0 = 1.0, p1 = 0.5 * (a - b + (a + b + 2.0) * x);
-    double d0 = 0.0, d1 = 0.5 * (a + b + 2.0);
-    if (n == 0) { *P = 1.0; *dP = 0.0; return; }
+    long double p0 = 1.0L, p1 = 0.5L * (a - b + (a + b + 2.0L) * x);
+    long double d0 = 0.0L, d1 = 0.5L * (a + b + 2.0L);
+    if (n == 0) { *P = 1.0L; *dP = 0.0L; return; }
     for (int k = 2; k <= n; ++k) {
-        double kk = (double)k;
-        double c1 = 2.0 * kk * (kk + a + b) * (2.0 * kk + a + b - 2.0);
-        double c2 = (2.0 * kk + a + b - 1.0) * (a * a - b * b);
-        double c3 = (2.0 * kk + a + b - 2.0) * (2.0 * kk + a + b - 1.0) * (2.0 * kk + a + b);
-        double c4 = 2.0 * (kk + a - 1.0) * (kk + b - 1.0) * (2.0 * kk + a + b);
-        double p2 = ((c2 + c3 * x) * p1 - c4 * p0) / c1;
-        double d2 = ((c2 + c3 * x) * d1 + c3 * p1 - c4 * d0) / c1;
+        long double kk = (long double)k;
+        long double c1 = 2.0L * kk * (kk + a + b) * (2.0L * kk + a + b - 2.0L);
+        long double c2 = (2.0L * kk + a + b - 1.0L) * (a * a - b * b);
+        long double c3 = (2.0L * kk + a + b - 2.0L) * (2.0L * kk + a + b - 1.0L) * (2.0L * kk + a + b);
+        long double c4 = 2.0L * (kk + a - 1.0L) * (kk + b - 1.0L) * (2.0L * kk + a + b);
+        long double p2 = ((c2 + c3 * x) * p1 - c4 * p0) / c1;
+        long double d2 = ((c2 + c3 * x) * d1 + c3 * p1 - c4 * d0) / c1;
         p0 = p1; p1 = p2; d0 = d1; d1 = d2;
     }
     *P = p1; *dP = d1;
 }
 
-/* n-point Gauss-Jacobi rule for the weight (1-x)^a (1+x)^b on [-1, 1];
- * nodes ascending.  Returns 0 on success. */
-int or_gauss_jacobi(int n, double a, double b, double *x, double *w)
+/* n-point Gauss-Jacobi rule for the weight (1-x)^a (1+x)^b on [-1, 1], nodes
+ * ascending, computed in extended precision (Newton iteration with deflation)
+ * and rounded once to double.  xl, wl (optional) receive the extended values. */
+static int gauss_jacobi_l(int n, double a_, double b_, long double *xl, long double *wl)
 {
     if (n < 1 || n > 64) return 1;
+    long double a = a_, b = b_;
+    const long double pi = 3.14159265358979323846264338327950288L;
     for (int k = 0; k < n; ++k) {
         /* Chebyshev-Gauss guess, then Newton with deflation */
-        double r = -cos((2.0 * k + 1.0) * M_PI / (2.0 * n));
+        long double r = -cosl((2.0L * k + 1.0L) * pi / (2.0L * n));
         for (int it = 0; it < 200; ++it) {
-            double P, dP;
+            long double P, dP;
             jacobi_eval(n, a, b, r, &P, &dP);
-            double s = 0.0;
-            for (int i = 0; i < k; ++i) s += 1.0 / (r - x[i]);
-            double delta = -P / (dP - s * P);
+            long double s = 0.0L;
+            for (int i = 0; i < k; ++i) s += 1.0L / (r - xl[i]);
+            long double delta = -P / (dP - s * P);
             r += delta;
-            if (fabs(delta) < 1e-16 * (1.0 + fabs(r))) break;
+            if (fabsl(delta) <= 1e-30L * (1.0L + fabsl(r)) || (it > 8 && fabsl(delta) < 1e-17L)) break;
         }
-        x[k] = r;
+        xl[k] = r;
     }
     /* sort ascending (deflation keeps them distinct but not necessarily ordered) */
     for (int i = 1; i < n; ++i) {
-        double t = x[i]; int j = i - 1;
-        while (j >= 0 && x[j] > t) { x[j + 1] = x[j]; --j; }
-        x[j + 1] = t;
+        long double t = xl[i]; int j = i - 1;
+        while (j >= 0 && xl[j] > t) { xl[j + 1] = xl[j]; --j; }
+        xl[j + 1] = t;
     }
-    double lg = lgamma(n + a + 1.0) + lgamma(n + b + 1.0) - lgamma(n + a + b + 1.0) - lgamma(n + 1.0);
-    double cst = pow(2.0, a + b + 1.0) * exp(lg);
+    long double lg = lgammal(n + a + 1.0L) + lgammal(n + b + 1.0L) - lgammal(n + a + b + 1.0L) - lgammal(n + 1.0L);
+    long double cst = powl(2.0L, a + b + 1.0L) * expl(lg);
     for (int k = 0; k < n; ++k) {
-        double P, dP;
-        jacobi_eval(n, a, b, x[k], &P, &dP);
-        w[k] = cst / ((1.0 - x[k] * x[k]) * dP * dP);
+        long double P, dP;
+        jacobi_eval(n, a, b, xl[k], &P, &dP);
+        wl[k] = cst / ((1.0L - xl[k] * xl[k]) * dP * dP);
     }
+    return 0;
+}
+
+int or_gauss_jacobi(int n, double a, double b, double *x, double *w)
+{
+    long double xl[64], wl[64];
+    if (gauss_jacobi_l(n, a, b, xl, wl)) return 1;
+    for (int k = 0; k < n; ++k) { x[k] = (double)xl[k]; w[k] = (double)wl[k]; }
     return 0;
 }
 
@@ -115,15 +126,15 @@ int or_gauss_legendre(int n, double *x, double *w) { return or_gauss_jacobi(n, 0
  * Point order: b-index outer, a-index inner. */
 int or_stroud(int n, double *r, double *s, double *w)
 {
-    double xa[64], wa[64], xb[64], wb[64];
-    if (or_gauss_jacobi(n, 0.0, 0.0, xa, wa)) return 1;
-    if (or_gauss_jacobi(n, 1.0, 0.0, xb, wb)) return 1;
+    long double xa[64], wa[64], xb[64], wb[64];
+    if (gauss_jacobi_l(n, 0.0, 0.0, xa, wa)) return 1;
+    if (gauss_jacobi_l(n, 1.0, 0.0, xb, wb)) return 1;
     for (int ib = 0; ib < n; ++ib)
         for (int ia = 0; ia < n; ++ia) {
             int k = ib * n + ia;
-            r[k] = 0.25 * (1.0 + xa[ia]) * (1.0 - xb[ib]);
-            s[k] = 0.5 * (1.0 + xb[ib]);
-            w[k] = 0.125 * wa[ia] * wb[ib];
+            r[k] = (double)(0.25L * (1.0L + xa[ia]) * (1.0L - xb[ib]));
+            s[k] = (double)(0.5L * (1.0L + xb[ib]));
+            w[k] = (double)(0.125L * wa[ia] * wb[ib]);
         }
     return 0;
 }
@@ -751,5 +762,200 @@ int or_totals(const oracle_dg *o, const double *C, double *out)
             for (int j = 0; j < np; ++j) s += C[((size_t)i * OM + m) * np + j] * o->phi_int[j];
             out[m] += o->detJ[i] * s;
         }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Discrete adjoint: transposed Jacobian-vector products of the RHS and of   */
+/* one SSP-RK3 step, taken through the forward steps in reverse order.       */
+/* Derivative conventions at the kinks of the Lax-Friedrichs flux:           */
+/*   d|x|/dx = sign(x) with sign(0) = 0;  d max(a, b) follows a when a >= b  */
+/*   (a tie goes to the left trace).                                         */
+/* ------------------------------------------------------------------------- */
+
+/* gradients of the pressure and of the sound speed with respect to U */
+static void pressure_grad(double g, const double *U, double *p, double *dp)
+{
+    double rho = U[0], u = U[1] / rho, v = U[2] / rho;
+    *p = (g - 1.0) * (U[3] - 0.5 * rho * (u * u + v * v));
+    dp[0] = (g - 1.0) * 0.5 * (u * u + v * v);
+    dp[1] = -(g - 1.0) * u;
+    dp[2] = -(g - 1.0) * v;
+    dp[3] = (g - 1.0);
+}
+
+/* J[a][b] = d (F(U).n)_a / d U_b for F.n = (rho vn, mx vn + p nx, my vn + p ny, (E+p) vn) */
+static void flux_n_jacobian(double g, const double *U, double nx, double ny, double J[OM][OM])
+{
+    double rho = U[0], vn = (U[1] * nx + U[2] * ny) / rho;
+    double dvn[OM] = {-vn / rho, nx / rho, ny / rho, 0.0};
+    double p, dp[OM];
+    pressure_grad(g, U, &p, dp);
+    for (int b = 0; b < OM; ++b) {
+        double e0 = b == 0, e1 = b == 1, e2 = b == 2, e3 = b == 3;
+        J[0][b] = e0 * vn + rho * dvn[b];
+        J[1][b] = e1 * vn + U[1] * dvn[b] + nx * dp[b];
+        J[2][b] = e2 * vn + U[2] * dvn[b] + ny * dp[b];
+        J[3][b] = (e3 + dp[b]) * vn + (U[3] + p) * dvn[b];
+    }
+}
+
+/* s(U) = |v.n| + c and its gradient */
+static double wave_speed_grad(double g, const double *U, double nx, double ny, double *ds)
+{
+    double rho = U[0], vn = (U[1] * nx + U[2] * ny) / rho;
+    double dvn[OM] = {-vn / rho, nx / rho, ny / rho, 0.0};
+    double p, dp[OM];
+    pressure_grad(g, U, &p, dp);
+    double c = sqrt(g * p / rho);
+    double sg = vn > 0.0 ? 1.0 : (vn < 0.0 ? -1.0 : 0.0);
+    for (int b = 0; b < OM; ++b) {
+        double dc = g / (2.0 * c) * (dp[b] / rho - (b == 0 ? p / (rho * rho) : 0.0));
+        ds[b] = sg * dvn[b] + dc;
+    }
+    return fabs(vn) + c;
+}
+
+/* Jacobians of the Lax-Friedrichs flux with respect to its two arguments */
+static void lax_friedrichs_jacobians(double g, const double *Ul, const double *Ur, double nx, double ny,
+                                     double Jl[OM][OM], double Jr[OM][OM])
+{
+    double Al[OM][OM], Ar[OM][OM], dsl[OM], dsr[OM];
+    flux_n_jacobian(g, Ul, nx, ny, Al);
+    flux_n_jacobian(g, Ur, nx, ny, Ar);
+    double sl = wave_speed_grad(g, Ul, nx, ny, dsl);
+    double sr = wave_speed_grad(g, Ur, nx, ny, dsr);
+    double alpha = sl >= sr ? sl : sr;
+    int left = sl >= sr;
+    for (int a = 0; a < OM; ++a)
+        for (int b = 0; b < OM; ++b) {
+            double jump = Ur[a] - Ul[a];
+            double dal = left ? dsl[b] : 0.0, dar = left ? 0.0 : dsr[b];
+            Jl[a][b] = 0.5 * Al[a][b] + (a == b ? 0.5 * alpha : 0.0) - 0.5 * jump * dal;
+            Jr[a][b] = 0.5 * Ar[a][b] - (a == b ? 0.5 * alpha : 0.0) - 0.5 * jump * dar;
+        }
+}
+
+int or_lax_friedrichs_jacobians(double g, const double *Ul, const double *Ur, double nx, double ny,
+                                double *Jl, double *Jr)
+{
+    double A[OM][OM], B[OM][OM];
+    lax_friedrichs_jacobians(g, Ul, Ur, nx, ny, A, B);
+    memcpy(Jl, A, sizeof A);
+    memcpy(Jr, B, sizeof B);
+    return 0;
+}
+
+int or_flux_jacobian(double g, const double *U, double nx, double ny, double *J)
+{
+    double A[OM][OM];
+    flux_n_jacobian(g, U, nx, ny, A);
+    memcpy(J, A, sizeof A);
+    return 0;
+}
+
+/* out = (dR/dC)^T lam, following Algorithms 3, 2 and 1 backwards */
+int or_rhs_vjp(oracle_dg *o, const double *C, const double *lam, double *out)
+{
+    int np = o->np, nq = o->nq, ne = o->ne;
+    size_t n = (size_t)o->N * OM * np;
+    for (size_t t = 0; t < n; ++t) out[t] = 0.0;
+    /* Algorithm 3 backwards: every contribution to R_i is divided by det J_i */
+    double *lb = malloc(sizeof(double) * n);
+    if (!lb) return 1;
+    for (int64_t i = 0; i < o->N; ++i)
+        for (int t = 0; t < OM * np; ++t) lb[(size_t)i * OM * np + t] = lam[(size_t)i * OM * np + t] / o->detJ[i];
+
+    /* Algorithm 2 backwards, edge by edge */
+    for (int64_t s = 0; s < o->Ns; ++s) {
+        int64_t l = o->el[s], r = o->er[s];
+        const double *cl = C + (size_t)l * OM * np, *cr = C + (size_t)r * OM * np;
+        const double *bl = lb + (size_t)l * OM * np, *br = lb + (size_t)r * OM * np;
+        double *ol = out + (size_t)l * OM * np, *orr = out + (size_t)r * OM * np;
+        int L = o->eL[s], R = o->eR[s];
+        double len = o->elen[s];
+        for (int k = 0; k < ne; ++k) {
+            int kr = ne - 1 - k;
+            const double *phiL = o->phif + ((size_t)L * ne + k) * np;
+            const double *phiR = o->phif + ((size_t)R * ne + kr) * np;
+            double ul[OM], ur[OM];
+            for (int m = 0; m < OM; ++m) {
+                ul[m] = 0.0; ur[m] = 0.0;
+                for (int j = 0; j < np; ++j) { ul[m] += cl[m * np + j] * phiL[j]; ur[m] += cr[m * np + j] * phiR[j]; }
+            }
+            /* cotangent of F_n at this point */
+            double fb[OM];
+            for (int m = 0; m < OM; ++m) {
+                double a = 0.0;
+                for (int j = 0; j < np; ++j)
+                    a += -bl[m * np + j] * len * o->ew[k] * phiL[j] / 2.0 + br[m * np + j] * len * o->ew[k] * phiR[j] / 2.0;
+                fb[m] = a;
+            }
+            double Jl[OM][OM], Jr[OM][OM];
+            lax_friedrichs_jacobians(o->gamma, ul, ur, o->enx[s], o->eny[s], Jl, Jr);
+            for (int b = 0; b < OM; ++b) {
+                double gl = 0.0, gr = 0.0;
+                for (int a = 0; a < OM; ++a) { gl += Jl[a][b] * fb[a]; gr += Jr[a][b] * fb[a]; }
+                for (int j = 0; j < np; ++j) { ol[b * np + j] += gl * phiL[j]; orr[b * np + j] += gr * phiR[j]; }
+            }
+        }
+    }
+
+    /* Algorithm 1 backwards, element by element */
+    for (int64_t i = 0; i < o->N; ++i) {
+        const double *c = C + (size_t)i * OM * np;
+        const double *bi = lb + (size_t)i * OM * np;
+        double *oi = out + (size_t)i * OM * np;
+        const double *T = o->JT + 4 * i;
+        for (int k = 0; k < nq; ++k) {
+            double u[OM];
+            for (int m = 0; m < OM; ++m) {
+                u[m] = 0.0;
+                for (int j = 0; j < np; ++j) u[m] += c[m * np + j] * o->phi[k * np + j];
+            }
+            double a1[OM] = {0}, a2[OM] = {0};
+            for (int j = 0; j < np; ++j) {
+                double dr = o->phir[k * np + j], ds = o->phis[k * np + j];
+                double gx = T[0] * dr + T[1] * ds, gy = T[2] * dr + T[3] * ds;
+                for (int m = 0; m < OM; ++m) { a1[m] += bi[m * np + j] * gx; a2[m] += bi[m * np + j] * gy; }
+            }
+            double A1[OM][OM], A2[OM][OM];
+            flux_n_jacobian(o->gamma, u, 1.0, 0.0, A1);
+            flux_n_jacobian(o->gamma, u, 0.0, 1.0, A2);
+            for (int b = 0; b < OM; ++b) {
+                double ub = 0.0;
+                for (int a = 0; a < OM; ++a) ub += A1[a][b] * a1[a] + A2[a][b] * a2[a];
+                ub *= o->vw[k];
+                for (int j = 0; j < np; ++j) oi[b * np + j] += ub * o->phi[k * np + j];
+            }
+        }
+    }
+    free(lb);
+    return 0;
+}
+
+/* lam_n = (d C_{n+1} / d C_n)^T lam_np1 for one SSP-RK3 step from C_n */
+int or_ssp_rk3_vjp(oracle_dg *o, const double *Cn, double dt, const double *lam_np1, double *lam_n)
+{
+    size_t n = (size_t)o->N * OM * o->np;
+    double *u1 = malloc(sizeof(double) * n), *u2 = malloc(sizeof(double) * n);
+    double *L = malloc(sizeof(double) * n), *b2 = malloc(sizeof(double) * n);
+    double *b1 = malloc(sizeof(double) * n), *t = malloc(sizeof(double) * n);
+    if (!u1 || !u2 || !L || !b2 || !b1 || !t) { free(u1); free(u2); free(L); free(b2); free(b1); free(t); return 1; }
+    /* forward stages */
+    or_rhs(o, Cn, L);
+    for (size_t i = 0; i < n; ++i) u1[i] = Cn[i] + dt * L[i];
+    or_rhs(o, u1, L);
+    for (size_t i = 0; i < n; ++i) u2[i] = 0.75 * Cn[i] + 0.25 * (u1[i] + dt * L[i]);
+    /* C_{n+1} = 1/3 C_n + 2/3 (u2 + dt R(u2)) */
+    or_rhs_vjp(o, u2, lam_np1, t);
+    for (size_t i = 0; i < n; ++i) b2[i] = 2.0 / 3.0 * (lam_np1[i] + dt * t[i]);
+    /* u2 = 3/4 C_n + 1/4 (u1 + dt R(u1)) */
+    or_rhs_vjp(o, u1, b2, t);
+    for (size_t i = 0; i < n; ++i) b1[i] = 0.25 * (b2[i] + dt * t[i]);
+    /* u1 = C_n + dt R(C_n) */
+    or_rhs_vjp(o, Cn, b1, t);
+    for (size_t i = 0; i < n; ++i) lam_n[i] = lam_np1[i] / 3.0 + 0.75 * b2[i] + b1[i] + dt * t[i];
+    free(u1); free(u2); free(L); free(b2); free(b1); free(t);
     return 0;
 }

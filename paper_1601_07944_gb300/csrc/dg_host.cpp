@@ -24,6 +24,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <vector>
 
@@ -54,41 +55,44 @@ dg_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 // ---------------------------------------------------------------------------
-// Gauss rules by Golub-Welsch
+// Gauss rules by Golub-Welsch.  Host tables are computed in long double and
+// rounded once to double, so they are correct to the last bit or so.
 // ---------------------------------------------------------------------------
+using real = long double;
 
 // Eigen-decomposition of a small symmetric matrix A (n x n, row-major) by cyclic
 // Jacobi rotations.  On return A's diagonal holds the eigenvalues and the
 // columns of V the orthonormal eigenvectors.
-void sym_eigen(int n, std::vector<double> &A, std::vector<double> &V) {
-  V.assign(n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 64; ++sweep) {
-    double off = 0.0, diag = 0.0;
+void sym_eigen(int n, std::vector<real> &A, std::vector<real> &V) {
+  V.assign(n * n, 0.0L);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0L;
+  const real eps = std::numeric_limits<real>::epsilon();
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    real off = 0.0L, diag = 0.0L;
     for (int i = 0; i < n; ++i) {
       diag += A[i * n + i] * A[i * n + i];
       for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
     }
-    if (off <= 1e-36 * (diag + 1e-300)) break;
+    if (off <= eps * eps * 1e-4L * (diag + 1e-300L)) break;
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) {
-        double apq = A[p * n + q];
-        if (apq == 0.0) continue;
-        double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        real apq = A[p * n + q];
+        if (apq == 0.0L) continue;
+        real theta = (A[q * n + q] - A[p * n + p]) / (2.0L * apq);
+        real t = (theta >= 0 ? 1.0L : -1.0L) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0L));
+        real c = 1.0L / std::sqrt(t * t + 1.0L), s = t * c;
         for (int k = 0; k < n; ++k) {          // A <- A R  (columns p, q)
-          double akp = A[k * n + p], akq = A[k * n + q];
+          real akp = A[k * n + p], akq = A[k * n + q];
           A[k * n + p] = c * akp - s * akq;
           A[k * n + q] = s * akp + c * akq;
         }
         for (int k = 0; k < n; ++k) {          // A <- R^T A (rows p, q)
-          double apk = A[p * n + k], aqk = A[q * n + k];
+          real apk = A[p * n + k], aqk = A[q * n + k];
           A[p * n + k] = c * apk - s * aqk;
           A[q * n + k] = s * apk + c * aqk;
         }
         for (int k = 0; k < n; ++k) {          // V <- V R
-          double vkp = V[k * n + p], vkq = V[k * n + q];
+          real vkp = V[k * n + p], vkq = V[k * n + q];
           V[k * n + p] = c * vkp - s * vkq;
           V[k * n + q] = s * vkp + c * vkq;
         }
@@ -97,23 +101,23 @@ void sym_eigen(int n, std::vector<double> &A, std::vector<double> &V) {
 }
 
 // n-point Gauss rule for the weight (1-x)^a (1+x)^b on [-1, 1], ascending nodes.
-void gauss_rule(int n, double a, double b, std::vector<double> &x, std::vector<double> &w) {
-  std::vector<double> J(n * n, 0.0), V;
+void gauss_rule(int n, real a, real b, std::vector<real> &x, std::vector<real> &w) {
+  std::vector<real> J(n * n, 0.0L), V;
   for (int k = 0; k < n; ++k) {
-    double s = 2.0 * k + a + b;
-    J[k * n + k] = (k == 0) ? (b - a) / (a + b + 2.0) : (b * b - a * a) / (s * (s + 2.0));
+    real s = 2.0L * k + a + b;
+    J[k * n + k] = (k == 0) ? (b - a) / (a + b + 2.0L) : (b * b - a * a) / (s * (s + 2.0L));
     if (k >= 1) {
-      double kk = k;
-      double num = 4.0 * kk * (kk + a) * (kk + b) * (kk + a + b);
-      double den = s * s * (s + 1.0) * (s - 1.0);
-      double off = std::sqrt(num / den);
+      real kk = k;
+      real num = 4.0L * kk * (kk + a) * (kk + b) * (kk + a + b);
+      real den = s * s * (s + 1.0L) * (s - 1.0L);
+      real off = std::sqrt(num / den);
       J[(k - 1) * n + k] = off;
       J[k * n + (k - 1)] = off;
     }
   }
   sym_eigen(n, J, V);
-  double mu0 = std::pow(2.0, a + b + 1.0) * std::exp(std::lgamma(a + 1.0) + std::lgamma(b + 1.0) -
-                                                      std::lgamma(a + b + 2.0));
+  real mu0 = std::pow(2.0L, a + b + 1.0L) * std::exp(std::lgamma(a + 1.0L) + std::lgamma(b + 1.0L) -
+                                                       std::lgamma(a + b + 2.0L));
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
   std::sort(idx.begin(), idx.end(), [&](int i, int j) { return J[i * n + i] < J[j * n + j]; });
@@ -129,17 +133,17 @@ void gauss_rule(int n, double a, double b, std::vector<double> &x, std::vector<d
 // Collapsed rule on the reference triangle: Gauss-Legendre in alpha, Gauss-Jacobi
 // (1,0) in beta; r = (1+alpha)(1-beta)/4, s = (1+beta)/2, weight wa*wb/8.
 // Point index = ib*n + ia.
-void collapsed_rule(int n, std::vector<double> &r, std::vector<double> &s, std::vector<double> &w) {
-  std::vector<double> xa, wa, xb, wb;
-  gauss_rule(n, 0.0, 0.0, xa, wa);
-  gauss_rule(n, 1.0, 0.0, xb, wb);
+void collapsed_rule(int n, std::vector<real> &r, std::vector<real> &s, std::vector<real> &w) {
+  std::vector<real> xa, wa, xb, wb;
+  gauss_rule(n, 0.0L, 0.0L, xa, wa);
+  gauss_rule(n, 1.0L, 0.0L, xb, wb);
   r.resize(n * n); s.resize(n * n); w.resize(n * n);
   for (int ib = 0; ib < n; ++ib)
     for (int ia = 0; ia < n; ++ia) {
       int k = ib * n + ia;
-      r[k] = 0.25 * (1.0 + xa[ia]) * (1.0 - xb[ib]);
-      s[k] = 0.5 * (1.0 + xb[ib]);
-      w[k] = 0.125 * wa[ia] * wb[ib];
+      r[k] = 0.25L * (1.0L + xa[ia]) * (1.0L - xb[ib]);
+      s[k] = 0.5L * (1.0L + xb[ib]);
+      w[k] = 0.125L * wa[ia] * wb[ib];
     }
 }
 
@@ -147,27 +151,27 @@ void collapsed_rule(int n, std::vector<double> &r, std::vector<double> &s, std::
 // Dubiner basis from Jacobi recurrences
 // ---------------------------------------------------------------------------
 
-double jacobi_p(int n, double a, double b, double x) {
-  if (n == 0) return 1.0;
-  double pm = 1.0, pc = 0.5 * (a - b + (a + b + 2.0) * x);
+real jacobi_p(int n, real a, real b, real x) {
+  if (n == 0) return 1.0L;
+  real pm = 1.0L, pc = 0.5L * (a - b + (a + b + 2.0L) * x);
   for (int k = 1; k < n; ++k) {
     // P_{k+1} from P_k, P_{k-1}
-    double kk = k;
-    double s = 2.0 * kk + a + b;
-    double A = 2.0 * (kk + 1.0) * (kk + a + b + 1.0) * s;
-    double B = (s + 1.0) * (a * a - b * b);
-    double C = s * (s + 1.0) * (s + 2.0);
-    double D = 2.0 * (kk + a) * (kk + b) * (s + 2.0);
-    double pn = ((B + C * x) * pc - D * pm) / A;
+    real kk = k;
+    real s = 2.0L * kk + a + b;
+    real A = 2.0L * (kk + 1.0L) * (kk + a + b + 1.0L) * s;
+    real B = (s + 1.0L) * (a * a - b * b);
+    real C = s * (s + 1.0L) * (s + 2.0L);
+    real D = 2.0L * (kk + a) * (kk + b) * (s + 2.0L);
+    real pn = ((B + C * x) * pc - D * pm) / A;
     pm = pc;
     pc = pn;
   }
   return pc;
 }
 
-double jacobi_dp(int n, double a, double b, double x) {
-  if (n == 0) return 0.0;
-  return 0.5 * (n + a + b + 1.0) * jacobi_p(n - 1, a + 1.0, b + 1.0, x);
+real jacobi_dp(int n, real a, real b, real x) {
+  if (n == 0) return 0.0L;
+  return 0.5L * (n + a + b + 1.0L) * jacobi_p(n - 1, a + 1.0L, b + 1.0L, x);
 }
 
 void mode_ab(int j, int *a, int *b) {
@@ -177,32 +181,41 @@ void mode_ab(int j, int *a, int *b) {
       if (k == j) { *a = d - bb; *b = bb; return; }
 }
 
-void dubiner(int p, double r, double s, double *phi, double *dr, double *ds) {
+// phi_j and its reference gradient at (r, s) for every mode j of degree <= p
+void dubiner(int p, real r, real s, double *phi, double *dr, double *ds) {
   int np = (p + 1) * (p + 2) / 2;
-  double oms = 1.0 - s;
-  double al = 2.0 * r / oms - 1.0, be = 2.0 * s - 1.0;
+  real oms = 1.0L - s;
+  real al = 2.0L * r / oms - 1.0L, be = 2.0L * s - 1.0L;
   for (int j = 0; j < np; ++j) {
     int a, b;
     mode_ab(j, &a, &b);
-    double N = std::sqrt(2.0 * (2 * a + 1) * (a + b + 1));
-    double Pa = jacobi_p(a, 0, 0, al), dPa = jacobi_dp(a, 0, 0, al);
-    double Pb = jacobi_p(b, 2 * a + 1, 0, be), dPb = jacobi_dp(b, 2 * a + 1, 0, be);
-    double oa = std::pow(oms, a);
-    double oa1 = a > 0 ? std::pow(oms, a - 1) : 0.0;
-    if (phi) phi[j] = N * Pa * oa * Pb;
+    real N = std::sqrt(2.0L * (2 * a + 1) * (a + b + 1));
+    real Pa = jacobi_p(a, 0, 0, al), dPa = jacobi_dp(a, 0, 0, al);
+    real Pb = jacobi_p(b, 2 * a + 1, 0, be), dPb = jacobi_dp(b, 2 * a + 1, 0, be);
+    real oa = std::pow(oms, (real)a);
+    real oa1 = a > 0 ? std::pow(oms, (real)(a - 1)) : 0.0L;
+    if (phi) phi[j] = (double)(N * Pa * oa * Pb);
     // d/dr: d alpha/dr = 2/(1-s)
-    if (dr) dr[j] = N * 2.0 * dPa * oa1 * Pb;
+    if (dr) dr[j] = (double)(N * 2.0L * dPa * oa1 * Pb);
     // d/ds: d alpha/ds = (1+alpha)/(1-s), d beta/ds = 2
-    if (ds) ds[j] = N * (oa1 * (dPa * (1.0 + al) - a * Pa) * Pb + 2.0 * Pa * oa * dPb);
+    if (ds) ds[j] = (double)(N * (oa1 * (dPa * (1.0L + al) - a * Pa) * Pb + 2.0L * Pa * oa * dPb));
   }
 }
 
-void face_point(int q, double xi, double *r, double *s) {
+// Reference point of edge coordinate xi on local face q (running from reference
+// vertex q to vertex q+1).  The stored points are doubles: the node is rounded
+// to double first and the point is formed in double arithmetic, and every basis
+// table is evaluated (in extended precision) at exactly these double points.
+void face_point(int q, real xi_, real *r, real *s) {
   static const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+  const double xi = (double)xi_;
   int q1 = (q + 1) % 3;
-  *r = 0.5 * (1.0 - xi) * V[q][0] + 0.5 * (1.0 + xi) * V[q1][0];
-  *s = 0.5 * (1.0 - xi) * V[q][1] + 0.5 * (1.0 + xi) * V[q1][1];
+  *r = (real)(0.5 * (1.0 - xi) * V[q][0] + 0.5 * (1.0 + xi) * V[q1][0]);
+  *s = (real)(0.5 * (1.0 - xi) * V[q][1] + 0.5 * (1.0 + xi) * V[q1][1]);
 }
+
+// a volume point as stored (rounded to double)
+inline real stored(real v) { return (real)(double)v; }
 
 bool supported(int p, int ne) {
   if (p < 1 || p > dg::PMAX) return false;
@@ -258,24 +271,24 @@ extern "C" dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s,
   if (ne == 0) ne = p + 1;
   if (p < 0 || p > 8 || ne < 1 || ne > 16) return fail(DG_EINVAL, "dg_host_tables: p=%d ne=%d", p, ne);
   int np = (p + 1) * (p + 2) / 2, nd = p + 1, nq = nd * nd;
-  std::vector<double> r, s, w, ex, ew;
+  std::vector<real> r, s, w, ex, ew;
   collapsed_rule(nd, r, s, w);
-  gauss_rule(ne, 0.0, 0.0, ex, ew);
+  gauss_rule(ne, 0.0L, 0.0L, ex, ew);
   for (int k = 0; k < nq; ++k) {
-    if (vol_r) vol_r[k] = r[k];
-    if (vol_s) vol_s[k] = s[k];
-    if (vol_w) vol_w[k] = w[k];
-    dubiner(p, r[k], s[k], phi ? phi + k * np : nullptr, dphi_r ? dphi_r + k * np : nullptr,
-            dphi_s ? dphi_s + k * np : nullptr);
+    if (vol_r) vol_r[k] = (double)r[k];
+    if (vol_s) vol_s[k] = (double)s[k];
+    if (vol_w) vol_w[k] = (double)w[k];
+    dubiner(p, stored(r[k]), stored(s[k]), phi ? phi + k * np : nullptr,
+            dphi_r ? dphi_r + k * np : nullptr, dphi_s ? dphi_s + k * np : nullptr);
   }
   for (int k = 0; k < ne; ++k) {
-    if (edge_x) edge_x[k] = ex[k];
-    if (edge_w) edge_w[k] = ew[k];
+    if (edge_x) edge_x[k] = (double)ex[k];
+    if (edge_w) edge_w[k] = (double)ew[k];
   }
   if (phi_face)
     for (int q = 0; q < 3; ++q)
       for (int k = 0; k < ne; ++k) {
-        double rr, ss;
+        real rr, ss;
         face_point(q, ex[k], &rr, &ss);
         dubiner(p, rr, ss, phi_face + (q * ne + k) * np, nullptr, nullptr);
       }
@@ -343,14 +356,14 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
 
   // --- tables ----------------------------------------------------------------
   const int np = (p + 1) * (p + 2) / 2, nd = p + 1, nq = nd * nd, nf = 3 * ne;
-  std::vector<double> r, s, w, ex, ew;
+  std::vector<real> r, s, w, ex, ew;
   collapsed_rule(nd, r, s, w);
-  gauss_rule(ne, 0.0, 0.0, ex, ew);
+  gauss_rule(ne, 0.0L, 0.0L, ex, ew);
   std::vector<double> phi(nq * np), dr(nq * np), ds(nq * np), phif(nf * np);
-  for (int k = 0; k < nq; ++k) dubiner(p, r[k], s[k], &phi[k * np], &dr[k * np], &ds[k * np]);
+  for (int k = 0; k < nq; ++k) dubiner(p, stored(r[k]), stored(s[k]), &phi[k * np], &dr[k * np], &ds[k * np]);
   for (int q = 0; q < 3; ++q)
     for (int k = 0; k < ne; ++k) {
-      double rr, ss;
+      real rr, ss;
       face_point(q, ex[k], &rr, &ss);
       dubiner(p, rr, ss, &phif[(q * ne + k) * np], nullptr, nullptr);
     }
@@ -362,18 +375,18 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   for (int k = 0; k < nq; ++k)
     for (int j = 0; j < np; ++j) {
       tb[oBvT + j * nq + k] = phi[k * np + j];
-      tb[oDr + k * np + j] = w[k] * dr[k * np + j];
-      tb[oDs + k * np + j] = w[k] * ds[k * np + j];
-      tb[oPw + k * np + j] = w[k] * phi[k * np + j];
+      tb[oDr + k * np + j] = (double)(w[k] * (real)dr[k * np + j]);
+      tb[oDs + k * np + j] = (double)(w[k] * (real)ds[k * np + j]);
+      tb[oPw + k * np + j] = (double)(w[k] * (real)phi[k * np + j]);
     }
   for (int q = 0; q < 3; ++q)
     for (int k = 0; k < ne; ++k)
       for (int j = 0; j < np; ++j) {
         int qk = q * ne + k;
-        tb[oLf + qk * np + j] = ew[k] * phif[qk * np + j];
+        tb[oLf + qk * np + j] = (double)(ew[k] * (real)phif[qk * np + j]);
         tb[oBfT + j * nf + qk] = phif[qk * np + j];
       }
-  for (int k = 0; k < nq; ++k) { tb[oVr + k] = r[k]; tb[oVs + k] = s[k]; }
+  for (int k = 0; k < nq; ++k) { tb[oVr + k] = (double)r[k]; tb[oVs + k] = (double)s[k]; }
 
   // --- device upload ---------------------------------------------------------
   dg_mesh *m = new (std::nothrow) dg_mesh();
