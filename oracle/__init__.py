@@ -65,6 +65,7 @@ def _load():
             "or_lax_friedrichs": (I, [D, P, P, D, D, P]),
             "or_euler_flux": (I, [D, P, P, P]),
             "or_rhs": (I, [P, P, P]),
+            "or_last_volume_term": (I, [P, P]),
             "or_ssp_rk3": (I, [P, P, D, I]),
             "or_totals": (I, [P, P, P]),
             "or_lax_friedrichs_jacobians": (I, [D, P, P, D, D, P, P]),
@@ -269,6 +270,15 @@ class OracleDG:
         R = np.zeros(self.coef_shape())
         _chk(_lib.or_rhs(self._h, _ptr(c), _ptr(R)))
         return R
+
+    def rhs_and_volume(self, c):
+        """(R, V / det J): the RHS and its volume term, whose size bounds the
+        rounding error of R (R is the small difference of the volume and surface
+        terms, each of which grows like 1/h)."""
+        R = self.rhs(c)
+        V = np.zeros(self.coef_shape())
+        _chk(_lib.or_last_volume_term(self._h, _ptr(V)))
+        return R, V
 
     def ssp_rk3(self, c, dt: float, nsteps: int):
         out = np.array(c, dtype=np.float64, copy=True, order="C")

@@ -732,6 +732,17 @@ int or_rhs(oracle_dg *o, const double *C, double *R)
     return 0;
 }
 
+/* The volume part (rhs_volume / det J) of the last or_rhs call: the size of the
+ * terms whose difference is the RHS, which sets the RHS's rounding error. */
+int or_last_volume_term(const oracle_dg *o, double *out)
+{
+    int np = o->np;
+    for (int64_t i = 0; i < o->N; ++i)
+        for (int t = 0; t < OM * np; ++t)
+            out[(size_t)i * OM * np + t] = o->rhs_volume[(size_t)i * OM * np + t] / o->detJ[i];
+    return 0;
+}
+
 /* Three-stage SSP Runge-Kutta (Shu-Osher form), nsteps steps in place:
  *   u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1)); u <- 1/3 u + 2/3 (u2 + dt L(u2)) */
 int or_ssp_rk3(oracle_dg *o, double *C, double dt, int nsteps)

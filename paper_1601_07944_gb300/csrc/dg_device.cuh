@@ -1,0 +1,131 @@
+/*
+ * dg_device.cuh -- device helpers shared by the forward and adjoint kernels:
+ * compile-time sizes of a discretisation, the Euler flux in reference form, the
+ * local Lax-Friedrichs flux and the transposed Jacobian products used by the
+ * discrete adjoint.
+ */
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+template <int P, int NE>
+struct Cfg {
+  static constexpr int NP = (P + 1) * (P + 2) / 2;
+  static constexpr int ND = P + 1;
+  static constexpr int NQ = ND * ND;
+  static constexpr int NF = 3 * NE;
+  static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);   // elements per tile
+  static constexpr int TAB = NP * NQ * 3 + NF * NP * 2;          // table doubles
+  static constexpr int TILE = EB * (M * NP * 2 + NQ * 8 + NF * M);
+  static constexpr int SMEM = (TAB + TILE) * 8;
+};
+
+constexpr int kThreads = 256;
+
+// Euler flux (Eq. euler) contracted with J^tau: the reference flux components
+// G_r, G_s of the four conserved variables at one point.
+__device__ __forceinline__ void ref_flux(const double U[M], const double *jt, double gamma,
+                                         double Gr[M], double Gs[M]) {
+  const double rho = U[0], inv = 1.0 / rho;
+  const double u = U[1] * inv, v = U[2] * inv;
+  const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+  double F1[M], F2[M];
+  F1[0] = U[1];          F2[0] = U[2];
+  F1[1] = U[1] * u + p;  F2[1] = U[1] * v;
+  F1[2] = U[2] * u;      F2[2] = U[2] * v + p;
+  F1[3] = (U[3] + p) * u; F2[3] = (U[3] + p) * v;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    Gr[m] = jt[0] * F1[m] + jt[1] * F2[m];
+    Gs[m] = jt[2] * F1[m] + jt[3] * F2[m];
+  }
+}
+
+// Local Lax-Friedrichs flux F_hat(Ul, Ur, n).  Written so that swapping the two
+// sides and negating n negates the result bit for bit.
+__device__ __forceinline__ void lax_friedrichs(const double ul[M], const double ur[M], double nx,
+                                               double ny, double gamma, double out[M]) {
+  const double il = 1.0 / ul[0], ir = 1.0 / ur[0];
+  const double uL = ul[1] * il, vL = ul[2] * il, uR = ur[1] * ir, vR = ur[2] * ir;
+  const double pL = (gamma - 1.0) * (ul[3] - 0.5 * (ul[1] * uL + ul[2] * vL));
+  const double pR = (gamma - 1.0) * (ur[3] - 0.5 * (ur[1] * uR + ur[2] * vR));
+  const double vnL = uL * nx + vL * ny, vnR = uR * nx + vR * ny;
+  const double sL = fabs(vnL) + sqrt(gamma * pL * il);
+  const double sR = fabs(vnR) + sqrt(gamma * pR * ir);
+  const double a = fmax(sL, sR);
+  double fL[M], fR[M];
+  fL[0] = ul[0] * vnL;              fR[0] = ur[0] * vnR;
+  fL[1] = ul[1] * vnL + pL * nx;    fR[1] = ur[1] * vnR + pR * nx;
+  fL[2] = ul[2] * vnL + pL * ny;    fR[2] = ur[2] * vnR + pR * ny;
+  fL[3] = (ul[3] + pL) * vnL;       fR[3] = (ur[3] + pR) * vnR;
+#pragma unroll
+  for (int m = 0; m < M; ++m) out[m] = 0.5 * (fL[m] + fR[m]) - 0.5 * a * (ur[m] - ul[m]);
+}
+
+
+// out = (d(F(U).n)/dU)^T b for the Euler flux F.n = (rho vn, mx vn + p nx,
+// my vn + p ny, (E+p) vn), using d vn/dU = (-vn, nx, ny, 0)/rho and
+// dp/dU = (gamma-1) (|v|^2/2, -u, -v, 1).
+__device__ __forceinline__ void flux_jac_t(const double U[M], double nx, double ny, double gamma,
+                                           const double b[M], double out[M]) {
+  const double inv = 1.0 / U[0];
+  const double u = U[1] * inv, v = U[2] * inv;
+  const double q2 = u * u + v * v;
+  const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * q2);
+  const double vn = u * nx + v * ny;
+  const double sig = (b[1] * U[1] + b[2] * U[2] + b[3] * (U[3] + p)) * inv;
+  const double tau = (gamma - 1.0) * (b[1] * nx + b[2] * ny + b[3] * vn);
+  out[0] = -sig * vn + 0.5 * tau * q2;
+  out[1] = b[0] * nx + b[1] * vn + sig * nx - tau * u;
+  out[2] = b[0] * ny + b[2] * vn + sig * ny - tau * v;
+  out[3] = b[3] * vn + tau;
+}
+
+// Wave speed s = |v.n| + c and its gradient (d|x|/dx = sign(x), sign(0) = 0).
+__device__ __forceinline__ double wave_speed_grad(const double U[M], double nx, double ny,
+                                                  double gamma, double ds[M]) {
+  const double inv = 1.0 / U[0];
+  const double u = U[1] * inv, v = U[2] * inv;
+  const double q2 = u * u + v * v;
+  const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * q2);
+  const double vn = u * nx + v * ny;
+  const double c = sqrt(gamma * p * inv);
+  const double sg = vn > 0.0 ? 1.0 : (vn < 0.0 ? -1.0 : 0.0);
+  const double k = gamma / (2.0 * c) * inv;          // dc = k (dp - p/rho drho)
+  const double g1 = gamma - 1.0;
+  ds[0] = sg * (-vn * inv) + k * (g1 * 0.5 * q2 - p * inv);
+  ds[1] = sg * (nx * inv) + k * (-g1 * u);
+  ds[2] = sg * (ny * inv) + k * (-g1 * v);
+  ds[3] = k * g1;
+  return fabs(vn) + c;
+}
+
+// Transposed Lax-Friedrichs Jacobians applied to a cotangent fb:
+//   gl = (dF_hat/dUl)^T fb,  gr = (dF_hat/dUr)^T fb,
+// dF_hat/dUl = A(Ul)/2 + alpha/2 I - (Ur-Ul)/2 (x) d alpha/dUl, and alike for Ur;
+// d alpha follows the larger wave speed, the left one at a tie.
+__device__ __forceinline__ void lax_friedrichs_vjp(const double ul[M], const double ur[M], double nx,
+                                                   double ny, double gamma, const double fb[M],
+                                                   double gl[M], double gr[M]) {
+  double dsl[M], dsr[M], jl[M], jr[M];
+  const double sl = wave_speed_grad(ul, nx, ny, gamma, dsl);
+  const double sr = wave_speed_grad(ur, nx, ny, gamma, dsr);
+  const bool left = sl >= sr;
+  const double a = left ? sl : sr;
+  double jump = 0.0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) jump += (ur[m] - ul[m]) * fb[m];
+  flux_jac_t(ul, nx, ny, gamma, fb, jl);
+  flux_jac_t(ur, nx, ny, gamma, fb, jr);
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    gl[m] = 0.5 * jl[m] + 0.5 * a * fb[m] - (left ? 0.5 * jump * dsl[m] : 0.0);
+    gr[m] = 0.5 * jr[m] - 0.5 * a * fb[m] - (left ? 0.0 : 0.5 * jump * dsr[m]);
+  }
+}
+
+}  // namespace dg

@@ -565,9 +565,53 @@ extern "C" dg_status dg_conserved_totals(dg_mesh *m, const double *c, double out
 
 extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, const double *lam_np1,
                                      double *lam_n, void *stream) {
-  (void)dt; (void)stream;
+  using namespace dg;
   if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "dg_adjoint_step: null argument");
-  return fail(DG_ENOTIMPL, "dg_adjoint_step: not built yet");
+  if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
+  if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
+  const size_t S = (size_t)m->N * M * m->np;           // one state
+  const size_t TR = (size_t)m->N * 3 * m->ne * M;       // one trace block
+  const size_t need = 5 * S + 2 * TR;
+  if (m->adj_doubles < need) {
+    cudaFree(m->adj_buf);
+    m->adj_buf = nullptr;
+    m->adj_doubles = 0;
+    cudaError_t e = cudaMalloc(&m->adj_buf, sizeof(double) * need);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(DG_ENOMEM, "dg_adjoint_step: cudaMalloc"); }
+    m->adj_doubles = need;
+  }
+  double *u1 = m->adj_buf, *u2 = u1 + S, *b1 = u2 + S, *b2 = b1 + S, *uvol = b2 + S;
+  double *G = uvol + S, *TB = G + TR;
+  // forward stages from c_n: u1 = c_n + dt R(c_n), u2 = 3/4 c_n + 1/4 (u1 + dt R(u1))
+  DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces(m, c_n, m->trace, stream); }),
+          "adjoint traces");
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
+          "adjoint stage 1 flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+            return launch_element(m, c_n, nullptr, u1, m->trace, m->fhat, dt, 0.0, 1.0, 1, stream);
+          }), "adjoint stage 1");
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
+          "adjoint stage 2 flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+            return launch_element(m, u1, c_n, u2, nullptr, m->fhat, dt, 0.75, 0.25, 1, stream);
+          }), "adjoint stage 2");
+  // reverse sweep of c_{n+1} = 1/3 c_n + 2/3 (u2 + dt R(u2))
+  auto vjp = [&](const double *u, const double *lam, const double *X, const double *Y, const double *Z,
+                 double x0, double x1, double x2, double s, double *out, const char *what) -> dg_status {
+    DG_CUDA((cudaError_t)timed(m, DG_K_ADJOINT, stream, [&] {
+              return launch_rhs_vjp(m, u, lam, uvol, G, m->trace, TB, X, Y, Z, x0, x1, x2, s, out, stream);
+            }), what);
+    return DG_OK;
+  };
+  dg_status st;
+  // b2 = 2/3 (lam + dt R'(u2)^T lam)
+  if ((st = vjp(u2, lam_np1, lam_np1, nullptr, nullptr, 2.0 / 3.0, 0, 0, 2.0 / 3.0 * dt, b2, "adjoint u2")) != DG_OK)
+    return st;
+  // b1 = 1/4 (b2 + dt R'(u1)^T b2)
+  if ((st = vjp(u1, b2, b2, nullptr, nullptr, 0.25, 0, 0, 0.25 * dt, b1, "adjoint u1")) != DG_OK) return st;
+  // lam_n = 1/3 lam + 3/4 b2 + b1 + dt R'(c_n)^T b1
+  if ((st = vjp(c_n, b1, lam_np1, b2, b1, 1.0 / 3.0, 0.75, 1.0, dt, lam_n, "adjoint c_n")) != DG_OK) return st;
+  return DG_OK;
 }
 
 extern "C" dg_status dg_set_timing(dg_mesh *m, int enable) {

@@ -26,64 +26,11 @@
 
 #include <cstdint>
 
+#include "dg_device.cuh"
 #include "dg_internal.h"
 
 namespace dg {
 namespace {
-
-template <int P, int NE>
-struct Cfg {
-  static constexpr int NP = (P + 1) * (P + 2) / 2;
-  static constexpr int ND = P + 1;
-  static constexpr int NQ = ND * ND;
-  static constexpr int NF = 3 * NE;
-  static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);   // elements per tile
-  static constexpr int TAB = NP * NQ * 3 + NF * NP * 2;          // table doubles
-  static constexpr int TILE = EB * (M * NP * 2 + NQ * 8 + NF * M);
-  static constexpr int SMEM = (TAB + TILE) * 8;
-};
-
-constexpr int kThreads = 256;
-
-// Euler flux (Eq. euler) contracted with J^tau: the reference flux components
-// G_r, G_s of the four conserved variables at one point.
-__device__ __forceinline__ void ref_flux(const double U[M], const double *jt, double gamma,
-                                         double Gr[M], double Gs[M]) {
-  const double rho = U[0], inv = 1.0 / rho;
-  const double u = U[1] * inv, v = U[2] * inv;
-  const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
-  double F1[M], F2[M];
-  F1[0] = U[1];          F2[0] = U[2];
-  F1[1] = U[1] * u + p;  F2[1] = U[1] * v;
-  F1[2] = U[2] * u;      F2[2] = U[2] * v + p;
-  F1[3] = (U[3] + p) * u; F2[3] = (U[3] + p) * v;
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    Gr[m] = jt[0] * F1[m] + jt[1] * F2[m];
-    Gs[m] = jt[2] * F1[m] + jt[3] * F2[m];
-  }
-}
-
-// Local Lax-Friedrichs flux F_hat(Ul, Ur, n).  Written so that swapping the two
-// sides and negating n negates the result bit for bit.
-__device__ __forceinline__ void lax_friedrichs(const double ul[M], const double ur[M], double nx,
-                                               double ny, double gamma, double out[M]) {
-  const double il = 1.0 / ul[0], ir = 1.0 / ur[0];
-  const double uL = ul[1] * il, vL = ul[2] * il, uR = ur[1] * ir, vR = ur[2] * ir;
-  const double pL = (gamma - 1.0) * (ul[3] - 0.5 * (ul[1] * uL + ul[2] * vL));
-  const double pR = (gamma - 1.0) * (ur[3] - 0.5 * (ur[1] * uR + ur[2] * vR));
-  const double vnL = uL * nx + vL * ny, vnR = uR * nx + vR * ny;
-  const double sL = fabs(vnL) + sqrt(gamma * pL * il);
-  const double sR = fabs(vnR) + sqrt(gamma * pR * ir);
-  const double a = fmax(sL, sR);
-  double fL[M], fR[M];
-  fL[0] = ul[0] * vnL;              fR[0] = ur[0] * vnR;
-  fL[1] = ul[1] * vnL + pL * nx;    fR[1] = ur[1] * vnR + pR * nx;
-  fL[2] = ul[2] * vnL + pL * ny;    fR[2] = ur[2] * vnR + pR * ny;
-  fL[3] = (ul[3] + pL) * vnL;       fR[3] = (ur[3] + pR) * vnR;
-#pragma unroll
-  for (int m = 0; m < M; ++m) out[m] = 0.5 * (fL[m] + fR[m]) - 0.5 * a * (ur[m] - ul[m]);
-}
 
 // ---------------------------------------------------------------------------
 // edge traces of a coefficient array: trace[e][q*NE+k][m] = sum_j c[e][m][j] phi_j(r_{q,k})

@@ -151,6 +151,7 @@ class Mesh:
         h = ctypes.c_void_p()
         _check(lib.dg_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h
+        self._xy = xy
         info = _Info()
         _check(lib.dg_mesh_info(h, ctypes.byref(info)))
         self.N, self.n_face, self.p = info.n_elem, info.n_face, info.p
@@ -178,6 +179,14 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+    def det_j(self, device="cuda"):
+        """det J of every element (twice its area), float64 tensor [N]."""
+        import torch
+        xy = self._xy
+        a = xy[:, 1] - xy[:, 0]
+        b = xy[:, 2] - xy[:, 0]
+        return torch.from_numpy(a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0]).to(device)
 
     # -- diagnostics --------------------------------------------------------
     def set_timing(self, enable: bool):

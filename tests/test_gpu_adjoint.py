@@ -1,0 +1,118 @@
+"""GPU discrete adjoint against the oracle's reverse sweep and central
+differences, through the C ABI (dg_adjoint_step) and the checkpointed
+torch.autograd wrapper."""
+import numpy as np
+import pytest
+
+from paper_1601_07944_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dgmod():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1601_07944_gb300 import _build, dg
+    _build.build()
+    dg.load()
+    return dg
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [6, 16])
+@pytest.mark.parametrize("p,ne", [(1, 0), (2, 0), (3, 0), (3, 3), (4, 0), (5, 0)])
+def test_adjoint_step_parity(dgmod, oracle_mod, p, ne, n):
+    mesh = I.periodic_mesh(n)
+    m = dgmod.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p, n_edge_pts=ne)
+    rng = np.random.default_rng(n + 10 * p)
+    c = o.project_ic(I.perturbed_vortex)
+    c = c + 0.002 * rng.standard_normal(c.shape)
+    lam = rng.standard_normal(c.shape)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    ref = o.ssp_rk3_vjp(c, dt, lam)
+    got = _host(m.adjoint_step(_dev(c), dt, _dev(lam)))
+    assert rel_l2(got, ref) < 1e-12
+
+
+def _loss_setup(dgmod, oracle_mod, n, p):
+    mesh = I.periodic_mesh(n)
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    c0 = m.project_function(I.perturbed_vortex)
+    tgt0 = m.project_function(lambda x, y: I.perturbed_vortex(x, y, seed=I.SEED_TARGET))
+    return mesh, m, dt, c0, tgt0
+
+
+def test_autograd_matches_oracle_reverse_sweep(dgmod, oracle_mod):
+    """40 steps, checkpoints every 8: the gradient of the density misfit with
+    respect to c0 equals the oracle's step-by-step reverse sweep."""
+    import torch
+    from paper_1601_07944_gb300 import autograd as AG
+    n, p, steps, every = 16, 2, 40, 8
+    mesh, m, dt, c0, tgt0 = _loss_setup(dgmod, oracle_mod, n, p)
+    target = tgt0.clone()
+    m.rk_step(target, dt, steps)
+    dJ = m.det_j()
+    x = c0.clone().requires_grad_(True)
+    loss = AG.density_misfit(dJ, AG.solve(m, x, dt, steps, every), target)
+    loss.backward()
+    g = _host(x.grad)
+    # oracle reverse sweep from the same c0 and target
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    cn = _host(c0)
+    states = [cn]
+    for _ in range(steps):
+        states.append(o.ssp_rk3(states[-1], dt, 1))
+    lam = np.zeros_like(cn)
+    dj = o.det_j()
+    lam[:, 0, :] = dj[:, None] * (states[-1][:, 0, :] - _host(target)[:, 0, :])
+    for s in range(steps - 1, -1, -1):
+        lam = o.ssp_rk3_vjp(states[s], dt, lam)
+    assert rel_l2(g, lam) < 1e-11
+
+
+@pytest.mark.parametrize("n,p,steps,every,nfd", [(16, 2, 40, 8, 16), (256, 2, 400, 20, 32)])
+def test_autograd_central_differences(dgmod, oracle_mod, n, p, steps, every, nfd):
+    """Gradient of the density misfit against central differences (h = 1e-6) on
+    random coefficients; the 256^2, p=2, 400-step, every-20 case is the full
+    differentiation workload."""
+    import torch
+    from paper_1601_07944_gb300 import autograd as AG
+    mesh, m, dt, c0, tgt0 = _loss_setup(dgmod, oracle_mod, n, p)
+    target = tgt0.clone()
+    m.rk_step(target, dt, steps)
+    dJ = m.det_j()
+
+    def loss_of(c):
+        cT = c.clone()
+        m.rk_step(cT, dt, steps)
+        return float(AG.density_misfit(dJ, cT, target).item())
+
+    x = c0.clone().requires_grad_(True)
+    AG.density_misfit(dJ, AG.solve(m, x, dt, steps, every), target).backward()
+    g = _host(x.grad)
+    gmax = np.abs(g).max()
+    rng = np.random.default_rng(I.SEED_FD)
+    h = 1e-6
+    for flat in rng.choice(c0.numel(), nfd, replace=False):
+        idx = np.unravel_index(flat, tuple(c0.shape))
+        cp = c0.clone(); cp[idx] += h
+        cm = c0.clone(); cm[idx] -= h
+        g_fd = (loss_of(cp) - loss_of(cm)) / (2 * h)
+        assert abs(g_fd - g[idx]) <= 1e-6 * max(abs(g[idx]), 1e-3 * gmax), (idx, g_fd, g[idx])

@@ -135,12 +135,22 @@ def test_host_entry_matches_device_entry(dgmod):
 
 
 def test_free_stream_full_size(dgmod):
-    """A uniform state is an exact steady solution on the full 1024^2 p=5 mesh."""
+    """A uniform state is an exact steady solution on the full 1024^2 p=5 mesh:
+    the RHS vanishes up to the rounding of its two terms, each of size about
+    |F| |grad phi| / h (eps times that is ~4e-12 here)."""
     mesh = I.periodic_mesh(1024)
-    m = dgmod.Mesh.from_mesh(mesh, 5)
+    p = 5
+    m = dgmod.Mesh.from_mesh(mesh, p)
     c = m.project_function(lambda x, y: I.uniform_state(x, y))
     r = _host(m.rhs(c))
-    assert np.abs(r).max() < 1e-12
+    U = I.uniform_state(np.zeros(1), np.zeros(1))[0]
+    rho, u, v = U[0], U[1] / U[0], U[2] / U[0]
+    pr = 0.4 * (U[3] - 0.5 * rho * (u * u + v * v))
+    fmax = max(abs(U[3] + pr) * max(abs(u), abs(v)), abs(U[1] * u + pr), abs(U[2] * v + pr))
+    T = dgmod.host_tables(p)
+    gmax = max(np.abs(T["dphi_r"]).max(), np.abs(T["dphi_s"]).max())
+    scale = np.finfo(float).eps * fmax * gmax / mesh.h
+    assert np.abs(r).max() < 16 * scale
 
 
 @pytest.mark.parametrize("n,p", [(256, 3), (512, 4)])
@@ -152,17 +162,31 @@ def test_full_size_parity(dgmod, oracle_mod, n, p):
     m = dgmod.Mesh.from_mesh(mesh, p)
     o = oracle_mod.OracleDG.from_mesh(mesh, p)
     c = o.project_ic(ic)
-    assert rel_l2(_host(m.rhs(_dev(c))), o.rhs(c)) < TOL
+    # R is the difference of two terms that each grow like 1/h; its rounding error
+    # is eps times their size, which at these h exceeds 1e-12 |R|
+    ref, vol = o.rhs_and_volume(c)
+    got = _host(m.rhs(_dev(c)))
+    eps = np.finfo(float).eps
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref) + 16 * eps * np.linalg.norm(vol)
     dt = I.fixed_dt(mesh, ic, p)
     cd = _dev(c)
     m.rk_step(cd, dt, 1)
     assert rel_l2(_host(cd), o.ssp_rk3(c, dt, 1)) < TOL
 
 
-def test_unbuilt_modes_report_not_implemented(dgmod):
+def test_argument_errors(dgmod):
+    import torch
     mesh = I.periodic_mesh(4)
     m = dgmod.Mesh.from_mesh(mesh, 1)
     c = m.project_function(I.vortex)
     with pytest.raises(dgmod.DGError) as ei:
-        m.adjoint_step(c, 0.01, c.clone())
-    assert ei.value.status == 7
+        m.rhs(c, out=c)                       # aliasing input and output
+    assert ei.value.status == 1
+    with pytest.raises(dgmod.DGError) as ei:
+        m.adjoint_step(c, 0.01, c, out=c)
+    assert ei.value.status == 1
+    with pytest.raises(dgmod.DGError) as ei:
+        m.rk_step(c, float("nan"), 1)
+    assert ei.value.status == 1
+    with pytest.raises(ValueError):
+        m.rhs(torch.zeros((3, 4, 3), dtype=torch.float64, device="cuda"))
