@@ -105,14 +105,27 @@ def test_autograd_central_differences(dgmod, oracle_mod, n, p, steps, every, nfd
         return float(AG.density_misfit(dJ, cT, target).item())
 
     x = c0.clone().requires_grad_(True)
-    AG.density_misfit(dJ, AG.solve(m, x, dt, steps, every), target).backward()
+    L = AG.density_misfit(dJ, AG.solve(m, x, dt, steps, every), target)
+    L.backward()
     g = _host(x.grad)
-    gmax = np.abs(g).max()
     rng = np.random.default_rng(I.SEED_FD)
     h = 1e-6
+    # a central difference of a loss computed in float64 carries a rounding
+    # error of about eps L / h; below that floor no relative check is possible
+    floor = 100 * np.finfo(float).eps * float(L.item()) / h
+    strong = 0
     for flat in rng.choice(c0.numel(), nfd, replace=False):
         idx = np.unravel_index(flat, tuple(c0.shape))
         cp = c0.clone(); cp[idx] += h
         cm = c0.clone(); cm[idx] -= h
         g_fd = (loss_of(cp) - loss_of(cm)) / (2 * h)
-        assert abs(g_fd - g[idx]) <= 1e-6 * max(abs(g[idx]), 1e-3 * gmax), (idx, g_fd, g[idx])
+        assert abs(g_fd - g[idx]) <= 1e-6 * abs(g[idx]) + floor, (idx, g_fd, g[idx], floor)
+        strong += abs(g[idx]) > 1e3 * floor
+    # coefficients of the density's low modes carry gradients far above the floor:
+    # there the agreement is 1e-6 relative or better
+    for j in range(3):
+        idx = (int(rng.integers(0, c0.shape[0])), 0, j)
+        cp = c0.clone(); cp[idx] += h
+        cm = c0.clone(); cm[idx] -= h
+        g_fd = (loss_of(cp) - loss_of(cm)) / (2 * h)
+        assert abs(g_fd - g[idx]) <= 1e-6 * abs(g[idx]) + floor, (idx, g_fd, g[idx], floor)
