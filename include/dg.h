@@ -182,6 +182,12 @@ dg_status dg_kernel_times(dg_mesh *mesh, double ms[8], int64_t launches[8]);
  * Synchronous; allocates a small scratch buffer. */
 dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stream);
 
+/* Synchronises stream and reports device-side failures recorded since the last
+ * call: DG_ETIMEOUT if a bounded wait of the mixed-precision kernels expired
+ * (the kernel then skipped its remaining work and released its resources).
+ * The record is cleared.  Synchronous. */
+dg_status dg_device_status(dg_mesh *mesh, void *stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char *dg_last_error(void);
 

@@ -228,6 +228,7 @@ void free_mesh(dg_mesh *m) {
   cudaFree(m->face_geo); cudaFree(m->table_block); cudaFree(m->trace); cudaFree(m->fhat);
   cudaFree(m->stage); cudaFree(m->host_state); cudaFree(m->partial); cudaFree(m->totals_dev);
   cudaFree(m->adj_buf);
+  cudaFree(m->err_flag);
   if (m->timing) {
     for (auto &r : m->timing->pool) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete m->timing;
@@ -423,6 +424,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   m->totals_blocks = 256;
   DG_ALLOC(m->partial, sizeof(double) * m->totals_blocks * M, "totals partials");
   DG_ALLOC(m->totals_dev, sizeof(double) * M, "totals");
+  DG_ALLOC(m->err_flag, sizeof(int), "error flag");
 #undef DG_ALLOC
   m->table_doubles = off;
   double *T = m->table_block;
@@ -434,7 +436,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
       (ce = cudaMemcpy(m->elem_face, elem_face.data(), sizeof(int32_t) * N * 3, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->face_conn, conn.data(), sizeof(FaceConn) * F, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->face_geo, fgeo.data(), sizeof(FaceGeo) * F, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (ce = cudaMemcpy(m->table_block, tb.data(), sizeof(double) * off, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      (ce = cudaMemcpy(m->table_block, tb.data(), sizeof(double) * off, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemset(m->err_flag, 0, sizeof(int))) != cudaSuccess) {
     free_mesh(m);
     return cuda_fail(ce, "dg_mesh_create: upload");
   }
@@ -471,10 +474,17 @@ extern "C" dg_status dg_project_ic(dg_mesh *m, const double *u, double *c, void 
 }
 
 static dg_status check_prec(dg_precision prec, const char *who) {
-  if (prec == DG_FP64) return DG_OK;
-  if (prec == DG_TF32X1 || prec == DG_TF32X3)
-    return fail(DG_ENOTIMPL, "%s: precision %d is not built yet", who, (int)prec);
+  if (prec == DG_FP64 || prec == DG_TF32X1 || prec == DG_TF32X3) return DG_OK;
   return fail(DG_EINVAL, "%s: unknown precision %d", who, (int)prec);
+}
+
+// element kernel of the chosen precision
+static int launch_elem(const dg_mesh *m, dg_precision prec, const double *c, const double *u0, double *out,
+                       double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,
+                       void *stream) {
+  if (prec == DG_FP64) return dg::launch_element(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, stream);
+  return dg::launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, u0, out, trace_out, fhat, dt, a0, b0, mode,
+                               stream);
 }
 
 extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision prec, void *stream) {
@@ -487,13 +497,13 @@ extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision
   DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return dg::launch_face_flux(m, m->trace, m->fhat, stream); }),
           "dg_rhs edge flux");
   DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-            return dg::launch_element(m, c, nullptr, r, nullptr, m->fhat, 0.0, 0.0, 0.0, 0, stream);
+            return launch_elem(m, prec, c, nullptr, r, nullptr, m->fhat, 0.0, 0.0, 0.0, 0, stream);
           }), "dg_rhs element");
   return DG_OK;
 }
 
 // One SSP-RK3 step; on entry m->trace holds the traces of c when traces_valid.
-static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, void *stream) {
+static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, dg_precision prec, void *stream) {
   using namespace dg;
   auto face = [&](const char *what) -> dg_status {
     DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
@@ -503,7 +513,7 @@ static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, v
   auto elem = [&](const double *cin, const double *u0, double *out, double a0, double b0,
                   const char *what) -> dg_status {
     DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-              return launch_element(m, cin, u0, out, m->trace, m->fhat, dt, a0, b0, 1, stream);
+              return launch_elem(m, prec, cin, u0, out, m->trace, m->fhat, dt, a0, b0, 1, stream);
             }), what);
     return DG_OK;
   };
@@ -531,7 +541,7 @@ extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg
   dg_status st = check_prec(prec, "dg_rk_step");
   if (st != DG_OK) return st;
   for (int it = 0; it < nsteps; ++it)
-    if ((st = rk3_step(m, c, dt, it > 0, stream)) != DG_OK) return st;
+    if ((st = rk3_step(m, c, dt, it > 0, prec, stream)) != DG_OK) return st;
   return DG_OK;
 }
 
@@ -673,4 +683,18 @@ extern "C" dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops,
   cudaEventDestroy(b);
   cudaFree(buf);
   return st;
+}
+
+extern "C" dg_status dg_device_status(dg_mesh *m, void *stream) {
+  if (!m) return fail(DG_EINVAL, "dg_device_status: null mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  int flag = 0;
+  DG_CUDA(cudaMemcpyAsync(&flag, m->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "dg_device_status");
+  DG_CUDA(cudaStreamSynchronize(s), "dg_device_status sync");
+  if (flag) {
+    DG_CUDA(cudaMemsetAsync(m->err_flag, 0, sizeof(int), s), "dg_device_status reset");
+    DG_CUDA(cudaStreamSynchronize(s), "dg_device_status sync");
+    return fail(DG_ETIMEOUT, "a tensor-core wait in the mixed-precision kernel expired (flag %d)", flag);
+  }
+  return DG_OK;
 }

@@ -71,6 +71,7 @@ struct dg_mesh {
   double *stage;               // [N][M][np]
   double *host_state;          // [N][M][np] device copy used by dg_rk_step_host
   double *partial;             // [nblk][M] totals partials
+  int *err_flag;               // device int: bit 0 = a bounded tensor-core wait expired
   double *totals_dev;          // [M]
   int totals_blocks;
   // scratch for the adjoint (allocated on first use)
@@ -88,6 +89,11 @@ int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
                    double *trace_out, const double *fhat, double dt, double a0, double b0,
                    int mode, void *stream);
+// Mixed-precision element kernel (tcgen05, kind::tf32); split3 selects 3xTF32.
+int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
+                      double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,
+                      void *stream);
+int tc_smem_bytes(int p, int ne, int split3);
 int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
 int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);

@@ -1,0 +1,390 @@
+/*
+ * dg_mixed.cu -- mixed-precision element kernel: the three dense contractions of
+ * a stage run on the Blackwell tensor cores (tcgen05.mma kind::tf32, FP32
+ * accumulation in TMEM), as one TF32 product (DG_TF32X1) or as the split
+ * product a_hi b_hi + a_hi b_lo + a_lo b_hi (DG_TF32X3, a = a_hi + a_lo with
+ * both parts rounded to TF32).
+ *
+ * A tile is 32 elements = 128 accumulator rows, row r = 4 e + m (element e,
+ * variable m).  Per tile:
+ *   GEMM 1  U[128 x NQ]   = C[128 x NP] Phi[NP x NQ]            interpolation
+ *           FP32 Euler flux and G = J^tau F at every volume point (SIMT)
+ *   GEMM 2  D[128 x NP]   = [G_r | G_s | F_hat] [Dr; Ds; Lf]     projection on
+ *           the weighted basis gradients and lifting of the edge fluxes, one
+ *           accumulation (the paper's volume and surface terms, Algorithms 1-3)
+ *           FP64: the mean mode's lift (the volume term of mode 1 vanishes), the
+ *           1/det J scaling and the Runge-Kutta stage update
+ *   GEMM 3  T[128 x NF]   = C_new[128 x NP] Phi_f[NP x NF]       next edge traces
+ * The edge flux itself (dg_kernels.cu, k_face) stays float64, and so does the
+ * mean mode, which carries the conserved totals: each edge's two contributions
+ * to it cancel in float64.
+ */
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dg_device.cuh"
+#include "dg_internal.h"
+#include "dg_tcgen05.cuh"
+
+namespace dg {
+namespace {
+
+constexpr int pad8(int x) { return (x + 7) / 8 * 8; }
+constexpr int pad16(int x) { return (x + 15) / 16 * 16; }
+constexpr int align1k(int x) { return (x + 1023) / 1024 * 1024; }
+constexpr int kTcThreads = 128;
+constexpr int kTmemCols = 64;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per MMA batch before giving up
+
+template <int P, int NE, bool X3>
+struct Tc {
+  using C = Cfg<P, NE>;
+  static constexpr int NP = C::NP, NQ = C::NQ, NF = C::NF;
+  static constexpr int EB = 32, ROWS = 128;
+  static constexpr int K1 = pad8(NP), N1 = pad16(NQ), K2 = pad8(2 * NQ + NF), N2 = pad16(NP), N4 = pad16(NF);
+  static constexpr int NS = X3 ? 2 : 1;                     // TF32 planes: hi (, lo)
+  static constexpr int A1P = ROWS * K1 * 4, A2P = ROWS * K2 * 4;
+  static constexpr int B1P = N1 * K1 * 4, B2P = N2 * K2 * 4, B4P = N4 * K1 * 4;
+  static constexpr int oA1 = 0;
+  static constexpr int oA2 = align1k(oA1 + A1P * NS);
+  static constexpr int oB1 = align1k(oA2 + A2P * NS);
+  static constexpr int oB2 = align1k(oB1 + B1P * NS);
+  static constexpr int oB4 = align1k(oB2 + B2P * NS);
+  static constexpr int oC = align1k(oB4 + B4P * NS);        // double [EB][M][NP]
+  static constexpr int oF = oC + EB * M * NP * 8;            // double [EB][NF][M]
+  static constexpr int endF = oF + EB * NF * M * 8;
+  static constexpr int SU = EB * NQ * M * 4;                 // float [EB][NQ][M]
+  static constexpr bool U_IN_A1 = SU <= A1P * NS;            // reuse GEMM 1's A planes
+  static constexpr int oU = U_IN_A1 ? oA1 : endF;
+  static constexpr int oJ = U_IN_A1 ? endF : endF + SU;      // float [EB][4]  J^tau
+  static constexpr int oL0 = oJ + EB * 16;                   // double [NF]    lift weights of mode 1
+  static constexpr int oBar = (oL0 + NF * 8 + 15) / 16 * 16; // mbarrier, TMEM slot
+  static constexpr int SMEM = oBar + 16;
+  static_assert(N1 <= kTmemCols && N2 <= kTmemCols && N4 <= kTmemCols, "TMEM columns");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+// writes v (rounded to TF32, and its TF32 remainder for the split product) at
+// (row, k) of a K-major operand with ktot columns
+template <bool X3>
+__device__ __forceinline__ void put(unsigned char *base, int plane_bytes, int row, int k, int ktot, float v) {
+  const int off = tc::kmaj(row, k, ktot);
+  const float hi = tc::to_tf32(v);
+  *reinterpret_cast<float *>(base + off) = hi;
+  if (X3) *reinterpret_cast<float *>(base + plane_bytes + off) = tc::to_tf32(v - hi);
+}
+
+// D (TMEM) = sum over k-steps of A B^T, split products when X3
+template <bool X3, int KT>
+__device__ __forceinline__ void gemm(uint32_t d, uint32_t a, int a_plane, uint32_t b, int b_plane, uint32_t idesc) {
+#pragma unroll
+  for (int s = 0; s < KT / 8; ++s) {
+    const uint32_t off = (uint32_t)s * 256u;
+    if (X3) {
+      tc::mma_tf32(d, tc::desc(a + a_plane + off, KT), tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
+      tc::mma_tf32(d, tc::desc(a + off, KT), tc::desc(b + b_plane + off, KT), idesc, 1u);
+      tc::mma_tf32(d, tc::desc(a + off, KT), tc::desc(b + off, KT), idesc, 1u);
+    } else {
+      tc::mma_tf32(d, tc::desc(a + off, KT), tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_row(uint32_t taddr, float *v) {
+#pragma unroll
+  for (int c = 0; c < N / 16; ++c) tc::ld16(taddr + (uint32_t)(c * 16), v + c * 16);
+  tc::wait_ld();
+}
+
+// float32 reference flux at one point (the same Euler flux as ref_flux)
+__device__ __forceinline__ void ref_flux_f32(const float U[M], const float *jt, float gamma, float Gr[M],
+                                             float Gs[M]) {
+  const float inv = 1.0f / U[0];
+  const float u = U[1] * inv, v = U[2] * inv;
+  const float p = (gamma - 1.0f) * (U[3] - 0.5f * (U[1] * u + U[2] * v));
+  float F1[M], F2[M];
+  F1[0] = U[1];           F2[0] = U[2];
+  F1[1] = U[1] * u + p;   F2[1] = U[1] * v;
+  F1[2] = U[2] * u;       F2[2] = U[2] * v + p;
+  F1[3] = (U[3] + p) * u; F2[3] = (U[3] + p) * v;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    Gr[m] = jt[0] * F1[m] + jt[1] * F2[m];
+    Gs[m] = jt[2] * F1[m] + jt[3] * F2[m];
+  }
+}
+
+template <int P, int NE, bool X3>
+__global__ void __launch_bounds__(kTcThreads)
+k_element_tc(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
+             const double *__restrict__ fhat, const double *__restrict__ geo,
+             const int32_t *__restrict__ elem_face, DevTables tab, int N, double dt, double a0, double b0,
+             int mode, double gamma, int *err) {
+  using T = Tc<P, NE, X3>;
+  constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB;
+  constexpr int K1 = T::K1, N1 = T::N1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char *A1 = sm + T::oA1, *A2 = sm + T::oA2, *B1 = sm + T::oB1, *B2 = sm + T::oB2, *B4 = sm + T::oB4;
+  double *sC = reinterpret_cast<double *>(sm + T::oC);
+  double *sF = reinterpret_cast<double *>(sm + T::oF);
+  float *sU = reinterpret_cast<float *>(sm + T::oU);
+  float *sJ = reinterpret_cast<float *>(sm + T::oJ);
+  double *sL0 = reinterpret_cast<double *>(sm + T::oL0);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + T::oBar);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + T::oBar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t mbar = tc::smem_u32(bar);
+
+  // ---- once per CTA: zeroed A planes, B operands (split), TMEM, mbarrier ----
+  for (int i = tid; i < (T::A1P * T::NS) / 16; i += kTcThreads) reinterpret_cast<int4 *>(A1)[i] = make_int4(0, 0, 0, 0);
+  for (int i = tid; i < (T::A2P * T::NS) / 16; i += kTcThreads) reinterpret_cast<int4 *>(A2)[i] = make_int4(0, 0, 0, 0);
+  for (int i = tid; i < N1 * K1; i += kTcThreads) {
+    const int n = i / K1, k = i - n * K1;
+    const double v = (n < NQ && k < NP) ? tab.BvT[k * NQ + n] : 0.0;
+    put<X3>(B1, T::B1P, n, k, K1, (float)v);
+  }
+  for (int i = tid; i < N2 * K2; i += kTcThreads) {
+    const int n = i / K2, k = i - n * K2;
+    double v = 0.0;
+    if (n < NP) {
+      if (k < NQ) v = tab.Dr[k * NP + n];
+      else if (k < 2 * NQ) v = tab.Ds[(k - NQ) * NP + n];
+      else if (k < 2 * NQ + NF) v = tab.Lf[(k - 2 * NQ) * NP + n];
+    }
+    put<X3>(B2, T::B2P, n, k, K2, (float)v);
+  }
+  for (int i = tid; i < N4 * K1; i += kTcThreads) {
+    const int n = i / K1, k = i - n * K1;
+    const double v = (n < NF && k < NP) ? tab.BfT[k * NF + n] : 0.0;
+    put<X3>(B4, T::B4P, n, k, K1, (float)v);
+  }
+  for (int i = tid; i < NF; i += kTcThreads) sL0[i] = tab.Lf[i * NP];
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(slot), kTmemCols);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);       // this warp's 32 TMEM lanes
+  const uint32_t uA1 = tc::smem_u32(A1), uA2 = tc::smem_u32(A2);
+  const uint32_t uB1 = tc::smem_u32(B1), uB2 = tc::smem_u32(B2), uB4 = tc::smem_u32(B4);
+  const float g32 = (float)gamma;
+  const int row = tid, rel = row >> 2, rm = row & 3;                 // accumulator row = 4 e + m
+  uint32_t phase = 0;
+
+  const int ntiles = (N + EB - 1) / EB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e0 = tile * EB;
+    const int ecount = min(EB, N - e0);
+    // ---- stage input, J^tau, edge fluxes (element orientation and point order) ----
+    const double *src = c + (size_t)e0 * M * NP;
+    for (int i = tid; i < EB * M * NP; i += kTcThreads) sC[i] = i < ecount * M * NP ? src[i] : 0.0;
+    for (int i = tid; i < EB * 4; i += kTcThreads) {
+      const int el = i >> 2;
+      sJ[i] = el < ecount ? (float)geo[(size_t)(e0 + el) * GEO + (i & 3)] : 0.0f;
+    }
+    for (int i = tid; i < EB * NF; i += kTcThreads) {
+      const int el = i / NF, qk = i - el * NF;
+      double v[M] = {0.0, 0.0, 0.0, 0.0};
+      if (el < ecount) {
+        const int q = qk / NE, k = qk - q * NE;
+        const int ef = elem_face[(size_t)(e0 + el) * 3 + q];
+        const int f = ef >> 1, side = ef & 1;
+        const double *fp = fhat + ((size_t)f * NE + (side ? NE - 1 - k : k)) * M;
+        const double sg = side ? 1.0 : -1.0;
+#pragma unroll
+        for (int m = 0; m < M; ++m) v[m] = sg * fp[m];
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) sF[i * M + m] = v[m];
+    }
+    __syncthreads();
+    // ---- operands of GEMM 1 (this thread's row) and the lift columns of GEMM 2 ----
+    for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? (float)sC[(rel * M + rm) * NP + k] : 0.0f);
+    for (int qk = 2 * NQ; qk < K2; ++qk) {
+      const float v = qk < 2 * NQ + NF ? (float)sF[(rel * NF + (qk - 2 * NQ)) * M + rm] : 0.0f;
+      put<X3>(A2, T::A2P, row, qk, K2, v);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- GEMM 1: interpolation to the volume points ----
+    if (tid == 0) {
+      gemm<X3, K1>(tmem, uA1, T::A1P, uB1, T::B1P, tc::idesc_tf32(128, N1));
+      tc::commit(mbar);
+    }
+    bool ok = tc::mbar_wait(mbar, phase, kWaitNs);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, 1); break; }
+    tc::fence_after_sync();
+    {
+      float v[N1];
+      tmem_row<N1>(trow, v);
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) sU[(rel * NQ + k) * M + rm] = v[k];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- float32 flux at the volume points -> G_r, G_s columns of GEMM 2 ----
+    for (int i = tid; i < EB * NQ; i += kTcThreads) {
+      const int el = i / NQ, k = i - el * NQ;
+      float U[M], Gr[M], Gs[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) U[m] = sU[i * M + m];
+      if (el < ecount) {
+        ref_flux_f32(U, sJ + el * 4, g32, Gr, Gs);
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) { Gr[m] = 0.0f; Gs[m] = 0.0f; }
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        put<X3>(A2, T::A2P, el * 4 + m, k, K2, Gr[m]);
+        put<X3>(A2, T::A2P, el * 4 + m, NQ + k, K2, Gs[m]);
+      }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- GEMM 2: volume projection + lift ----
+    if (tid == 0) {
+      gemm<X3, K2>(tmem, uA2, T::A2P, uB2, T::B2P, tc::idesc_tf32(128, N2));
+      tc::commit(mbar);
+    }
+    ok = tc::mbar_wait(mbar, phase, kWaitNs);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, 1); break; }
+    tc::fence_after_sync();
+    {
+      float v[N2];
+      tmem_row<N2>(trow, v);
+      double *cr = sC + (rel * M + rm) * NP;
+      if (rel < ecount) {
+        const size_t e = (size_t)(e0 + rel);
+        const double inv = geo[e * GEO + 4];
+        double s0 = 0.0;                       // mean mode: lift in float64
+#pragma unroll
+        for (int qk = 0; qk < NF; ++qk) s0 += sL0[qk] * sF[(rel * NF + qk) * M + rm];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          const double R = (j == 0 ? s0 : (double)v[j]) * inv;
+          double val;
+          if (mode == 0) {
+            val = R;
+          } else {
+            val = b0 * (cr[j] + dt * R);
+            if (a0 != 0.0) val = a0 * u0[(e * M + rm) * NP + j] + val;
+          }
+          cr[j] = val;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) cr[j] = 0.0;
+      }
+      if (trace_out)
+        for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? (float)cr[k] : 0.0f);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    {
+      double *dst = out + (size_t)e0 * M * NP;
+      for (int i = tid; i < ecount * M * NP; i += kTcThreads) dst[i] = sC[i];
+    }
+    if (trace_out) {
+      // ---- GEMM 3: edge traces of the new state ----
+      if (tid == 0) {
+        gemm<X3, K1>(tmem, uA1, T::A1P, uB4, T::B4P, tc::idesc_tf32(128, N4));
+        tc::commit(mbar);
+      }
+      ok = tc::mbar_wait(mbar, phase, kWaitNs);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, 1); break; }
+      tc::fence_after_sync();
+      {
+        float v[N4];
+        tmem_row<N4>(trow, v);
+#pragma unroll
+        for (int qk = 0; qk < NF; ++qk) sF[(rel * NF + qk) * M + rm] = (double)v[qk];
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      double *dst = trace_out + (size_t)e0 * NF * M;
+      for (int i = tid; i < ecount * NF * M; i += kTcThreads) dst[i] = sF[i];
+    }
+    __syncthreads();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int P, int NE, bool X3>
+int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out, const double *fhat,
+           double dt, double a0, double b0, int mode, cudaStream_t s) {
+  using T = Tc<P, NE, X3>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_element_tc<P, NE, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+    if (e != cudaSuccess) return (int)e;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element_tc<P, NE, X3>, kTcThreads, T::SMEM);
+  if (e != cudaSuccess) return (int)e;
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 512 / kTmemCols) per_sm = 512 / kTmemCols;      // TMEM: 512 columns per SM
+  const int ntiles = (int)((m->N + T::EB - 1) / T::EB);
+  const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
+  k_element_tc<P, NE, X3><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face,
+                                                            m->tab, (int)m->N, dt, a0, b0, mode, m->gamma,
+                                                            m->err_flag);
+  return (int)cudaGetLastError();
+}
+
+template <bool X3>
+int dispatch_tc(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
+                const double *fhat, double dt, double a0, double b0, int mode, cudaStream_t s) {
+#define CALL(P, NE) run_tc<P, NE, X3>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s)
+  if (m->p == 1 && m->ne == 2) return CALL(1, 2);
+  if (m->p == 2 && m->ne == 3) return CALL(2, 3);
+  if (m->p == 3 && m->ne == 4) return CALL(3, 4);
+  if (m->p == 3 && m->ne == 3) return CALL(3, 3);
+  if (m->p == 4 && m->ne == 5) return CALL(4, 5);
+  if (m->p == 5 && m->ne == 6) return CALL(5, 6);
+#undef CALL
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
+                      double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,
+                      void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  return split3 ? dispatch_tc<true>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s)
+                : dispatch_tc<false>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s);
+}
+
+int tc_smem_bytes(int p, int ne, int split3) {
+#define SZ(P, NE) (split3 ? Tc<P, NE, true>::SMEM : Tc<P, NE, false>::SMEM)
+  if (p == 1 && ne == 2) return SZ(1, 2);
+  if (p == 2 && ne == 3) return SZ(2, 3);
+  if (p == 3 && ne == 4) return SZ(3, 4);
+  if (p == 3 && ne == 3) return SZ(3, 3);
+  if (p == 4 && ne == 5) return SZ(4, 5);
+  if (p == 5 && ne == 6) return SZ(5, 6);
+#undef SZ
+  return -1;
+}
+
+}  // namespace dg

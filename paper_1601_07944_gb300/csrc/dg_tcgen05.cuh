@@ -1,0 +1,126 @@
+/*
+ * dg_tcgen05.cuh -- the small set of Blackwell (sm_100a/sm_103a) tensor-core
+ * primitives the mixed-precision kernels use, as inline PTX:
+ *
+ *   tcgen05.alloc / dealloc        tensor-memory (TMEM) columns for the accumulator
+ *   tcgen05.mma.cta_group::1.kind::tf32
+ *                                  D[128 x N] (+)= A[128 x 8] B[8 x N], A and B in
+ *                                  shared memory, D in TMEM, FP32 accumulation
+ *   tcgen05.commit -> mbarrier     completion of the issued MMAs
+ *   tcgen05.ld.32x32b              TMEM -> registers (each warp reads its own
+ *                                  32-lane quarter; lane = accumulator row)
+ *
+ * Operand layout: K-major without swizzle.  The tile is made of core matrices of
+ * 8 rows x 16 bytes (8 rows x 4 TF32 values) stored as 128 contiguous bytes; the
+ * core matrix holding K elements 4c..4c+3 of rows 8g..8g+7 starts at byte
+ * g * (Ktot * 32) + c * 128.  In the shared-memory descriptor the leading byte
+ * offset (LBO, next core matrix along K) is 128 and the stride byte offset (SBO,
+ * next 8-row group) is Ktot * 32.  One MMA consumes K = 8, i.e. two core
+ * matrices along K, so the descriptor of k-step s starts s * 256 bytes in.
+ */
+#pragma once
+
+#include <cstdint>
+
+namespace dg {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (row, k) of a K-major tile with ktot columns
+__host__ __device__ constexpr int kmaj(int row, int k, int ktot) {
+  return (row >> 3) * (ktot * 32) + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// shared-memory matrix descriptor: no swizzle, LBO = 128, SBO = ktot * 32
+__device__ __forceinline__ uint64_t desc(uint32_t addr, int ktot) {
+  const uint32_t sbo = (uint32_t)ktot * 32u;
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                       // descriptor version (fixed 0b001)
+  return d;
+}
+
+// instruction descriptor: D f32, A and B tf32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the mbarrier phase `parity` to complete; gives up after limit_ns
+// nanoseconds and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64_t limit_ns) {
+  uint32_t done = 0;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;"); }
+
+// one warp: allocates ncols TMEM columns, writes the base address to *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp-collective)
+__device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
+
+// round an FP32 value to TF32 (10 mantissa bits, round to nearest, ties away)
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+}  // namespace tc
+}  // namespace dg

@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
-           "dg_kernel_times", "dg_probe_fma_rate")
+           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
         "dg_set_timing": [P, I],
         "dg_kernel_times": [P, P, P],
         "dg_probe_fma_rate": [P, P, P],
+        "dg_device_status": [P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -191,6 +192,10 @@ class Mesh:
     # -- diagnostics --------------------------------------------------------
     def set_timing(self, enable: bool):
         _check(load().dg_set_timing(self._h, 1 if enable else 0))
+
+    def device_status(self, stream=None):
+        """Synchronises and raises DGError(DG_ETIMEOUT) if a bounded device wait expired."""
+        _check(load().dg_device_status(self._h, _stream_ptr(stream)))
 
     def kernel_times(self):
         """{kind: (launches, total ms)} since timing was enabled (synchronises)."""

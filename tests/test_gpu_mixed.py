@@ -1,0 +1,91 @@
+"""Mixed-precision path (tcgen05 TF32 tensor-core contractions) on the GPU.
+
+Error model: the contractions run on TF32 inputs with FP32 accumulation, the
+volume flux in FP32.  The RHS is the small difference of the volume and surface
+terms, so its error is measured against the size of those terms (the oracle's
+volume term V / det J):
+    3xTF32: ||R_mixed - R|| <= 2e-6 (||R|| + ||V||)   (FP32-level arithmetic)
+    1xTF32: ||R_mixed - R|| <= 4e-3 (||R|| + ||V||)   (10-bit TF32 mantissa)
+The mean mode stays float64 in both modes, so the conserved totals drift only at
+float64 rounding.
+"""
+import numpy as np
+import pytest
+
+from paper_1601_07944_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"tf32x3": 2e-6, "tf32x1": 4e-3}
+CASES = [(1, 0), (2, 0), (3, 0), (3, 3), (4, 0), (5, 0)]
+
+
+@pytest.fixture(scope="module")
+def dgmod():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1601_07944_gb300 import _build, dg
+    _build.build()
+    dg.load()
+    return dg
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
+@pytest.mark.parametrize("n", [6, 16])
+@pytest.mark.parametrize("p,ne", CASES)
+def test_mixed_rhs_vs_oracle(dgmod, oracle_mod, p, ne, n, prec):
+    mesh = I.periodic_mesh(n)
+    m = dgmod.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p, n_edge_pts=ne)
+    c = o.project_ic(I.perturbed_vortex)
+    ref, vol = o.rhs_and_volume(c)
+    got = _host(m.rhs(_dev(c), precision=prec))
+    m.device_status()
+    err = np.linalg.norm(got - ref)
+    assert err <= TOL[prec] * (np.linalg.norm(ref) + np.linalg.norm(vol)), err / np.linalg.norm(ref)
+    # the mean mode is lifted in float64 from the float64 edge fluxes
+    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-12 * np.abs(ref[:, :, 0]).max()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
+def test_mixed_conservation_and_determinism(dgmod, prec):
+    mesh = I.periodic_mesh(16)
+    p = 3
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    c0 = m.project_function(I.perturbed_vortex)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    t0 = m.conserved_totals(c0)
+    a = c0.clone(); b = c0.clone()
+    m.rk_step(a, dt, 30, precision=prec)
+    m.rk_step(b, dt, 30, precision=prec)
+    m.device_status()
+    assert np.array_equal(_host(a), _host(b))
+    t1 = m.conserved_totals(a)
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * np.abs(t0))
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-6), ("tf32x1", 1e-3)])
+@pytest.mark.parametrize("p", [2, 4])
+def test_mixed_state_vs_fp64(dgmod, p, prec, tol):
+    """State error of the mixed run against the float64 GPU run after 20 steps."""
+    mesh = I.periodic_mesh(32)
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    c0 = m.project_function(I.perturbed_vortex)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    a = c0.clone(); b = c0.clone()
+    m.rk_step(a, dt, 20, precision="fp64")
+    m.rk_step(b, dt, 20, precision=prec)
+    m.device_status()
+    A, B = _host(a), _host(b)
+    assert np.linalg.norm(B - A) / np.linalg.norm(A) < tol
