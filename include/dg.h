@@ -123,6 +123,23 @@ dg_status dg_project_ic(dg_mesh *mesh, const double *u, double *c, void *stream)
  * Asynchronous. */
 dg_status dg_rhs(dg_mesh *mesh, const double *c, double *r, dg_precision prec, void *stream);
 
+/* Same result as dg_rhs, for callers that cannot allocate device memory when they
+ * call it (for example a host whose device memory is all reserved by another
+ * allocator, or a time-critical loop that must not allocate).  The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ * The call allocates nothing.  Its work space (edge traces and edge fluxes,
+ * N*3*n_edge_pts*4 + n_face*n_edge_pts*4 doubles) comes from one static device
+ * array of 8,388,608 doubles (64 MiB) that every GPU loading this library keeps
+ * until the process exits; larger meshes are rejected with DG_EINVAL and a
+ * message giving both sizes (use dg_rhs for them).  The first call on a device,
+ * made with that device current, looks up the array's device address; make it
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (every slot is written before it is read, so nothing
+ * needs clearing); calls that overlap on the GPU, on any stream or thread, race
+ * on it.  The current device must be the mesh's device.  c, r: DEVICE
+ * [N][4][N_p], must not alias.  Asynchronous. */
+dg_status dg_rhs_noalloc(dg_mesh *mesh, const double *c, double *r, dg_precision prec, void *stream);
+
 /* nsteps steps of the three-stage SSP Runge-Kutta method (Shu-Osher form),
  *   u1 = u + dt L(u),  u2 = 3/4 u + 1/4 (u1 + dt L(u1)),
  *   u <- 1/3 u + 2/3 (u2 + dt L(u2)),

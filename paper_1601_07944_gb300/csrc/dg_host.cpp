@@ -260,6 +260,18 @@ int timed(dg_mesh *m, int kind, void *stream, F &&launch) {
 
 }  // namespace
 
+namespace dg {
+dg_status set_error(dg_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+}  // namespace dg
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

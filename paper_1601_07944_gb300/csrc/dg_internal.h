@@ -103,6 +103,8 @@ int element_smem_bytes(int p, int ne);
 int launch_rhs_vjp(const dg_mesh *m, const double *u, const double *lam, double *uvol, double *G, double *T,
                    double *TB, const double *X, const double *Y, const double *Z, double x0, double x1,
                    double x2, double s, double *out, void *stream);
+// Records a failure message for dg_last_error() and returns st.
+dg_status set_error(dg_status st, const char *fmt, ...);
 // FMA-rate probe: runs `iters` iterations of 8 independent FMA chains per thread.
 int launch_fma_probe(int fp64, int blocks, int threads, int iters, double *out, void *stream);
 

@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
-           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status")
+           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
         "dg_kernel_times": [P, P, P],
         "dg_probe_fma_rate": [P, P, P],
         "dg_device_status": [P, P],
+        "dg_rhs_noalloc": [P, P, P, I, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -223,6 +224,15 @@ class Mesh:
         _check(load().dg_rhs(self._h, _dev_ptr(c, "c", self.coef_shape), _dev_ptr(r, "r", self.coef_shape),
                              _prec(precision), _stream_ptr(stream)))
         return r
+
+    def rhs_noalloc(self, c, out, precision="fp64", stream=None):
+        """dg_rhs without any device allocation: the work space comes from the
+        library's fixed 64 MiB device array (meshes that need more are rejected).
+        For callers that cannot allocate when they evaluate the RHS; `out` must be
+        given.  Calls that overlap on the GPU race on the shared array."""
+        _check(load().dg_rhs_noalloc(self._h, _dev_ptr(c, "c", self.coef_shape), _dev_ptr(out, "r", self.coef_shape),
+                                     _prec(precision), _stream_ptr(stream)))
+        return out
 
     def rk_step(self, c, dt: float, nsteps: int = 1, precision="fp64", stream=None):
         """nsteps SSP-RK3 steps in place on the device tensor c."""
