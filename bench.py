@@ -10,6 +10,10 @@ between timed steps, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+With N = 1 the line also carries the tensor-core modes on the same workload
+(throughput, speedup over float64 and state error against the float64 run) and
+the adjoint/forward cost ratio on the 256 x 256, p = 2 workload.
+
 Under torchrun (N > 1) every rank runs an independent replica of the workload on
 its own GPU (the path is replicated, not sharded): value = all ranks' DOF
 updates / the slowest rank's time.  --impl reference times the CPU oracle on
@@ -143,6 +147,23 @@ def _dof_per_step(N: int, p: int) -> int:
     return N * (p + 1) * (p + 2) // 2 * 4 * 3
 
 
+def slowest_rank_ms(ms: float, world: int, device: str = "cuda") -> float:
+    """The timed region's duration of the slowest rank (all ranks call this)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(dof_per_step_per_rank: int, steps: int, t_max_ms: float, world: int) -> float:
+    """DOF updates per second of the whole job: every rank's replica advanced the
+    same workload, and the job took as long as its slowest rank."""
+    return world * dof_per_step_per_rank * steps / (t_max_ms * 1e-3)
+
+
 def run_reference(args, world, rank):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     if rank != 0:
@@ -213,6 +234,76 @@ def cpu_baseline(seconds: float = 12.0):
                       "(%.1f s)" % (steps, el)}
 
 
+def mixed_modes(m, c0, dt, steps, flush, fp64_ms_per_step):
+    """Throughput of the tensor-core modes on the same workload and their state
+    error against the float64 GPU run after the same number of steps."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    ref = c0.clone()
+    m.rk_step(ref, dt, steps, precision="fp64")
+    out = {}
+    for prec in ("tf32x3", "tf32x1"):
+        c = c0.clone()
+        for _ in range(3):
+            m.rk_step(c, dt, 1, precision=prec)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream); m.rk_step(c, dt, 1, precision=prec); m.conserved_totals(c); b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        m.device_status()
+        x = c0.clone()
+        m.rk_step(x, dt, steps, precision=prec)
+        R, X = ref.cpu().numpy(), x.cpu().numpy()
+        out[prec] = {"value": _dof_per_step(m.N, m.p) * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "speedup_vs_fp64": fp64_ms_per_step / (ms / steps),
+                     "rel_l2_vs_fp64": float(np.linalg.norm(X - R) / np.linalg.norm(R)),
+                     "error_after_steps": steps}
+    return out
+
+
+def adjoint_ratio(steps: int = 20, every: int = 10):
+    """Cost of the discrete adjoint relative to the forward pass on the 256x256,
+    p=2 differentiation workload: one dg_adjoint_step against one dg_rk_step, and
+    the checkpointed backward (recomputation included) against its forward."""
+    import torch
+    from paper_1601_07944_gb300 import autograd as AG, dg, inputs as I
+    mesh = I.periodic_mesh(256)
+    p = 2
+    m = dg.Mesh.from_mesh(mesh, p)
+    c0 = m.project_function(I.perturbed_vortex)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    lam = torch.randn_like(c0)
+    out = torch.empty_like(c0)
+    c = c0.clone()
+    m.rk_step(c, dt, 2); m.adjoint_step(c0, dt, lam, out=out)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(); m.rk_step(c, dt, steps); e[1].record()
+    for _ in range(steps):
+        m.adjoint_step(c0, dt, lam, out=out)
+    e[2].record(); torch.cuda.synchronize()
+    fwd, adj = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    dJ = m.det_j()
+    tgt = c0.clone()
+    for rep in range(2):                   # the first pass warms up torch's autograd path
+        x = c0.clone().requires_grad_(True)
+        torch.cuda.synchronize(); t0 = time.perf_counter()
+        cT = AG.solve(m, x, dt, steps, every)
+        loss = AG.density_misfit(dJ, cT, tgt)
+        torch.cuda.synchronize(); t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize(); t2 = time.perf_counter()
+    return {"workload": "perturbed vortex, 256x256 mesh, p=2, %d steps, checkpoint every %d" % (steps, every),
+            "adjoint_step_over_rk_step": adj / fwd,
+            "backward_over_forward_with_recompute": (t2 - t1) / (t1 - t0),
+            "rk_step_ms": fwd / steps, "adjoint_step_ms": adj / steps}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -272,13 +363,8 @@ def run_ours(args, world, rank, local):
     m.set_timing(False)
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
 
-    t_max = dev_ms
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * dof_step * args.steps / (t_max * 1e-3)
+    t_max = slowest_rank_ms(dev_ms, world, "cuda")
+    value = whole_job_value(dof_step, args.steps, t_max, world)
 
     # end to end through the host-buffer entry point: H2D, step, D2H every step
     e2e_steps = max(1, min(args.steps, 20))
@@ -327,6 +413,10 @@ def run_ours(args, world, rank, local):
             "wall_s_timed_region": wall,
             "totals_last_step": [float(x) for x in totals] if totals is not None else None,
         }
+        if world == 1 and not args.no_extras:
+            c0 = m.project_function(I.vortex)
+            line["mixed"] = mixed_modes(m, c0, dt, max(5, min(args.steps, 20)), flush, t_max / args.steps)
+            line["adjoint"] = adjoint_ratio()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
     if world > 1:
@@ -344,6 +434,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

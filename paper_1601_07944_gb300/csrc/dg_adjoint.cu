@@ -227,6 +227,10 @@ int run_adj(const dg_mesh *m, const double *u, const double *lam, double *uvol, 
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_adj_element<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, A::SMEM);
     if (e != cudaSuccess) return (int)e;
+    // all of the SM's unified L1/shared storage as shared memory, so that the
+    // occupancy query and the launch see every CTA that fits
+    e = cudaFuncSetAttribute(k_adj_element<P, NE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
   int per_sm = 0;
