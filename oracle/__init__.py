@@ -55,6 +55,7 @@ def _load():
             "or_destroy": (None, [P]),
             "or_info": (I, [P, P]),
             "or_volume_rule": (I, [P, P, P, P]),
+            "or_volume_tables": (I, [P, P, P, P]),
             "or_edge_rule": (I, [P, P, P]),
             "or_edges": (I, [P, P, P, P, P, P, P, P]),
             "or_det_j": (I, [P, P]),
@@ -215,6 +216,13 @@ class OracleDG:
         r = np.zeros(self.nq); s = np.zeros(self.nq); w = np.zeros(self.nq)
         _lib.or_volume_rule(self._h, _ptr(r), _ptr(s), _ptr(w))
         return r, s, w
+
+    def volume_tables(self):
+        """phi, dphi/dr, dphi/ds [nq, Np] at the volume points (evaluated at the
+        exact images of the rounded 1D nodes)."""
+        a = np.zeros((self.nq, self.np)); b = np.zeros((self.nq, self.np)); c = np.zeros((self.nq, self.np))
+        _chk(_lib.or_volume_tables(self._h, _ptr(a), _ptr(b), _ptr(c)))
+        return a, b, c
 
     def edge_rule(self):
         x = np.zeros(self.ne); w = np.zeros(self.ne)

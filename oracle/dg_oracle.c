@@ -123,8 +123,11 @@ int or_gauss_legendre(int n, double *x, double *w) { return or_gauss_jacobi(n, 0
  * {(0,0),(1,0),(0,1)}: Gauss-Legendre in a, Gauss-Jacobi(1,0) in b,
  * r = (1+a)(1-b)/4, s = (1+b)/2, weight w_a w_b / 8.  n^2 points, exact for
  * polynomials of degree 2n-1; the weights sum to 1/2 (the triangle's area).
- * Point order: b-index outer, a-index inner. */
-int or_stroud(int n, double *r, double *s, double *w)
+ * Point order: b-index outer, a-index inner.  The 1D nodes are rounded to
+ * double; the points are the exact (extended-precision) images of those rounded
+ * nodes, which is where the basis tables are evaluated, and they are stored
+ * rounded to double.  rl, sl (optional) receive the extended points. */
+static int stroud_l(int n, double *r, double *s, double *w, long double *rl, long double *sl)
 {
     long double xa[64], wa[64], xb[64], wb[64];
     if (gauss_jacobi_l(n, 0.0, 0.0, xa, wa)) return 1;
@@ -132,12 +135,18 @@ int or_stroud(int n, double *r, double *s, double *w)
     for (int ib = 0; ib < n; ++ib)
         for (int ia = 0; ia < n; ++ia) {
             int k = ib * n + ia;
-            r[k] = (double)(0.25L * (1.0L + xa[ia]) * (1.0L - xb[ib]));
-            s[k] = (double)(0.5L * (1.0L + xb[ib]));
+            long double a = (double)xa[ia], b = (double)xb[ib];
+            long double rr = 0.25L * (1.0L + a) * (1.0L - b), ss = 0.5L * (1.0L + b);
+            r[k] = (double)rr;
+            s[k] = (double)ss;
             w[k] = (double)(0.125L * wa[ia] * wb[ib]);
+            if (rl) rl[k] = rr;
+            if (sl) sl[k] = ss;
         }
     return 0;
 }
+
+int or_stroud(int n, double *r, double *s, double *w) { return stroud_l(n, r, s, w, NULL, NULL); }
 
 /* ------------------------------------------------------------------------- */
 /* Orthonormal Dubiner basis on the reference triangle.                      */
@@ -256,10 +265,10 @@ static long double powli(long double x, int k)
 }
 
 /* value and gradient of the normalised psi_ab at (r, s) from the two sums */
-static void psi_eval(int a, int b, long double nrm, double r_, double s_,
+static void psi_eval(int a, int b, long double nrm, long double r, long double s,
                      double *v, double *dr, double *ds)
 {
-    long double r = r_, s = s_, t = r + s - 1.0L, u = s - 1.0L;
+    long double t = r + s - 1.0L, u = s - 1.0L;
     long double A = 0, Ar = 0, As = 0;
     for (int m = 0; m <= a; ++m) {
         long double cf = (long double)(ibinom(a, m) * ibinom(a, m));
@@ -297,6 +306,23 @@ static int mode_ab(int p, int j, int *a, int *b)
  * out arrays are [npts][Np].  Any of dphir, dphis may be NULL. */
 int or_dubiner_eval(int p, int npts, const double *r, const double *s,
                     double *phi, double *dphir, double *dphis)
+{
+    if (p < 0 || 2 * p > OPMAX) return 1;
+    int np = (p + 1) * (p + 2) / 2;
+    for (int j = 0; j < np; ++j) {
+        int a = 0, b = 0;
+        mode_ab(p, j, &a, &b);
+        long double nrm = psi_norm(a, b);
+        for (int k = 0; k < npts; ++k)
+            psi_eval(a, b, nrm, r[k], s[k], &phi[k * np + j],
+                     dphir ? &dphir[k * np + j] : NULL, dphis ? &dphis[k * np + j] : NULL);
+    }
+    return 0;
+}
+
+/* the same at extended-precision points */
+static int dubiner_eval_l(int p, int npts, const long double *r, const long double *s,
+                          double *phi, double *dphir, double *dphis)
 {
     if (p < 0 || 2 * p > OPMAX) return 1;
     int np = (p + 1) * (p + 2) / 2;
@@ -435,8 +461,12 @@ oracle_dg *or_create(int p, int ne, int nvol, double gamma, int64_t N, const dou
     o->phi = xcalloc((size_t)nq * np, sizeof(double));
     o->phir = xcalloc((size_t)nq * np, sizeof(double));
     o->phis = xcalloc((size_t)nq * np, sizeof(double));
-    or_stroud(nd, o->vr, o->vs, o->vw);
-    or_dubiner_eval(p, nq, o->vr, o->vs, o->phi, o->phir, o->phis);
+    {
+        long double rl[4096], sl[4096];
+        if (nq > 4096) { or_destroy(o); return NULL; }
+        stroud_l(nd, o->vr, o->vs, o->vw, rl, sl);
+        dubiner_eval_l(p, nq, rl, sl, o->phi, o->phir, o->phis);
+    }
     or_dubiner_integrals(p, o->phi_int);
 
     o->ex = xcalloc(o->ne, sizeof(double)); o->ew = xcalloc(o->ne, sizeof(double));
@@ -514,6 +544,16 @@ int or_volume_rule(const oracle_dg *o, double *r, double *s, double *w)
     memcpy(r, o->vr, sizeof(double) * o->nq);
     memcpy(s, o->vs, sizeof(double) * o->nq);
     memcpy(w, o->vw, sizeof(double) * o->nq);
+    return 0;
+}
+
+/* the volume tables phi, dphi/dr, dphi/ds at the volume points, [nq][np] each */
+int or_volume_tables(const oracle_dg *o, double *phi, double *dr, double *ds)
+{
+    size_t n = (size_t)o->nq * o->np;
+    memcpy(phi, o->phi, sizeof(double) * n);
+    memcpy(dr, o->phir, sizeof(double) * n);
+    memcpy(ds, o->phis, sizeof(double) * n);
     return 0;
 }
 

@@ -132,11 +132,18 @@ void gauss_rule(int n, real a, real b, std::vector<real> &x, std::vector<real> &
 
 // Collapsed rule on the reference triangle: Gauss-Legendre in alpha, Gauss-Jacobi
 // (1,0) in beta; r = (1+alpha)(1-beta)/4, s = (1+beta)/2, weight wa*wb/8.
-// Point index = ib*n + ia.
-void collapsed_rule(int n, std::vector<real> &r, std::vector<real> &s, std::vector<real> &w) {
+// Point index = ib*n + ia.  The 1D nodes are rounded to double (xa, xb hold the
+// rounded values); the points r, s are the exact images of the rounded nodes
+// (extended precision), where every volume table is evaluated, and are stored
+// rounded to double.
+void collapsed_rule(int n, std::vector<real> &r, std::vector<real> &s, std::vector<real> &w,
+                    std::vector<real> *xa_out = nullptr, std::vector<real> *xb_out = nullptr,
+                    std::vector<real> *wa_out = nullptr, std::vector<real> *wb_out = nullptr) {
   std::vector<real> xa, wa, xb, wb;
   gauss_rule(n, 0.0L, 0.0L, xa, wa);
   gauss_rule(n, 1.0L, 0.0L, xb, wb);
+  for (auto &v : xa) v = (real)(double)v;
+  for (auto &v : xb) v = (real)(double)v;
   r.resize(n * n); s.resize(n * n); w.resize(n * n);
   for (int ib = 0; ib < n; ++ib)
     for (int ia = 0; ia < n; ++ia) {
@@ -145,6 +152,10 @@ void collapsed_rule(int n, std::vector<real> &r, std::vector<real> &s, std::vect
       s[k] = 0.5L * (1.0L + xb[ib]);
       w[k] = 0.125L * wa[ia] * wb[ib];
     }
+  if (xa_out) *xa_out = xa;
+  if (xb_out) *xb_out = xb;
+  if (wa_out) *wa_out = wa;
+  if (wb_out) *wb_out = wb;
 }
 
 // ---------------------------------------------------------------------------
@@ -214,8 +225,6 @@ void face_point(int q, real xi_, real *r, real *s) {
   *s = (real)(0.5 * (1.0 - xi) * V[q][1] + 0.5 * (1.0 + xi) * V[q1][1]);
 }
 
-// a volume point as stored (rounded to double)
-inline real stored(real v) { return (real)(double)v; }
 
 bool supported(int p, int ne) {
   if (p < 1 || p > dg::PMAX) return false;
@@ -291,8 +300,8 @@ extern "C" dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s,
     if (vol_r) vol_r[k] = (double)r[k];
     if (vol_s) vol_s[k] = (double)s[k];
     if (vol_w) vol_w[k] = (double)w[k];
-    dubiner(p, stored(r[k]), stored(s[k]), phi ? phi + k * np : nullptr,
-            dphi_r ? dphi_r + k * np : nullptr, dphi_s ? dphi_s + k * np : nullptr);
+    dubiner(p, r[k], s[k], phi ? phi + k * np : nullptr, dphi_r ? dphi_r + k * np : nullptr,
+            dphi_s ? dphi_s + k * np : nullptr);
   }
   for (int k = 0; k < ne; ++k) {
     if (edge_x) edge_x[k] = (double)ex[k];
@@ -369,11 +378,11 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
 
   // --- tables ----------------------------------------------------------------
   const int np = (p + 1) * (p + 2) / 2, nd = p + 1, nq = nd * nd, nf = 3 * ne;
-  std::vector<real> r, s, w, ex, ew;
-  collapsed_rule(nd, r, s, w);
+  std::vector<real> r, s, w, ex, ew, xa, xb, wa_, wb_;
+  collapsed_rule(nd, r, s, w, &xa, &xb, &wa_, &wb_);
   gauss_rule(ne, 0.0L, 0.0L, ex, ew);
   std::vector<double> phi(nq * np), dr(nq * np), ds(nq * np), phif(nf * np);
-  for (int k = 0; k < nq; ++k) dubiner(p, stored(r[k]), stored(s[k]), &phi[k * np], &dr[k * np], &ds[k * np]);
+  for (int k = 0; k < nq; ++k) dubiner(p, r[k], s[k], &phi[k * np], &dr[k * np], &ds[k * np]);
   for (int q = 0; q < 3; ++q)
     for (int k = 0; k < ne; ++k) {
       real rr, ss;
@@ -384,6 +393,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   auto take = [&](size_t n) { size_t o = off; off += (n + 3) & ~size_t(3); return o; };
   size_t oBvT = take(np * nq), oDr = take(nq * np), oDs = take(nq * np), oLf = take(nf * np),
          oBfT = take(np * nf), oPw = take(nq * np), oVr = take(nq), oVs = take(nq);
+  size_t oSPa = take(nd * nd), oSdPa = take(nd * nd), oSChi = take(np * nd), oSdChi = take(np * nd),
+         oSK = take(3 * nq);
   std::vector<double> tb(off, 0.0);
   for (int k = 0; k < nq; ++k)
     for (int j = 0; j < np; ++j) {
@@ -400,6 +411,32 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
         tb[oBfT + j * nf + qk] = phif[qk * np + j];
       }
   for (int k = 0; k < nq; ++k) { tb[oVr + k] = (double)r[k]; tb[oVs + k] = (double)s[k]; }
+  // sum-factorisation tables
+  for (int a = 0; a < nd; ++a)
+    for (int ia = 0; ia < nd; ++ia) {
+      tb[oSPa + a * nd + ia] = (double)jacobi_p(a, 0, 0, xa[ia]);
+      tb[oSdPa + a * nd + ia] = (double)jacobi_dp(a, 0, 0, xa[ia]);
+    }
+  for (int j = 0; j < np; ++j) {
+    int a, b;
+    mode_ab(j, &a, &b);
+    real N = std::sqrt(2.0L * (2 * a + 1) * (a + b + 1));
+    for (int ib = 0; ib < nd; ++ib) {
+      real be = xb[ib], h = 0.5L * (1.0L - be);
+      real Pb = jacobi_p(b, 2 * a + 1, 0, be), dPb = jacobi_dp(b, 2 * a + 1, 0, be);
+      real ha = std::pow(h, (real)a), ha1 = a > 0 ? std::pow(h, (real)(a - 1)) : 0.0L;
+      tb[oSChi + j * nd + ib] = (double)(N * ha * Pb);
+      tb[oSdChi + j * nd + ib] = (double)(N * (-0.5L * a * ha1 * Pb + ha * dPb));
+    }
+  }
+  for (int ib = 0; ib < nd; ++ib)
+    for (int ia = 0; ia < nd; ++ia) {
+      int k = ib * nd + ia;
+      real oms = 0.5L * (1.0L - xb[ib]);           // 1 - s
+      tb[oSK + k] = (double)(2.0L * w[k] / oms);
+      tb[oSK + nq + k] = (double)(w[k] * (1.0L + xa[ia]) / oms);
+      tb[oSK + 2 * nq + k] = (double)(2.0L * w[k]);
+    }
 
   // --- device upload ---------------------------------------------------------
   dg_mesh *m = new (std::nothrow) dg_mesh();
@@ -442,6 +479,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   double *T = m->table_block;
   m->tab.BvT = T + oBvT; m->tab.Dr = T + oDr; m->tab.Ds = T + oDs; m->tab.Lf = T + oLf;
   m->tab.BfT = T + oBfT; m->tab.Pw = T + oPw; m->tab.vr = T + oVr; m->tab.vs = T + oVs;
+  m->tab.SPa = T + oSPa; m->tab.SdPa = T + oSdPa; m->tab.SChi = T + oSChi; m->tab.SdChi = T + oSdChi;
+  m->tab.SK = T + oSK;
   cudaError_t ce;
   if ((ce = cudaMemcpy(m->geo, geo.data(), sizeof(double) * N * GEO, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->xy, xy, sizeof(double) * N * 6, cudaMemcpyHostToDevice)) != cudaSuccess ||
