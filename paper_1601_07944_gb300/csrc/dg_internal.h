@@ -101,6 +101,7 @@ int launch_element_tc(const dg_mesh *m, int split3, const double *c, const doubl
                       double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,
                       void *stream);
 int tc_smem_bytes(int p, int ne, int split3);
+int launch_convert_check(int n, unsigned long long *bad, void *stream);
 int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
 int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);

@@ -184,7 +184,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     for (int i = tid; i < EB * M * NP; i += kTcThreads) sC[i] = i < ecount * M * NP ? src[i] : 0.0;
     for (int i = tid; i < EB * 4; i += kTcThreads) {
       const int el = i >> 2;
-      sJ[i] = el < ecount ? (float)geo[(size_t)(e0 + el) * GEO + (i & 3)] : 0.0f;
+      sJ[i] = el < ecount ? tc::f64_to_f32(geo[(size_t)(e0 + el) * GEO + (i & 3)]) : 0.0f;
     }
     for (int i = tid; i < EB * NF; i += kTcThreads) {
       const int el = i / NF, qk = i - el * NF;
@@ -194,18 +194,18 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
         const int ef = elem_face[(size_t)(e0 + el) * 3 + q];
         const int f = ef >> 1, side = ef & 1;
         const double *fp = fhat + ((size_t)f * NE + (side ? NE - 1 - k : k)) * M;
-        const double sg = side ? 1.0 : -1.0;
 #pragma unroll
-        for (int m = 0; m < M; ++m) v[m] = sg * fp[m];
+        for (int m = 0; m < M; ++m) v[m] = side ? fp[m] : tc::neg_bits(fp[m]);
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) sF[i * M + m] = v[m];
     }
     __syncthreads();
     // ---- operands of GEMM 1 (this thread's row) and the lift columns of GEMM 2 ----
-    for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? (float)sC[(rel * M + rm) * NP + k] : 0.0f);
+    for (int k = 0; k < K1; ++k)
+      put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(sC[(rel * M + rm) * NP + k]) : 0.0f);
     for (int qk = 2 * NQ; qk < K2; ++qk) {
-      const float v = qk < 2 * NQ + NF ? (float)sF[(rel * NF + (qk - 2 * NQ)) * M + rm] : 0.0f;
+      const float v = qk < 2 * NQ + NF ? tc::f64_to_f32(sF[(rel * NF + (qk - 2 * NQ)) * M + rm]) : 0.0f;
       put<X3>(A2, T::A2P, row, qk, K2, v);
     }
     tc::fence_proxy_async();
@@ -271,24 +271,26 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
         double s0 = 0.0;                       // mean mode: lift in float64
 #pragma unroll
         for (int qk = 0; qk < NF; ++qk) s0 += sL0[qk] * sF[(rel * NF + qk) * M + rm];
+        if (mode == 0) {
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          const double R = (j == 0 ? s0 : (double)v[j]) * inv;
-          double val;
-          if (mode == 0) {
-            val = R;
-          } else {
-            val = b0 * (cr[j] + dt * R);
-            if (a0 != 0.0) val = a0 * u0[(e * M + rm) * NP + j] + val;
+          for (int j = 0; j < NP; ++j) cr[j] = (j == 0 ? s0 : tc::f32_to_f64(v[j])) * inv;
+        } else {
+          // b0 (c + dt R) + a0 u0 with R = D / det J, as b0 c + a0 u0 + (b0 dt / det J) D
+          const double kap = b0 * dt * inv;
+          const double *u0r = u0 + (e * M + rm) * NP;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            double t = b0 * cr[j];
+            if (a0 != 0.0) t = fma(a0, u0r[j], t);
+            cr[j] = fma(kap, j == 0 ? s0 : tc::f32_to_f64(v[j]), t);
           }
-          cr[j] = val;
         }
       } else {
 #pragma unroll
         for (int j = 0; j < NP; ++j) cr[j] = 0.0;
       }
       if (trace_out)
-        for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? (float)cr[k] : 0.0f);
+        for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cr[k]) : 0.0f);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -312,7 +314,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
         float v[N4];
         tmem_row<N4>(trow, v);
 #pragma unroll
-        for (int qk = 0; qk < NF; ++qk) sF[(rel * NF + qk) * M + rm] = (double)v[qk];
+        for (int qk = 0; qk < NF; ++qk) sF[(rel * NF + qk) * M + rm] = tc::f32_to_f64(v[qk]);
       }
       tc::fence_before_sync();
       __syncthreads();
@@ -342,11 +344,19 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, dou
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element_tc<P, NE, X3>, kTcThreads, T::SMEM);
-  if (e != cudaSuccess) return (int)e;
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 512 / kTmemCols) per_sm = 512 / kTmemCols;      // TMEM: 512 columns per SM
+  // CTAs per SM from the shared memory each needs (the occupancy query
+  // under-reports for this kernel), at most 8 (TMEM: 512 columns per SM)
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int smem_sm = 0, reserved = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device);
+    if (e != cudaSuccess) return (int)e;
+    per_sm = smem_sm / (T::SMEM + reserved);
+    if (per_sm > 512 / kTmemCols) per_sm = 512 / kTmemCols;
+    if (per_sm < 1) per_sm = 1;
+  }
   const int ntiles = (int)((m->N + T::EB - 1) / T::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
   k_element_tc<P, NE, X3><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face,
@@ -369,7 +379,34 @@ int dispatch_tc(const dg_mesh *m, const double *c, const double *u0, double *out
   return (int)cudaErrorInvalidValue;
 }
 
+// Self-check of the integer float64 <-> float32 conversions against the hardware
+// conversions on n values spread over the float32 normal range (both signs, with
+// rounding ties and exact zeros among them).
+__global__ void k_convert_check(int n, unsigned long long *bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // a deterministic spread of bit patterns: exponent in [-120, 120], random mantissa
+  unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+  z ^= z >> 31; z *= 0xBF58476D1CE4E5B9ull; z ^= z >> 29;
+  const int ex = (int)((z >> 52) % 241) - 120;
+  unsigned long long mant = z & 0xFFFFFFFFFFFFFull;
+  if ((i & 15) == 3) mant = (mant & ~0x1FFFFFFFull) | 0x10000000ull;   // exact float32 rounding tie
+  unsigned long long bits = ((unsigned long long)(ex + 1023) << 52) | mant;
+  if (i & 1) bits |= 0x8000000000000000ull;
+  double x = __longlong_as_double((long long)bits);
+  if ((i & 255) == 7) x = (i & 512) ? -0.0 : 0.0;
+  const float f_hw = (float)x, f_int = tc::f64_to_f32(x);
+  const double d_hw = (double)f_hw, d_int = tc::f32_to_f64(f_hw);
+  if (__float_as_uint(f_hw) != __float_as_uint(f_int)) atomicAdd(bad, 1ull);
+  if (__double_as_longlong(d_hw) != __double_as_longlong(d_int)) atomicAdd(bad + 1, 1ull);
+}
+
 }  // namespace
+
+int launch_convert_check(int n, unsigned long long *bad, void *stream) {
+  k_convert_check<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, bad);
+  return (int)cudaGetLastError();
+}
 
 int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
                       double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,

@@ -122,5 +122,42 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// float32 -> float64 from the bit pattern (exact), with integer instructions only.
+// Zeros and float32 subnormals map to signed zero; non-finite values keep their
+// class.  (The float64 pipe of this GPU is narrow; conversions through it would
+// compete with the stage update.)
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint32_t sign = b & 0x80000000u;
+  uint32_t hi = sign, lo = 0u;
+  if (e != 0u) {
+    const uint32_t e64 = e == 0xFFu ? 0x7FFu : e + 896u;
+    hi = sign | (e64 << 20) | ((b & 0x7FFFFFu) >> 3);
+    lo = b << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// float64 -> float32, round to nearest even, from the bit pattern with integer
+// instructions only.  Magnitudes below the float32 normal range flush to signed
+// zero; above it, to infinity.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 896;        // float32 biased exponent
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  uint32_t f = ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const uint32_t rnd = (lo >> 28) & 1u, sticky = (lo & 0x0FFFFFFFu) != 0u, lsb = f & 1u;
+  f += rnd & (sticky | lsb);                              // a carry rolls into the exponent
+  return __uint_as_float(sign | f);
+}
+
+// -x for a float64 by flipping the sign bit (integer instruction)
+__device__ __forceinline__ double neg_bits(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
 }  // namespace tc
 }  // namespace dg

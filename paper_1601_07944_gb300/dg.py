@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
-           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc")
+           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         "dg_probe_fma_rate": [P, P, P],
         "dg_device_status": [P, P],
         "dg_rhs_noalloc": [P, P, P, I, P],
+        "dg_self_test": [P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -125,6 +126,14 @@ def probe_fma_rate(stream=None):
     a = ctypes.c_double(); b = ctypes.c_double()
     _check(load().dg_probe_fma_rate(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
     return a.value, b.value
+
+
+def self_test(stream=None):
+    """(float64->float32, float32->float64) bit mismatches of the integer
+    conversions against the hardware's, over 2^20 values."""
+    out = np.zeros(2, dtype=np.int64)
+    _check(load().dg_self_test(_np_ptr(out), _stream_ptr(stream)))
+    return int(out[0]), int(out[1])
 
 
 def host_tables(p: int, ne: int = 0):

@@ -41,6 +41,10 @@ def _host(t):
     return t.cpu().numpy()
 
 
+def test_integer_conversions_match_hardware(dgmod):
+    assert dgmod.self_test() == (0, 0)
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
 @pytest.mark.parametrize("n", [6, 16])
 @pytest.mark.parametrize("p,ne", CASES)
