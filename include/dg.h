@@ -205,13 +205,15 @@ dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stre
  * The record is cleared.  Synchronous. */
 dg_status dg_device_status(dg_mesh *mesh, void *stream);
 
-/* Device self-check of the integer float64 <-> float32 conversions the
- * mixed-precision kernels use instead of the float64 pipe: on 2^20 values over the
- * float32 normal range (both signs, exact rounding ties, zeros) it counts the
- * results that differ bit for bit from the hardware conversions:
- * mismatches[0] for float64 -> float32 (round to nearest even), mismatches[1] for
- * float32 -> float64.  HOST int64_t[2].  Synchronous; allocates 16 bytes. */
-dg_status dg_self_test(int64_t mismatches[2], void *stream);
+/* Device self-check of two arithmetic helpers the kernels use to spare the
+ * narrow float64 pipe: on 2^20 values over the float32 normal range (both signs,
+ * exact rounding ties, zeros) it counts
+ *   mismatches[0]: integer float64 -> float32 conversions (round to nearest even)
+ *                  that differ bit for bit from the hardware conversion,
+ *   mismatches[1]: integer float32 -> float64 conversions that differ,
+ *   mismatches[2]: Newton-refined reciprocals more than 1 ulp from 1/x.
+ * HOST int64_t[3].  Synchronous; allocates 24 bytes. */
+dg_status dg_self_test(int64_t mismatches[3], void *stream);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char *dg_last_error(void);

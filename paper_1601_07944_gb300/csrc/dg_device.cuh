@@ -9,8 +9,12 @@
 #include <cuda_runtime.h>
 
 #include "dg_internal.h"
+#include "dg_tcgen05.cuh"
 
 namespace dg {
+
+__device__ __forceinline__ float f64_to_f32_dev(double x) { return tc::f64_to_f32(x); }
+__device__ __forceinline__ double f32_to_f64_dev(float f) { return tc::f32_to_f64(f); }
 
 template <int P, int NE>
 struct Cfg {
@@ -26,11 +30,25 @@ struct Cfg {
 
 constexpr int kThreads = 256;
 
+// 1/x for a positive normal x: Newton-Raphson refinement r <- r + r (1 - x r) of
+// the hardware's approximate float64 reciprocal (rcp.approx.ftz.f64); each step
+// doubles the number of correct bits, two steps reach double precision
+// (checked against 1/x by dg_self_test).
+__device__ __forceinline__ double recip(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+
 // Euler flux (Eq. euler) contracted with J^tau: the reference flux components
 // G_r, G_s of the four conserved variables at one point.
 __device__ __forceinline__ void ref_flux(const double U[M], const double *jt, double gamma,
                                          double Gr[M], double Gs[M]) {
-  const double rho = U[0], inv = 1.0 / rho;
+  const double inv = recip(U[0]);
   const double u = U[1] * inv, v = U[2] * inv;
   const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
   double F1[M], F2[M];
@@ -45,34 +63,45 @@ __device__ __forceinline__ void ref_flux(const double U[M], const double *jt, do
   }
 }
 
-// Local Lax-Friedrichs flux F_hat(Ul, Ur, n).  Written so that swapping the two
-// sides and negating n negates the result bit for bit.
-__device__ __forceinline__ void lax_friedrichs(const double ul[M], const double ur[M], double nx,
-                                               double ny, double gamma, double out[M]) {
-  const double il = 1.0 / ul[0], ir = 1.0 / ur[0];
+// Local Lax-Friedrichs flux, scaled: out = h (F(Ul).n + F(Ur).n - alpha (Ur - Ul)),
+// alpha = max(|v_l.n| + c_l, |v_r.n| + c_r).  With h = l/2 this is l F_hat.
+// FAST_ALPHA (mixed-precision modes only): alpha, a dissipation coefficient, is
+// formed in float32 from the float64 pressure, density and normal velocity; the
+// flux itself stays float64.
+template <bool FAST_ALPHA = false>
+__device__ __forceinline__ void lax_friedrichs_scaled(const double ul[M], const double ur[M], double nx,
+                                                      double ny, double gamma, double h, double out[M]) {
+  const double il = recip(ul[0]), ir = recip(ur[0]);
   const double uL = ul[1] * il, vL = ul[2] * il, uR = ur[1] * ir, vR = ur[2] * ir;
   const double pL = (gamma - 1.0) * (ul[3] - 0.5 * (ul[1] * uL + ul[2] * vL));
   const double pR = (gamma - 1.0) * (ur[3] - 0.5 * (ur[1] * uR + ur[2] * vR));
   const double vnL = uL * nx + vL * ny, vnR = uR * nx + vR * ny;
-  const double sL = fabs(vnL) + sqrt(gamma * pL * il);
-  const double sR = fabs(vnR) + sqrt(gamma * pR * ir);
-  const double a = fmax(sL, sR);
+  double a;
+  if (FAST_ALPHA) {
+    const float g = (float)gamma;
+    const float sL = fabsf(f64_to_f32_dev(vnL)) + sqrtf(g * f64_to_f32_dev(pL) * f64_to_f32_dev(il));
+    const float sR = fabsf(f64_to_f32_dev(vnR)) + sqrtf(g * f64_to_f32_dev(pR) * f64_to_f32_dev(ir));
+    a = f32_to_f64_dev(fmaxf(sL, sR));
+  } else {
+    const double sL = fabs(vnL) + sqrt(gamma * pL * il);
+    const double sR = fabs(vnR) + sqrt(gamma * pR * ir);
+    a = fmax(sL, sR);
+  }
   double fL[M], fR[M];
   fL[0] = ul[0] * vnL;              fR[0] = ur[0] * vnR;
   fL[1] = ul[1] * vnL + pL * nx;    fR[1] = ur[1] * vnR + pR * nx;
   fL[2] = ul[2] * vnL + pL * ny;    fR[2] = ur[2] * vnR + pR * ny;
   fL[3] = (ul[3] + pL) * vnL;       fR[3] = (ur[3] + pR) * vnR;
 #pragma unroll
-  for (int m = 0; m < M; ++m) out[m] = 0.5 * (fL[m] + fR[m]) - 0.5 * a * (ur[m] - ul[m]);
+  for (int m = 0; m < M; ++m) out[m] = h * fma(-a, ur[m] - ul[m], fL[m] + fR[m]);
 }
-
 
 // out = (d(F(U).n)/dU)^T b for the Euler flux F.n = (rho vn, mx vn + p nx,
 // my vn + p ny, (E+p) vn), using d vn/dU = (-vn, nx, ny, 0)/rho and
 // dp/dU = (gamma-1) (|v|^2/2, -u, -v, 1).
 __device__ __forceinline__ void flux_jac_t(const double U[M], double nx, double ny, double gamma,
                                            const double b[M], double out[M]) {
-  const double inv = 1.0 / U[0];
+  const double inv = recip(U[0]);
   const double u = U[1] * inv, v = U[2] * inv;
   const double q2 = u * u + v * v;
   const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * q2);
@@ -88,7 +117,7 @@ __device__ __forceinline__ void flux_jac_t(const double U[M], double nx, double 
 // Wave speed s = |v.n| + c and its gradient (d|x|/dx = sign(x), sign(0) = 0).
 __device__ __forceinline__ double wave_speed_grad(const double U[M], double nx, double ny,
                                                   double gamma, double ds[M]) {
-  const double inv = 1.0 / U[0];
+  const double inv = recip(U[0]);
   const double u = U[1] * inv, v = U[2] * inv;
   const double q2 = u * u + v * v;
   const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * q2);

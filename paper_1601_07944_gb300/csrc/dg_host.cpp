@@ -545,8 +545,9 @@ extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision
   if (st != DG_OK) return st;
   DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return dg::launch_traces(m, c, m->trace, stream); }),
           "dg_rhs traces");
-  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return dg::launch_face_flux(m, m->trace, m->fhat, stream); }),
-          "dg_rhs edge flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] {
+            return dg::launch_face_flux(m, m->trace, m->fhat, stream, prec != DG_FP64);
+          }), "dg_rhs edge flux");
   DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
             return launch_elem(m, prec, c, nullptr, r, nullptr, m->fhat, 0.0, 0.0, 0.0, 0, stream);
           }), "dg_rhs element");
@@ -557,8 +558,9 @@ extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision
 static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, dg_precision prec, void *stream) {
   using namespace dg;
   auto face = [&](const char *what) -> dg_status {
-    DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
-            what);
+    DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] {
+              return launch_face_flux(m, m->trace, m->fhat, stream, prec != DG_FP64);
+            }), what);
     return DG_OK;
   };
   auto elem = [&](const double *cin, const double *u0, double *out, double a0, double b0,
@@ -750,12 +752,12 @@ extern "C" dg_status dg_device_status(dg_mesh *m, void *stream) {
   return DG_OK;
 }
 
-extern "C" dg_status dg_self_test(int64_t mismatches[2], void *stream) {
+extern "C" dg_status dg_self_test(int64_t mismatches[3], void *stream) {
   if (!mismatches) return fail(DG_EINVAL, "dg_self_test: null argument");
   unsigned long long *bad = nullptr;
-  DG_CUDA(cudaMalloc(&bad, 2 * sizeof(unsigned long long)), "dg_self_test alloc");
+  DG_CUDA(cudaMalloc(&bad, 3 * sizeof(unsigned long long)), "dg_self_test alloc");
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof h, s);
   if (e == cudaSuccess) e = (cudaError_t)dg::launch_convert_check(1 << 20, bad, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, bad, sizeof h, cudaMemcpyDeviceToHost, s);
@@ -764,5 +766,6 @@ extern "C" dg_status dg_self_test(int64_t mismatches[2], void *stream) {
   if (e != cudaSuccess) return cuda_fail(e, "dg_self_test");
   mismatches[0] = (int64_t)h[0];
   mismatches[1] = (int64_t)h[1];
+  mismatches[2] = (int64_t)h[2];
   return DG_OK;
 }

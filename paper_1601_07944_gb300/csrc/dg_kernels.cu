@@ -72,7 +72,7 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
 // ---------------------------------------------------------------------------
 // edge flux: fhat[f][k][m] = l_f * F_hat(U_l(r_{L,k}), U_r(r_{R,NE-1-k}), n_f)
 // ---------------------------------------------------------------------------
-template <int NE>
+template <int NE, bool FAST_ALPHA>
 __global__ void __launch_bounds__(kThreads)
 k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
        const FaceGeo *__restrict__ fg, int64_t F, double gamma) {
@@ -88,10 +88,11 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
   double ul[M], ur[M], Fh[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
-  lax_friedrichs(ul, ur, g.nx, g.ny, gamma, Fh);
+  // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
+  lax_friedrichs_scaled<FAST_ALPHA>(ul, ur, g.nx, g.ny, gamma, 0.5 * g.hl, Fh);
   double *dst = fhat + (size_t)i * M;
 #pragma unroll
-  for (int m = 0; m < M; ++m) dst[m] = g.hl * Fh[m];
+  for (int m = 0; m < M; ++m) dst[m] = Fh[m];
 }
 
 // ---------------------------------------------------------------------------
@@ -357,7 +358,7 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
         // (Ha, Hb) = (ka G_r + kb G_s, kc G_s) with (G_r, G_s) = J^tau (F1, F2)
         const double A1 = ka * g[0] + kb * g[2], A2 = ka * g[1] + kb * g[3];
         const double B1 = kc * g[2], B2 = kc * g[3];
-        const double rho = U[0], inv = 1.0 / rho;
+        const double inv = recip(U[0]);
         const double u = U[1] * inv, v = U[2] * inv;
         const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
         double F1[M], F2[M];
@@ -646,18 +647,22 @@ int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream
   return (int)cudaErrorInvalidValue;
 }
 
-int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream) {
+int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream, bool fast_alpha) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = m->F * m->ne;
   const int grid = (int)((n + kThreads - 1) / kThreads);
+#define FACE(NE)                                                                                      \
+  (fast_alpha ? (k_face<NE, true><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma), 0) \
+              : (k_face<NE, false><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma), 0))
   switch (m->ne) {
-    case 2: k_face<2><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
-    case 3: k_face<3><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
-    case 4: k_face<4><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
-    case 5: k_face<5><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
-    case 6: k_face<6><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma); break;
+    case 2: FACE(2); break;
+    case 3: FACE(3); break;
+    case 4: FACE(4); break;
+    case 5: FACE(5); break;
+    case 6: FACE(6); break;
     default: return (int)cudaErrorInvalidValue;
   }
+#undef FACE
   return (int)cudaGetLastError();
 }
 

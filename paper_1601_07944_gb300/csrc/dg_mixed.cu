@@ -399,6 +399,13 @@ __global__ void k_convert_check(int n, unsigned long long *bad) {
   const double d_hw = (double)f_hw, d_int = tc::f32_to_f64(f_hw);
   if (__float_as_uint(f_hw) != __float_as_uint(f_int)) atomicAdd(bad, 1ull);
   if (__double_as_longlong(d_hw) != __double_as_longlong(d_int)) atomicAdd(bad + 1, 1ull);
+  // Newton-refined reciprocal against the correctly rounded 1/x: at most 1 ulp apart
+  const double ax = fabs(x);
+  if (ax != 0.0) {
+    const long long q = __double_as_longlong(1.0 / ax), r = __double_as_longlong(recip(ax));
+    const long long d = q > r ? q - r : r - q;
+    if (d > 1) atomicAdd(bad + 2, 1ull);
+  }
 }
 
 }  // namespace

@@ -70,7 +70,7 @@ extern "C" dg_status dg_rhs_noalloc(dg_mesh *m, const double *c, double *r, dg_p
   // array needs clearing between calls.
   double *trace = scratch, *fhat = scratch + n_trace;
   if ((e = (cudaError_t)dg::launch_traces(m, c, trace, stream)) != cudaSuccess ||
-      (e = (cudaError_t)dg::launch_face_flux(m, trace, fhat, stream)) != cudaSuccess)
+      (e = (cudaError_t)dg::launch_face_flux(m, trace, fhat, stream, prec != DG_FP64)) != cudaSuccess)
     return dg::set_error(DG_ECUDA, "dg_rhs_noalloc: %s", cudaGetErrorString(e));
   if (prec == DG_FP64)
     e = (cudaError_t)dg::launch_element(m, c, nullptr, r, nullptr, fhat, 0.0, 0.0, 0.0, 0, stream);

@@ -6,8 +6,9 @@ terms, so its error is measured against the size of those terms (the oracle's
 volume term V / det J):
     3xTF32: ||R_mixed - R|| <= 2e-6 (||R|| + ||V||)   (FP32-level arithmetic)
     1xTF32: ||R_mixed - R|| <= 4e-3 (||R|| + ||V||)   (10-bit TF32 mantissa)
-The mean mode stays float64 in both modes, so the conserved totals drift only at
-float64 rounding.
+The mean mode is lifted in float64 from the float64 edge flux in both modes (only
+the flux's dissipation coefficient alpha is formed in float32), so the conserved
+totals drift only at float64 rounding.
 """
 import numpy as np
 import pytest
@@ -41,8 +42,8 @@ def _host(t):
     return t.cpu().numpy()
 
 
-def test_integer_conversions_match_hardware(dgmod):
-    assert dgmod.self_test() == (0, 0)
+def test_arithmetic_helpers_match_hardware(dgmod):
+    assert dgmod.self_test() == (0, 0, 0)
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
@@ -58,8 +59,9 @@ def test_mixed_rhs_vs_oracle(dgmod, oracle_mod, p, ne, n, prec):
     m.device_status()
     err = np.linalg.norm(got - ref)
     assert err <= TOL[prec] * (np.linalg.norm(ref) + np.linalg.norm(vol)), err / np.linalg.norm(ref)
-    # the mean mode is lifted in float64 from the float64 edge fluxes
-    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-12 * np.abs(ref[:, :, 0]).max()
+    # the mean mode is lifted in float64 from the float64 edge fluxes; only the
+    # dissipation coefficient alpha is rounded to float32, far below TF32 error
+    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-6 * np.abs(ref[:, :, 0]).max()
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
