@@ -23,9 +23,7 @@ struct Cfg {
   static constexpr int NQ = ND * ND;
   static constexpr int NF = 3 * NE;
   static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);   // elements per tile
-  static constexpr int TAB = NP * NQ * 3 + NF * NP * 2;          // table doubles
-  static constexpr int TILE = EB * (M * NP * 2 + NQ * 8 + NF * M);
-  static constexpr int SMEM = (TAB + TILE) * 8;
+  static constexpr int TAB = NP * NQ * 3 + NF * NP * 2;          // direct tables, doubles
 };
 
 constexpr int kThreads = 256;
@@ -43,25 +41,6 @@ __device__ __forceinline__ double recip(double x) {
   return fma(r, e, r);
 }
 
-
-// Euler flux (Eq. euler) contracted with J^tau: the reference flux components
-// G_r, G_s of the four conserved variables at one point.
-__device__ __forceinline__ void ref_flux(const double U[M], const double *jt, double gamma,
-                                         double Gr[M], double Gs[M]) {
-  const double inv = recip(U[0]);
-  const double u = U[1] * inv, v = U[2] * inv;
-  const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
-  double F1[M], F2[M];
-  F1[0] = U[1];          F2[0] = U[2];
-  F1[1] = U[1] * u + p;  F2[1] = U[1] * v;
-  F1[2] = U[2] * u;      F2[2] = U[2] * v + p;
-  F1[3] = (U[3] + p) * u; F2[3] = (U[3] + p) * v;
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    Gr[m] = jt[0] * F1[m] + jt[1] * F2[m];
-    Gs[m] = jt[2] * F1[m] + jt[3] * F2[m];
-  }
-}
 
 // Local Lax-Friedrichs flux, scaled: out = h (F(Ul).n + F(Ur).n - alpha (Ur - Ul)),
 // alpha = max(|v_l.n| + c_l, |v_r.n| + c_r).  With h = l/2 this is l F_hat.

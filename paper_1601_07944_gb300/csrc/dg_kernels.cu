@@ -9,14 +9,15 @@
  *              right element's at the reversed point (Eq. edgeint), evaluates the
  *              local Lax-Friedrichs flux once per edge and stores it scaled by the
  *              edge Jacobian l = |edge|/2 (Eq. len).
- *   k_element  one CTA per tile of EB elements, staged through shared memory:
+ *   k_element_sf  one CTA per tile of EB elements, staged through shared memory:
  *              interpolation to the volume points, Euler flux and the reference
  *              flux G = J^tau F, projection onto the weighted basis gradients
- *              (Eq. volume, Algorithm 1), lifting of the three edge fluxes
- *              (Algorithm 3), scaling by 1/det J (Eq. 2ddg0), the Runge-Kutta
- *              stage update, and, for the next stage, the edge traces of the new
- *              state.  Writing the traces from the element that owns the state
- *              replaces a separate pass over the coefficients.
+ *              (Eq. volume, Algorithm 1) -- both sum-factorised on the collapsed
+ *              volume grid -- lifting of the three edge fluxes (Algorithm 3),
+ *              scaling by 1/det J (Eq. 2ddg0), the Runge-Kutta stage update, and,
+ *              for the next stage, the edge traces of the new state.  Writing the
+ *              traces from the element that owns the state replaces a separate
+ *              pass over the coefficients.
  *
  * The paper's per-edge temporaries (rhs_surface_left/right) become one flux
  * block per edge; each element gathers its three blocks, so no atomics are used
@@ -96,153 +97,6 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
 }
 
 // ---------------------------------------------------------------------------
-// element kernel: residual, stage update and next traces
-// ---------------------------------------------------------------------------
-template <int P, int NE>
-__global__ void __launch_bounds__(kThreads)
-k_element(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
-          const double *__restrict__ fhat, const double *__restrict__ geo,
-          const int32_t *__restrict__ elem_face, DevTables tab, int N, double dt, double a0,
-          double b0, int mode, double gamma) {
-  using C = Cfg<P, NE>;
-  constexpr int NP = C::NP, NQ = C::NQ, NF = C::NF, EB = C::EB;
-  extern __shared__ double smem[];
-  double *sBvT = smem;                 // [NP][NQ]
-  double *sDr = sBvT + NP * NQ;        // [NQ][NP]
-  double *sDs = sDr + NQ * NP;         // [NQ][NP]
-  double *sLf = sDs + NQ * NP;         // [NF][NP]
-  double *sBfT = sLf + NF * NP;        // [NP][NF]
-  double *sC = sBfT + NP * NF;         // [EB][M][NP]  stage input
-  double *sH = sC + EB * M * NP;       // [EB][NQ][8]  w-free reference fluxes G_r, G_s
-  double *sF = sH + EB * NQ * 8;       // [EB][NF][M]  -F_hat_out * l, element's point order
-  double *sO = sF + EB * NF * M;       // [EB][M][NP]  new state
-
-  for (int i = threadIdx.x; i < NP * NQ; i += blockDim.x) {
-    sBvT[i] = tab.BvT[i];
-    sDr[i] = tab.Dr[i];
-    sDs[i] = tab.Ds[i];
-  }
-  for (int i = threadIdx.x; i < NF * NP; i += blockDim.x) {
-    sLf[i] = tab.Lf[i];
-    sBfT[i] = tab.BfT[i];
-  }
-
-  const int ntiles = (N + EB - 1) / EB;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e0 = tile * EB;
-    const int ecount = min(EB, N - e0);
-    __syncthreads();
-    // stage input, coalesced
-    const double *src = c + (size_t)e0 * M * NP;
-    for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x)
-      sC[i] = i < ecount * M * NP ? src[i] : 0.0;
-    // edge fluxes in this element's outward orientation and point order
-    for (int i = threadIdx.x; i < EB * NF; i += blockDim.x) {
-      const int el = i / NF, qk = i - el * NF;
-      double v[M] = {0.0, 0.0, 0.0, 0.0};
-      if (el < ecount) {
-        const int q = qk / NE, k = qk - q * NE;
-        const int ef = elem_face[(size_t)(e0 + el) * 3 + q];
-        const int f = ef >> 1, side = ef & 1;
-        const int kk = side ? NE - 1 - k : k;
-        const double *fp = fhat + ((size_t)f * NE + kk) * M;
-        const double sg = side ? 1.0 : -1.0;    // surface term enters with a minus sign
-#pragma unroll
-        for (int m = 0; m < M; ++m) v[m] = sg * fp[m];
-      }
-#pragma unroll
-      for (int m = 0; m < M; ++m) sF[i * M + m] = v[m];
-    }
-    __syncthreads();
-
-    // volume points: U = sum_j c_j phi_j(r_k); G = J^tau F(U)
-    for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
-      const int el = i / NQ, k = i - el * NQ;
-      double U[M] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const double b = sBvT[j * NQ + k];
-#pragma unroll
-        for (int m = 0; m < M; ++m) U[m] += sC[(el * M + m) * NP + j] * b;
-      }
-      double Gr[M], Gs[M];
-      if (el < ecount) {
-        const double *g = geo + (size_t)(e0 + el) * GEO;
-        const double jt[4] = {g[0], g[1], g[2], g[3]};
-        ref_flux(U, jt, gamma, Gr, Gs);
-      } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) { Gr[m] = 0.0; Gs[m] = 0.0; }
-      }
-      double *h = sH + (size_t)i * 8;
-#pragma unroll
-      for (int m = 0; m < M; ++m) { h[m] = Gr[m]; h[4 + m] = Gs[m]; }
-    }
-    __syncthreads();
-
-    // modes: volume projection + lifted edge fluxes, 1/det J, stage update
-    for (int i = threadIdx.x; i < EB * NP; i += blockDim.x) {
-      const int el = i / NP, j = i - el * NP;
-      double acc[M] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
-      for (int k = 0; k < NQ; ++k) {
-        const double *h = sH + (el * NQ + k) * 8;
-        const double dr = sDr[k * NP + j], ds = sDs[k * NP + j];
-#pragma unroll
-        for (int m = 0; m < M; ++m) acc[m] += h[m] * dr + h[4 + m] * ds;
-      }
-#pragma unroll
-      for (int qk = 0; qk < NF; ++qk) {
-        const double *fv = sF + (el * NF + qk) * M;
-        const double l = sLf[qk * NP + j];
-#pragma unroll
-        for (int m = 0; m < M; ++m) acc[m] += fv[m] * l;
-      }
-      if (el < ecount) {
-        const size_t e = (size_t)(e0 + el);
-        const double inv = geo[e * GEO + 4];
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const size_t idx = (e * M + m) * NP + j;
-          const double R = acc[m] * inv;
-          double v;
-          if (mode == 0) {
-            v = R;
-          } else {
-            const double cj = sC[(el * M + m) * NP + j];
-            v = b0 * (cj + dt * R);
-            if (a0 != 0.0) v = a0 * u0[idx] + v;
-          }
-          out[idx] = v;
-          sO[(el * M + m) * NP + j] = v;
-        }
-      } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) sO[(el * M + m) * NP + j] = 0.0;
-      }
-    }
-
-    if (trace_out) {
-      __syncthreads();
-      for (int i = threadIdx.x; i < ecount * NF; i += blockDim.x) {
-        const int el = i / NF, qk = i - el * NF;
-        double T[M] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          const double b = sBfT[j * NF + qk];
-#pragma unroll
-          for (int m = 0; m < M; ++m) T[m] += sO[(el * M + m) * NP + j] * b;
-        }
-        double *dst = trace_out + ((size_t)(e0 + el) * NF + qk) * M;
-#pragma unroll
-        for (int m = 0; m < M; ++m) dst[m] = T[m];
-      }
-    }
-  }
-}
-
-
-// ---------------------------------------------------------------------------
 // element kernel, sum-factorised volume term (float64 path)
 //
 // The volume rule is a tensor grid in the collapsed coordinates (alpha, beta)
@@ -316,9 +170,8 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
         const int ef = elem_face[(size_t)(e0 + el) * 3 + q];
         const int f = ef >> 1, side = ef & 1;
         const double *fp = fhat + ((size_t)f * NE + (side ? NE - 1 - k : k)) * M;
-        const double sg = side ? 1.0 : -1.0;
 #pragma unroll
-        for (int m = 0; m < M; ++m) v[m] = sg * fp[m];
+        for (int m = 0; m < M; ++m) v[m] = side ? fp[m] : tc::neg_bits(fp[m]);
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) sF[i * M + m] = v[m];
@@ -420,16 +273,19 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
       if (el < ecount) {
         const size_t e = (size_t)(e0 + el);
         const double inv = geo[e * GEO + 4];
+        // stage update b0 (c + dt R) + a0 u0 with R = acc / det J, as
+        // b0 c + a0 u0 + (b0 dt / det J) acc
+        const double kap = b0 * dt * inv;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           const size_t idx = (e * M + m) * NP + j;
-          const double R = acc[m] * inv;
           double v;
           if (mode == 0) {
-            v = R;
+            v = acc[m] * inv;
           } else {
-            v = b0 * (sC[(el * M + m) * NP + j] + dt * R);
-            if (a0 != 0.0) v = a0 * u0[idx] + v;
+            double t = b0 * sC[(el * M + m) * NP + j];
+            if (a0 != 0.0) t = fma(a0, u0[idx], t);
+            v = fma(kap, acc[m], t);
           }
           out[idx] = v;
           nv[m] = v;
@@ -566,31 +422,6 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 // dispatch
 // ---------------------------------------------------------------------------
 template <int P, int NE>
-int run_element(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
-                const double *fhat, double dt, double a0, double b0, int mode, cudaStream_t s) {
-  using C = Cfg<P, NE>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_element<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return (int)e;
-    // all of the SM's unified L1/shared storage as shared memory, so that the
-    // occupancy query and the launch see every CTA that fits
-    e = cudaFuncSetAttribute(k_element<P, NE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return (int)e;
-    attr_set = true;
-  }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element<P, NE>, kThreads, C::SMEM);
-  if (e != cudaSuccess) return (int)e;
-  if (per_sm < 1) per_sm = 1;
-  const int ntiles = (int)((m->N + C::EB - 1) / C::EB);
-  const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_element<P, NE><<<grid, kThreads, C::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
-                                                   (int)m->N, dt, a0, b0, mode, m->gamma);
-  return (int)cudaGetLastError();
-}
-
-template <int P, int NE>
 int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
                    const double *fhat, double dt, double a0, double b0, int mode, cudaStream_t s) {
   using S = SfCfg<P, NE>;
@@ -623,16 +454,6 @@ int run_traces(const dg_mesh *m, const double *c, double *trace, cudaStream_t s)
 }
 
 }  // namespace
-
-int element_smem_bytes(int p, int ne) {
-  if (p == 1 && ne == 2) return Cfg<1, 2>::SMEM;
-  if (p == 2 && ne == 3) return Cfg<2, 3>::SMEM;
-  if (p == 3 && ne == 4) return Cfg<3, 4>::SMEM;
-  if (p == 3 && ne == 3) return Cfg<3, 3>::SMEM;
-  if (p == 4 && ne == 5) return Cfg<4, 5>::SMEM;
-  if (p == 5 && ne == 6) return Cfg<5, 6>::SMEM;
-  return -1;
-}
 
 int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;

@@ -51,16 +51,17 @@ struct Tc {
   static constexpr int oB1 = align1k(oA2 + A2P * NS);
   static constexpr int oB2 = align1k(oB1 + B1P * NS);
   static constexpr int oB4 = align1k(oB2 + B2P * NS);
-  static constexpr int oC = align1k(oB4 + B4P * NS);        // double [EB][M][NP]
-  static constexpr int oF = oC + EB * M * NP * 8;            // double [EB][NF][M]
-  static constexpr int endF = oF + EB * NF * M * 8;
+  static constexpr int endB = align1k(oB4 + B4P * NS);
   static constexpr int SU = EB * NQ * M * 4;                 // float [EB][NQ][M]
   static constexpr bool U_IN_A1 = SU <= A1P * NS;            // reuse GEMM 1's A planes
-  static constexpr int oU = U_IN_A1 ? oA1 : endF;
-  static constexpr int oJ = U_IN_A1 ? endF : endF + SU;      // float [EB][4]  J^tau
+  static constexpr int oU = U_IN_A1 ? oA1 : endB;
+  static constexpr int oJ = U_IN_A1 ? endB : endB + SU;      // float [EB][4]  J^tau
   static constexpr int oL0 = oJ + EB * 16;                   // double [NF]    lift weights of mode 1
   static constexpr int oBar = (oL0 + NF * 8 + 15) / 16 * 16; // mbarrier, TMEM slot
   static constexpr int SMEM = oBar + 16;
+  // the new state and the new traces are staged for coalesced stores in GEMM 2's
+  // A planes, which are free once GEMM 2 has completed
+  static_assert(EB * M * NP * 8 <= A2P * NS && EB * NF * M * 8 <= A2P * NS, "staging");
   static_assert(N1 <= kTmemCols && N2 <= kTmemCols && N4 <= kTmemCols, "TMEM columns");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -98,7 +99,7 @@ __device__ __forceinline__ void tmem_row(uint32_t taddr, float *v) {
   tc::wait_ld();
 }
 
-// float32 reference flux at one point (the same Euler flux as ref_flux)
+// float32 reference flux G = J^tau F at one point (Euler flux, Eq. euler)
 __device__ __forceinline__ void ref_flux_f32(const float U[M], const float *jt, float gamma, float Gr[M],
                                              float Gs[M]) {
   const float inv = 1.0f / U[0];
@@ -127,8 +128,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
   constexpr int K1 = T::K1, N1 = T::N1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char *A1 = sm + T::oA1, *A2 = sm + T::oA2, *B1 = sm + T::oB1, *B2 = sm + T::oB2, *B4 = sm + T::oB4;
-  double *sC = reinterpret_cast<double *>(sm + T::oC);
-  double *sF = reinterpret_cast<double *>(sm + T::oF);
+  double *sStage = reinterpret_cast<double *>(sm + T::oA2);   // after GEMM 2 only
   float *sU = reinterpret_cast<float *>(sm + T::oU);
   float *sJ = reinterpret_cast<float *>(sm + T::oJ);
   double *sL0 = reinterpret_cast<double *>(sm + T::oL0);
@@ -179,35 +179,39 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int e0 = tile * EB;
     const int ecount = min(EB, N - e0);
-    // ---- stage input, J^tau, edge fluxes (element orientation and point order) ----
-    const double *src = c + (size_t)e0 * M * NP;
-    for (int i = tid; i < EB * M * NP; i += kTcThreads) sC[i] = i < ecount * M * NP ? src[i] : 0.0;
+    // ---- J^tau of the tile's elements ----
     for (int i = tid; i < EB * 4; i += kTcThreads) {
       const int el = i >> 2;
       sJ[i] = el < ecount ? tc::f64_to_f32(geo[(size_t)(e0 + el) * GEO + (i & 3)]) : 0.0f;
     }
-    for (int i = tid; i < EB * NF; i += kTcThreads) {
-      const int el = i / NF, qk = i - el * NF;
-      double v[M] = {0.0, 0.0, 0.0, 0.0};
-      if (el < ecount) {
-        const int q = qk / NE, k = qk - q * NE;
-        const int ef = elem_face[(size_t)(e0 + el) * 3 + q];
-        const int f = ef >> 1, side = ef & 1;
-        const double *fp = fhat + ((size_t)f * NE + (side ? NE - 1 - k : k)) * M;
+    // ---- this thread's row: stage input (kept in registers for the update) ----
+    const bool live = rel < ecount;
+    double cr[NP];
+    {
+      const double *src = c + ((size_t)(e0 + rel) * M + rm) * NP;
 #pragma unroll
-        for (int m = 0; m < M; ++m) v[m] = side ? fp[m] : tc::neg_bits(fp[m]);
+      for (int j = 0; j < NP; ++j) cr[j] = live ? src[j] : 0.0;
+    }
+    for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cr[k]) : 0.0f);
+    // ---- its edge fluxes in the element's orientation and point order: the lift
+    // columns of GEMM 2, and the mean mode's lift in float64 ----
+    double s0 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int ef = live ? elem_face[(size_t)(e0 + rel) * 3 + q] : 0;
+      const int f = ef >> 1, side = ef & 1;
+#pragma unroll
+      for (int k = 0; k < NE; ++k) {
+        double v = 0.0;
+        if (live) {
+          const double x = fhat[((size_t)f * NE + (side ? NE - 1 - k : k)) * M + rm];
+          v = side ? x : tc::neg_bits(x);
+        }
+        s0 = fma(sL0[q * NE + k], v, s0);
+        put<X3>(A2, T::A2P, row, 2 * NQ + q * NE + k, K2, tc::f64_to_f32(v));
       }
-#pragma unroll
-      for (int m = 0; m < M; ++m) sF[i * M + m] = v[m];
     }
-    __syncthreads();
-    // ---- operands of GEMM 1 (this thread's row) and the lift columns of GEMM 2 ----
-    for (int k = 0; k < K1; ++k)
-      put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(sC[(rel * M + rm) * NP + k]) : 0.0f);
-    for (int qk = 2 * NQ; qk < K2; ++qk) {
-      const float v = qk < 2 * NQ + NF ? tc::f64_to_f32(sF[(rel * NF + (qk - 2 * NQ)) * M + rm]) : 0.0f;
-      put<X3>(A2, T::A2P, row, qk, K2, v);
-    }
+    for (int qk = 2 * NQ + NF; qk < K2; ++qk) put<X3>(A2, T::A2P, row, qk, K2, 0.0f);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -264,13 +268,9 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     {
       float v[N2];
       tmem_row<N2>(trow, v);
-      double *cr = sC + (rel * M + rm) * NP;
-      if (rel < ecount) {
+      if (live) {
         const size_t e = (size_t)(e0 + rel);
         const double inv = geo[e * GEO + 4];
-        double s0 = 0.0;                       // mean mode: lift in float64
-#pragma unroll
-        for (int qk = 0; qk < NF; ++qk) s0 += sL0[qk] * sF[(rel * NF + qk) * M + rm];
         if (mode == 0) {
 #pragma unroll
           for (int j = 0; j < NP; ++j) cr[j] = (j == 0 ? s0 : tc::f32_to_f64(v[j])) * inv;
@@ -289,6 +289,9 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
 #pragma unroll
         for (int j = 0; j < NP; ++j) cr[j] = 0.0;
       }
+      // GEMM 2 has completed: its A planes stage the new state
+#pragma unroll
+      for (int j = 0; j < NP; ++j) sStage[(rel * M + rm) * NP + j] = cr[j];
       if (trace_out)
         for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cr[k]) : 0.0f);
     }
@@ -298,7 +301,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     tc::fence_after_sync();
     {
       double *dst = out + (size_t)e0 * M * NP;
-      for (int i = tid; i < ecount * M * NP; i += kTcThreads) dst[i] = sC[i];
+      for (int i = tid; i < ecount * M * NP; i += kTcThreads) dst[i] = sStage[i];
     }
     if (trace_out) {
       // ---- GEMM 3: edge traces of the new state ----
@@ -314,13 +317,13 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
         float v[N4];
         tmem_row<N4>(trow, v);
 #pragma unroll
-        for (int qk = 0; qk < NF; ++qk) sF[(rel * NF + qk) * M + rm] = tc::f32_to_f64(v[qk]);
+        for (int qk = 0; qk < NF; ++qk) sStage[(rel * NF + qk) * M + rm] = tc::f32_to_f64(v[qk]);
       }
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
       double *dst = trace_out + (size_t)e0 * NF * M;
-      for (int i = tid; i < ecount * NF * M; i += kTcThreads) dst[i] = sF[i];
+      for (int i = tid; i < ecount * NF * M; i += kTcThreads) dst[i] = sStage[i];
     }
     __syncthreads();
   }
