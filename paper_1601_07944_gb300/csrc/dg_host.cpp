@@ -572,8 +572,13 @@ static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, d
   };
   dg_status st;
   if (!traces_valid)
-    DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces(m, c, m->trace, stream); }),
-            "rk traces");
+    DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] {
+              // mixed modes: the first stage's traces on the tensor cores, like the
+              // traces the element kernel writes for the later stages
+              return prec == DG_FP64 ? launch_traces(m, c, m->trace, stream)
+                                     : launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, nullptr, nullptr,
+                                                         m->trace, nullptr, 0.0, 0.0, 0.0, 2, stream);
+            }), "rk traces");
   // stage 1: u1 = c + dt L(c)
   if ((st = face("rk stage 1 flux")) != DG_OK) return st;
   if ((st = elem(c, nullptr, m->stage, 0.0, 1.0, "rk stage 1")) != DG_OK) return st;

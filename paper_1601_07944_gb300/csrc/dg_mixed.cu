@@ -15,6 +15,7 @@
  *           FP64: the mean mode's lift (the volume term of mode 1 vanishes), the
  *           1/det J scaling and the Runge-Kutta stage update
  *   GEMM 3  T[128 x NF]   = C_new[128 x NP] Phi_f[NP x NF]       next edge traces
+ * (mode 2 runs GEMM 3 alone on the stage input: the first stage's traces.)
  * The edge flux itself (dg_kernels.cu, k_face) stays float64, and so does the
  * mean mode, which carries the conserved totals: each edge's two contributions
  * to it cancel in float64.
@@ -175,10 +176,40 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
   const int row = tid, rel = row >> 2, rm = row & 3;                 // accumulator row = 4 e + m
   uint32_t phase = 0;
 
+  int e0 = 0, ecount = 0;
+  // GEMM 3: edge traces of the state held in A1's planes -> trace_out (float64),
+  // staged through GEMM 2's A planes.  Returns false if the tensor-core wait
+  // expired (recorded in *err).
+  auto traces_of_A1 = [&]() -> bool {
+    if (tid == 0) {
+      gemm<X3, K1>(tmem, uA1, T::A1P, uB4, T::B4P, tc::idesc_tf32(128, N4));
+      tc::commit(mbar);
+    }
+    const bool done = tc::mbar_wait(mbar, phase, kWaitNs);
+    phase ^= 1u;
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) atomicOr(err, 1);
+      return false;
+    }
+    tc::fence_after_sync();
+    {
+      float v[N4];
+      tmem_row<N4>(trow, v);
+#pragma unroll
+      for (int qk = 0; qk < NF; ++qk) sStage[(rel * NF + qk) * M + rm] = tc::f32_to_f64(v[qk]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    double *dst = trace_out + (size_t)e0 * NF * M;
+    for (int i = tid; i < ecount * NF * M; i += kTcThreads) dst[i] = sStage[i];
+    return true;
+  };
+
   const int ntiles = (N + EB - 1) / EB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e0 = tile * EB;
-    const int ecount = min(EB, N - e0);
+    e0 = tile * EB;
+    ecount = min(EB, N - e0);
     // ---- J^tau of the tile's elements ----
     for (int i = tid; i < EB * 4; i += kTcThreads) {
       const int el = i >> 2;
@@ -193,6 +224,16 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
       for (int j = 0; j < NP; ++j) cr[j] = live ? src[j] : 0.0;
     }
     for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cr[k]) : 0.0f);
+    if (mode == 2) {
+      // ---- traces only: GEMM 3 on the stage input ----
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (!traces_of_A1()) break;
+      __syncthreads();
+      continue;
+    }
     // ---- its edge fluxes in the element's orientation and point order: the lift
     // columns of GEMM 2, and the mean mode's lift in float64 ----
     double s0 = 0.0;
@@ -303,28 +344,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
       double *dst = out + (size_t)e0 * M * NP;
       for (int i = tid; i < ecount * M * NP; i += kTcThreads) dst[i] = sStage[i];
     }
-    if (trace_out) {
-      // ---- GEMM 3: edge traces of the new state ----
-      if (tid == 0) {
-        gemm<X3, K1>(tmem, uA1, T::A1P, uB4, T::B4P, tc::idesc_tf32(128, N4));
-        tc::commit(mbar);
-      }
-      ok = tc::mbar_wait(mbar, phase, kWaitNs);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, 1); break; }
-      tc::fence_after_sync();
-      {
-        float v[N4];
-        tmem_row<N4>(trow, v);
-#pragma unroll
-        for (int qk = 0; qk < NF; ++qk) sStage[(rel * NF + qk) * M + rm] = tc::f32_to_f64(v[qk]);
-      }
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-      double *dst = trace_out + (size_t)e0 * NF * M;
-      for (int i = tid; i < ecount * NF * M; i += kTcThreads) dst[i] = sStage[i];
-    }
+    if (trace_out && !traces_of_A1()) break;
     __syncthreads();
   }
   tc::fence_before_sync();
