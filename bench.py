@@ -43,15 +43,23 @@ WORKLOAD = dict(name="isentropic vortex, 256x256 jittered periodic triangle mesh
 
 
 def flops_element_per_elem(p: int, ne: int) -> float:
-    """Algorithmic float64 flops of one element-kernel launch per element (stage
-    update with next traces), counting an FMA as 2 flops:
-      interpolation 2*NQ*NP*4, flux + J^tau transform 40 per point,
-      projection 2*2NQ*NP*4, lift 2*3NE*NP*4, stage update 5*NP*4,
-      next traces 2*3NE*NP*4."""
+    """Float64 flops of one element-kernel launch per element, for the algorithm
+    the kernel executes (sum factorisation on the collapsed grid), counting an
+    FMA as 2 flops:
+      W = chi c                2 N_p (p+1) 4
+      U = P W                  2 (p+1)^3 4
+      flux, 1/rho, weights     56 per volume point
+      Xa, Xb                   4 (p+1)^3 4
+      V = chi Xa + chi' Xb     4 N_p (p+1) 4
+      lift                     2 (3 n_e) N_p 4
+      stage update             5 N_p 4
+      next traces              2 (3 n_e) N_p 4"""
     NP = (p + 1) * (p + 2) // 2
-    NQ = (p + 1) ** 2
+    ND = p + 1
+    NQ = ND * ND
     NF = 3 * ne
-    return 2 * NQ * NP * 4 + 40 * NQ + 4 * NQ * NP * 4 + 2 * NF * NP * 4 + 5 * NP * 4 + 2 * NF * NP * 4
+    return (2 * NP * ND * 4 + 2 * ND ** 3 * 4 + 56 * NQ + 4 * ND ** 3 * 4 + 4 * NP * ND * 4
+            + 2 * NF * NP * 4 + 5 * NP * 4 + 2 * NF * NP * 4)
 
 
 def _src_hash(*names) -> str:
@@ -65,7 +73,10 @@ def _src_hash(*names) -> str:
 # DRAM bytes per launch of the element kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum) from one ncu capture, keyed by the hash of the kernel
 # source it was taken on; a source change voids the entry.
-TRAFFIC = {}
+TRAFFIC = {
+    # k_element_sf<3,4>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
+    "a58fab90de624b23": 77164288 + 39253760,
+}
 
 
 class ClockSampler:
@@ -384,7 +395,7 @@ def run_ours(args, world, rank, local):
         avg_el_ms = el_ms / max(1, el_n)
         flops = flops_element_per_elem(p, ne) * m.N
         achieved = flops / (avg_el_ms * 1e-3) / 1e12
-        khash = _src_hash("dg_kernels.cu")
+        khash = _src_hash("dg_kernels.cu", "dg_device.cuh", "dg_tcgen05.cuh")
         traffic = TRAFFIC.get(khash)
         share = {k: round(ms / max(1e-12, sum(x for _, x in ktimes.values())), 4)
                  for k, (_, ms) in ktimes.items()}
@@ -397,7 +408,7 @@ def run_ours(args, world, rank, local):
                        "n_vol_pts": m.nq, "precision": "fp64", "dt": dt,
                        "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_element (float64 FMA pipe)",
+            "roofline": {"bound": "alu", "kernel": "k_element_sf (float64 FMA pipe)",
                          "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak if fp64_peak else None, "traffic": traffic,
                          "peak_source": "measured live: dg_probe_fma_rate float64 FMA chain",
