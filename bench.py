@@ -62,6 +62,25 @@ def flops_element_per_elem(p: int, ne: int) -> float:
             + 2 * NF * NP * 4 + 5 * NP * 4 + 2 * NF * NP * 4)
 
 
+def bytes_element_tc_per_elem(p: int, ne: int) -> float:
+    """Algorithmic HBM bytes of one mixed-precision element-kernel launch per
+    element, averaged over the three stages: stage input 8*4*N_p, u^n in two of
+    three stages, both sides' gathers of the edge fluxes 8*4*3n_e, geometry 64 B
+    + face map 12 B, new state 8*4*N_p, new traces 8*4*3n_e."""
+    NP = (p + 1) * (p + 2) // 2
+    NF = 3 * ne
+    return 32 * NP + (2.0 / 3.0) * 32 * NP + 32 * NF + 76 + 32 * NP + 32 * NF
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
 def _src_hash(*names) -> str:
     h = hashlib.sha256()
     for n in names:
@@ -71,11 +90,12 @@ def _src_hash(*names) -> str:
 
 
 # DRAM bytes per launch of the element kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum) from one ncu capture, keyed by the hash of the kernel
-# source it was taken on; a source change voids the entry.
+# dram__bytes_write.sum) from one ncu capture, keyed by the hash of the kernel's
+# source files (dg_element.cu and the device headers) it was taken on; a source
+# change voids the entry.
 TRAFFIC = {
     # k_element_sf<3,4>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
-    "a58fab90de624b23": 77164288 + 39253760,
+    "86a86ec8bb6bf538": 77164288 + 39253760,
 }
 
 
@@ -277,6 +297,25 @@ def mixed_modes(m, c0, dt, steps, flush, fp64_ms_per_step):
     return out
 
 
+def vortex_error(steps: int = 200):
+    """The 256x256, p=3 workload as stated: 200 float64 SSP-RK3 steps from the
+    vortex, then the L2 density error against the exact translated vortex."""
+    import torch
+    from paper_1601_07944_gb300 import dg, inputs as I
+    mesh = I.periodic_mesh(WORKLOAD["n"])
+    p = WORKLOAD["p"]
+    m = dg.Mesh.from_mesh(mesh, p, n_edge_pts=WORKLOAD["ne"])
+    c = m.project_function(I.vortex)
+    dt = I.fixed_dt(mesh, I.vortex, p, WORKLOAD["cfl"])
+    e0 = m.l2_error(c, lambda x, y: I.vortex(x, y, 0.0))
+    m.rk_step(c, dt, steps)
+    t = steps * dt
+    e1 = m.l2_error(c, lambda x, y: I.vortex(x, y, t))
+    return {"steps": steps, "final_time": t, "l2_density_error": e1, "l2_density_error_t0": e0,
+            "note": "the vortex is not exactly periodic on [-5,5]^2 (velocity perturbation ~2.4e-5 "
+                    "at the seams); part of the error comes from there"}
+
+
 def adjoint_ratio(steps: int = 20, every: int = 10):
     """Cost of the discrete adjoint relative to the forward pass on the 256x256,
     p=2 differentiation workload: one dg_adjoint_step against one dg_rk_step, and
@@ -345,8 +384,9 @@ def run_ours(args, world, rank, local):
     fp64_peak, fp32_peak = dg.probe_fma_rate()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
+    prec = args.precision
     for _ in range(args.warmup):
-        m.rk_step(c, dt, 1)
+        m.rk_step(c, dt, 1, precision=prec)
         m.conserved_totals(c)
     torch.cuda.synchronize()
 
@@ -363,7 +403,7 @@ def run_ours(args, world, rank, local):
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         starts[i].record(stream)
-        m.rk_step(c, dt, 1)
+        m.rk_step(c, dt, 1, precision=prec)
         totals = m.conserved_totals(c)
         ends[i].record(stream)
     torch.cuda.synchronize()
@@ -384,7 +424,7 @@ def run_ours(args, world, rank, local):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        m.rk_step_host(h, dt, 1)
+        m.rk_step_host(h, dt, 1, precision=prec)
     e2e_s = time.perf_counter() - t0
     state_bytes = m.N * 4 * m.np * 8
 
@@ -393,26 +433,36 @@ def run_ours(args, world, rank, local):
         launches = sum(n for n, _ in ktimes.values())
         el_n, el_ms = ktimes.get("element", (0, 0.0))
         avg_el_ms = el_ms / max(1, el_n)
-        flops = flops_element_per_elem(p, ne) * m.N
-        achieved = flops / (avg_el_ms * 1e-3) / 1e12
-        khash = _src_hash("dg_kernels.cu", "dg_device.cuh", "dg_tcgen05.cuh")
-        traffic = TRAFFIC.get(khash)
+        if prec == "fp64":
+            flops = flops_element_per_elem(p, ne) * m.N
+            achieved = flops / (avg_el_ms * 1e-3) / 1e12
+            khash = _src_hash("dg_element.cu", "dg_device.cuh", "dg_tcgen05.cuh")
+            roofline = {"bound": "alu", "kernel": "k_element_sf (float64 FMA pipe)",
+                        "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": achieved / fp64_peak if fp64_peak else None, "traffic": TRAFFIC.get(khash),
+                        "peak_source": "measured live: dg_probe_fma_rate float64 FMA chain",
+                        "flops_per_launch": flops, "avg_launch_ms": avg_el_ms}
+        else:
+            nbytes = bytes_element_tc_per_elem(p, ne) * m.N
+            achieved = nbytes / (avg_el_ms * 1e-3) / 1e9
+            hbm, src = hbm_peak()
+            roofline = {"bound": "hbm", "kernel": "k_element_tc (tcgen05, %s)" % prec,
+                        "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "traffic": None, "peak_source": src, "bytes_per_launch": nbytes,
+                        "avg_launch_ms": avg_el_ms}
         share = {k: round(ms / max(1e-12, sum(x for _, x in ktimes.values())), 4)
                  for k, (_, ms) in ktimes.items()}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else prec + " contractions, f64 flux/update",
             "data": "synthetic (seeded jittered periodic mesh, isentropic vortex)",
             "config": {"workload": WORKLOAD["name"], "n_elem": m.N, "p": p, "n_edge_pts": ne,
-                       "n_vol_pts": m.nq, "precision": "fp64", "dt": dt,
+                       "n_vol_pts": m.nq, "precision": prec, "dt": dt,
                        "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_element_sf (float64 FMA pipe)",
-                         "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak if fp64_peak else None, "traffic": traffic,
-                         "peak_source": "measured live: dg_probe_fma_rate float64 FMA chain",
-                         "flops_per_launch": flops, "avg_launch_ms": avg_el_ms},
+            "roofline": roofline,
             "kernel_share": share,
             "kernel_times_ms": {k: {"launches": n, "total_ms": ms} for k, (n, ms) in ktimes.items()},
             "fp32_fma_tflops": fp32_peak,
@@ -424,10 +474,11 @@ def run_ours(args, world, rank, local):
             "wall_s_timed_region": wall,
             "totals_last_step": [float(x) for x in totals] if totals is not None else None,
         }
-        if world == 1 and not args.no_extras:
+        if world == 1 and not args.no_extras and prec == "fp64":
             c0 = m.project_function(I.vortex)
             line["mixed"] = mixed_modes(m, c0, dt, max(5, min(args.steps, 20)), flush, t_max / args.steps)
             line["adjoint"] = adjoint_ratio()
+            line["vortex_200_steps"] = vortex_error()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
     if world > 1:
@@ -445,6 +496,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "tf32x3", "tf32x1"], default="fp64",
+                    help="arithmetic of the timed steps (the headline line is fp64)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision and adjoint measurements")
     args = ap.parse_args()

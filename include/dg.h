@@ -109,6 +109,14 @@ dg_status dg_mesh_info(const dg_mesh *mesh, dg_mesh_info_t *info);
  * reference rule): xy[N][n_vol_pts][2], DEVICE.  Asynchronous. */
 dg_status dg_volume_points(const dg_mesh *mesh, double *xy, void *stream);
 
+/* Values of the solution U = sum_j c_j phi_j (Section 2) at npts reference points
+ * (r[k], s[k]) of every element: out[e][k][m], DEVICE [N][npts][4].  r, s are
+ * HOST arrays (points inside the reference triangle {(0,0),(1,0),(0,1)}); the
+ * basis table at the points is built on the host and copied to a temporary
+ * device buffer.  Synchronous (the table is freed before returning). */
+dg_status dg_eval_points(dg_mesh *mesh, int npts, const double *r, const double *s, const double *c,
+                         double *out, void *stream);
+
 /* L2 projection of point values onto the orthonormal basis (Section 2, the
  * initial data u_0):  c[e][m][j] = sum_k w_k u[e][k][m] phi_j(r_k), with u the
  * conserved state at the points returned by dg_volume_points.

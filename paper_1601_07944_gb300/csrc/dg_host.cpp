@@ -517,6 +517,27 @@ extern "C" dg_status dg_volume_points(const dg_mesh *m, double *xy, void *stream
   return DG_OK;
 }
 
+extern "C" dg_status dg_eval_points(dg_mesh *m, int npts, const double *r, const double *s, const double *c,
+                                    double *out, void *stream) {
+  if (!m || !r || !s || !c || !out) return fail(DG_EINVAL, "dg_eval_points: null argument");
+  if (npts < 1 || npts > 1 << 20) return fail(DG_EINVAL, "dg_eval_points: npts=%d", npts);
+  std::vector<double> tab((size_t)npts * m->np);
+  for (int k = 0; k < npts; ++k) {
+    if (!(r[k] >= 0.0 && s[k] >= 0.0 && r[k] + s[k] < 1.0))
+      return fail(DG_EINVAL, "dg_eval_points: point %d = (%g, %g) is not inside the reference triangle", k, r[k], s[k]);
+    dubiner(m->p, (real)r[k], (real)s[k], &tab[(size_t)k * m->np], nullptr, nullptr);
+  }
+  double *dtab = nullptr;
+  DG_CUDA(cudaMalloc(&dtab, sizeof(double) * tab.size()), "dg_eval_points alloc");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = (cudaError_t)dg::launch_eval_points(m, c, dtab, npts, out, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dtab);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_eval_points");
+  return DG_OK;
+}
+
 extern "C" dg_status dg_project_ic(dg_mesh *m, const double *u, double *c, void *stream) {
   if (!m || !u || !c) return fail(DG_EINVAL, "dg_project_ic: null argument");
   DG_CUDA((cudaError_t)timed(m, DG_K_PROJECT, stream, [&] { return dg::launch_project(m, u, c, stream); }),

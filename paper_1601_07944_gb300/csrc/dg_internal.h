@@ -105,6 +105,7 @@ int tc_smem_bytes(int p, int ne, int split3);
 int launch_convert_check(int n, unsigned long long *bad, void *stream);
 int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
+int launch_eval_points(const dg_mesh *m, const double *c, const double *tab, int npts, double *out, void *stream);
 int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);
 // (dR/du)^T lam combined as out = x0 X + x1 Y + x2 Z + s (dR/du)^T lam (X, Y, Z may
 // be null).  uvol [N][M][np], G, T, TB [N][3 ne][M] are work buffers.

@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
-           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test")
+           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "dg_device_status": [P, P],
         "dg_rhs_noalloc": [P, P, P, I, P],
         "dg_self_test": [P, P],
+        "dg_eval_points": [P, I, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -220,6 +221,34 @@ class Mesh:
         xy = torch.empty((self.N, self.nq, 2), dtype=torch.float64, device="cuda")
         _check(load().dg_volume_points(self._h, _dev_ptr(xy, "xy"), _stream_ptr(stream)))
         return xy
+
+    def eval_points(self, c, r, s, stream=None):
+        """Solution values [N, npts, 4] at reference points (r, s) of every element."""
+        import torch
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        out = torch.empty((self.N, r.size, 4), dtype=torch.float64, device="cuda")
+        _check(load().dg_eval_points(self._h, r.size, _np_ptr(r), _np_ptr(s), _dev_ptr(c, "c", self.coef_shape),
+                                     _dev_ptr(out, "out"), _stream_ptr(stream)))
+        return out
+
+    def l2_error(self, c, exact, var: int = 0, n_dir: int = 0, rule=None):
+        """sqrt(sum_e int_e (U_h - U_exact)^2) for one variable.  `rule` = (r, s, w) is
+        a reference-triangle rule (default: the library's collapsed rule with p+4
+        points per direction, exact to degree 2p+7); exact(x, y) -> [..., 4]."""
+        import torch
+        if rule is None:
+            T = host_tables(n_dir - 1 if n_dir else self.p + 3)
+            r, s, w = T["vol_r"], T["vol_s"], T["vol_w"]
+        else:
+            r, s, w = rule
+        vals = self.eval_points(c, r, s)[..., var].cpu().numpy()
+        xy = self._xy
+        x = xy[:, 0, 0][:, None] * (1 - r - s) + xy[:, 1, 0][:, None] * r + xy[:, 2, 0][:, None] * s
+        y = xy[:, 0, 1][:, None] * (1 - r - s) + xy[:, 1, 1][:, None] * r + xy[:, 2, 1][:, None] * s
+        ex = exact(x, y)[..., var]
+        dJ = self.det_j("cpu").numpy()
+        return float(np.sqrt(np.sum(dJ[:, None] * w[None, :] * (vals - ex) ** 2)))
 
     def project_ic(self, u, out=None, stream=None):
         import torch

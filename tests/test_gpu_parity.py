@@ -190,3 +190,24 @@ def test_argument_errors(dgmod):
     assert ei.value.status == 1
     with pytest.raises(ValueError):
         m.rhs(torch.zeros((3, 4, 3), dtype=torch.float64, device="cuda"))
+
+
+def test_eval_points_and_l2_error(dgmod, oracle_mod):
+    """Point values of the solution (dg_eval_points) and the L2 error built on them
+    agree with the oracle's."""
+    mesh = I.periodic_mesh(8)
+    p = 3
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    c = o.project_ic(I.vortex)
+    rng = np.random.default_rng(2)
+    r = rng.uniform(0.02, 0.48, 9)
+    s = rng.uniform(0.02, 0.48, 9)
+    got = _host(m.eval_points(_dev(c), r, s))
+    ref = o.eval_points(c, r, s)
+    assert rel_l2(got, ref) < 1e-14
+    T = dgmod.host_tables(p + 3)
+    rule = (T["vol_r"], T["vol_s"], T["vol_w"])
+    e_gpu = m.l2_error(_dev(c), lambda x, y: I.vortex(x, y, 0.0), rule=rule)
+    e_or = o.l2_error(c, lambda x, y: I.vortex(x, y, 0.0))
+    assert abs(e_gpu - e_or) <= 1e-10 * e_or
