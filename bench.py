@@ -470,6 +470,9 @@ def run_ours(args, world, rank, local):
                     "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                     "entry": "dg_rk_step_host"},
             "gpu_launches": launches,
+            "paper_context": "GTX 580 (Fermi, FP64), double Mach reflection, p=1, RK2 with limiter: "
+                             "1.31e8-1.53e8 DOF-updates/s per stage, derived from the paper's runtime "
+                             "table; another problem and machine, context only",
             "clocks": clk,
             "wall_s_timed_region": wall,
             "totals_last_step": [float(x) for x in totals] if totals is not None else None,

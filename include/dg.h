@@ -162,6 +162,13 @@ dg_status dg_rk_step(dg_mesh *mesh, double *c, double dt, int nsteps, dg_precisi
 dg_status dg_rk_step_host(dg_mesh *mesh, double *c_host, double dt, int nsteps,
                           dg_precision prec, void *stream);
 
+/* Discrete adjoint of dg_rhs (float64): out = (dR/dc)^T lam, the transpose of the
+ * RHS Jacobian at c applied to lam, taken backwards through the edge traces,
+ * the Lax-Friedrichs flux (same kink conventions as dg_adjoint_step), the lift,
+ * the volume integral and the 1/det J scaling.  All arrays DEVICE [N][4][N_p];
+ * out must not alias c or lam.  Asynchronous. */
+dg_status dg_rhs_adjoint(dg_mesh *mesh, const double *c, const double *lam, double *out, void *stream);
+
 /* Discrete adjoint of one SSP-RK3 step (float64): given the state c_n at the start
  * of the step and lam_np1 = dJ/dc_{n+1}, writes lam_n = dJ/dc_n = (d c_{n+1}/d c_n)^T
  * lam_np1.  The stages are recomputed from c_n.  At a tie of the two wave speeds in

@@ -652,23 +652,47 @@ extern "C" dg_status dg_conserved_totals(dg_mesh *m, const double *c, double out
   return DG_OK;
 }
 
-extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, const double *lam_np1,
-                                     double *lam_n, void *stream) {
-  using namespace dg;
-  if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "dg_adjoint_step: null argument");
-  if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
-  if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
-  const size_t S = (size_t)m->N * M * m->np;           // one state
-  const size_t TR = (size_t)m->N * 3 * m->ne * M;       // one trace block
+// adjoint work space: 5 states and 2 trace blocks, allocated on first use
+static dg_status adjoint_buffers(dg_mesh *m, const char *who) {
+  const size_t S = (size_t)m->N * dg::M * m->np;
+  const size_t TR = (size_t)m->N * 3 * m->ne * dg::M;
   const size_t need = 5 * S + 2 * TR;
   if (m->adj_doubles < need) {
     cudaFree(m->adj_buf);
     m->adj_buf = nullptr;
     m->adj_doubles = 0;
     cudaError_t e = cudaMalloc(&m->adj_buf, sizeof(double) * need);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(DG_ENOMEM, "dg_adjoint_step: cudaMalloc"); }
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(DG_ENOMEM, "%s: cudaMalloc", who); }
     m->adj_doubles = need;
   }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_rhs_adjoint(dg_mesh *m, const double *c, const double *lam, double *out, void *stream) {
+  using namespace dg;
+  if (!m || !c || !lam || !out) return fail(DG_EINVAL, "dg_rhs_adjoint: null argument");
+  if (out == c || out == lam) return fail(DG_EINVAL, "dg_rhs_adjoint: out aliases an input");
+  dg_status st = adjoint_buffers(m, "dg_rhs_adjoint");
+  if (st != DG_OK) return st;
+  const size_t S = (size_t)m->N * M * m->np, TR = (size_t)m->N * 3 * m->ne * M;
+  double *uvol = m->adj_buf + 4 * S, *G = m->adj_buf + 5 * S, *TB = G + TR;
+  DG_CUDA((cudaError_t)timed(m, DG_K_ADJOINT, stream, [&] {
+            return launch_rhs_vjp(m, c, lam, uvol, G, m->trace, TB, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, 1.0,
+                                  out, stream);
+          }), "dg_rhs_adjoint");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, const double *lam_np1,
+                                     double *lam_n, void *stream) {
+  using namespace dg;
+  if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "dg_adjoint_step: null argument");
+  if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
+  if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
+  dg_status ast = adjoint_buffers(m, "dg_adjoint_step");
+  if (ast != DG_OK) return ast;
+  const size_t S = (size_t)m->N * M * m->np;           // one state
+  const size_t TR = (size_t)m->N * 3 * m->ne * M;       // one trace block
   double *u1 = m->adj_buf, *u2 = u1 + S, *b1 = u2 + S, *b2 = b1 + S, *uvol = b2 + S;
   double *G = uvol + S, *TB = G + TR;
   // forward stages from c_n: u1 = c_n + dt R(c_n), u2 = 3/4 c_n + 1/4 (u1 + dt R(u1))

@@ -152,12 +152,37 @@ k_volume_points(const double *__restrict__ xy, const double *__restrict__ vr,
 }
 
 // ---------------------------------------------------------------------------
-// conserved totals: fixed-order two-pass reduction of det J * c[e][m][0]
+// conserved totals: fixed-order reduction of det J * c[e][m][0] -- per thread
+// over a strided range, then warp shuffles, then across the warps of the block,
+// then one block over the block partials.  The order never depends on timing,
+// so repeated calls give the same bits.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_sum4(double acc[M]) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += __shfl_down_sync(0xFFFFFFFFu, acc[m], off);
+}
+
+// lane 0 of warp 0 ends with the block sum of acc
+__device__ __forceinline__ void block_sum4(double acc[M]) {
+  __shared__ double red[kThreads / 32][M];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum4(acc);
+  if (lane == 0)
+#pragma unroll
+    for (int m = 0; m < M; ++m) red[warp][m] = acc[m];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = lane < kThreads / 32 ? red[lane][m] : 0.0;
+    warp_sum4(acc);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_totals_partial(const double *__restrict__ c, const double *__restrict__ geo, int N, int np,
                  double *__restrict__ partial) {
-  __shared__ double red[M][kThreads];
   double acc[M] = {0.0, 0.0, 0.0, 0.0};
   const int64_t chunk = ((int64_t)N + gridDim.x - 1) / gridDim.x;
   const int64_t beg = blockIdx.x * chunk;
@@ -167,36 +192,23 @@ k_totals_partial(const double *__restrict__ c, const double *__restrict__ geo, i
 #pragma unroll
     for (int m = 0; m < M; ++m) acc[m] += dj * c[(e * M + m) * np];
   }
+  block_sum4(acc);
+  if (threadIdx.x == 0)
 #pragma unroll
-  for (int m = 0; m < M; ++m) red[m][threadIdx.x] = acc[m];
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-#pragma unroll
-      for (int m = 0; m < M; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x < M) partial[blockIdx.x * M + threadIdx.x] = red[threadIdx.x][0];
+    for (int m = 0; m < M; ++m) partial[blockIdx.x * M + m] = acc[m];
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_totals_final(const double *__restrict__ partial, int nb, double *__restrict__ out) {
-  __shared__ double red[M][kThreads];
   double acc[M] = {0.0, 0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nb; b += blockDim.x)
 #pragma unroll
     for (int m = 0; m < M; ++m) acc[m] += partial[b * M + m];
-#pragma unroll
-  for (int m = 0; m < M; ++m) red[m][threadIdx.x] = acc[m];
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-#pragma unroll
-      for (int m = 0; m < M; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + s];
-    __syncthreads();
-  }
+  block_sum4(acc);
   // int phi_1 over the reference triangle is 1/sqrt(2); the other modes have zero mean
-  if (threadIdx.x < M) out[threadIdx.x] = red[threadIdx.x][0] * 0.70710678118654752440;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int m = 0; m < M; ++m) out[m] = acc[m] * 0.70710678118654752440;
 }
 
 // ---------------------------------------------------------------------------

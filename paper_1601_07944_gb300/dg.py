@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
-           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points")
+           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "dg_rhs_noalloc": [P, P, P, I, P],
         "dg_self_test": [P, P],
         "dg_eval_points": [P, I, P, P, P, P, P],
+        "dg_rhs_adjoint": [P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -295,6 +296,14 @@ class Mesh:
         _check(load().dg_rk_step_host(self._h, ptr, float(dt), int(nsteps), _prec(precision),
                                       _stream_ptr(stream)))
         return c_host
+
+    def rhs_adjoint(self, c, lam, out=None, stream=None):
+        """(dR/dc)^T lam at c."""
+        import torch
+        o = out if out is not None else torch.empty(self.coef_shape, dtype=torch.float64, device="cuda")
+        _check(load().dg_rhs_adjoint(self._h, _dev_ptr(c, "c", self.coef_shape), _dev_ptr(lam, "lam", self.coef_shape),
+                                     _dev_ptr(o, "out", self.coef_shape), _stream_ptr(stream)))
+        return o
 
     def adjoint_step(self, c_n, dt: float, lam_np1, out=None, stream=None):
         import torch

@@ -50,6 +50,19 @@ def test_adjoint_step_parity(dgmod, oracle_mod, p, ne, n):
     assert rel_l2(got, ref) < 1e-12
 
 
+@pytest.mark.parametrize("n", [6, 16])
+@pytest.mark.parametrize("p,ne", [(1, 0), (2, 0), (3, 0), (3, 3), (4, 0), (5, 0)])
+def test_rhs_adjoint_parity(dgmod, oracle_mod, p, ne, n):
+    mesh = I.periodic_mesh(n)
+    m = dgmod.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p, n_edge_pts=ne)
+    rng = np.random.default_rng(3 * n + p)
+    c = o.project_ic(I.perturbed_vortex) + 0.002 * rng.standard_normal((o.N, 4, o.np))
+    lam = rng.standard_normal(c.shape)
+    got = _host(m.rhs_adjoint(_dev(c), _dev(lam)))
+    assert rel_l2(got, o.rhs_vjp(c, lam)) < 1e-12
+
+
 def _loss_setup(dgmod, oracle_mod, n, p):
     mesh = I.periodic_mesh(n)
     m = dgmod.Mesh.from_mesh(mesh, p)

@@ -211,3 +211,44 @@ def test_eval_points_and_l2_error(dgmod, oracle_mod):
     e_gpu = m.l2_error(_dev(c), lambda x, y: I.vortex(x, y, 0.0), rule=rule)
     e_or = o.l2_error(c, lambda x, y: I.vortex(x, y, 0.0))
     assert abs(e_gpu - e_or) <= 1e-10 * e_or
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_vortex_convergence_order(dgmod, p):
+    """The closed-form isentropic vortex: the L2 density error of the GPU solver at
+    t = 0.5 falls like h^(p+1) on n = 32, 64, 128 (dt fixed from the finest mesh,
+    small enough that the time error stays below the spatial one)."""
+    import math
+    ns = (32, 64, 128)
+    T = 0.5
+    dt = 0.5 * I.fixed_dt(I.periodic_mesh(ns[-1]), I.vortex, p)
+    steps = int(math.ceil(T / dt))
+    dt = T / steps
+    errs = []
+    for n in ns:
+        mesh = I.periodic_mesh(n)
+        m = dgmod.Mesh.from_mesh(mesh, p)
+        c = m.project_function(I.vortex)
+        m.rk_step(c, dt, steps)
+        errs.append(m.l2_error(c, lambda x, y: I.vortex(x, y, T)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert rates[-1] > p + 1 - 0.3, (errs, rates)
+
+
+def test_full_size_parity_1024_p5(dgmod, oracle_mod):
+    """The 1024^2, p=5 workload (2,097,152 elements, 176 M DOF) at full size: one RHS
+    and one SSP-RK3 step against the oracle."""
+    mesh = I.periodic_mesh(1024)
+    p = 5
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    c = o.project_ic(I.vortex)
+    ref, vol = o.rhs_and_volume(c)
+    got = _host(m.rhs(_dev(c)))
+    eps = np.finfo(float).eps
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref) + 16 * eps * np.linalg.norm(vol)
+    del got, ref, vol
+    dt = I.fixed_dt(mesh, I.vortex, p)
+    cd = _dev(c)
+    m.rk_step(cd, dt, 1)
+    assert rel_l2(_host(cd), o.ssp_rk3(c, dt, 1)) < TOL
