@@ -354,6 +354,118 @@ def adjoint_ratio(steps: int = 20, every: int = 10):
             "rk_step_ms": fwd / steps, "adjoint_step_ms": adj / steps}
 
 
+def run_configs():
+    """Every workload of the five configurations as stated, one JSON line each
+    (device-timed full runs; parity with the oracle is the tests' job)."""
+    import numpy as np
+    import torch
+    from paper_1601_07944_gb300 import _build, autograd as AG, dg, inputs as I
+    _build.build()
+    dg.load()
+
+    def timed_run(m, c, dt, steps, prec, chunk=None):
+        chunk = chunk or steps
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(); a.record()
+        done = 0
+        while done < steps:
+            k = min(chunk, steps - done)
+            m.rk_step(c, dt, k, precision=prec)
+            done += k
+        b.record(); torch.cuda.synchronize()
+        m.device_status()
+        return a.elapsed_time(b)
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    precs = ("fp64", "tf32x3", "tf32x1")
+    # 1: 16^2, p=1, vortex, 100 steps
+    mesh = I.periodic_mesh(16); m = dg.Mesh.from_mesh(mesh, 1)
+    dt = I.fixed_dt(mesh, I.vortex, 1)
+    c0 = m.project_function(I.vortex); t0 = m.conserved_totals(c0)
+    c = c0.clone(); timed_run(m, c, dt, 100, "fp64")
+    c = c0.clone(); ms = timed_run(m, c, dt, 100, "fp64")
+    emit({"config": 1, "workload": "vortex 16x16 (512 elements), p=1, 100 steps", "precision": "fp64",
+          "ms_per_step": ms / 100, "dof_updates_per_s": _dof_per_step(m.N, 1) * 100 / (ms * 1e-3),
+          "totals_rel_drift": (np.abs(m.conserved_totals(c) - t0) / np.abs(t0)).tolist(),
+          "l2_density_error_vs_exact": m.l2_error(c, lambda x, y: I.vortex(x, y, 100 * dt))})
+    # 2: 256^2, p=3, vortex, 200 steps, 4 and 3 edge points
+    for ne in (0, 3):
+        mesh = I.periodic_mesh(256); m = dg.Mesh.from_mesh(mesh, 3, n_edge_pts=ne)
+        dt = I.fixed_dt(mesh, I.vortex, 3)
+        c0 = m.project_function(I.vortex)
+        ref = None
+        for prec in precs:
+            c = c0.clone(); timed_run(m, c, dt, 3, prec)
+            c = c0.clone(); ms = timed_run(m, c, dt, 200, prec)
+            if ref is None:
+                ref = c.clone()
+            emit({"config": 2, "workload": "vortex 256x256 (131072 elements), p=3, %d edge points, 200 steps"
+                  % m.ne, "precision": prec, "ms_per_step": ms / 200,
+                  "dof_updates_per_s": _dof_per_step(m.N, 3) * 200 / (ms * 1e-3),
+                  "rel_l2_vs_fp64": float(torch.linalg.norm(c - ref) / torch.linalg.norm(ref)),
+                  "l2_density_error_vs_exact": m.l2_error(c, lambda x, y: I.vortex(x, y, 200 * dt))})
+        del m
+    # 3: 512^2, p=4, perturbed vortex
+    mesh = I.periodic_mesh(512); m = dg.Mesh.from_mesh(mesh, 4)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, 4)
+    c0 = m.project_function(I.perturbed_vortex)
+    ref = None
+    for prec in precs:
+        c = c0.clone(); timed_run(m, c, dt, 3, prec)
+        c = c0.clone(); ms = timed_run(m, c, dt, 100, prec)
+        if ref is None:
+            ref = c.clone()
+        emit({"config": 3, "workload": "perturbed vortex 512x512 (524288 elements), p=4, 100 steps",
+              "precision": prec, "ms_per_step": ms / 100,
+              "dof_updates_per_s": _dof_per_step(m.N, 4) * 100 / (ms * 1e-3),
+              "rel_l2_vs_fp64": float(torch.linalg.norm(c - ref) / torch.linalg.norm(ref))})
+    del m
+    # 4: 256^2, p=2, 400 steps, checkpoint every 20: forward vs checkpointed backward
+    mesh = I.periodic_mesh(256); m = dg.Mesh.from_mesh(mesh, 2)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, 2)
+    c0 = m.project_function(I.perturbed_vortex)
+    tgt = m.project_function(lambda x, y: I.perturbed_vortex(x, y, seed=I.SEED_TARGET))
+    m.rk_step(tgt, dt, 400)
+    dJ = m.det_j()
+    for rep in range(2):
+        x = c0.clone().requires_grad_(True)
+        torch.cuda.synchronize(); w0 = time.perf_counter()
+        loss = AG.density_misfit(dJ, AG.solve(m, x, dt, 400, 20), tgt)
+        torch.cuda.synchronize(); w1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize(); w2 = time.perf_counter()
+    emit({"config": 4, "workload": "perturbed vortex 256x256, p=2, 400 steps, checkpoint every 20",
+          "precision": "fp64", "forward_s": w1 - w0, "backward_s": w2 - w1,
+          "backward_over_forward": (w2 - w1) / (w1 - w0), "loss": float(loss.item())})
+    del m
+    # 5: 1024^2, p=5, perturbed vortex, 100 steps: throughput and totals drift
+    mesh = I.periodic_mesh(1024); m = dg.Mesh.from_mesh(mesh, 5)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, 5)
+    c0 = m.project_function(I.perturbed_vortex); t0 = m.conserved_totals(c0)
+    ref = None
+    for prec in precs:
+        c = c0.clone(); timed_run(m, c, dt, 2, prec)
+        c = c0.clone()
+        m.set_timing(True)
+        ms = timed_run(m, c, dt, 100, prec)
+        kt = m.kernel_times(); m.set_timing(False)
+        if ref is None:
+            ref = c.clone()
+        line = {"config": 5, "workload": "perturbed vortex 1024x1024 (2097152 elements, 176M DOF), p=5, 100 steps",
+                "precision": prec, "ms_per_step": ms / 100,
+                "dof_updates_per_s": _dof_per_step(m.N, 5) * 100 / (ms * 1e-3),
+                "totals_rel_drift": (np.abs(m.conserved_totals(c) - t0) / np.abs(t0)).tolist(),
+                "rel_l2_vs_fp64": float(torch.linalg.norm(c - ref) / torch.linalg.norm(ref)),
+                "kernel_ms_per_launch": {k: v[1] / v[0] for k, v in kt.items()}}
+        if prec != "fp64":
+            el_ms = kt["element"][1] / kt["element"][0]
+            hbm, _ = hbm_peak()
+            line["element_hbm_frac"] = bytes_element_tc_per_elem(5, 6) * m.N / (el_ms * 1e-3) / 1e9 / hbm
+        emit(line)
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -499,6 +611,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs", action="store_true",
+                    help="run the five stated workloads (one JSON line each) instead of the benchmark")
     ap.add_argument("--precision", choices=["fp64", "tf32x3", "tf32x1"], default="fp64",
                     help="arithmetic of the timed steps (the headline line is fp64)")
     ap.add_argument("--no-extras", action="store_true",
@@ -507,6 +621,10 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     world, rank, local = _dist()
+    if args.configs:
+        if rank == 0:
+            run_configs()
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
