@@ -152,7 +152,9 @@ dg_status dg_rhs_noalloc(dg_mesh *mesh, const double *c, double *r, dg_precision
  *   u1 = u + dt L(u),  u2 = 3/4 u + 1/4 (u1 + dt L(u1)),
  *   u <- 1/3 u + 2/3 (u2 + dt L(u2)),
  * in place on c (DEVICE [N][4][N_p]).  The stage accumulation is float64 in every
- * precision mode.  Asynchronous. */
+ * precision mode.  Asynchronous.  Long calls replay whole chunks of 16 steps as a
+ * CUDA graph, captured once per (c, dt, precision) on an internal stream that is
+ * ordered after, and then before, `stream` with events. */
 dg_status dg_rk_step(dg_mesh *mesh, double *c, double dt, int nsteps, dg_precision prec,
                      void *stream);
 

@@ -242,6 +242,13 @@ void free_mesh(dg_mesh *m) {
     for (auto &r : m->timing->pool) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete m->timing;
   }
+  if (m->graph) {
+    if (m->graph->exec) cudaGraphExecDestroy(m->graph->exec);
+    if (m->graph->ready) cudaEventDestroy(m->graph->ready);
+    if (m->graph->done) cudaEventDestroy(m->graph->done);
+    if (m->graph->stream) cudaStreamDestroy(m->graph->stream);
+    delete m->graph;
+  }
   delete m;
 }
 
@@ -612,6 +619,41 @@ static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, d
   return DG_OK;
 }
 
+// Steps per captured graph.  Replaying a graph runs its launches back to back,
+// which is what small meshes (a few microseconds of work per kernel) need.
+constexpr int kGraphSteps = 16;
+
+// The cached graph of kGraphSteps steps for (c, dt, prec), capturing it if the
+// key changed; nullptr if capture is unavailable (plain launches are used).
+static cudaGraphExec_t step_graph(dg_mesh *m, double *c, double dt, dg_precision prec) {
+  if (!m->graph) m->graph = new (std::nothrow) dg::GraphCache();
+  dg::GraphCache *g = m->graph;
+  if (!g || g->broken) return nullptr;
+  if (g->exec && g->c == c && g->dt == dt && g->prec == (int)prec && g->steps == kGraphSteps) return g->exec;
+  if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+  if (!g->stream && cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) g->stream = nullptr;
+  if (g->stream && !g->ready && cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming) != cudaSuccess) g->ready = nullptr;
+  if (g->stream && !g->done && cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) g->done = nullptr;
+  if (!g->stream || !g->ready || !g->done) { cudaGetLastError(); g->broken = true; return nullptr; }
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+  if (ok) {
+    for (int i = 0; i < kGraphSteps && ok; ++i) ok = rk3_step(m, c, dt, true, prec, g->stream) == DG_OK;
+    ok = (cudaStreamEndCapture(g->stream, &graph) == cudaSuccess) && ok && graph;
+  }
+  if (ok) ok = cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    g->exec = nullptr;
+    g->broken = true;
+    g_err.clear();
+    return nullptr;
+  }
+  g->c = c; g->dt = dt; g->prec = (int)prec; g->steps = kGraphSteps;
+  return g->exec;
+}
+
 extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg_precision prec,
                                 void *stream) {
   if (!m || !c) return fail(DG_EINVAL, "dg_rk_step: null argument");
@@ -619,8 +661,29 @@ extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg
   if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_rk_step: dt is not finite");
   dg_status st = check_prec(prec, "dg_rk_step");
   if (st != DG_OK) return st;
-  for (int it = 0; it < nsteps; ++it)
-    if ((st = rk3_step(m, c, dt, it > 0, prec, stream)) != DG_OK) return st;
+  int done = 0;
+  if (nsteps > 0) {
+    if ((st = rk3_step(m, c, dt, false, prec, stream)) != DG_OK) return st;
+    done = 1;
+  }
+  // whole chunks of steps as a replayed CUDA graph (not while per-kernel timing is on)
+  if (nsteps - done >= kGraphSteps && !(m->timing && m->timing->on)) {
+    cudaGraphExec_t exec = step_graph(m, c, dt, prec);
+    if (exec) {
+      dg::GraphCache *g = m->graph;
+      cudaStream_t s = (cudaStream_t)stream;
+      DG_CUDA(cudaEventRecord(g->ready, s), "dg_rk_step graph order");
+      DG_CUDA(cudaStreamWaitEvent(g->stream, g->ready, 0), "dg_rk_step graph order");
+      while (nsteps - done >= kGraphSteps) {
+        DG_CUDA(cudaGraphLaunch(exec, g->stream), "dg_rk_step graph launch");
+        done += kGraphSteps;
+      }
+      DG_CUDA(cudaEventRecord(g->done, g->stream), "dg_rk_step graph order");
+      DG_CUDA(cudaStreamWaitEvent(s, g->done, 0), "dg_rk_step graph order");
+    }
+  }
+  for (; done < nsteps; ++done)
+    if ((st = rk3_step(m, c, dt, true, prec, stream)) != DG_OK) return st;
   return DG_OK;
 }
 

@@ -55,6 +55,18 @@ struct Timing {
   int64_t launches[DG_NKINDS] = {};
 };
 
+// A CUDA graph of several SSP-RK3 steps, captured once per (state pointer, dt,
+// precision, step count) and replayed by dg_rk_step on an internal stream.
+struct GraphCache {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double *c = nullptr;
+  double dt = 0.0;
+  int prec = -1, steps = 0;
+  bool broken = false;        // capture failed once: use plain launches from then on
+};
+
 }  // namespace dg
 
 struct dg_mesh {
@@ -85,6 +97,7 @@ struct dg_mesh {
   double *adj_buf;
   size_t adj_doubles;
   dg::Timing *timing;
+  dg::GraphCache *graph;
 };
 
 namespace dg {

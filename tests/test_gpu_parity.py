@@ -252,3 +252,23 @@ def test_full_size_parity_1024_p5(dgmod, oracle_mod):
     cd = _dev(c)
     m.rk_step(cd, dt, 1)
     assert rel_l2(_host(cd), o.ssp_rk3(c, dt, 1)) < TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_graph_replay_matches_plain_launches(dgmod, prec):
+    """A 40-step call (one plain step, two replays of the 16-step CUDA graph, seven
+    plain steps) gives bit for bit the state of 40 one-step calls."""
+    mesh = I.periodic_mesh(16)
+    m = dgmod.Mesh.from_mesh(mesh, 2)
+    c0 = m.project_function(I.perturbed_vortex)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, 2)
+    a = c0.clone(); b = c0.clone()
+    m.rk_step(a, dt, 40, precision=prec)
+    for _ in range(40):
+        m.rk_step(b, dt, 1, precision=prec)
+    m.device_status()
+    assert np.array_equal(_host(a), _host(b))
+    m.rk_step(a, dt, 20, precision=prec)          # replay of the cached graph
+    for _ in range(20):
+        m.rk_step(b, dt, 1, precision=prec)
+    assert np.array_equal(_host(a), _host(b))
