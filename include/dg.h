@@ -179,6 +179,14 @@ dg_status dg_rhs_adjoint(dg_mesh *mesh, const double *c, const double *lam, doub
 dg_status dg_adjoint_step(dg_mesh *mesh, const double *c_n, double dt, const double *lam_np1,
                           double *lam_n, void *stream);
 
+/* A stable time step (the paper gives none; Section 4.3.1 computes one with a
+ * reduction): dt = cfl * r_min / ((2p+1) * s_max), with r_min the smallest
+ * inscribed radius (twice the area over the perimeter) of the mesh and s_max the
+ * largest |v| + c of the solution c over the volume quadrature points (an exact,
+ * order-free maximum).  c: DEVICE.  *dt_out: HOST.  DG_ENONPHYS if rho <= 0 or
+ * p <= 0 at a point.  Synchronous. */
+dg_status dg_stable_dt(dg_mesh *mesh, const double *c, double cfl, double *dt_out, void *stream);
+
 /* Domain integrals of the conserved variables,
  *   T_m = sum_e int_{Omega_e} U_m = sum_e det J_e c[e][m][0] / sqrt(2)
  * (only the constant mode has a non-zero mean), as a fixed-order float64
@@ -218,8 +226,10 @@ dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stre
 
 /* Synchronises stream and reports device-side failures recorded since the last
  * call: DG_ETIMEOUT if a bounded wait of the mixed-precision kernels expired
- * (the kernel then skipped its remaining work and released its resources).
- * The record is cleared.  Synchronous. */
+ * (the kernel then skipped its remaining work and released its resources);
+ * DG_ENONPHYS if a kernel met rho <= 0 or p <= 0 (or NaN) at a volume or edge
+ * quadrature point (the results of that call are then meaningless).  The record
+ * is cleared.  Synchronous. */
 dg_status dg_device_status(dg_mesh *mesh, void *stream);
 
 /* Device self-check of two arithmetic helpers the kernels use to spare the

@@ -47,8 +47,16 @@ __device__ __forceinline__ double recip(double x) {
 // FAST_ALPHA (mixed-precision modes only): alpha, a dissipation coefficient, is
 // formed in float32 from the float64 pressure, density and normal velocity; the
 // flux itself stays float64.
+// x > 0 and finite, tested on the bit pattern with integer instructions (a float64
+// compare would take a slot of the narrow float64 pipe)
+__device__ __forceinline__ bool positive_finite(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  return hi < 0x7FF00000u && (hi | lo) != 0u;      // sign clear, exponent not all ones, not zero
+}
+
+// Returns false if either trace is non-physical (rho <= 0 or p <= 0, or NaN).
 template <bool FAST_ALPHA = false>
-__device__ __forceinline__ void lax_friedrichs_scaled(const double ul[M], const double ur[M], double nx,
+__device__ __forceinline__ bool lax_friedrichs_scaled(const double ul[M], const double ur[M], double nx,
                                                       double ny, double gamma, double h, double out[M]) {
   const double il = recip(ul[0]), ir = recip(ur[0]);
   const double uL = ul[1] * il, vL = ul[2] * il, uR = ur[1] * ir, vR = ur[2] * ir;
@@ -73,7 +81,12 @@ __device__ __forceinline__ void lax_friedrichs_scaled(const double ul[M], const 
   fL[3] = (ul[3] + pL) * vnL;       fR[3] = (ur[3] + pR) * vnR;
 #pragma unroll
   for (int m = 0; m < M; ++m) out[m] = h * fma(-a, ur[m] - ul[m], fL[m] + fR[m]);
+  return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(pL) & positive_finite(pR);
 }
+
+// device error flag bits (read by dg_device_status)
+constexpr int kErrTimeout = 1;      // a bounded tensor-core wait expired
+constexpr int kErrNonPhysical = 2;  // rho <= 0 or p <= 0 met at a quadrature point
 
 // out = (d(F(U).n)/dU)^T b for the Euler flux F.n = (rho vn, mx vn + p nx,
 // my vn + p ny, (E+p) vn), using d vn/dU = (-vn, nx, ny, 0)/rho and

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads)
 k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
              const double *__restrict__ fhat, const double *__restrict__ geo,
              const int32_t *__restrict__ elem_face, DevTables tab, int N, double dt, double a0,
-             double b0, int mode, double gamma) {
+             double b0, int mode, double gamma, int *err) {
   using S = SfCfg<P, NE>;
   constexpr int NP = S::NP, ND = S::ND, NQ = S::NQ, NF = S::NF, EB = S::EB;
   extern __shared__ double smem[];
@@ -133,6 +133,7 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
         const double inv = recip(U[0]);
         const double u = U[1] * inv, v = U[2] * inv;
         const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+        if (!(positive_finite(U[0]) & positive_finite(p))) atomicOr(err, kErrNonPhysical);
         double F1[M], F2[M];
         F1[0] = U[1];           F2[0] = U[2];
         F1[1] = U[1] * u + p;   F2[1] = U[1] * v;
@@ -255,7 +256,7 @@ int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *
   const int ntiles = (int)((m->N + S::EB - 1) / S::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
   k_element_sf<P, NE><<<grid, kThreads, S::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
-                                                      (int)m->N, dt, a0, b0, mode, m->gamma);
+                                                      (int)m->N, dt, a0, b0, mode, m->gamma, m->err_flag);
   return (int)cudaGetLastError();
 }
 

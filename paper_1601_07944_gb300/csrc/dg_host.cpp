@@ -340,6 +340,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   const double *xy = d->elem_xy;
   // --- validation and edge list ------------------------------------------
   std::vector<double> geo(N * GEO);
+  double rin_min = INFINITY;
   for (int64_t e = 0; e < N; ++e) {
     const double *v = xy + 6 * e;
     double a = v[2] - v[0], b = v[4] - v[0], c = v[3] - v[1], dd = v[5] - v[1];
@@ -348,6 +349,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
       return fail(DG_EMESH, "element %lld is not counter-clockwise (det J = %g)", (long long)e, det);
     double *g = &geo[e * GEO];
     g[0] = dd; g[1] = -b; g[2] = -c; g[3] = a;      // det J * J^{-1}
+    const double per = std::hypot(a, c) + std::hypot(b, dd) + std::hypot(b - a, dd - c);
+    rin_min = std::min(rin_min, det / per);         // inscribed radius = 2 area / perimeter
     g[4] = 1.0 / det; g[5] = det; g[6] = 0.0; g[7] = 0.0;
   }
   std::vector<int32_t> elem_face(N * 3, -1);
@@ -452,6 +455,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   if (!m->timing) { delete m; return fail(DG_ENOMEM, "dg_mesh_create: host allocation"); }
   m->p = p; m->np = np; m->nq = nq; m->nd = nd; m->ne = ne; m->gamma = d->gamma;
   m->N = N; m->F = F;
+  m->rin_min = rin_min;
   cudaGetDevice(&m->device);
   if (cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess || m->num_sms < 1) {
     cudaGetLastError();
@@ -860,7 +864,10 @@ extern "C" dg_status dg_device_status(dg_mesh *m, void *stream) {
   if (flag) {
     DG_CUDA(cudaMemsetAsync(m->err_flag, 0, sizeof(int), s), "dg_device_status reset");
     DG_CUDA(cudaStreamSynchronize(s), "dg_device_status sync");
-    return fail(DG_ETIMEOUT, "a tensor-core wait in the mixed-precision kernel expired (flag %d)", flag);
+    if (flag & 1)
+      return fail(DG_ETIMEOUT, "a tensor-core wait in the mixed-precision kernel expired%s",
+                  (flag & 2) ? "; a non-physical state was also met" : "");
+    return fail(DG_ENONPHYS, "a non-physical state (rho <= 0 or p <= 0) was met at a quadrature point");
   }
   return DG_OK;
 }
@@ -880,5 +887,25 @@ extern "C" dg_status dg_self_test(int64_t mismatches[3], void *stream) {
   mismatches[0] = (int64_t)h[0];
   mismatches[1] = (int64_t)h[1];
   mismatches[2] = (int64_t)h[2];
+  return DG_OK;
+}
+
+extern "C" dg_status dg_stable_dt(dg_mesh *m, const double *c, double cfl, double *dt_out, void *stream) {
+  if (!m || !c || !dt_out) return fail(DG_EINVAL, "dg_stable_dt: null argument");
+  if (!(cfl > 0.0)) return fail(DG_EINVAL, "dg_stable_dt: cfl must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  double smax = 0.0;
+  int flag = 0;
+  DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return dg::launch_wave_speed(m, c, m->totals_dev, stream); }),
+          "dg_stable_dt");
+  DG_CUDA(cudaMemcpyAsync(&smax, m->totals_dev, sizeof(double), cudaMemcpyDeviceToHost, s), "dg_stable_dt D2H");
+  DG_CUDA(cudaMemcpyAsync(&flag, m->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "dg_stable_dt D2H");
+  DG_CUDA(cudaStreamSynchronize(s), "dg_stable_dt sync");
+  if (flag & 2) {
+    DG_CUDA(cudaMemset(m->err_flag, 0, sizeof(int)), "dg_stable_dt reset");
+    return fail(DG_ENONPHYS, "dg_stable_dt: a non-physical state (rho <= 0 or p <= 0) was met");
+  }
+  if (!(smax > 0.0)) return fail(DG_ENONPHYS, "dg_stable_dt: no positive wave speed");
+  *dt_out = cfl * m->rin_min / ((2 * m->p + 1) * smax);
   return DG_OK;
 }

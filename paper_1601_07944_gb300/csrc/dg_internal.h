@@ -90,7 +90,9 @@ struct dg_mesh {
   double *stage;               // [N][M][np]
   double *host_state;          // [N][M][np] device copy used by dg_rk_step_host
   double *partial;             // [nblk][M] totals partials
-  int *err_flag;               // device int: bit 0 = a bounded tensor-core wait expired
+  int *err_flag;               // device int: bit 0 = a bounded tensor-core wait expired,
+                               //             bit 1 = a non-physical state was met
+  double rin_min;              // smallest inscribed radius 2 area / perimeter
   double *totals_dev;          // [M]
   int totals_blocks;
   // scratch for the adjoint (allocated on first use)
@@ -120,6 +122,8 @@ int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
 int launch_eval_points(const dg_mesh *m, const double *c, const double *tab, int npts, double *out, void *stream);
 int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);
+// largest |v| + c over the volume points -> out_dev[0]
+int launch_wave_speed(const dg_mesh *m, const double *c, double *out_dev, void *stream);
 // (dR/du)^T lam combined as out = x0 X + x1 Y + x2 Z + s (dR/du)^T lam (X, Y, Z may
 // be null).  uvol [N][M][np], G, T, TB [N][3 ne][M] are work buffers.
 int launch_rhs_vjp(const dg_mesh *m, const double *u, const double *lam, double *uvol, double *G, double *T,

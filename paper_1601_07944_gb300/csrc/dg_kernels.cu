@@ -76,7 +76,7 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
 template <int NE, bool FAST_ALPHA>
 __global__ void __launch_bounds__(kThreads)
 k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
-       const FaceGeo *__restrict__ fg, int64_t F, double gamma) {
+       const FaceGeo *__restrict__ fg, int64_t F, double gamma, int *err) {
   constexpr int NF = 3 * NE;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F * NE) return;
@@ -90,7 +90,7 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
 #pragma unroll
   for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
   // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
-  lax_friedrichs_scaled<FAST_ALPHA>(ul, ur, g.nx, g.ny, gamma, 0.5 * g.hl, Fh);
+  if (!lax_friedrichs_scaled<FAST_ALPHA>(ul, ur, g.nx, g.ny, gamma, 0.5 * g.hl, Fh)) atomicOr(err, kErrNonPhysical);
   double *dst = fhat + (size_t)i * M;
 #pragma unroll
   for (int m = 0; m < M; ++m) dst[m] = Fh[m];
@@ -212,6 +212,59 @@ k_totals_final(const double *__restrict__ partial, int nb, double *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// largest wave speed |v| + c over the volume points (max is exact, so the result
+// does not depend on the order)
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+k_wave_partial(const double *__restrict__ c, const double *__restrict__ BvT, int N, double gamma,
+               double *__restrict__ partial, int *err) {
+  constexpr int NP = (P + 1) * (P + 2) / 2, NQ = (P + 1) * (P + 1);
+  __shared__ double red[kThreads / 32];
+  double smax = 0.0;
+  const int64_t chunk = ((int64_t)N * NQ + gridDim.x - 1) / gridDim.x;
+  const int64_t beg = blockIdx.x * chunk;
+  const int64_t end = min((int64_t)N * NQ, beg + chunk);
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const int64_t e = i / NQ;
+    const int k = (int)(i - e * NQ);
+    const double *ce = c + (size_t)e * M * NP;
+    double U[M] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const double b = BvT[j * NQ + k];
+#pragma unroll
+      for (int m = 0; m < M; ++m) U[m] += ce[m * NP + j] * b;
+    }
+    const double inv = recip(U[0]);
+    const double u = U[1] * inv, v = U[2] * inv;
+    const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+    if (!(U[0] > 0.0 && p > 0.0)) {
+      atomicOr(err, kErrNonPhysical);
+      continue;
+    }
+    smax = fmax(smax, sqrt(u * u + v * v) + sqrt(gamma * p * inv));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_down_sync(0xFFFFFFFFu, smax, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) b = fmax(b, red[w]);
+    partial[blockIdx.x] = b;
+  }
+}
+
+__global__ void k_wave_final(const double *__restrict__ partial, int nb, double *__restrict__ out) {
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < nb; ++i) b = fmax(b, partial[i]);
+    out[0] = b;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FMA-rate probe: 8 independent dependency chains per thread, all in registers
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -262,8 +315,8 @@ int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *
   const int64_t n = m->F * m->ne;
   const int grid = (int)((n + kThreads - 1) / kThreads);
 #define FACE(NE)                                                                                      \
-  (fast_alpha ? (k_face<NE, true><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma), 0) \
-              : (k_face<NE, false><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma), 0))
+  (fast_alpha ? (k_face<NE, true><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag), 0) \
+              : (k_face<NE, false><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag), 0))
   switch (m->ne) {
     case 2: FACE(2); break;
     case 3: FACE(3); break;
@@ -311,6 +364,21 @@ int launch_fma_probe(int fp64, int blocks, int threads, int iters, double *out, 
   if (threads != kThreads) return (int)cudaErrorInvalidValue;
   if (fp64) k_fma_probe<double><<<blocks, threads, 0, s>>>(iters, out);
   else k_fma_probe<float><<<blocks, threads, 0, s>>>(iters, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_wave_speed(const dg_mesh *m, const double *c, double *out_dev, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = m->totals_blocks;
+  switch (m->p) {
+    case 1: k_wave_partial<1><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
+    case 2: k_wave_partial<2><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
+    case 3: k_wave_partial<3><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
+    case 4: k_wave_partial<4><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
+    case 5: k_wave_partial<5><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  k_wave_final<<<1, 32, 0, s>>>(m->partial, nb, out_dev);
   return (int)cudaGetLastError();
 }
 

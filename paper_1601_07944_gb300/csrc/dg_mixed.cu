@@ -101,7 +101,7 @@ __device__ __forceinline__ void tmem_row(uint32_t taddr, float *v) {
 }
 
 // float32 reference flux G = J^tau F at one point (Euler flux, Eq. euler)
-__device__ __forceinline__ void ref_flux_f32(const float U[M], const float *jt, float gamma, float Gr[M],
+__device__ __forceinline__ bool ref_flux_f32(const float U[M], const float *jt, float gamma, float Gr[M],
                                              float Gs[M]) {
   const float inv = 1.0f / U[0];
   const float u = U[1] * inv, v = U[2] * inv;
@@ -116,6 +116,7 @@ __device__ __forceinline__ void ref_flux_f32(const float U[M], const float *jt, 
     Gr[m] = jt[0] * F1[m] + jt[1] * F2[m];
     Gs[m] = jt[2] * F1[m] + jt[3] * F2[m];
   }
+  return U[0] > 0.0f && p > 0.0f;      // false also for NaN
 }
 
 template <int P, int NE, bool X3>
@@ -188,7 +189,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     const bool done = tc::mbar_wait(mbar, phase, kWaitNs);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {
-      if (tid == 0) atomicOr(err, 1);
+      if (tid == 0) atomicOr(err, kErrTimeout);
       return false;
     }
     tc::fence_after_sync();
@@ -264,7 +265,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     }
     bool ok = tc::mbar_wait(mbar, phase, kWaitNs);
     phase ^= 1u;
-    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, 1); break; }
+    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, kErrTimeout); break; }
     tc::fence_after_sync();
     {
       float v[N1];
@@ -282,7 +283,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
 #pragma unroll
       for (int m = 0; m < M; ++m) U[m] = sU[i * M + m];
       if (el < ecount) {
-        ref_flux_f32(U, sJ + el * 4, g32, Gr, Gs);
+        if (!ref_flux_f32(U, sJ + el * 4, g32, Gr, Gs)) atomicOr(err, kErrNonPhysical);
       } else {
 #pragma unroll
         for (int m = 0; m < M; ++m) { Gr[m] = 0.0f; Gs[m] = 0.0f; }
@@ -304,7 +305,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     }
     ok = tc::mbar_wait(mbar, phase, kWaitNs);
     phase ^= 1u;
-    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, 1); break; }
+    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, kErrTimeout); break; }
     tc::fence_after_sync();
     {
       float v[N2];

@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
-           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint")
+           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "dg_self_test": [P, P],
         "dg_eval_points": [P, I, P, P, P, P, P],
         "dg_rhs_adjoint": [P, P, P, P, P],
+        "dg_stable_dt": [P, P, D, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -312,6 +313,13 @@ class Mesh:
                                       _dev_ptr(lam_np1, "lam_np1", self.coef_shape),
                                       _dev_ptr(lam, "lam_n", self.coef_shape), _stream_ptr(stream)))
         return lam
+
+    def stable_dt(self, c, cfl: float = 0.3, stream=None) -> float:
+        """cfl * r_min / ((2p+1) max(|v| + c)) over the volume points of c."""
+        out = ctypes.c_double()
+        _check(load().dg_stable_dt(self._h, _dev_ptr(c, "c", self.coef_shape), float(cfl), ctypes.byref(out),
+                                   _stream_ptr(stream)))
+        return out.value
 
     def conserved_totals(self, c, stream=None):
         out = np.zeros(4)

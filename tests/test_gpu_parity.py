@@ -272,3 +272,45 @@ def test_graph_replay_matches_plain_launches(dgmod, prec):
     for _ in range(20):
         m.rk_step(b, dt, 1, precision=prec)
     assert np.array_equal(_host(a), _host(b))
+
+
+def test_stable_dt(dgmod, oracle_mod):
+    """dg_stable_dt against the same formula evaluated from the oracle's point values."""
+    mesh = I.periodic_mesh(12)
+    p = 3
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    c = o.project_ic(I.perturbed_vortex)
+    r, s, _ = o.volume_rule()
+    U = o.eval_points(c, r, s)
+    rho, u, v = U[..., 0], U[..., 1] / U[..., 0], U[..., 2] / U[..., 0]
+    pr = 0.4 * (U[..., 3] - 0.5 * rho * (u * u + v * v))
+    smax = np.max(np.sqrt(u * u + v * v) + np.sqrt(1.4 * pr / rho))
+    xy = mesh.elem_xy
+    a2 = np.abs((xy[:, 1, 0] - xy[:, 0, 0]) * (xy[:, 2, 1] - xy[:, 0, 1])
+                - (xy[:, 1, 1] - xy[:, 0, 1]) * (xy[:, 2, 0] - xy[:, 0, 0]))
+    per = sum(np.hypot(*(xy[:, (q + 1) % 3] - xy[:, q]).T) for q in range(3))
+    ref = 0.3 * np.min(a2 / per) / ((2 * p + 1) * smax)
+    assert abs(m.stable_dt(_dev(c), 0.3) - ref) <= 1e-13 * ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_non_physical_state_reported(dgmod, prec):
+    """A state with negative density in one element is reported as DG_ENONPHYS by
+    dg_device_status (and by dg_stable_dt); the record then clears."""
+    mesh = I.periodic_mesh(8)
+    m = dgmod.Mesh.from_mesh(mesh, 2)
+    c = m.project_function(I.vortex)
+    m.device_status()
+    bad = c.clone()
+    bad[5, 0, 0] = -1.0
+    m.rhs(bad, precision=prec)
+    with pytest.raises(dgmod.DGError) as ei:
+        m.device_status()
+    assert ei.value.status == 5
+    m.device_status()                       # cleared
+    with pytest.raises(dgmod.DGError) as ei:
+        m.stable_dt(bad)
+    assert ei.value.status == 5
+    m.rhs(c, precision=prec)
+    m.device_status()
