@@ -218,11 +218,29 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     }
     // ---- this thread's row: stage input (kept in registers for the update) ----
     const bool live = rel < ecount;
-    double cr[NP];
-    {
-      const double *src = c + ((size_t)(e0 + rel) * M + rm) * NP;
+    // every global load of this row is issued before any of it is used: the
+    // element's three edge records, then its stage input and u^n, then (once the
+    // edge records arrive) the edge-flux values
+    const bool gather = live && mode != 2;
+    int ef[3];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) cr[j] = live ? src[j] : 0.0;
+    for (int q = 0; q < 3; ++q) ef[q] = gather ? elem_face[(size_t)(e0 + rel) * 3 + q] : 0;
+    double cr[NP], ur[NP], fv[NF];
+    {
+      const size_t o = ((size_t)(e0 + rel) * M + rm) * NP;
+      const bool need_u0 = live && mode == 1 && a0 != 0.0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        cr[j] = live ? c[o + j] : 0.0;
+        ur[j] = need_u0 ? u0[o + j] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int f = ef[q] >> 1, side = ef[q] & 1;
+#pragma unroll
+      for (int k = 0; k < NE; ++k)
+        fv[q * NE + k] = gather ? fhat[((size_t)f * NE + (side ? NE - 1 - k : k)) * M + rm] : 0.0;
     }
     for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cr[k]) : 0.0f);
     if (mode == 2) {
@@ -240,15 +258,10 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     double s0 = 0.0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const int ef = live ? elem_face[(size_t)(e0 + rel) * 3 + q] : 0;
-      const int f = ef >> 1, side = ef & 1;
+      const int side = ef[q] & 1;
 #pragma unroll
       for (int k = 0; k < NE; ++k) {
-        double v = 0.0;
-        if (live) {
-          const double x = fhat[((size_t)f * NE + (side ? NE - 1 - k : k)) * M + rm];
-          v = side ? x : tc::neg_bits(x);
-        }
+        const double v = side ? fv[q * NE + k] : tc::neg_bits(fv[q * NE + k]);
         s0 = fma(sL0[q * NE + k], v, s0);
         put<X3>(A2, T::A2P, row, 2 * NQ + q * NE + k, K2, tc::f64_to_f32(v));
       }
@@ -319,11 +332,10 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
         } else {
           // b0 (c + dt R) + a0 u0 with R = D / det J, as b0 c + a0 u0 + (b0 dt / det J) D
           const double kap = b0 * dt * inv;
-          const double *u0r = u0 + (e * M + rm) * NP;
 #pragma unroll
           for (int j = 0; j < NP; ++j) {
             double t = b0 * cr[j];
-            if (a0 != 0.0) t = fma(a0, u0r[j], t);
+            if (a0 != 0.0) t = fma(a0, ur[j], t);
             cr[j] = fma(kap, j == 0 ? s0 : tc::f32_to_f64(v[j]), t);
           }
         }
