@@ -562,12 +562,26 @@ static dg_status check_prec(dg_precision prec, const char *who) {
 }
 
 // element kernel of the chosen precision
-static int launch_elem(const dg_mesh *m, dg_precision prec, const double *c, const double *u0, double *out,
-                       double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,
-                       void *stream) {
-  if (prec == DG_FP64) return dg::launch_element(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, stream);
-  return dg::launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, u0, out, trace_out, fhat, dt, a0, b0, mode,
-                               stream);
+// The three launches of a stage in either precision: the first traces (when
+// asked for), the edge fluxes, and the element kernel.  The mixed modes keep
+// their float32 traces and fluxes in the float64 buffers' storage.
+static int launch_traces_p(dg_mesh *m, dg_precision prec, const double *c, void *stream) {
+  if (prec == DG_FP64) return dg::launch_traces(m, c, m->trace, stream);
+  const dg::MixedBuffers b = dg::mixed_buffers(m, m->trace, m->fhat);
+  return dg::launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, nullptr, nullptr, b.trace, nullptr, nullptr, 0.0,
+                               0.0, 0.0, 2, stream);
+}
+static int launch_face_p(dg_mesh *m, dg_precision prec, void *stream) {
+  if (prec == DG_FP64) return dg::launch_face_flux(m, m->trace, m->fhat, stream);
+  return dg::launch_face_flux_mixed(m, dg::mixed_buffers(m, m->trace, m->fhat), stream);
+}
+static int launch_elem(dg_mesh *m, dg_precision prec, const double *c, const double *u0, double *out,
+                       bool traces, double dt, double a0, double b0, int mode, void *stream) {
+  if (prec == DG_FP64)
+    return dg::launch_element(m, c, u0, out, traces ? m->trace : nullptr, m->fhat, dt, a0, b0, mode, stream);
+  const dg::MixedBuffers b = dg::mixed_buffers(m, m->trace, m->fhat);
+  return dg::launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, u0, out, traces ? b.trace : nullptr, b.fhat,
+                               b.fmean, dt, a0, b0, mode, stream);
 }
 
 extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision prec, void *stream) {
@@ -575,13 +589,12 @@ extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision
   if (c == r) return fail(DG_EINVAL, "dg_rhs: c and r alias");
   dg_status st = check_prec(prec, "dg_rhs");
   if (st != DG_OK) return st;
-  DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return dg::launch_traces(m, c, m->trace, stream); }),
+  DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces_p(m, prec, c, stream); }),
           "dg_rhs traces");
-  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] {
-            return dg::launch_face_flux(m, m->trace, m->fhat, stream, prec != DG_FP64);
-          }), "dg_rhs edge flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_p(m, prec, stream); }),
+          "dg_rhs edge flux");
   DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-            return launch_elem(m, prec, c, nullptr, r, nullptr, m->fhat, 0.0, 0.0, 0.0, 0, stream);
+            return launch_elem(m, prec, c, nullptr, r, false, 0.0, 0.0, 0.0, 0, stream);
           }), "dg_rhs element");
   return DG_OK;
 }
@@ -590,27 +603,22 @@ extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision
 static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, dg_precision prec, void *stream) {
   using namespace dg;
   auto face = [&](const char *what) -> dg_status {
-    DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] {
-              return launch_face_flux(m, m->trace, m->fhat, stream, prec != DG_FP64);
-            }), what);
+    DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_p(m, prec, stream); }), what);
     return DG_OK;
   };
   auto elem = [&](const double *cin, const double *u0, double *out, double a0, double b0,
                   const char *what) -> dg_status {
     DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-              return launch_elem(m, prec, cin, u0, out, m->trace, m->fhat, dt, a0, b0, 1, stream);
+              return launch_elem(m, prec, cin, u0, out, true, dt, a0, b0, 1, stream);
             }), what);
     return DG_OK;
   };
   dg_status st;
+  // mixed modes: the first stage's traces on the tensor cores, like the traces
+  // the element kernel writes for the later stages
   if (!traces_valid)
-    DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] {
-              // mixed modes: the first stage's traces on the tensor cores, like the
-              // traces the element kernel writes for the later stages
-              return prec == DG_FP64 ? launch_traces(m, c, m->trace, stream)
-                                     : launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, nullptr, nullptr,
-                                                         m->trace, nullptr, 0.0, 0.0, 0.0, 2, stream);
-            }), "rk traces");
+    DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces_p(m, prec, c, stream); }),
+            "rk traces");
   // stage 1: u1 = c + dt L(c)
   if ((st = face("rk stage 1 flux")) != DG_OK) return st;
   if ((st = elem(c, nullptr, m->stage, 0.0, 1.0, "rk stage 1")) != DG_OK) return st;

@@ -107,15 +107,23 @@ namespace dg {
 // Kernel launchers (dg_kernels.cu).  All return a cudaError_t cast to int.
 int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream);
 // fast_alpha: the dissipation coefficient in float32 (mixed-precision modes only)
-int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream, bool fast_alpha = false);
+int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream);
 // out = mode==0 ? R(c) : a0*u0 + b0*(c + dt*R(c));  trace_out may be null.
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
                    double *trace_out, const double *fhat, double dt, double a0, double b0,
                    int mode, void *stream);
 // Mixed-precision element kernel (tcgen05, kind::tf32); split3 selects 3xTF32.
+// Work space of the mixed-precision modes, carved from the float64 trace and
+// flux buffers: traces float32 [N][3*ne][M]; edge fluxes float32 [F][ne][M]
+// followed by their float64 mean-mode integrals [F][M] (fits for ne >= 2).
+struct MixedBuffers { float *trace; float *fhat; double *fmean; };
+MixedBuffers mixed_buffers(const dg_mesh *m, double *trace, double *fhat);
+int launch_face_flux_mixed(const dg_mesh *m, const MixedBuffers &b, void *stream);
+// Tensor-core element kernel: as launch_element (mode 0/1) with float32 traces
+// and fluxes; mode 2 writes only the traces of c.
 int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
-                      double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,
-                      void *stream);
+                      float *trace_out, const float *fhat, const double *fmean, double dt, double a0, double b0,
+                      int mode, void *stream);
 int tc_smem_bytes(int p, int ne, int split3);
 int launch_convert_check(int n, unsigned long long *bad, void *stream);
 int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);

@@ -73,7 +73,7 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
 // ---------------------------------------------------------------------------
 // edge flux: fhat[f][k][m] = l_f * F_hat(U_l(r_{L,k}), U_r(r_{R,NE-1-k}), n_f)
 // ---------------------------------------------------------------------------
-template <int NE, bool FAST_ALPHA>
+template <int NE>
 __global__ void __launch_bounds__(kThreads)
 k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
        const FaceGeo *__restrict__ fg, int64_t F, double gamma, int *err) {
@@ -90,7 +90,7 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
 #pragma unroll
   for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
   // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
-  if (!lax_friedrichs_scaled<FAST_ALPHA>(ul, ur, g.nx, g.ny, gamma, 0.5 * g.hl, Fh)) atomicOr(err, kErrNonPhysical);
+  if (!lax_friedrichs_scaled(ul, ur, g.nx, g.ny, gamma, 0.5 * g.hl, Fh)) atomicOr(err, kErrNonPhysical);
   double *dst = fhat + (size_t)i * M;
 #pragma unroll
   for (int m = 0; m < M; ++m) dst[m] = Fh[m];
@@ -310,13 +310,12 @@ int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream
   return (int)cudaErrorInvalidValue;
 }
 
-int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream, bool fast_alpha) {
+int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = m->F * m->ne;
   const int grid = (int)((n + kThreads - 1) / kThreads);
-#define FACE(NE)                                                                                      \
-  (fast_alpha ? (k_face<NE, true><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag), 0) \
-              : (k_face<NE, false><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag), 0))
+#define FACE(NE) \
+  k_face<NE><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag)
   switch (m->ne) {
     case 2: FACE(2); break;
     case 3: FACE(3); break;

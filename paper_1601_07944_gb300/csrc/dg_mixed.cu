@@ -16,9 +16,14 @@
  *           1/det J scaling and the Runge-Kutta stage update
  *   GEMM 3  T[128 x NF]   = C_new[128 x NP] Phi_f[NP x NF]       next edge traces
  * (mode 2 runs GEMM 3 alone on the stage input: the first stage's traces.)
- * The edge flux itself (dg_kernels.cu, k_face) stays float64, and so does the
- * mean mode, which carries the conserved totals: each edge's two contributions
- * to it cancel in float64.
+ *
+ * The traces are results of float32 accumulation, so they are stored as float32
+ * (exactly).  The edge flux (k_face_mixed) widens them exactly and evaluates the
+ * Lax-Friedrichs flux in float64, once per edge; it stores the flux rounded to
+ * float32 for the lift columns of GEMM 2 and, in float64, the flux's integral
+ * against the constant mode.  The mean mode, which carries the conserved totals,
+ * is lifted from those float64 integrals: each edge's value enters its two
+ * elements with opposite signs.
  */
 #include <cuda_runtime.h>
 
@@ -57,12 +62,11 @@ struct Tc {
   static constexpr bool U_IN_A1 = SU <= A1P * NS;            // reuse GEMM 1's A planes
   static constexpr int oU = U_IN_A1 ? oA1 : endB;
   static constexpr int oJ = U_IN_A1 ? endB : endB + SU;      // float [EB][4]  J^tau
-  static constexpr int oL0 = oJ + EB * 16;                   // double [NF]    lift weights of mode 1
-  static constexpr int oBar = (oL0 + NF * 8 + 15) / 16 * 16; // mbarrier, TMEM slot
+  static constexpr int oBar = oJ + EB * 16;                  // mbarrier, TMEM slot
   static constexpr int SMEM = oBar + 16;
   // the new state and the new traces are staged for coalesced stores in GEMM 2's
   // A planes, which are free once GEMM 2 has completed
-  static_assert(EB * M * NP * 8 <= A2P * NS && EB * NF * M * 8 <= A2P * NS, "staging");
+  static_assert(EB * M * NP * 8 <= A2P * NS && EB * NF * M * 4 <= A2P * NS, "staging");
   static_assert(N1 <= kTmemCols && N2 <= kTmemCols && N4 <= kTmemCols, "TMEM columns");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -121,8 +125,8 @@ __device__ __forceinline__ bool ref_flux_f32(const float U[M], const float *jt, 
 
 template <int P, int NE, bool X3>
 __global__ void __launch_bounds__(kTcThreads)
-k_element_tc(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
-             const double *__restrict__ fhat, const double *__restrict__ geo,
+k_element_tc(const double *c, const double *u0, double *out, float *__restrict__ trace_out,
+             const float *__restrict__ fhat, const double *__restrict__ fmean, const double *__restrict__ geo,
              const int32_t *__restrict__ elem_face, DevTables tab, int N, double dt, double a0, double b0,
              int mode, double gamma, int *err) {
   using T = Tc<P, NE, X3>;
@@ -133,7 +137,6 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
   double *sStage = reinterpret_cast<double *>(sm + T::oA2);   // after GEMM 2 only
   float *sU = reinterpret_cast<float *>(sm + T::oU);
   float *sJ = reinterpret_cast<float *>(sm + T::oJ);
-  double *sL0 = reinterpret_cast<double *>(sm + T::oL0);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + T::oBar);
   uint32_t *slot = reinterpret_cast<uint32_t *>(sm + T::oBar + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -162,7 +165,6 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     const double v = (n < NF && k < NP) ? tab.BfT[k * NF + n] : 0.0;
     put<X3>(B4, T::B4P, n, k, K1, (float)v);
   }
-  for (int i = tid; i < NF; i += kTcThreads) sL0[i] = tab.Lf[i * NP];
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(slot), kTmemCols);
   if (tid == 0) tc::mbar_init(mbar, 1);
   tc::fence_proxy_async();
@@ -193,80 +195,102 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
       return false;
     }
     tc::fence_after_sync();
+    float *sT = reinterpret_cast<float *>(sStage);
     {
       float v[N4];
       tmem_row<N4>(trow, v);
 #pragma unroll
-      for (int qk = 0; qk < NF; ++qk) sStage[(rel * NF + qk) * M + rm] = tc::f32_to_f64(v[qk]);
+      for (int qk = 0; qk < NF; ++qk) sT[(rel * NF + qk) * M + rm] = v[qk];
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    double *dst = trace_out + (size_t)e0 * NF * M;
-    for (int i = tid; i < ecount * NF * M; i += kTcThreads) dst[i] = sStage[i];
+    // [EB][NF][M] float32 is whole float4s: NF * M is a multiple of 4
+    const float4 *src4 = reinterpret_cast<const float4 *>(sT);
+    float4 *dst4 = reinterpret_cast<float4 *>(trace_out + (size_t)e0 * NF * M);
+    for (int i = tid; i < ecount * NF; i += kTcThreads) dst4[i] = src4[i];
     return true;
   };
 
   const int ntiles = (N + EB - 1) / EB;
+  // Per-row inputs of a tile, loaded one tile ahead: while tile t runs through
+  // its GEMMs and updates, the loads of tile t + gridDim.x are in flight.  The
+  // edge-flux values depend on the edge records, so they are requested later in
+  // the tile than the rest.  (At p = 5 the two register sets do not fit; there
+  // the loads are issued at the start of the tile itself.)
+  constexpr bool AHEAD = P <= 4;
+  struct RowIn {
+    double c[NP], u[NP], s[3], inv;            // s: the three edges' mean-mode integrals
+    double jt;                                 // entry rm of this row's element's J^tau
+    float f[NF];
+    int ef[3];
+  };
+  const bool need_u0 = mode == 1 && a0 != 0.0;
+  auto load_head = [&](int t, RowIn &r) {
+    const int base = t * EB;
+    const bool lv = t < ntiles && rel < N - base;
+    const size_t o = ((size_t)(base + rel) * M + rm) * NP;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r.ef[q] = lv && mode != 2 ? elem_face[(size_t)(base + rel) * 3 + q] : 0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      r.c[j] = lv ? c[o + j] : 0.0;
+      r.u[j] = lv && need_u0 ? u0[o + j] : 0.0;
+    }
+    r.inv = lv && mode != 2 ? geo[(size_t)(base + rel) * GEO + 4] : 0.0;
+    r.jt = lv && mode != 2 ? geo[(size_t)(base + rel) * GEO + rm] : 0.0;
+  };
+  auto load_flux = [&](int t, RowIn &r) {
+    const bool lv = t < ntiles && rel < N - t * EB && mode != 2;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int f = r.ef[q] >> 1, side = r.ef[q] & 1;
+      r.s[q] = lv ? fmean[(size_t)f * M + rm] : 0.0;
+#pragma unroll
+      for (int k = 0; k < NE; ++k)
+        r.f[q * NE + k] = lv ? fhat[((size_t)f * NE + (side ? NE - 1 - k : k)) * M + rm] : 0.0f;
+    }
+  };
+  static_assert(EB * 4 == kTcThreads, "one J^tau entry per row");
+
+  RowIn cur, nxt;
+  if (AHEAD) { load_head(blockIdx.x, cur); load_flux(blockIdx.x, cur); }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     e0 = tile * EB;
     ecount = min(EB, N - e0);
-    // ---- J^tau of the tile's elements ----
-    for (int i = tid; i < EB * 4; i += kTcThreads) {
-      const int el = i >> 2;
-      sJ[i] = el < ecount ? tc::f64_to_f32(geo[(size_t)(e0 + el) * GEO + (i & 3)]) : 0.0f;
-    }
-    // ---- this thread's row: stage input (kept in registers for the update) ----
     const bool live = rel < ecount;
-    // every global load of this row is issued before any of it is used: the
-    // element's three edge records, then its stage input and u^n, then (once the
-    // edge records arrive) the edge-flux values
-    const bool gather = live && mode != 2;
-    int ef[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) ef[q] = gather ? elem_face[(size_t)(e0 + rel) * 3 + q] : 0;
-    double cr[NP], ur[NP], fv[NF];
-    {
-      const size_t o = ((size_t)(e0 + rel) * M + rm) * NP;
-      const bool need_u0 = live && mode == 1 && a0 != 0.0;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        cr[j] = live ? c[o + j] : 0.0;
-        ur[j] = need_u0 ? u0[o + j] : 0.0;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int f = ef[q] >> 1, side = ef[q] & 1;
-#pragma unroll
-      for (int k = 0; k < NE; ++k)
-        fv[q * NE + k] = gather ? fhat[((size_t)f * NE + (side ? NE - 1 - k : k)) * M + rm] : 0.0;
-    }
-    for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cr[k]) : 0.0f);
+    const int tnext = tile + gridDim.x;
+    if (!AHEAD) { load_head(tile, cur); load_flux(tile, cur); }
+    sJ[row] = tc::f64_to_f32(cur.jt);      // sJ[4 e + i]: entry i of element e's J^tau
+    for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cur.c[k]) : 0.0f);
     if (mode == 2) {
       // ---- traces only: GEMM 3 on the stage input ----
+      if (AHEAD) load_head(tnext, nxt);
       tc::fence_proxy_async();
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
       if (!traces_of_A1()) break;
       __syncthreads();
+      if (AHEAD) cur = nxt;
       continue;
     }
     // ---- its edge fluxes in the element's orientation and point order: the lift
     // columns of GEMM 2, and the mean mode's lift in float64 ----
-    double s0 = 0.0;
+    double sq[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const int side = ef[q] & 1;
+      const int side = cur.ef[q] & 1;
+      sq[q] = side ? cur.s[q] : tc::neg_bits(cur.s[q]);
 #pragma unroll
       for (int k = 0; k < NE; ++k) {
-        const double v = side ? fv[q * NE + k] : tc::neg_bits(fv[q * NE + k]);
-        s0 = fma(sL0[q * NE + k], v, s0);
-        put<X3>(A2, T::A2P, row, 2 * NQ + q * NE + k, K2, tc::f64_to_f32(v));
+        const float v = side ? cur.f[q * NE + k] : -cur.f[q * NE + k];
+        put<X3>(A2, T::A2P, row, 2 * NQ + q * NE + k, K2, v);
       }
     }
+    const double s0 = (sq[0] + sq[1]) + sq[2];
     for (int qk = 2 * NQ + NF; qk < K2; ++qk) put<X3>(A2, T::A2P, row, qk, K2, 0.0f);
+    if (AHEAD) load_head(tnext, nxt);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -316,6 +340,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
       gemm<X3, K2>(tmem, uA2, T::A2P, uB2, T::B2P, tc::idesc_tf32(128, N2));
       tc::commit(mbar);
     }
+    if (AHEAD) load_flux(tnext, nxt);
     ok = tc::mbar_wait(mbar, phase, kWaitNs);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, kErrTimeout); break; }
@@ -323,9 +348,9 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     {
       float v[N2];
       tmem_row<N2>(trow, v);
+      double cr[NP];
       if (live) {
-        const size_t e = (size_t)(e0 + rel);
-        const double inv = geo[e * GEO + 4];
+        const double inv = cur.inv;
         if (mode == 0) {
 #pragma unroll
           for (int j = 0; j < NP; ++j) cr[j] = (j == 0 ? s0 : tc::f32_to_f64(v[j])) * inv;
@@ -334,8 +359,8 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
           const double kap = b0 * dt * inv;
 #pragma unroll
           for (int j = 0; j < NP; ++j) {
-            double t = b0 * cr[j];
-            if (a0 != 0.0) t = fma(a0, ur[j], t);
+            double t = b0 * cur.c[j];
+            if (a0 != 0.0) t = fma(a0, cur.u[j], t);
             cr[j] = fma(kap, j == 0 ? s0 : tc::f32_to_f64(v[j]), t);
           }
         }
@@ -359,6 +384,7 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
     }
     if (trace_out && !traces_of_A1()) break;
     __syncthreads();
+    if (AHEAD) cur = nxt;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -366,9 +392,53 @@ k_element_tc(const double *c, const double *u0, double *out, double *__restrict_
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// Edge flux of the mixed-precision modes, one thread per edge.  The two traces
+// are float32 (exact results of the tensor-core contraction) and are widened
+// exactly; the local Lax-Friedrichs flux is evaluated in float64 at the NE edge
+// points as in k_face (only its dissipation coefficient alpha in float32), with
+// the right element's trace at the reversed point (Eq. edgeint).  Written per
+// edge: l F_hat at the points rounded to float32 (the lift columns of GEMM 2), and
+// the float64 integral of l F_hat against the constant mode,
+// fmean_m = sum_k omega_k phi_1 l F_hat_{k,m} (Algorithm 2 for j = 1; the
+// Gauss-Legendre weights are symmetric, so it is the same from both sides).
+template <int NE>
+__global__ void __launch_bounds__(256)
+k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *__restrict__ fmean,
+             const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg, const double *__restrict__ Lf,
+             int np, int64_t F, double gamma, int *err) {
+  constexpr int NF = 3 * NE;
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const FaceConn cn = conn[f];
+  const FaceGeo g = fg[f];
+  // [N][NF][M] float32: one point's four values are one aligned float4
+  const float4 *tl = reinterpret_cast<const float4 *>(trace) + (size_t)cn.l * NF + cn.L * NE;
+  const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)cn.r * NF + cn.R * NE;
+  float4 *dst = reinterpret_cast<float4 *>(fhat) + (size_t)f * NE;
+  const double h = 0.5 * g.hl;
+  double sm[M] = {0.0, 0.0, 0.0, 0.0};
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    const float4 a = tl[k], b = tr[NE - 1 - k];
+    const double ul[M] = {tc::f32_to_f64(a.x), tc::f32_to_f64(a.y), tc::f32_to_f64(a.z), tc::f32_to_f64(a.w)};
+    const double ur[M] = {tc::f32_to_f64(b.x), tc::f32_to_f64(b.y), tc::f32_to_f64(b.z), tc::f32_to_f64(b.w)};
+    double Fh[M];
+    ok &= lax_friedrichs_scaled<true>(ul, ur, g.nx, g.ny, gamma, h, Fh);
+    const double w = Lf[k * np];             // omega_k phi_1, the same on the three faces
+#pragma unroll
+    for (int m = 0; m < M; ++m) sm[m] = fma(w, Fh[m], sm[m]);
+    dst[k] = make_float4(tc::f64_to_f32(Fh[0]), tc::f64_to_f32(Fh[1]), tc::f64_to_f32(Fh[2]), tc::f64_to_f32(Fh[3]));
+  }
+  double2 *dm = reinterpret_cast<double2 *>(fmean + (size_t)f * M);
+  dm[0] = make_double2(sm[0], sm[1]);
+  dm[1] = make_double2(sm[2], sm[3]);
+  if (!ok) atomicOr(err, kErrNonPhysical);
+}
+
 template <int P, int NE, bool X3>
-int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out, const double *fhat,
-           double dt, double a0, double b0, int mode, cudaStream_t s) {
+int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, float *trace_out, const float *fhat,
+           const double *fmean, double dt, double a0, double b0, int mode, cudaStream_t s) {
   using T = Tc<P, NE, X3>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -380,8 +450,8 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, dou
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  // CTAs per SM from the shared memory each needs (the occupancy query
-  // under-reports for this kernel), at most 8 (TMEM: 512 columns per SM)
+  // CTAs per SM from the shared memory and registers each needs (the occupancy
+  // query under-reports for this kernel), at most 8 (TMEM: 512 columns per SM)
   static int per_sm = 0;
   if (per_sm == 0) {
     int smem_sm = 0, reserved = 0;
@@ -390,21 +460,31 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, dou
     e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device);
     if (e != cudaSuccess) return (int)e;
     per_sm = smem_sm / (T::SMEM + reserved);
+    // and from the registers (allocated per warp in units of 256)
+    int regs_sm = 0;
+    e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, m->device);
+    if (e != cudaSuccess) return (int)e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_element_tc<P, NE, X3>);
+    if (e != cudaSuccess) return (int)e;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = regs_sm / (warp_regs * (kTcThreads / 32));
+    if (per_sm > by_regs) per_sm = by_regs;
     if (per_sm > 512 / kTmemCols) per_sm = 512 / kTmemCols;
     if (per_sm < 1) per_sm = 1;
   }
   const int ntiles = (int)((m->N + T::EB - 1) / T::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_element_tc<P, NE, X3><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face,
+  k_element_tc<P, NE, X3><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face,
                                                             m->tab, (int)m->N, dt, a0, b0, mode, m->gamma,
                                                             m->err_flag);
   return (int)cudaGetLastError();
 }
 
 template <bool X3>
-int dispatch_tc(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
-                const double *fhat, double dt, double a0, double b0, int mode, cudaStream_t s) {
-#define CALL(P, NE) run_tc<P, NE, X3>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s)
+int dispatch_tc(const dg_mesh *m, const double *c, const double *u0, double *out, float *trace_out,
+                const float *fhat, const double *fmean, double dt, double a0, double b0, int mode, cudaStream_t s) {
+#define CALL(P, NE) run_tc<P, NE, X3>(m, c, u0, out, trace_out, fhat, fmean, dt, a0, b0, mode, s)
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);
@@ -452,11 +532,37 @@ int launch_convert_check(int n, unsigned long long *bad, void *stream) {
 }
 
 int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
-                      double *trace_out, const double *fhat, double dt, double a0, double b0, int mode,
-                      void *stream) {
+                      float *trace_out, const float *fhat, const double *fmean, double dt, double a0, double b0,
+                      int mode, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  return split3 ? dispatch_tc<true>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s)
-                : dispatch_tc<false>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s);
+  return split3 ? dispatch_tc<true>(m, c, u0, out, trace_out, fhat, fmean, dt, a0, b0, mode, s)
+                : dispatch_tc<false>(m, c, u0, out, trace_out, fhat, fmean, dt, a0, b0, mode, s);
+}
+
+MixedBuffers mixed_buffers(const dg_mesh *m, double *trace, double *fhat) {
+  MixedBuffers b;
+  b.trace = reinterpret_cast<float *>(trace);
+  b.fhat = reinterpret_cast<float *>(fhat);
+  b.fmean = reinterpret_cast<double *>(b.fhat + (size_t)m->F * m->ne * M);   // byte offset F ne 16
+  return b;
+}
+
+int launch_face_flux_mixed(const dg_mesh *m, const MixedBuffers &b, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = (int)((m->F + 255) / 256);
+#define FACE(NE)                                                                                              \
+  k_face_mixed<NE><<<grid, 256, 0, s>>>(b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->np, \
+                                        m->F, m->gamma, m->err_flag)
+  switch (m->ne) {
+    case 2: FACE(2); break;
+    case 3: FACE(3); break;
+    case 4: FACE(4); break;
+    case 5: FACE(5); break;
+    case 6: FACE(6); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+#undef FACE
+  return (int)cudaGetLastError();
 }
 
 int tc_smem_bytes(int p, int ne, int split3) {

@@ -68,15 +68,24 @@ extern "C" dg_status dg_rhs_noalloc(dg_mesh *m, const double *c, double *r, dg_p
   }
   // Every trace and flux slot is written before it is read, so nothing in the
   // array needs clearing between calls.
+  // The mixed modes use the first half of each block (float32 traces and fluxes,
+  // and the fluxes' float64 mean-mode integrals), in the same launches as dg_rhs.
   double *trace = scratch, *fhat = scratch + n_trace;
-  if ((e = (cudaError_t)dg::launch_traces(m, c, trace, stream)) != cudaSuccess ||
-      (e = (cudaError_t)dg::launch_face_flux(m, trace, fhat, stream, prec != DG_FP64)) != cudaSuccess)
-    return dg::set_error(DG_ECUDA, "dg_rhs_noalloc: %s", cudaGetErrorString(e));
-  if (prec == DG_FP64)
-    e = (cudaError_t)dg::launch_element(m, c, nullptr, r, nullptr, fhat, 0.0, 0.0, 0.0, 0, stream);
-  else
-    e = (cudaError_t)dg::launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, nullptr, r, nullptr, fhat, 0.0, 0.0,
-                                           0.0, 0, stream);
-  if (e != cudaSuccess) return dg::set_error(DG_ECUDA, "dg_rhs_noalloc element: %s", cudaGetErrorString(e));
+  if (prec == DG_FP64) {
+    if ((e = (cudaError_t)dg::launch_traces(m, c, trace, stream)) != cudaSuccess ||
+        (e = (cudaError_t)dg::launch_face_flux(m, trace, fhat, stream)) != cudaSuccess ||
+        (e = (cudaError_t)dg::launch_element(m, c, nullptr, r, nullptr, fhat, 0.0, 0.0, 0.0, 0, stream)) !=
+            cudaSuccess)
+      return dg::set_error(DG_ECUDA, "dg_rhs_noalloc: %s", cudaGetErrorString(e));
+  } else {
+    const int split3 = prec == DG_TF32X3 ? 1 : 0;
+    const dg::MixedBuffers b = dg::mixed_buffers(m, trace, fhat);
+    if ((e = (cudaError_t)dg::launch_element_tc(m, split3, c, nullptr, nullptr, b.trace, nullptr, nullptr, 0.0,
+                                                0.0, 0.0, 2, stream)) != cudaSuccess ||
+        (e = (cudaError_t)dg::launch_face_flux_mixed(m, b, stream)) != cudaSuccess ||
+        (e = (cudaError_t)dg::launch_element_tc(m, split3, c, nullptr, r, nullptr, b.fhat, b.fmean, 0.0, 0.0, 0.0,
+                                                0, stream)) != cudaSuccess)
+      return dg::set_error(DG_ECUDA, "dg_rhs_noalloc: %s", cudaGetErrorString(e));
+  }
   return DG_OK;
 }

@@ -6,9 +6,13 @@ terms, so its error is measured against the size of those terms (the oracle's
 volume term V / det J):
     3xTF32: ||R_mixed - R|| <= 2e-6 (||R|| + ||V||)   (FP32-level arithmetic)
     1xTF32: ||R_mixed - R|| <= 4e-3 (||R|| + ||V||)   (10-bit TF32 mantissa)
-The mean mode is lifted in float64 from the float64 edge flux in both modes (only
-the flux's dissipation coefficient alpha is formed in float32), so the conserved
-totals drift only at float64 rounding.
+The edge traces come from the tensor-core contraction (float32 accumulation) in
+dg_rhs as in every Runge-Kutta stage; the edge flux is evaluated from them in
+float64 (only its dissipation coefficient alpha in float32), and the mean mode is
+lifted in float64 from each edge's float64 flux integral, which its two elements
+take with opposite signs.  So the conserved totals drift only at float64
+rounding, while the mean mode's error follows the traces': it is bounded at the
+mode's tolerance against the size of the surface term S / det J = V / det J - R.
 """
 import numpy as np
 import pytest
@@ -59,9 +63,9 @@ def test_mixed_rhs_vs_oracle(dgmod, oracle_mod, p, ne, n, prec):
     m.device_status()
     err = np.linalg.norm(got - ref)
     assert err <= TOL[prec] * (np.linalg.norm(ref) + np.linalg.norm(vol)), err / np.linalg.norm(ref)
-    # the mean mode is lifted in float64 from the float64 edge fluxes; only the
-    # dissipation coefficient alpha is rounded to float32, far below TF32 error
-    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-6 * np.abs(ref[:, :, 0]).max()
+    # mean mode: no volume term, so its error is the surface term's, whose inputs
+    # (the traces) carry the contraction's rounding
+    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= TOL[prec] * np.abs(vol - ref).max()
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
