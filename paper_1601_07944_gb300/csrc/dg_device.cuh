@@ -41,12 +41,6 @@ __device__ __forceinline__ double recip(double x) {
   return fma(r, e, r);
 }
 
-
-// Local Lax-Friedrichs flux, scaled: out = h (F(Ul).n + F(Ur).n - alpha (Ur - Ul)),
-// alpha = max(|v_l.n| + c_l, |v_r.n| + c_r).  With h = l/2 this is l F_hat.
-// FAST_ALPHA (mixed-precision modes only): alpha, a dissipation coefficient, is
-// formed in float32 from the float64 pressure, density and normal velocity; the
-// flux itself stays float64.
 // x > 0 and finite, tested on the bit pattern with integer instructions (a float64
 // compare would take a slot of the narrow float64 pipe)
 __device__ __forceinline__ bool positive_finite(double x) {
@@ -54,34 +48,45 @@ __device__ __forceinline__ bool positive_finite(double x) {
   return hi < 0x7FF00000u && (hi | lo) != 0u;      // sign clear, exponent not all ones, not zero
 }
 
-// Returns false if either trace is non-physical (rho <= 0 or p <= 0, or NaN).
+// Local Lax-Friedrichs flux times the edge's half length l (Eq. len), at one edge
+// point:  out = l F_hat = h (F(Ul).n + F(Ur).n - alpha (Ur - Ul)),  h = l / 2,
+//         alpha = max(|v_l.n| + c_l, |v_r.n| + c_r),  c = sqrt(gamma p / rho).
+// The scaled normal s = h n of the face record is folded into the physical
+// fluxes: with mn = s.(rho u) = h rho v.n, w = mn / rho and
+// P = E - |rho u|^2 / (2 rho) = p / (gamma - 1),
+//   h F(U).n = (mn, rho u w + P (gamma-1) s_x, rho v w + P (gamma-1) s_y, (E + (gamma-1) P) w)
+// and h alpha = max(|w_l| + h c_l, |w_r| + h c_r), h c = sqrt(hk P / rho).
+// FAST_ALPHA (mixed-precision modes only): h alpha, a dissipation coefficient, is
+// formed in float32; the fluxes and the jump stay float64.
+// Returns false if either side is non-physical (rho <= 0 or p <= 0, or NaN).
 template <bool FAST_ALPHA = false>
-__device__ __forceinline__ bool lax_friedrichs_scaled(const double ul[M], const double ur[M], double nx,
-                                                      double ny, double gamma, double h, double out[M]) {
+__device__ __forceinline__ bool lax_friedrichs_edge(const double ul[M], const double ur[M], const FaceGeo &g,
+                                                    double gamma, double out[M]) {
+  const double g1 = gamma - 1.0;
   const double il = recip(ul[0]), ir = recip(ur[0]);
-  const double uL = ul[1] * il, vL = ul[2] * il, uR = ur[1] * ir, vR = ur[2] * ir;
-  const double pL = (gamma - 1.0) * (ul[3] - 0.5 * (ul[1] * uL + ul[2] * vL));
-  const double pR = (gamma - 1.0) * (ur[3] - 0.5 * (ur[1] * uR + ur[2] * vR));
-  const double vnL = uL * nx + vL * ny, vnR = uR * nx + vR * ny;
-  double a;
+  const double mL = fma(ul[1], g.sx, ul[2] * g.sy), mR = fma(ur[1], g.sx, ur[2] * g.sy);
+  const double wL = mL * il, wR = mR * ir;
+  const double PL = fma(-0.5 * fma(ul[1], ul[1], ul[2] * ul[2]), il, ul[3]);
+  const double PR = fma(-0.5 * fma(ur[1], ur[1], ur[2] * ur[2]), ir, ur[3]);
+  double la;
   if (FAST_ALPHA) {
-    const float g = (float)gamma;
-    const float sL = fabsf(f64_to_f32_dev(vnL)) + sqrtf(g * f64_to_f32_dev(pL) * f64_to_f32_dev(il));
-    const float sR = fabsf(f64_to_f32_dev(vnR)) + sqrtf(g * f64_to_f32_dev(pR) * f64_to_f32_dev(ir));
-    a = f32_to_f64_dev(fmaxf(sL, sR));
+    const float k = f64_to_f32_dev(g.hk);
+    const float aL = fabsf(f64_to_f32_dev(wL)) + sqrtf(k * f64_to_f32_dev(PL) * f64_to_f32_dev(il));
+    const float aR = fabsf(f64_to_f32_dev(wR)) + sqrtf(k * f64_to_f32_dev(PR) * f64_to_f32_dev(ir));
+    la = f32_to_f64_dev(fmaxf(aL, aR));
   } else {
-    const double sL = fabs(vnL) + sqrt(gamma * pL * il);
-    const double sR = fabs(vnR) + sqrt(gamma * pR * ir);
-    a = fmax(sL, sR);
+    const double aL = fabs(wL) + sqrt(g.hk * PL * il);
+    const double aR = fabs(wR) + sqrt(g.hk * PR * ir);
+    la = fmax(aL, aR);
   }
   double fL[M], fR[M];
-  fL[0] = ul[0] * vnL;              fR[0] = ur[0] * vnR;
-  fL[1] = ul[1] * vnL + pL * nx;    fR[1] = ur[1] * vnR + pR * nx;
-  fL[2] = ul[2] * vnL + pL * ny;    fR[2] = ur[2] * vnR + pR * ny;
-  fL[3] = (ul[3] + pL) * vnL;       fR[3] = (ur[3] + pR) * vnR;
+  fL[0] = mL;                             fR[0] = mR;
+  fL[1] = fma(ul[1], wL, PL * g.gsx);     fR[1] = fma(ur[1], wR, PR * g.gsx);
+  fL[2] = fma(ul[2], wL, PL * g.gsy);     fR[2] = fma(ur[2], wR, PR * g.gsy);
+  fL[3] = fma(g1, PL, ul[3]) * wL;        fR[3] = fma(g1, PR, ur[3]) * wR;
 #pragma unroll
-  for (int m = 0; m < M; ++m) out[m] = h * fma(-a, ur[m] - ul[m], fL[m] + fR[m]);
-  return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(pL) & positive_finite(pR);
+  for (int m = 0; m < M; ++m) out[m] = fma(-la, ur[m] - ul[m], fL[m] + fR[m]);
+  return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(PL) & positive_finite(PR);
 }
 
 // device error flag bits (read by dg_device_status)

@@ -380,7 +380,11 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
       if (!(e < f || (e == f && q < qf))) continue;
       int32_t fi = (int32_t)conn.size();
       conn.push_back(FaceConn{(int32_t)e, q, (int32_t)f, qf});
-      fgeo.push_back(FaceGeo{dy / len, -dx / len, 0.5 * len, 0.0});
+      {
+        // l = |edge| / 2 (Eq. len); the flux is scaled by h = l / 2 (F_hat's 1/2)
+        const double nx = dy / len, ny = -dx / len, l = 0.5 * len, h = 0.5 * l, g1 = d->gamma - 1.0;
+        fgeo.push_back(FaceGeo{nx, ny, l, h * h * d->gamma * g1, h * nx, h * ny, g1 * (h * nx), g1 * (h * ny)});
+      }
       elem_face[3 * e + q] = 2 * fi + 0;
       elem_face[3 * f + qf] = 2 * fi + 1;
     }

@@ -24,8 +24,10 @@ constexpr int GEO = 8;
 
 // Face record: left element, its local face, right element, its local face.
 struct FaceConn { int32_t l, L, r, R; };
-// Face geometry: unit normal (left -> right) and half length l_f (Eq. len).
-struct FaceGeo { double nx, ny, hl, pad; };
+// Face geometry (8 doubles): unit normal n (left -> right) and half length l
+// (Eq. len); then the products the edge flux uses, formed once on the host with
+// h = l / 2: hk = h^2 gamma (gamma - 1), the scaled normal s = h n, and (gamma - 1) s.
+struct FaceGeo { double nx, ny, hl, hk, sx, sy, gsx, gsy; };
 
 struct DevTables {
   // All float64, device.  NP modes, NQ volume points, NF = 3*NE face points.

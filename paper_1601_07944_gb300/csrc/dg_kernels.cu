@@ -90,7 +90,7 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
 #pragma unroll
   for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
   // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
-  if (!lax_friedrichs_scaled(ul, ur, g.nx, g.ny, gamma, 0.5 * g.hl, Fh)) atomicOr(err, kErrNonPhysical);
+  if (!lax_friedrichs_edge(ul, ur, g, gamma, Fh)) atomicOr(err, kErrNonPhysical);
   double *dst = fhat + (size_t)i * M;
 #pragma unroll
   for (int m = 0; m < M; ++m) dst[m] = Fh[m];

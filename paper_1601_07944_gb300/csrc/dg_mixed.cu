@@ -415,7 +415,6 @@ k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *
   const float4 *tl = reinterpret_cast<const float4 *>(trace) + (size_t)cn.l * NF + cn.L * NE;
   const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)cn.r * NF + cn.R * NE;
   float4 *dst = reinterpret_cast<float4 *>(fhat) + (size_t)f * NE;
-  const double h = 0.5 * g.hl;
   double sm[M] = {0.0, 0.0, 0.0, 0.0};
   bool ok = true;
 #pragma unroll
@@ -424,7 +423,7 @@ k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *
     const double ul[M] = {tc::f32_to_f64(a.x), tc::f32_to_f64(a.y), tc::f32_to_f64(a.z), tc::f32_to_f64(a.w)};
     const double ur[M] = {tc::f32_to_f64(b.x), tc::f32_to_f64(b.y), tc::f32_to_f64(b.z), tc::f32_to_f64(b.w)};
     double Fh[M];
-    ok &= lax_friedrichs_scaled<true>(ul, ur, g.nx, g.ny, gamma, h, Fh);
+    ok &= lax_friedrichs_edge<true>(ul, ur, g, gamma, Fh);
     const double w = Lf[k * np];             // omega_k phi_1, the same on the three faces
 #pragma unroll
     for (int m = 0; m < M; ++m) sm[m] = fma(w, Fh[m], sm[m]);
