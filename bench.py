@@ -65,11 +65,12 @@ def flops_element_per_elem(p: int, ne: int) -> float:
 def bytes_element_tc_per_elem(p: int, ne: int) -> float:
     """Algorithmic HBM bytes of one mixed-precision element-kernel launch per
     element, averaged over the three stages: stage input 8*4*N_p, u^n in two of
-    three stages, both sides' gathers of the edge fluxes 8*4*3n_e, geometry 64 B
-    + face map 12 B, new state 8*4*N_p, new traces 8*4*3n_e."""
+    three stages, the gathers of the three edges' float32 fluxes 4*4*3n_e and
+    their float64 mean-mode integrals 3*4*8, geometry 64 B + face map 12 B, new
+    state 8*4*N_p, new float32 traces 4*4*3n_e."""
     NP = (p + 1) * (p + 2) // 2
     NF = 3 * ne
-    return 32 * NP + (2.0 / 3.0) * 32 * NP + 32 * NF + 76 + 32 * NP + 32 * NF
+    return 32 * NP + (2.0 / 3.0) * 32 * NP + 16 * NF + 96 + 76 + 32 * NP + 16 * NF
 
 
 def hbm_peak():
@@ -95,7 +96,7 @@ def _src_hash(*names) -> str:
 # change voids the entry.
 TRAFFIC = {
     # k_element_sf<3,4>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
-    "86a86ec8bb6bf538": 77164288 + 39253760,
+    "f1cb4b0e5de84012": 77178624 + 39680768,
 }
 
 

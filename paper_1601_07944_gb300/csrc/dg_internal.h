@@ -110,6 +110,7 @@ namespace dg {
 int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream);
 // fast_alpha: the dissipation coefficient in float32 (mixed-precision modes only)
 int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream);
+int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, int *per_sm);
 // out = mode==0 ? R(c) : a0*u0 + b0*(c + dt*R(c));  trace_out may be null.
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
                    double *trace_out, const double *fhat, double dt, double a0, double b0,

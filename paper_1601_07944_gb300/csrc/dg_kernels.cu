@@ -78,22 +78,29 @@ __global__ void __launch_bounds__(kThreads)
 k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
        const FaceGeo *__restrict__ fg, int64_t F, double gamma, int *err) {
   constexpr int NF = 3 * NE;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= F * NE) return;
-  const int64_t f = i / NE;
-  const int k = (int)(i - f * NE);
-  const FaceConn cn = conn[f];
-  const FaceGeo g = fg[f];
-  const double *pl = trace + ((size_t)cn.l * NF + cn.L * NE + k) * M;
-  const double *pr = trace + ((size_t)cn.r * NF + cn.R * NE + (NE - 1 - k)) * M;
-  double ul[M], ur[M], Fh[M];
+  bool ok = true;
+  // The grid is what fits on the GPU at once; block b takes the b-th of gridDim.x
+  // equal slices of the (edge, point) items, so every SM gets the same share
+  // and there is no partial last wave.
+  const int64_t n = F * NE;
+  const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int64_t f = i / NE;
+    const int k = (int)(i - f * NE);
+    const FaceConn cn = conn[f];
+    const FaceGeo g = fg[f];
+    const double *pl = trace + ((size_t)cn.l * NF + cn.L * NE + k) * M;
+    const double *pr = trace + ((size_t)cn.r * NF + cn.R * NE + (NE - 1 - k)) * M;
+    double ul[M], ur[M], Fh[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
-  // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
-  if (!lax_friedrichs_edge(ul, ur, g, gamma, Fh)) atomicOr(err, kErrNonPhysical);
-  double *dst = fhat + (size_t)i * M;
+    for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
+    // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
+    ok &= lax_friedrichs_edge(ul, ur, g, gamma, Fh);
+    double *dst = fhat + (size_t)i * M;
 #pragma unroll
-  for (int m = 0; m < M; ++m) dst[m] = Fh[m];
+    for (int m = 0; m < M; ++m) dst[m] = Fh[m];
+  }
+  if (!ok) atomicOr(err, kErrNonPhysical);
 }
 
 // ---------------------------------------------------------------------------
@@ -310,12 +317,31 @@ int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream
   return (int)cudaErrorInvalidValue;
 }
 
+// blocks of `threads` threads needed for n items, at most what is resident on
+// the GPU at once (a grid-stride kernel covers the rest); per_sm is the kernel's
+// resident blocks per SM (0: ask the occupancy calculator)
+int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, int *per_sm) {
+  if (*per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 1;
+    }
+    *per_sm = v;
+  }
+  const int64_t need = (n + threads - 1) / threads, cap = (int64_t)m->num_sms * *per_sm;
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
 int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = m->F * m->ne;
-  const int grid = (int)((n + kThreads - 1) / kThreads);
-#define FACE(NE) \
-  k_face<NE><<<grid, kThreads, 0, s>>>(trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag)
+#define FACE(NE)                                                                                        \
+  do {                                                                                                  \
+    static int per_sm = 0;                                                                              \
+    k_face<NE><<<resident_grid(m, (const void *)k_face<NE>, kThreads, n, &per_sm), kThreads, 0, s>>>(   \
+        trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag);                           \
+  } while (0)
   switch (m->ne) {
     case 2: FACE(2); break;
     case 3: FACE(3); break;

@@ -74,11 +74,14 @@ struct Tc {
 // writes v (rounded to TF32, and its TF32 remainder for the split product) at
 // (row, k) of a K-major operand with ktot columns
 template <bool X3>
-__device__ __forceinline__ void put(unsigned char *base, int plane_bytes, int row, int k, int ktot, float v) {
-  const int off = tc::kmaj(row, k, ktot);
+__device__ __forceinline__ void put_at(unsigned char *base, int plane_bytes, int off, float v) {
   const float hi = tc::to_tf32(v);
   *reinterpret_cast<float *>(base + off) = hi;
   if (X3) *reinterpret_cast<float *>(base + plane_bytes + off) = tc::to_tf32(v - hi);
+}
+template <bool X3>
+__device__ __forceinline__ void put(unsigned char *base, int plane_bytes, int row, int k, int ktot, float v) {
+  put_at<X3>(base, plane_bytes, tc::kmaj(row, k, ktot), v);
 }
 
 // D (TMEM) = sum over k-steps of A B^T, split products when X3
@@ -216,9 +219,12 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   // Per-row inputs of a tile, loaded one tile ahead: while tile t runs through
   // its GEMMs and updates, the loads of tile t + gridDim.x are in flight.  The
   // edge-flux values depend on the edge records, so they are requested later in
-  // the tile than the rest.  (At p = 5 the two register sets do not fit; there
-  // the loads are issued at the start of the tile itself.)
-  constexpr bool AHEAD = P <= 4;
+  // the tile than the rest.  The second register set costs resident CTAs where
+  // registers, not shared memory, bound them: at p = 5 it does not fit at all,
+  // and for the 1xTF32 kernels at p = 2 and 4 (small shared memory) the CTAs it
+  // displaces hide more latency than it does (measured); there the loads are
+  // issued at the start of the tile itself.
+  constexpr bool AHEAD = P <= 4 && (X3 || P == 3);
   struct RowIn {
     double c[NP], u[NP], s[3], inv;            // s: the three edges' mean-mode integrals
     double jt;                                 // entry rm of this row's element's J^tau
@@ -300,6 +306,15 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
       gemm<X3, K1>(tmem, uA1, T::A1P, uB1, T::B1P, tc::idesc_tf32(128, N1));
       tc::commit(mbar);
     }
+    // the part of the stage update that does not depend on the RHS, b0 c + a0 u0,
+    // in float64 while the tensor core runs GEMM 1:
+    // b0 (c + dt R) + a0 u0 with R = D / det J is b0 c + a0 u0 + (b0 dt / det J) D
+    double tb[NP];
+    const double kap = b0 * dt * cur.inv;
+    if (mode == 1) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) tb[j] = need_u0 ? fma(a0, cur.u[j], b0 * cur.c[j]) : b0 * cur.c[j];
+    }
     bool ok = tc::mbar_wait(mbar, phase, kWaitNs);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, kErrTimeout); break; }
@@ -314,22 +329,33 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     __syncthreads();
     tc::fence_after_sync();
     // ---- float32 flux at the volume points -> G_r, G_s columns of GEMM 2 ----
-    for (int i = tid; i < EB * NQ; i += kTcThreads) {
-      const int el = i / NQ, k = i - el * NQ;
-      float U[M], Gr[M], Gs[M];
+    // Thread (element rel, kk = rm) takes the points k = kk + 4 i of its element.
+    // Column C0 + kk + 4 i of row 4 rel + m sits at byte kmaj(4 rel, C0 + kk) +
+    // 16 m + 128 i, so every store below is a fixed offset from two bases.
+    {
+      const int oGr = tc::kmaj(4 * rel, rm, K2), oGs = tc::kmaj(4 * rel, NQ + rm, K2);
+      bool phys = true;
 #pragma unroll
-      for (int m = 0; m < M; ++m) U[m] = sU[i * M + m];
-      if (el < ecount) {
-        if (!ref_flux_f32(U, sJ + el * 4, g32, Gr, Gs)) atomicOr(err, kErrNonPhysical);
-      } else {
+      for (int i = 0; i < (NQ + 3) / 4; ++i) {
+        const int k = rm + 4 * i;
+        if (k < NQ) {
+          const float4 U4 = *reinterpret_cast<const float4 *>(sU + (rel * NQ + k) * M);
+          const float U[M] = {U4.x, U4.y, U4.z, U4.w};
+          float Gr[M], Gs[M];
+          if (live) {
+            phys &= ref_flux_f32(U, sJ + rel * 4, g32, Gr, Gs);
+          } else {
 #pragma unroll
-        for (int m = 0; m < M; ++m) { Gr[m] = 0.0f; Gs[m] = 0.0f; }
+            for (int m = 0; m < M; ++m) { Gr[m] = 0.0f; Gs[m] = 0.0f; }
+          }
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            put_at<X3>(A2, T::A2P, oGr + 16 * m + 128 * i, Gr[m]);
+            put_at<X3>(A2, T::A2P, oGs + 16 * m + 128 * i, Gs[m]);
+          }
+        }
       }
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        put<X3>(A2, T::A2P, el * 4 + m, k, K2, Gr[m]);
-        put<X3>(A2, T::A2P, el * 4 + m, NQ + k, K2, Gs[m]);
-      }
+      if (!phys) atomicOr(err, kErrNonPhysical);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -355,14 +381,8 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
 #pragma unroll
           for (int j = 0; j < NP; ++j) cr[j] = (j == 0 ? s0 : tc::f32_to_f64(v[j])) * inv;
         } else {
-          // b0 (c + dt R) + a0 u0 with R = D / det J, as b0 c + a0 u0 + (b0 dt / det J) D
-          const double kap = b0 * dt * inv;
 #pragma unroll
-          for (int j = 0; j < NP; ++j) {
-            double t = b0 * cur.c[j];
-            if (a0 != 0.0) t = fma(a0, cur.u[j], t);
-            cr[j] = fma(kap, j == 0 ? s0 : tc::f32_to_f64(v[j]), t);
-          }
+          for (int j = 0; j < NP; ++j) cr[j] = fma(kap, j == 0 ? s0 : tc::f32_to_f64(v[j]), tb[j]);
         }
       } else {
 #pragma unroll
@@ -407,31 +427,35 @@ k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *
              const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg, const double *__restrict__ Lf,
              int np, int64_t F, double gamma, int *err) {
   constexpr int NF = 3 * NE;
-  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F) return;
-  const FaceConn cn = conn[f];
-  const FaceGeo g = fg[f];
-  // [N][NF][M] float32: one point's four values are one aligned float4
-  const float4 *tl = reinterpret_cast<const float4 *>(trace) + (size_t)cn.l * NF + cn.L * NE;
-  const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)cn.r * NF + cn.R * NE;
-  float4 *dst = reinterpret_cast<float4 *>(fhat) + (size_t)f * NE;
-  double sm[M] = {0.0, 0.0, 0.0, 0.0};
   bool ok = true;
+  // the grid is what is resident at once; block b takes the b-th of gridDim.x
+  // equal slices of the edges
+  const int64_t lo = F * blockIdx.x / gridDim.x, hi = F * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t f = lo + threadIdx.x; f < hi; f += blockDim.x) {
+    const FaceConn cn = conn[f];
+    const FaceGeo g = fg[f];
+    // [N][NF][M] float32: one point's four values are one aligned float4
+    const float4 *tl = reinterpret_cast<const float4 *>(trace) + (size_t)cn.l * NF + cn.L * NE;
+    const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)cn.r * NF + cn.R * NE;
+    float4 *dst = reinterpret_cast<float4 *>(fhat) + (size_t)f * NE;
+    double sm[M] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-  for (int k = 0; k < NE; ++k) {
-    const float4 a = tl[k], b = tr[NE - 1 - k];
-    const double ul[M] = {tc::f32_to_f64(a.x), tc::f32_to_f64(a.y), tc::f32_to_f64(a.z), tc::f32_to_f64(a.w)};
-    const double ur[M] = {tc::f32_to_f64(b.x), tc::f32_to_f64(b.y), tc::f32_to_f64(b.z), tc::f32_to_f64(b.w)};
-    double Fh[M];
-    ok &= lax_friedrichs_edge<true>(ul, ur, g, gamma, Fh);
-    const double w = Lf[k * np];             // omega_k phi_1, the same on the three faces
+    for (int k = 0; k < NE; ++k) {
+      const float4 a = tl[k], b = tr[NE - 1 - k];
+      const double ul[M] = {tc::f32_to_f64(a.x), tc::f32_to_f64(a.y), tc::f32_to_f64(a.z), tc::f32_to_f64(a.w)};
+      const double ur[M] = {tc::f32_to_f64(b.x), tc::f32_to_f64(b.y), tc::f32_to_f64(b.z), tc::f32_to_f64(b.w)};
+      double Fh[M];
+      ok &= lax_friedrichs_edge<true>(ul, ur, g, gamma, Fh);
+      const double w = Lf[k * np];           // omega_k phi_1, the same on the three faces
 #pragma unroll
-    for (int m = 0; m < M; ++m) sm[m] = fma(w, Fh[m], sm[m]);
-    dst[k] = make_float4(tc::f64_to_f32(Fh[0]), tc::f64_to_f32(Fh[1]), tc::f64_to_f32(Fh[2]), tc::f64_to_f32(Fh[3]));
+      for (int m = 0; m < M; ++m) sm[m] = fma(w, Fh[m], sm[m]);
+      dst[k] = make_float4(tc::f64_to_f32(Fh[0]), tc::f64_to_f32(Fh[1]), tc::f64_to_f32(Fh[2]),
+                           tc::f64_to_f32(Fh[3]));
+    }
+    double2 *dm = reinterpret_cast<double2 *>(fmean + (size_t)f * M);
+    dm[0] = make_double2(sm[0], sm[1]);
+    dm[1] = make_double2(sm[2], sm[3]);
   }
-  double2 *dm = reinterpret_cast<double2 *>(fmean + (size_t)f * M);
-  dm[0] = make_double2(sm[0], sm[1]);
-  dm[1] = make_double2(sm[2], sm[3]);
   if (!ok) atomicOr(err, kErrNonPhysical);
 }
 
@@ -548,10 +572,12 @@ MixedBuffers mixed_buffers(const dg_mesh *m, double *trace, double *fhat) {
 
 int launch_face_flux_mixed(const dg_mesh *m, const MixedBuffers &b, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  const int grid = (int)((m->F + 255) / 256);
-#define FACE(NE)                                                                                              \
-  k_face_mixed<NE><<<grid, 256, 0, s>>>(b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->np, \
-                                        m->F, m->gamma, m->err_flag)
+#define FACE(NE)                                                                                          \
+  do {                                                                                                    \
+    static int per_sm = 0;                                                                                \
+    k_face_mixed<NE><<<resident_grid(m, (const void *)k_face_mixed<NE>, 256, m->F, &per_sm), 256, 0, s>>>( \
+        b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->np, m->F, m->gamma, m->err_flag); \
+  } while (0)
   switch (m->ne) {
     case 2: FACE(2); break;
     case 3: FACE(3); break;
