@@ -68,6 +68,8 @@ def _load():
             "or_rhs": (I, [P, P, P]),
             "or_last_volume_term": (I, [P, P]),
             "or_ssp_rk3": (I, [P, P, D, I]),
+            "or_rk2": (I, [P, P, D, I]),
+            "or_rk4": (I, [P, P, D, I]),
             "or_totals": (I, [P, P, P]),
             "or_lax_friedrichs_jacobians": (I, [D, P, P, D, D, P, P]),
             "or_flux_jacobian": (I, [D, P, D, D, P]),
@@ -291,6 +293,18 @@ class OracleDG:
     def ssp_rk3(self, c, dt: float, nsteps: int):
         out = np.array(c, dtype=np.float64, copy=True, order="C")
         _chk(_lib.or_ssp_rk3(self._h, _ptr(out), dt, nsteps))
+        return out
+
+    def rk2(self, c, dt: float, nsteps: int):
+        """Heun's two-stage method (the paper's classic RK2), nsteps steps."""
+        out = np.array(c, dtype=np.float64, copy=True, order="C")
+        _chk(_lib.or_rk2(self._h, _ptr(out), dt, nsteps))
+        return out
+
+    def rk4(self, c, dt: float, nsteps: int):
+        """The classical four-stage RK4 (the paper's RK4), nsteps steps."""
+        out = np.array(c, dtype=np.float64, copy=True, order="C")
+        _chk(_lib.or_rk4(self._h, _ptr(out), dt, nsteps))
         return out
 
     def rhs_vjp(self, c, lam):

@@ -33,7 +33,7 @@
  *     two traces at each quadrature point;
  *   - the surface temporaries are per edge (one left and one right block).
  *   - time integration: the three-stage SSP Runge-Kutta method in Shu-Osher
- *     form (the paper itself uses classic RK2/RK4).
+ *     form, and the paper's own classic RK2 (read as Heun's method) and RK4.
  *
  * Layout of every coefficient array: c[e][m][j], element e, variable m (M=4),
  * mode j (N_p), float64.
@@ -799,6 +799,52 @@ int or_ssp_rk3(oracle_dg *o, double *C, double dt, int nsteps)
         for (size_t t = 0; t < n; ++t) C[t] = C[t] / 3.0 + 2.0 / 3.0 * (u2[t] + dt * L[t]);
     }
     free(u1); free(u2); free(L);
+    return 0;
+}
+
+/* The paper's own time integrators (Section 4.3.1, classic explicit Runge-Kutta
+ * methods of order two and four), in Butcher form with every stage derivative
+ * k_i = L(u + dt sum_j a_ij k_j) kept, nsteps steps in place.
+ *   RK2 (reading: Heun's method, c = (0, 1), b = (1/2, 1/2)):
+ *     k1 = L(u), k2 = L(u + dt k1), u <- u + dt/2 (k1 + k2)
+ *   RK4 (the classical method, c = (0, 1/2, 1/2, 1), b = (1, 2, 2, 1)/6):
+ *     k1 = L(u), k2 = L(u + dt/2 k1), k3 = L(u + dt/2 k2), k4 = L(u + dt k3),
+ *     u <- u + dt/6 (k1 + 2 k2 + 2 k3 + k4) */
+int or_rk2(oracle_dg *o, double *C, double dt, int nsteps)
+{
+    size_t n = (size_t)o->N * OM * o->np;
+    double *y = malloc(sizeof(double) * n), *k1 = malloc(sizeof(double) * n), *k2 = malloc(sizeof(double) * n);
+    if (!y || !k1 || !k2) { free(y); free(k1); free(k2); return 1; }
+    for (int it = 0; it < nsteps; ++it) {
+        or_rhs(o, C, k1);
+        for (size_t t = 0; t < n; ++t) y[t] = C[t] + dt * k1[t];
+        or_rhs(o, y, k2);
+        for (size_t t = 0; t < n; ++t) C[t] = C[t] + 0.5 * dt * (k1[t] + k2[t]);
+    }
+    free(y); free(k1); free(k2);
+    return 0;
+}
+
+int or_rk4(oracle_dg *o, double *C, double dt, int nsteps)
+{
+    size_t n = (size_t)o->N * OM * o->np;
+    double *y = malloc(sizeof(double) * n), *k[4];
+    for (int i = 0; i < 4; ++i) k[i] = malloc(sizeof(double) * n);
+    if (!y || !k[0] || !k[1] || !k[2] || !k[3]) {
+        free(y); for (int i = 0; i < 4; ++i) free(k[i]);
+        return 1;
+    }
+    static const double a[4] = {0.0, 0.5, 0.5, 1.0};   /* a_{i,i-1}; every other a_ij is 0 */
+    for (int it = 0; it < nsteps; ++it) {
+        or_rhs(o, C, k[0]);
+        for (int i = 1; i < 4; ++i) {
+            for (size_t t = 0; t < n; ++t) y[t] = C[t] + a[i] * dt * k[i - 1][t];
+            or_rhs(o, y, k[i]);
+        }
+        for (size_t t = 0; t < n; ++t)
+            C[t] = C[t] + dt / 6.0 * (k[0][t] + 2.0 * k[1][t] + 2.0 * k[2][t] + k[3][t]);
+    }
+    free(y); for (int i = 0; i < 4; ++i) free(k[i]);
     return 0;
 }
 
