@@ -9,6 +9,9 @@ hot path, on inputs already resident in HBM.  L2 is flushed (256 MiB write)
 between timed steps, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64|tf32x3|tf32x1] [--method ssp_rk3|rk2|rk4]
+  python bench.py --configs     the five stated workloads, one JSON line each
+  python bench.py --sweep       mesh-size scaling (RK4, p = 1 and 4, 200 to 184,832 elements)
 
 With N = 1 the line also carries the tensor-core modes on the same workload
 (throughput, speedup over float64 and state error against the float64 run) and
@@ -175,8 +178,12 @@ def _dist():
     return world, rank, local
 
 
-def _dof_per_step(N: int, p: int) -> int:
-    return N * (p + 1) * (p + 2) // 2 * 4 * 3
+STAGES = {"ssp_rk3": 3, "rk2": 2, "rk4": 4}
+
+
+def _dof_per_step(N: int, p: int, method: str = "ssp_rk3") -> int:
+    """DOF updates of one time step: every stage updates all N N_p 4 unknowns."""
+    return N * (p + 1) * (p + 2) // 2 * 4 * STAGES[method]
 
 
 def slowest_rank_ms(ms: float, world: int, device: str = "cuda") -> float:
@@ -296,6 +303,62 @@ def mixed_modes(m, c0, dt, steps, flush, fp64_ms_per_step):
                      "rel_l2_vs_fp64": float(np.linalg.norm(X - R) / np.linalg.norm(R)),
                      "error_after_steps": steps}
     return out
+
+
+def paper_steppers(m, c0, dt, steps, flush):
+    """Float64 throughput of the paper's own integrators (classic RK2 read as
+    Heun's method, and RK4) on the same workload, per RK stage as the headline."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    for method in ("rk2", "rk4"):
+        c = c0.clone()
+        for _ in range(3):
+            m.rk_step(c, dt, 1, method=method)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream); m.rk_step(c, dt, 1, method=method); m.conserved_totals(c); b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        m.device_status()
+        out[method] = {"value": _dof_per_step(m.N, m.p, method) * steps / (ms * 1e-3),
+                       "stages": STAGES[method], "ms_per_step": ms / steps}
+    return out
+
+
+def run_sweep(precisions=("fp64",)):
+    """Mesh-size scaling in the manner of the paper's Section 5 scaling runs
+    (p = 1 for 10,000 steps and p = 4 for 1,000 steps, RK4, on meshes of 180 to
+    184,320 elements): jittered periodic meshes of 200 to 184,832 elements, the
+    perturbed vortex, classical RK4, device-timed whole runs (CUDA graphs)."""
+    import torch
+    from paper_1601_07944_gb300 import _build, dg, inputs as I
+    _build.build()
+    dg.load()
+    for p, steps in ((1, 10000), (4, 1000)):
+        for n in (10, 20, 40, 80, 160, 304):
+            mesh = I.periodic_mesh(n)
+            m = dg.Mesh.from_mesh(mesh, p)
+            dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+            c0 = m.project_function(I.perturbed_vortex)
+            for prec in precisions:
+                c = c0.clone()
+                m.rk_step(c, dt, 17, precision=prec, method="rk4")     # capture + warm the graph
+                a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(); a.record()
+                m.rk_step(c, dt, steps, precision=prec, method="rk4")
+                b.record(); torch.cuda.synchronize()
+                m.device_status()
+                ms = a.elapsed_time(b)
+                print(json.dumps({"sweep": "mesh size", "method": "rk4", "p": p, "n": n, "n_elem": m.N,
+                                  "precision": prec, "steps": steps, "time_s": ms * 1e-3,
+                                  "ms_per_step": ms / steps,
+                                  "dof_updates_per_s": _dof_per_step(m.N, p, "rk4") * steps / (ms * 1e-3)}),
+                      flush=True)
+            del m
 
 
 def vortex_error(steps: int = 200):
@@ -486,12 +549,13 @@ def run_ours(args, world, rank, local):
             tdist.barrier()
 
     p, ne = WORKLOAD["p"], WORKLOAD["ne"]
+    method = args.method
     mesh = I.periodic_mesh(WORKLOAD["n"])
     m = dg.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
     ne = m.ne
     c = m.project_function(I.vortex)
     dt = I.fixed_dt(mesh, I.vortex, p, WORKLOAD["cfl"])
-    dof_step = _dof_per_step(m.N, p)
+    dof_step = _dof_per_step(m.N, p, method)
     stream = torch.cuda.current_stream()
 
     fp64_peak, fp32_peak = dg.probe_fma_rate()
@@ -499,7 +563,7 @@ def run_ours(args, world, rank, local):
 
     prec = args.precision
     for _ in range(args.warmup):
-        m.rk_step(c, dt, 1, precision=prec)
+        m.rk_step(c, dt, 1, precision=prec, method=method)
         m.conserved_totals(c)
     torch.cuda.synchronize()
 
@@ -516,7 +580,7 @@ def run_ours(args, world, rank, local):
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         starts[i].record(stream)
-        m.rk_step(c, dt, 1, precision=prec)
+        m.rk_step(c, dt, 1, precision=prec, method=method)
         totals = m.conserved_totals(c)
         ends[i].record(stream)
     torch.cuda.synchronize()
@@ -536,8 +600,16 @@ def run_ours(args, world, rank, local):
     h.copy_(c.cpu())
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        m.rk_step_host(h, dt, 1, precision=prec)
+    if method == "ssp_rk3":
+        for _ in range(e2e_steps):
+            m.rk_step_host(h, dt, 1, precision=prec)
+    else:
+        # the same copies around dg_rk_step_method (pinned host buffer, one stream)
+        for _ in range(e2e_steps):
+            c.copy_(h, non_blocking=True)
+            m.rk_step(c, dt, 1, precision=prec, method=method)
+            h.copy_(c, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
     state_bytes = m.N * 4 * m.np * 8
 
@@ -571,7 +643,9 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else prec + " contractions, f64 flux/update",
             "data": "synthetic (seeded jittered periodic mesh, isentropic vortex)",
-            "config": {"workload": WORKLOAD["name"], "n_elem": m.N, "p": p, "n_edge_pts": ne,
+            "config": {"workload": WORKLOAD["name"] if method == "ssp_rk3"
+                       else WORKLOAD["name"].replace("SSP-RK3", method.upper()),
+                       "n_elem": m.N, "p": p, "n_edge_pts": ne, "method": method,
                        "n_vol_pts": m.nq, "precision": prec, "dt": dt,
                        "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -581,7 +655,7 @@ def run_ours(args, world, rank, local):
             "fp32_fma_tflops": fp32_peak,
             "e2e": {"value": dof_step * e2e_steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-                    "entry": "dg_rk_step_host"},
+                    "entry": "dg_rk_step_host" if method == "ssp_rk3" else "dg_rk_step_method"},
             "gpu_launches": launches,
             "paper_context": "GTX 580 (Fermi, FP64), double Mach reflection, p=1, RK2 with limiter: "
                              "1.31e8-1.53e8 DOF-updates/s per stage, derived from the paper's runtime "
@@ -590,9 +664,10 @@ def run_ours(args, world, rank, local):
             "wall_s_timed_region": wall,
             "totals_last_step": [float(x) for x in totals] if totals is not None else None,
         }
-        if world == 1 and not args.no_extras and prec == "fp64":
+        if world == 1 and not args.no_extras and prec == "fp64" and method == "ssp_rk3":
             c0 = m.project_function(I.vortex)
             line["mixed"] = mixed_modes(m, c0, dt, max(5, min(args.steps, 20)), flush, t_max / args.steps)
+            line["paper_steppers"] = paper_steppers(m, c0, dt, max(5, min(args.steps, 20)), flush)
             line["adjoint"] = adjoint_ratio()
             line["vortex_200_steps"] = vortex_error()
         if world == 1 and not args.no_cpu_baseline:
@@ -618,6 +693,10 @@ def main():
                     help="arithmetic of the timed steps (the headline line is fp64)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision and adjoint measurements")
+    ap.add_argument("--method", choices=sorted(STAGES), default="ssp_rk3",
+                    help="time integrator of the timed steps (the headline line is ssp_rk3)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="mesh-size scaling runs (p=1 x 10000 and p=4 x 1000 RK4 steps) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -625,6 +704,10 @@ def main():
     if args.configs:
         if rank == 0:
             run_configs()
+        return
+    if args.sweep:
+        if rank == 0:
+            run_sweep((args.precision,))
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

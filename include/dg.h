@@ -20,7 +20,8 @@
  * index), a collapsed Gauss-Jacobi volume rule with p+1 points per direction,
  * Gauss-Legendre edge rules with n_edge_pts points (default p+1, as in the
  * paper's Section 4.3.3), the local Lax-Friedrichs flux and the three-stage
- * SSP Runge-Kutta method.
+ * SSP Runge-Kutta method (the paper's own classic RK2, read as Heun's method,
+ * and RK4 are available through dg_rk_step_method).
  *
  * Conventions for every call:
  *   - Coefficient arrays are element-major, c[e][m][j]: element e, conserved
@@ -66,6 +67,15 @@ typedef enum {
     DG_TF32X1 = 1,      /* contractions on the tensor cores, one TF32 product, FP32 accumulate */
     DG_TF32X3 = 2       /* contractions as split 3xTF32 products, FP32 accumulate */
 } dg_precision;
+
+/* Explicit Runge-Kutta methods of dg_rk_step_method.  The paper integrates
+ * Eq. 2ddg0 with classic explicit RK methods of order two and four (Section
+ * 4.3.1); the three-stage SSP method is the default of dg_rk_step. */
+typedef enum {
+    DG_SSP_RK3 = 0,     /* three-stage SSP method, third order (Shu-Osher form) */
+    DG_RK2 = 1,         /* Heun's method: u + dt/2 (k1 + k2), k2 = L(u + dt k1); second order */
+    DG_RK4 = 2          /* the classical four-stage method, fourth order */
+} dg_rk_method;
 
 /* Host description of a mesh; dg_mesh_create copies everything it needs. */
 typedef struct {
@@ -157,6 +167,19 @@ dg_status dg_rhs_noalloc(dg_mesh *mesh, const double *c, double *r, dg_precision
  * ordered after, and then before, `stream` with events. */
 dg_status dg_rk_step(dg_mesh *mesh, double *c, double dt, int nsteps, dg_precision prec,
                      void *stream);
+
+/* nsteps steps of the Runge-Kutta method `method` (see dg_rk_method) in place on c
+ * (DEVICE [N][4][N_p]); dg_rk_step is this call with DG_SSP_RK3.  Heun's method
+ * runs as u1 = u + dt L(u), u <- 1/2 u + 1/2 (u1 + dt L(u1)); the classical RK4
+ * (Section 4.3.1) keeps the running sum u + dt sum_i b_i k_i of its stages in a
+ * work array of the mesh (N * 4 * N_p doubles, allocated by the first DG_RK4 call
+ * on the handle: make that call before any stream capture).  Each stage is one
+ * edge-flux launch and one element launch in every precision mode; the stage
+ * accumulation is float64.  Asynchronous; graph replay as for dg_rk_step, keyed
+ * also by the method.  Errors: DG_EINVAL (unknown method or precision, nsteps < 0,
+ * dt not finite), DG_ENOMEM (the RK4 work array), DG_ECUDA. */
+dg_status dg_rk_step_method(dg_mesh *mesh, double *c, double dt, int nsteps, dg_rk_method method,
+                            dg_precision prec, void *stream);
 
 /* Same as dg_rk_step with c in HOST memory (pinned memory gives the fastest
  * copies): copies c to the device, takes nsteps steps and copies the result back

@@ -2,8 +2,9 @@
  * dg_element.cu -- the float64 element kernel of one stage (k_element_sf): the
  * volume integral (Eq. volume, Algorithm 1) sum-factorised on the collapsed
  * volume grid, the lift of the three edge fluxes (Algorithms 2-3), the 1/det J
- * scaling (Eq. 2ddg0), the Runge-Kutta stage update and the next stage's edge
- * traces, for one tile of elements per CTA.
+ * scaling (Eq. 2ddg0), the Runge-Kutta stage update (with, for the classical
+ * RK4, the running sum of its stages as a second output) and the next stage's
+ * edge traces, for one tile of elements per CTA.
  */
 #include <cuda_runtime.h>
 
@@ -50,8 +51,8 @@ template <int P, int NE>
 __global__ void __launch_bounds__(kThreads)
 k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
              const double *__restrict__ fhat, const double *__restrict__ geo,
-             const int32_t *__restrict__ elem_face, DevTables tab, int N, double dt, double a0,
-             double b0, int mode, double gamma, int *err) {
+             const int32_t *__restrict__ elem_face, DevTables tab, int N, StageUpdate su, int mode,
+             double gamma, int *err) {
   using S = SfCfg<P, NE>;
   constexpr int NP = S::NP, ND = S::ND, NQ = S::NQ, NF = S::NF, EB = S::EB;
   extern __shared__ double smem[];
@@ -193,9 +194,9 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
       if (el < ecount) {
         const size_t e = (size_t)(e0 + el);
         const double inv = geo[e * GEO + 4];
-        // stage update b0 (c + dt R) + a0 u0 with R = acc / det J, as
-        // b0 c + a0 u0 + (b0 dt / det J) acc
-        const double kap = b0 * dt * inv;
+        // stage update a0 u0 + b0 c + g dt R with R = acc / det J, as
+        // b0 c + a0 u0 + (g dt / det J) acc (and the second output alike)
+        const double kap = su.g * su.dt * inv;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           const size_t idx = (e * M + m) * NP + j;
@@ -203,9 +204,14 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
           if (mode == 0) {
             v = acc[m] * inv;
           } else {
-            double t = b0 * sC[(el * M + m) * NP + j];
-            if (a0 != 0.0) t = fma(a0, u0[idx], t);
+            double t = su.b0 * sC[(el * M + m) * NP + j];
+            if (su.a0 != 0.0) t = fma(su.a0, u0[idx], t);
             v = fma(kap, acc[m], t);
+            if (su.out2) {
+              double t2 = su.y * v;
+              if (su.x != 0.0) t2 = fma(su.x, su.acc[idx], t2);
+              su.out2[idx] = fma(su.w * su.dt * inv, acc[m], t2);
+            }
           }
           out[idx] = v;
           nv[m] = v;
@@ -239,7 +245,7 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 
 template <int P, int NE>
 int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
-                   const double *fhat, double dt, double a0, double b0, int mode, cudaStream_t s) {
+                   const double *fhat, const StageUpdate &su, int mode, cudaStream_t s) {
   using S = SfCfg<P, NE>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -256,16 +262,16 @@ int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *
   const int ntiles = (int)((m->N + S::EB - 1) / S::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
   k_element_sf<P, NE><<<grid, kThreads, S::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
-                                                      (int)m->N, dt, a0, b0, mode, m->gamma, m->err_flag);
+                                                      (int)m->N, su, mode, m->gamma, m->err_flag);
   return (int)cudaGetLastError();
 }
 
 }  // namespace
 
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
-                   const double *fhat, double dt, double a0, double b0, int mode, void *stream) {
+                   const double *fhat, const StageUpdate &su, int mode, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
-#define CALL(P, NE) run_element_sf<P, NE>(m, c, u0, out, trace_out, fhat, dt, a0, b0, mode, s)
+#define CALL(P, NE) run_element_sf<P, NE>(m, c, u0, out, trace_out, fhat, su, mode, s)
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);

@@ -235,7 +235,7 @@ void free_mesh(dg_mesh *m) {
   if (!m) return;
   cudaFree(m->geo); cudaFree(m->xy); cudaFree(m->elem_face); cudaFree(m->face_conn);
   cudaFree(m->face_geo); cudaFree(m->table_block); cudaFree(m->trace); cudaFree(m->fhat);
-  cudaFree(m->stage); cudaFree(m->host_state); cudaFree(m->partial); cudaFree(m->totals_dev);
+  cudaFree(m->stage); cudaFree(m->host_state); cudaFree(m->rk_acc); cudaFree(m->partial); cudaFree(m->totals_dev);
   cudaFree(m->adj_buf);
   cudaFree(m->err_flag);
   if (m->timing) {
@@ -580,12 +580,12 @@ static int launch_face_p(dg_mesh *m, dg_precision prec, void *stream) {
   return dg::launch_face_flux_mixed(m, dg::mixed_buffers(m, m->trace, m->fhat), stream);
 }
 static int launch_elem(dg_mesh *m, dg_precision prec, const double *c, const double *u0, double *out,
-                       bool traces, double dt, double a0, double b0, int mode, void *stream) {
+                       bool traces, const dg::StageUpdate &su, int mode, void *stream) {
   if (prec == DG_FP64)
-    return dg::launch_element(m, c, u0, out, traces ? m->trace : nullptr, m->fhat, dt, a0, b0, mode, stream);
+    return dg::launch_element(m, c, u0, out, traces ? m->trace : nullptr, m->fhat, su, mode, stream);
   const dg::MixedBuffers b = dg::mixed_buffers(m, m->trace, m->fhat);
   return dg::launch_element_tc(m, prec == DG_TF32X3 ? 1 : 0, c, u0, out, traces ? b.trace : nullptr, b.fhat,
-                               b.fmean, dt, a0, b0, mode, stream);
+                               b.fmean, su, mode, stream);
 }
 
 extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision prec, void *stream) {
@@ -598,24 +598,38 @@ extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision
   DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_p(m, prec, stream); }),
           "dg_rhs edge flux");
   DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-            return launch_elem(m, prec, c, nullptr, r, false, 0.0, 0.0, 0.0, 0, stream);
+            return launch_elem(m, prec, c, nullptr, r, false, dg::shu_osher(0.0, 0.0, 0.0), 0, stream);
           }), "dg_rhs element");
   return DG_OK;
 }
 
-// One SSP-RK3 step; on entry m->trace holds the traces of c when traces_valid.
-static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, dg_precision prec, void *stream) {
+static dg_status check_method(dg_rk_method method, const char *who) {
+  if (method == DG_SSP_RK3 || method == DG_RK2 || method == DG_RK4) return DG_OK;
+  return fail(DG_EINVAL, "%s: unknown Runge-Kutta method %d", who, (int)method);
+}
+
+// One step of the chosen Runge-Kutta method; on entry m->trace holds the traces
+// of c when traces_valid.  Every stage is an edge-flux launch and an element
+// launch; each element launch also writes the traces of its output, which the
+// next stage (or step) reads.
+static dg_status rk_step_one(dg_mesh *m, double *c, double dt, bool traces_valid, dg_rk_method method,
+                             dg_precision prec, void *stream) {
   using namespace dg;
   auto face = [&](const char *what) -> dg_status {
     DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_p(m, prec, stream); }), what);
     return DG_OK;
   };
-  auto elem = [&](const double *cin, const double *u0, double *out, double a0, double b0,
+  auto elem = [&](const double *cin, const double *u0, double *out, const StageUpdate &su,
                   const char *what) -> dg_status {
     DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-              return launch_elem(m, prec, cin, u0, out, true, dt, a0, b0, 1, stream);
+              return launch_elem(m, prec, cin, u0, out, true, su, 1, stream);
             }), what);
     return DG_OK;
+  };
+  auto stage = [&](const double *cin, const double *u0, double *out, const StageUpdate &su,
+                   const char *what) -> dg_status {
+    dg_status st = face(what);
+    return st != DG_OK ? st : elem(cin, u0, out, su, what);
   };
   dg_status st;
   // mixed modes: the first stage's traces on the tensor cores, like the traces
@@ -623,16 +637,37 @@ static dg_status rk3_step(dg_mesh *m, double *c, double dt, bool traces_valid, d
   if (!traces_valid)
     DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces_p(m, prec, c, stream); }),
             "rk traces");
-  // stage 1: u1 = c + dt L(c)
-  if ((st = face("rk stage 1 flux")) != DG_OK) return st;
-  if ((st = elem(c, nullptr, m->stage, 0.0, 1.0, "rk stage 1")) != DG_OK) return st;
-  // stage 2: u2 = 3/4 c + 1/4 (u1 + dt L(u1)), written over u1
-  if ((st = face("rk stage 2 flux")) != DG_OK) return st;
-  if ((st = elem(m->stage, c, m->stage, 0.75, 0.25, "rk stage 2")) != DG_OK) return st;
-  // stage 3: c <- 1/3 c + 2/3 (u2 + dt L(u2))
-  if ((st = face("rk stage 3 flux")) != DG_OK) return st;
-  if ((st = elem(m->stage, c, c, 1.0 / 3.0, 2.0 / 3.0, "rk stage 3")) != DG_OK) return st;
-  return DG_OK;
+  double *S = m->stage;
+  switch (method) {
+    case DG_SSP_RK3:
+      // u1 = c + dt L(c);  u2 = 3/4 c + 1/4 (u1 + dt L(u1)), over u1;
+      // c <- 1/3 c + 2/3 (u2 + dt L(u2))
+      if ((st = stage(c, nullptr, S, shu_osher(dt, 0.0, 1.0), "ssp-rk3 stage 1")) != DG_OK) return st;
+      if ((st = stage(S, c, S, shu_osher(dt, 0.75, 0.25), "ssp-rk3 stage 2")) != DG_OK) return st;
+      return stage(S, c, c, shu_osher(dt, 1.0 / 3.0, 2.0 / 3.0), "ssp-rk3 stage 3");
+    case DG_RK2:
+      // Heun's method c + dt/2 (k1 + k2) in Shu-Osher form:
+      // u1 = c + dt L(c);  c <- 1/2 c + 1/2 (u1 + dt L(u1))
+      if ((st = stage(c, nullptr, S, shu_osher(dt, 0.0, 1.0), "rk2 stage 1")) != DG_OK) return st;
+      return stage(S, c, c, shu_osher(dt, 0.5, 0.5), "rk2 stage 2");
+    case DG_RK4: {
+      // classical RK4 with the running sum A of dt b_i k_i:
+      //   stage 1: S = c + dt/2 k1,  A = S - dt/3 k1   (= c + dt/6 k1)
+      //   stage 2: S = c + dt/2 k2,  A += dt/3 k2
+      //   stage 3: S = c + dt k3,    A += dt/3 k3
+      //   stage 4: c = A + dt/6 k4
+      double *A = m->rk_acc;
+      StageUpdate s1{dt, 0.0, 1.0, 0.5, nullptr, A, 0.0, 1.0, -1.0 / 3.0};
+      StageUpdate s2{dt, 1.0, 0.0, 0.5, A, A, 1.0, 0.0, 1.0 / 3.0};
+      StageUpdate s3{dt, 1.0, 0.0, 1.0, A, A, 1.0, 0.0, 1.0 / 3.0};
+      StageUpdate s4{dt, 1.0, 0.0, 1.0 / 6.0, nullptr, nullptr, 0.0, 0.0, 0.0};
+      if ((st = stage(c, nullptr, S, s1, "rk4 stage 1")) != DG_OK) return st;
+      if ((st = stage(S, c, S, s2, "rk4 stage 2")) != DG_OK) return st;
+      if ((st = stage(S, c, S, s3, "rk4 stage 3")) != DG_OK) return st;
+      return stage(S, A, c, s4, "rk4 stage 4");
+    }
+  }
+  return fail(DG_EINVAL, "rk step: unknown method");
 }
 
 // Steps per captured graph.  Replaying a graph runs its launches back to back,
@@ -641,11 +676,13 @@ constexpr int kGraphSteps = 16;
 
 // The cached graph of kGraphSteps steps for (c, dt, prec), capturing it if the
 // key changed; nullptr if capture is unavailable (plain launches are used).
-static cudaGraphExec_t step_graph(dg_mesh *m, double *c, double dt, dg_precision prec) {
+static cudaGraphExec_t step_graph(dg_mesh *m, double *c, double dt, dg_rk_method method, dg_precision prec) {
   if (!m->graph) m->graph = new (std::nothrow) dg::GraphCache();
   dg::GraphCache *g = m->graph;
   if (!g || g->broken) return nullptr;
-  if (g->exec && g->c == c && g->dt == dt && g->prec == (int)prec && g->steps == kGraphSteps) return g->exec;
+  if (g->exec && g->c == c && g->dt == dt && g->prec == (int)prec && g->method == (int)method &&
+      g->steps == kGraphSteps)
+    return g->exec;
   if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
   if (!g->stream && cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) g->stream = nullptr;
   if (g->stream && !g->ready && cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming) != cudaSuccess) g->ready = nullptr;
@@ -654,7 +691,7 @@ static cudaGraphExec_t step_graph(dg_mesh *m, double *c, double dt, dg_precision
   cudaGraph_t graph = nullptr;
   bool ok = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
   if (ok) {
-    for (int i = 0; i < kGraphSteps && ok; ++i) ok = rk3_step(m, c, dt, true, prec, g->stream) == DG_OK;
+    for (int i = 0; i < kGraphSteps && ok; ++i) ok = rk_step_one(m, c, dt, true, method, prec, g->stream) == DG_OK;
     ok = (cudaStreamEndCapture(g->stream, &graph) == cudaSuccess) && ok && graph;
   }
   if (ok) ok = cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
@@ -666,25 +703,30 @@ static cudaGraphExec_t step_graph(dg_mesh *m, double *c, double dt, dg_precision
     g_err.clear();
     return nullptr;
   }
-  g->c = c; g->dt = dt; g->prec = (int)prec; g->steps = kGraphSteps;
+  g->c = c; g->dt = dt; g->prec = (int)prec; g->method = (int)method; g->steps = kGraphSteps;
   return g->exec;
 }
 
-extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg_precision prec,
-                                void *stream) {
+extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nsteps, dg_rk_method method,
+                                       dg_precision prec, void *stream) {
   if (!m || !c) return fail(DG_EINVAL, "dg_rk_step: null argument");
   if (nsteps < 0) return fail(DG_EINVAL, "dg_rk_step: nsteps < 0");
   if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_rk_step: dt is not finite");
   dg_status st = check_prec(prec, "dg_rk_step");
   if (st != DG_OK) return st;
+  if ((st = check_method(method, "dg_rk_step")) != DG_OK) return st;
+  if (method == DG_RK4 && !m->rk_acc && nsteps > 0) {
+    cudaError_t e = cudaMalloc(&m->rk_acc, sizeof(double) * m->N * dg::M * m->np);
+    if (e != cudaSuccess) { cudaGetLastError(); m->rk_acc = nullptr; return fail(DG_ENOMEM, "dg_rk_step: RK4 buffer"); }
+  }
   int done = 0;
   if (nsteps > 0) {
-    if ((st = rk3_step(m, c, dt, false, prec, stream)) != DG_OK) return st;
+    if ((st = rk_step_one(m, c, dt, false, method, prec, stream)) != DG_OK) return st;
     done = 1;
   }
   // whole chunks of steps as a replayed CUDA graph (not while per-kernel timing is on)
   if (nsteps - done >= kGraphSteps && !(m->timing && m->timing->on)) {
-    cudaGraphExec_t exec = step_graph(m, c, dt, prec);
+    cudaGraphExec_t exec = step_graph(m, c, dt, method, prec);
     if (exec) {
       dg::GraphCache *g = m->graph;
       cudaStream_t s = (cudaStream_t)stream;
@@ -699,8 +741,13 @@ extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg
     }
   }
   for (; done < nsteps; ++done)
-    if ((st = rk3_step(m, c, dt, true, prec, stream)) != DG_OK) return st;
+    if ((st = rk_step_one(m, c, dt, true, method, prec, stream)) != DG_OK) return st;
   return DG_OK;
+}
+
+extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg_precision prec,
+                                void *stream) {
+  return dg_rk_step_method(m, c, dt, nsteps, DG_SSP_RK3, prec, stream);
 }
 
 extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int nsteps,

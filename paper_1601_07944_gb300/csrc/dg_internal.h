@@ -47,6 +47,23 @@ struct DevTables {
   double *SK;    // [3][NQ]    2w/(1-s), w(1+alpha)/(1-s), 2w: weights of the collapsed chain rule
 };
 
+// One Runge-Kutta stage update of the element kernels (their mode 1), with
+// R = R(c) the right-hand side of the stage input c:
+//   out  = a0 u0 + b0 c + g dt R
+//   out2 = x acc + y out + w dt R      (only when out2 is not null; acc may be out2)
+// The SSP methods in Shu-Osher form use g = b0, i.e. out = a0 u0 + b0 (c + dt R),
+// and no out2; the classical RK4 keeps the running sum of its stage derivatives
+// in out2.
+struct StageUpdate {
+  double dt, a0, b0, g;
+  const double *acc;
+  double *out2;
+  double x, y, w;
+};
+inline StageUpdate shu_osher(double dt, double a0, double b0) {
+  return StageUpdate{dt, a0, b0, b0, nullptr, nullptr, 0.0, 0.0, 0.0};
+}
+
 // Per-kernel CUDA-event timing (dg_set_timing / dg_kernel_times).
 struct Timing {
   bool on = false;
@@ -57,15 +74,16 @@ struct Timing {
   int64_t launches[DG_NKINDS] = {};
 };
 
-// A CUDA graph of several SSP-RK3 steps, captured once per (state pointer, dt,
-// precision, step count) and replayed by dg_rk_step on an internal stream.
+// A CUDA graph of several Runge-Kutta steps, captured once per (state pointer,
+// dt, precision, method, step count) and replayed by dg_rk_step on an internal
+// stream.
 struct GraphCache {
   cudaStream_t stream = nullptr;
   cudaEvent_t ready = nullptr, done = nullptr;
   cudaGraphExec_t exec = nullptr;
   double *c = nullptr;
   double dt = 0.0;
-  int prec = -1, steps = 0;
+  int prec = -1, steps = 0, method = -1;
   bool broken = false;        // capture failed once: use plain launches from then on
 };
 
@@ -91,6 +109,7 @@ struct dg_mesh {
   double *fhat;                // [F][ne][M]
   double *stage;               // [N][M][np]
   double *host_state;          // [N][M][np] device copy used by dg_rk_step_host
+  double *rk_acc;              // [N][M][np] running sum of the RK4 stages (first RK4 call)
   double *partial;             // [nblk][M] totals partials
   int *err_flag;               // device int: bit 0 = a bounded tensor-core wait expired,
                                //             bit 1 = a non-physical state was met
@@ -111,10 +130,15 @@ int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream
 // fast_alpha: the dissipation coefficient in float32 (mixed-precision modes only)
 int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream);
 int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, int *per_sm);
-// out = mode==0 ? R(c) : a0*u0 + b0*(c + dt*R(c));  trace_out may be null.
+// out = mode==0 ? R(c) : the stage update su (and su.out2);  trace_out may be null.
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
-                   double *trace_out, const double *fhat, double dt, double a0, double b0,
-                   int mode, void *stream);
+                   double *trace_out, const double *fhat, const StageUpdate &su, int mode, void *stream);
+// out = mode==0 ? R(c) : a0*u0 + b0*(c + dt*R(c))
+inline int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
+                          double *trace_out, const double *fhat, double dt, double a0, double b0,
+                          int mode, void *stream) {
+  return launch_element(m, c, u0, out, trace_out, fhat, shu_osher(dt, a0, b0), mode, stream);
+}
 // Mixed-precision element kernel (tcgen05, kind::tf32); split3 selects 3xTF32.
 // Work space of the mixed-precision modes, carved from the float64 trace and
 // flux buffers: traces float32 [N][3*ne][M]; edge fluxes float32 [F][ne][M]
@@ -125,8 +149,13 @@ int launch_face_flux_mixed(const dg_mesh *m, const MixedBuffers &b, void *stream
 // Tensor-core element kernel: as launch_element (mode 0/1) with float32 traces
 // and fluxes; mode 2 writes only the traces of c.
 int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
-                      float *trace_out, const float *fhat, const double *fmean, double dt, double a0, double b0,
+                      float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
                       int mode, void *stream);
+inline int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
+                             float *trace_out, const float *fhat, const double *fmean, double dt, double a0,
+                             double b0, int mode, void *stream) {
+  return launch_element_tc(m, split3, c, u0, out, trace_out, fhat, fmean, shu_osher(dt, a0, b0), mode, stream);
+}
 int tc_smem_bytes(int p, int ne, int split3);
 int launch_convert_check(int n, unsigned long long *bad, void *stream);
 int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);

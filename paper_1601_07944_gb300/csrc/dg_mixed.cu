@@ -126,12 +126,14 @@ __device__ __forceinline__ bool ref_flux_f32(const float U[M], const float *jt, 
   return U[0] > 0.0f && p > 0.0f;      // false also for NaN
 }
 
-template <int P, int NE, bool X3>
+// OUT2: the stage also writes the classical RK4's running sum (StageUpdate::out2);
+// a separate instantiation, so that the kernels without it keep their registers.
+template <int P, int NE, bool X3, bool OUT2>
 __global__ void __launch_bounds__(kTcThreads)
 k_element_tc(const double *c, const double *u0, double *out, float *__restrict__ trace_out,
              const float *__restrict__ fhat, const double *__restrict__ fmean, const double *__restrict__ geo,
-             const int32_t *__restrict__ elem_face, DevTables tab, int N, double dt, double a0, double b0,
-             int mode, double gamma, int *err) {
+             const int32_t *__restrict__ elem_face, DevTables tab, int N, StageUpdate su, int mode,
+             double gamma, int *err) {
   using T = Tc<P, NE, X3>;
   constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB;
   constexpr int K1 = T::K1, N1 = T::N1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
@@ -231,7 +233,7 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     float f[NF];
     int ef[3];
   };
-  const bool need_u0 = mode == 1 && a0 != 0.0;
+  const bool need_u0 = mode == 1 && su.a0 != 0.0;
   auto load_head = [&](int t, RowIn &r) {
     const int base = t * EB;
     const bool lv = t < ntiles && rel < N - base;
@@ -308,12 +310,12 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     }
     // the part of the stage update that does not depend on the RHS, b0 c + a0 u0,
     // in float64 while the tensor core runs GEMM 1:
-    // b0 (c + dt R) + a0 u0 with R = D / det J is b0 c + a0 u0 + (b0 dt / det J) D
+    // a0 u0 + b0 c + g dt R with R = D / det J is b0 c + a0 u0 + (g dt / det J) D
     double tb[NP];
-    const double kap = b0 * dt * cur.inv;
+    const double kap = su.g * su.dt * cur.inv;
     if (mode == 1) {
 #pragma unroll
-      for (int j = 0; j < NP; ++j) tb[j] = need_u0 ? fma(a0, cur.u[j], b0 * cur.c[j]) : b0 * cur.c[j];
+      for (int j = 0; j < NP; ++j) tb[j] = need_u0 ? fma(su.a0, cur.u[j], su.b0 * cur.c[j]) : su.b0 * cur.c[j];
     }
     bool ok = tc::mbar_wait(mbar, phase, kWaitNs);
     phase ^= 1u;
@@ -381,8 +383,20 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
 #pragma unroll
           for (int j = 0; j < NP; ++j) cr[j] = (j == 0 ? s0 : tc::f32_to_f64(v[j])) * inv;
         } else {
+          // with the second output (the classical RK4's running sum)
+          // x acc + y out + (w dt / det J) D beside it
+          const size_t o = ((size_t)(e0 + rel) * M + rm) * NP;
+          const double kw = su.w * su.dt * inv;
 #pragma unroll
-          for (int j = 0; j < NP; ++j) cr[j] = fma(kap, j == 0 ? s0 : tc::f32_to_f64(v[j]), tb[j]);
+          for (int j = 0; j < NP; ++j) {
+            const double D = j == 0 ? s0 : tc::f32_to_f64(v[j]);
+            cr[j] = fma(kap, D, tb[j]);
+            if (OUT2) {
+              double t2 = su.y * cr[j];
+              if (su.x != 0.0) t2 = fma(su.x, su.acc[o + j], t2);
+              su.out2[o + j] = fma(kw, D, t2);
+            }
+          }
         }
       } else {
 #pragma unroll
@@ -459,17 +473,18 @@ k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *
   if (!ok) atomicOr(err, kErrNonPhysical);
 }
 
-template <int P, int NE, bool X3>
+template <int P, int NE, bool X3, bool OUT2>
 int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, float *trace_out, const float *fhat,
-           const double *fmean, double dt, double a0, double b0, int mode, cudaStream_t s) {
+           const double *fmean, const StageUpdate &su, int mode, cudaStream_t s) {
   using T = Tc<P, NE, X3>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_element_tc<P, NE, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_element_tc<P, NE, X3, OUT2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T::SMEM);
     if (e != cudaSuccess) return (int)e;
     // all of the SM's unified L1/shared storage as shared memory, so that the
     // occupancy query and the launch see every CTA that fits
-    e = cudaFuncSetAttribute(k_element_tc<P, NE, X3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(k_element_tc<P, NE, X3, OUT2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
@@ -488,7 +503,7 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, flo
     e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, m->device);
     if (e != cudaSuccess) return (int)e;
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, k_element_tc<P, NE, X3>);
+    e = cudaFuncGetAttributes(&fa, k_element_tc<P, NE, X3, OUT2>);
     if (e != cudaSuccess) return (int)e;
     const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
     const int by_regs = regs_sm / (warp_regs * (kTcThreads / 32));
@@ -498,16 +513,18 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, flo
   }
   const int ntiles = (int)((m->N + T::EB - 1) / T::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_element_tc<P, NE, X3><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face,
-                                                            m->tab, (int)m->N, dt, a0, b0, mode, m->gamma,
+  k_element_tc<P, NE, X3, OUT2><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face,
+                                                            m->tab, (int)m->N, su, mode, m->gamma,
                                                             m->err_flag);
   return (int)cudaGetLastError();
 }
 
 template <bool X3>
 int dispatch_tc(const dg_mesh *m, const double *c, const double *u0, double *out, float *trace_out,
-                const float *fhat, const double *fmean, double dt, double a0, double b0, int mode, cudaStream_t s) {
-#define CALL(P, NE) run_tc<P, NE, X3>(m, c, u0, out, trace_out, fhat, fmean, dt, a0, b0, mode, s)
+                const float *fhat, const double *fmean, const StageUpdate &su, int mode, cudaStream_t s) {
+#define CALL(P, NE)                                                                         \
+  (su.out2 && mode == 1 ? run_tc<P, NE, X3, true>(m, c, u0, out, trace_out, fhat, fmean, su, mode, s) \
+                        : run_tc<P, NE, X3, false>(m, c, u0, out, trace_out, fhat, fmean, su, mode, s))
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);
@@ -555,11 +572,11 @@ int launch_convert_check(int n, unsigned long long *bad, void *stream) {
 }
 
 int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
-                      float *trace_out, const float *fhat, const double *fmean, double dt, double a0, double b0,
+                      float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
                       int mode, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  return split3 ? dispatch_tc<true>(m, c, u0, out, trace_out, fhat, fmean, dt, a0, b0, mode, s)
-                : dispatch_tc<false>(m, c, u0, out, trace_out, fhat, fmean, dt, a0, b0, mode, s);
+  return split3 ? dispatch_tc<true>(m, c, u0, out, trace_out, fhat, fmean, su, mode, s)
+                : dispatch_tc<false>(m, c, u0, out, trace_out, fhat, fmean, su, mode, s);
 }
 
 MixedBuffers mixed_buffers(const dg_mesh *m, double *trace, double *fhat) {

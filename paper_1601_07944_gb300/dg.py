@@ -20,12 +20,14 @@ DG_OK = 0
 STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EMESH",
           5: "DG_ENONPHYS", 6: "DG_ETIMEOUT", 7: "DG_ENOTIMPL"}
 PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
+METHOD = {"ssp_rk3": 0, "rk2": 1, "rk4": 2}
 
 # every entry point declared in include/dg.h
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
-           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt")
+           "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt",
+           "dg_rk_step_method")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -68,6 +70,7 @@ def load(path: str = LIB_PATH):
         "dg_project_ic": [P, P, P, P],
         "dg_rhs": [P, P, P, I, P],
         "dg_rk_step": [P, P, D, I, I, P],
+        "dg_rk_step_method": [P, P, D, I, I, I, P],
         "dg_rk_step_host": [P, P, D, I, I, P],
         "dg_adjoint_step": [P, P, D, P, P, P],
         "dg_conserved_totals": [P, P, P, P],
@@ -275,10 +278,17 @@ class Mesh:
                                      _prec(precision), _stream_ptr(stream)))
         return out
 
-    def rk_step(self, c, dt: float, nsteps: int = 1, precision="fp64", stream=None):
-        """nsteps SSP-RK3 steps in place on the device tensor c."""
-        _check(load().dg_rk_step(self._h, _dev_ptr(c, "c", self.coef_shape), float(dt), int(nsteps),
-                                 _prec(precision), _stream_ptr(stream)))
+    def rk_step(self, c, dt: float, nsteps: int = 1, precision="fp64", stream=None, method="ssp_rk3"):
+        """nsteps Runge-Kutta steps in place on the device tensor c: "ssp_rk3"
+        (dg_rk_step), or the paper's "rk2" (Heun) or "rk4" (dg_rk_step_method)."""
+        if method == "ssp_rk3":
+            _check(load().dg_rk_step(self._h, _dev_ptr(c, "c", self.coef_shape), float(dt), int(nsteps),
+                                     _prec(precision), _stream_ptr(stream)))
+            return c
+        if method not in METHOD:
+            raise ValueError("method must be one of %s" % sorted(METHOD))
+        _check(load().dg_rk_step_method(self._h, _dev_ptr(c, "c", self.coef_shape), float(dt), int(nsteps),
+                                        METHOD[method], _prec(precision), _stream_ptr(stream)))
         return c
 
     def rk_step_host(self, c_host, dt: float, nsteps: int = 1, precision="fp64", stream=None):
