@@ -22,19 +22,23 @@ namespace {
 // The volume rule is a tensor grid in the collapsed coordinates (alpha, beta)
 // and the basis factors as phi_j = P_a(alpha) chi_j(beta), so
 //   interpolation  U(ia,ib) = sum_a P_a(alpha_ia) W(a,ib),  W(a,ib) = sum_{j:a(j)=a} chi_j(beta_ib) c_j
-//   projection     V_j = sum_ib chi_j(beta_ib) Xa(a,ib) + chi_j'(beta_ib) Xb(a,ib),
-//                  Xa(a,ib) = sum_ia Ha(ia,ib) P_a'(alpha_ia),  Xb(a,ib) = sum_ia Hb(ia,ib) P_a(alpha_ia),
-// with Ha = w (2 G_r + (1+alpha) G_s)/(1-s) and Hb = 2 w G_s from the chain rule
-// d/dr = 2/(1-s) d/dalpha, d/ds = (1+alpha)/(1-s) d/dalpha + 2 d/dbeta.  This is the
-// same sum as the direct projection (Eq. volume), in (p+1)(N_p + (p+1)^2) instead
-// of (p+1)^2 N_p products per variable for each of the two contractions.
+//   projection     V_j = sum_ib chiA_j(ib) Xa(a,ib) + dchiB_j(ib) Xb(a,ib),
+//                  Xa(a,ib) = sum_ia wa P_a'(alpha_ia) Ha(ia,ib),  Xb(a,ib) = sum_ia wa P_a(alpha_ia) Hb(ia,ib),
+// with Ha = G_r + (1+alpha)/2 G_s, Hb = G_s at the points and the weights and
+// chain-rule factors of the collapsed map, d/dr = 2/(1-s) d/dalpha and
+// d/ds = (1+alpha)/(1-s) d/dalpha + 2 d/dbeta, folded into the tables
+// (chiA = chi wb / (4 (1-s)), dchiB = chi' wb / 4).  This is the same sum as the
+// direct projection (Eq. volume), in (p+1)(N_p + (p+1)^2) instead of
+// (p+1)^2 N_p products per variable for each of the two contractions.  The
+// reference fluxes (G_r, G_s) = J^tau (F1, F2) are formed as the Euler flux
+// along the two rows of J^tau, which are constant on the element.
 // ---------------------------------------------------------------------------
 template <int P, int NE>
 struct SfCfg {
   using C = Cfg<P, NE>;
   static constexpr int NP = C::NP, ND = C::ND, NQ = C::NQ, NF = C::NF;
   static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);
-  static constexpr int TAB = 2 * ND * ND + 2 * NP * ND + 3 * NQ + 2 * NF * NP;
+  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 2 * NF * NP;
   static constexpr int TILE = EB * (M * NP + 8 * ND * ND + 8 * NQ + NF * M);
   static constexpr int SMEM = (TAB + TILE) * 8;
   static_assert(8 * NQ >= M * NP, "the new state reuses the point buffer");
@@ -56,12 +60,14 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   using S = SfCfg<P, NE>;
   constexpr int NP = S::NP, ND = S::ND, NQ = S::NQ, NF = S::NF, EB = S::EB;
   extern __shared__ double smem[];
-  double *sPa = smem;                  // [ND][ND]
-  double *sdPa = sPa + ND * ND;        // [ND][ND]
-  double *sChi = sdPa + ND * ND;       // [NP][ND]
-  double *sdChi = sChi + NP * ND;      // [NP][ND]
-  double *sK = sdChi + NP * ND;        // [3][NQ]
-  double *sLf = sK + 3 * NQ;           // [NF][NP]
+  double *sPa = smem;                  // [ND][ND]   P_a(alpha_ia)
+  double *sPaW = sPa + ND * ND;        // [ND][ND]   wa P_a
+  double *sdPaW = sPaW + ND * ND;      // [ND][ND]   wa P_a'
+  double *sChi = sdPaW + ND * ND;      // [NP][ND]   chi_j(beta_ib)
+  double *sChiA = sChi + NP * ND;      // [NP][ND]   chi_j wb / (4 (1-s))
+  double *sdChiB = sChiA + NP * ND;    // [NP][ND]   chi_j' wb / 4
+  double *sHalf = sdChiB + NP * ND;    // [ND]       (1 + alpha_ia) / 2
+  double *sLf = sHalf + ND;            // [NF][NP]
   double *sBfT = sLf + NF * NP;        // [NP][NF]
   double *sC = sBfT + NP * NF;         // [EB][M][NP]        stage input
   double *sX = sC + EB * M * NP;       // [EB][ND][ND][8]    W (first 4), then Xa, Xb
@@ -69,9 +75,13 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   double *sF = sH + EB * NQ * 8;       // [EB][NF][M]        -F_hat_out * l
   double *sO = sH;
 
-  for (int i = threadIdx.x; i < ND * ND; i += blockDim.x) { sPa[i] = tab.SPa[i]; sdPa[i] = tab.SdPa[i]; }
-  for (int i = threadIdx.x; i < NP * ND; i += blockDim.x) { sChi[i] = tab.SChi[i]; sdChi[i] = tab.SdChi[i]; }
-  for (int i = threadIdx.x; i < 3 * NQ; i += blockDim.x) sK[i] = tab.SK[i];
+  for (int i = threadIdx.x; i < ND * ND; i += blockDim.x) {
+    sPa[i] = tab.SPa[i]; sPaW[i] = tab.SPaW[i]; sdPaW[i] = tab.SdPaW[i];
+  }
+  for (int i = threadIdx.x; i < NP * ND; i += blockDim.x) {
+    sChi[i] = tab.SChi[i]; sChiA[i] = tab.SChiA[i]; sdChiB[i] = tab.SdChiB[i];
+  }
+  for (int i = threadIdx.x; i < ND; i += blockDim.x) sHalf[i] = tab.SHalf[i];
   for (int i = threadIdx.x; i < NF * NP; i += blockDim.x) { sLf[i] = tab.Lf[i]; sBfT[i] = tab.BfT[i]; }
 
   const int ntiles = (N + EB - 1) / EB;
@@ -98,18 +108,24 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
     }
     __syncthreads();
 
-    // W(a, ib) = sum over the modes with first index a of chi_j(beta_ib) c_j
-    for (int i = threadIdx.x; i < EB * ND * ND; i += blockDim.x) {
-      const int el = i / (ND * ND), a = (i / ND) % ND, ib = i % ND;
-      double w[M] = {0.0, 0.0, 0.0, 0.0};
-      for (int b = 0; b <= P - a; ++b) {
-        const int d = a + b, j = d * (d + 1) / 2 + b;
-        const double x = sChi[j * ND + ib];
+    // W(a, ib) = sum over the modes with first index a of chi_j(beta_ib) c_j; one
+    // item per (element, ib, variable) runs over all modes (the same unrolled
+    // sequence in every lane)
+    for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
+      const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
+      const double *cm = sC + (el * M + m) * NP;
+      double w[ND];
 #pragma unroll
-        for (int m = 0; m < M; ++m) w[m] += x * sC[(el * M + m) * NP + j];
-      }
+      for (int a = 0; a < ND; ++a) w[a] = 0.0;
 #pragma unroll
-      for (int m = 0; m < M; ++m) sX[i * 8 + m] = w[m];
+      for (int d = 0; d <= P; ++d)
+#pragma unroll
+        for (int b = 0; b <= d; ++b) {
+          const int j = d * (d + 1) / 2 + b;
+          w[d - b] = fma(sChi[j * ND + ib], cm[j], w[d - b]);
+        }
+#pragma unroll
+      for (int a = 0; a < ND; ++a) sX[((el * ND + a) * ND + ib) * 8 + m] = w[a];
     }
     __syncthreads();
 
@@ -127,23 +143,27 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
       double Ha[M], Hb[M];
       if (el < ecount) {
         const double *g = geo + (size_t)(e0 + el) * GEO;
-        const double ka = sK[k], kb = sK[NQ + k], kc = sK[2 * NQ + k];
-        // (Ha, Hb) = (ka G_r + kb G_s, kc G_s) with (G_r, G_s) = J^tau (F1, F2)
-        const double A1 = ka * g[0] + kb * g[2], A2 = ka * g[1] + kb * g[3];
-        const double B1 = kc * g[2], B2 = kc * g[3];
+        // G_r = J^tau row 0 . (F1, F2), G_s = row 1 . (F1, F2): the Euler flux along
+        // a direction d is (rho v_d, rho u v_d + p d_x, rho v v_d + p d_y, (E + p) v_d)
+        // with v_d = (rho u d_x + rho v d_y) / rho
         const double inv = recip(U[0]);
-        const double u = U[1] * inv, v = U[2] * inv;
-        const double p = (gamma - 1.0) * (U[3] - 0.5 * (U[1] * u + U[2] * v));
+        const double p = (gamma - 1.0) * fma(fma(U[1], U[1], U[2] * U[2]), -0.5 * inv, U[3]);
         if (!(positive_finite(U[0]) & positive_finite(p))) atomicOr(err, kErrNonPhysical);
-        double F1[M], F2[M];
-        F1[0] = U[1];           F2[0] = U[2];
-        F1[1] = U[1] * u + p;   F2[1] = U[1] * v;
-        F1[2] = U[2] * u;       F2[2] = U[2] * v + p;
-        F1[3] = (U[3] + p) * u; F2[3] = (U[3] + p) * v;
+        const double Ep = U[3] + p;
+        double Gr[M], Gs[M];
+        {
+          const double mn = fma(U[1], g[0], U[2] * g[1]), vd = mn * inv;
+          Gr[0] = mn; Gr[1] = fma(U[1], vd, p * g[0]); Gr[2] = fma(U[2], vd, p * g[1]); Gr[3] = Ep * vd;
+        }
+        {
+          const double mn = fma(U[1], g[2], U[2] * g[3]), vd = mn * inv;
+          Gs[0] = mn; Gs[1] = fma(U[1], vd, p * g[2]); Gs[2] = fma(U[2], vd, p * g[3]); Gs[3] = Ep * vd;
+        }
+        const double half = sHalf[ia];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          Ha[m] = A1 * F1[m] + A2 * F2[m];
-          Hb[m] = B1 * F1[m] + B2 * F2[m];
+          Ha[m] = fma(half, Gs[m], Gr[m]);
+          Hb[m] = Gs[m];
         }
       } else {
 #pragma unroll
@@ -155,13 +175,13 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
     }
     __syncthreads();
 
-    // Xa(a, ib) = sum_ia Ha P_a', Xb(a, ib) = sum_ia Hb P_a
+    // Xa(a, ib) = sum_ia Ha wa P_a', Xb(a, ib) = sum_ia Hb wa P_a
     for (int i = threadIdx.x; i < EB * ND * ND; i += blockDim.x) {
       const int el = i / (ND * ND), a = (i / ND) % ND, ib = i % ND;
       double xa[M] = {0.0, 0.0, 0.0, 0.0}, xb[M] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int ia = 0; ia < ND; ++ia) {
-        const double dp = sdPa[a * ND + ia], pa = sPa[a * ND + ia];
+        const double dp = sdPaW[a * ND + ia], pa = sPaW[a * ND + ia];
         const double *h = sH + ((el * NQ) + ib * ND + ia) * 8;
 #pragma unroll
         for (int m = 0; m < M; ++m) { xa[m] += h[m] * dp; xb[m] += h[4 + m] * pa; }
@@ -178,10 +198,10 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
       double acc[M] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int ib = 0; ib < ND; ++ib) {
-        const double ch = sChi[j * ND + ib], dch = sdChi[j * ND + ib];
+        const double ch = sChiA[j * ND + ib], dch = sdChiB[j * ND + ib];
         const double *x = sX + ((el * ND + a) * ND + ib) * 8;
 #pragma unroll
-        for (int m = 0; m < M; ++m) acc[m] += ch * x[m] + dch * x[4 + m];
+        for (int m = 0; m < M; ++m) acc[m] = fma(dch, x[4 + m], fma(ch, x[m], acc[m]));
       }
 #pragma unroll
       for (int qk = 0; qk < NF; ++qk) {

@@ -407,8 +407,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   auto take = [&](size_t n) { size_t o = off; off += (n + 3) & ~size_t(3); return o; };
   size_t oBvT = take(np * nq), oDr = take(nq * np), oDs = take(nq * np), oLf = take(nf * np),
          oBfT = take(np * nf), oPw = take(nq * np), oVr = take(nq), oVs = take(nq);
-  size_t oSPa = take(nd * nd), oSdPa = take(nd * nd), oSChi = take(np * nd), oSdChi = take(np * nd),
-         oSK = take(3 * nq);
+  size_t oSPa = take(nd * nd), oSPaW = take(nd * nd), oSdPaW = take(nd * nd), oSChi = take(np * nd),
+         oSChiA = take(np * nd), oSdChiB = take(np * nd), oSHalf = take(nd);
   std::vector<double> tb(off, 0.0);
   for (int k = 0; k < nq; ++k)
     for (int j = 0; j < np; ++j) {
@@ -425,32 +425,37 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
         tb[oBfT + j * nf + qk] = phif[qk * np + j];
       }
   for (int k = 0; k < nq; ++k) { tb[oVr + k] = (double)r[k]; tb[oVs + k] = (double)s[k]; }
-  // sum-factorisation tables
+  // sum-factorisation tables.  The volume weight w = wa(ia) wb(ib) / 8 and the
+  // chain-rule factors of the collapsed map are folded into the projection
+  // tables: the element kernel forms H_alpha = G_r + (1+alpha)/2 G_s and
+  // H_beta = G_s at the points, and
+  //   V_j = sum_ib chiA_j(ib) sum_ia wa P_a'(alpha_ia) H_alpha
+  //       + sum_ib dchiB_j(ib) sum_ia wa P_a(alpha_ia) H_beta,
+  //   chiA_j = chi_j wb / (4 (1-s)),  dchiB_j = chi_j' wb / 4,
+  // which is the projection on w (d phi_j/dr, d phi_j/ds) . (G_r, G_s) with
+  // d/dr = 2/(1-s) d/dalpha and d/ds = (1+alpha)/(1-s) d/dalpha + 2 d/dbeta.
   for (int a = 0; a < nd; ++a)
     for (int ia = 0; ia < nd; ++ia) {
-      tb[oSPa + a * nd + ia] = (double)jacobi_p(a, 0, 0, xa[ia]);
-      tb[oSdPa + a * nd + ia] = (double)jacobi_dp(a, 0, 0, xa[ia]);
+      const real P = jacobi_p(a, 0, 0, xa[ia]), dP = jacobi_dp(a, 0, 0, xa[ia]);
+      tb[oSPa + a * nd + ia] = (double)P;
+      tb[oSPaW + a * nd + ia] = (double)(wa_[ia] * P);
+      tb[oSdPaW + a * nd + ia] = (double)(wa_[ia] * dP);
     }
   for (int j = 0; j < np; ++j) {
     int a, b;
     mode_ab(j, &a, &b);
     real N = std::sqrt(2.0L * (2 * a + 1) * (a + b + 1));
     for (int ib = 0; ib < nd; ++ib) {
-      real be = xb[ib], h = 0.5L * (1.0L - be);
+      real be = xb[ib], h = 0.5L * (1.0L - be);   // h = 1 - s
       real Pb = jacobi_p(b, 2 * a + 1, 0, be), dPb = jacobi_dp(b, 2 * a + 1, 0, be);
       real ha = std::pow(h, (real)a), ha1 = a > 0 ? std::pow(h, (real)(a - 1)) : 0.0L;
-      tb[oSChi + j * nd + ib] = (double)(N * ha * Pb);
-      tb[oSdChi + j * nd + ib] = (double)(N * (-0.5L * a * ha1 * Pb + ha * dPb));
+      const real chi = N * ha * Pb, dchi = N * (-0.5L * a * ha1 * Pb + ha * dPb);
+      tb[oSChi + j * nd + ib] = (double)chi;
+      tb[oSChiA + j * nd + ib] = (double)(chi * wb_[ib] / (4.0L * h));
+      tb[oSdChiB + j * nd + ib] = (double)(dchi * wb_[ib] / 4.0L);
     }
   }
-  for (int ib = 0; ib < nd; ++ib)
-    for (int ia = 0; ia < nd; ++ia) {
-      int k = ib * nd + ia;
-      real oms = 0.5L * (1.0L - xb[ib]);           // 1 - s
-      tb[oSK + k] = (double)(2.0L * w[k] / oms);
-      tb[oSK + nq + k] = (double)(w[k] * (1.0L + xa[ia]) / oms);
-      tb[oSK + 2 * nq + k] = (double)(2.0L * w[k]);
-    }
+  for (int ia = 0; ia < nd; ++ia) tb[oSHalf + ia] = (double)(0.5L * (1.0L + xa[ia]));
 
   // --- device upload ---------------------------------------------------------
   dg_mesh *m = new (std::nothrow) dg_mesh();
@@ -494,8 +499,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   double *T = m->table_block;
   m->tab.BvT = T + oBvT; m->tab.Dr = T + oDr; m->tab.Ds = T + oDs; m->tab.Lf = T + oLf;
   m->tab.BfT = T + oBfT; m->tab.Pw = T + oPw; m->tab.vr = T + oVr; m->tab.vs = T + oVs;
-  m->tab.SPa = T + oSPa; m->tab.SdPa = T + oSdPa; m->tab.SChi = T + oSChi; m->tab.SdChi = T + oSdChi;
-  m->tab.SK = T + oSK;
+  m->tab.SPa = T + oSPa; m->tab.SPaW = T + oSPaW; m->tab.SdPaW = T + oSdPaW; m->tab.SChi = T + oSChi;
+  m->tab.SChiA = T + oSChiA; m->tab.SdChiB = T + oSdChiB; m->tab.SHalf = T + oSHalf;
   cudaError_t ce;
   if ((ce = cudaMemcpy(m->geo, geo.data(), sizeof(double) * N * GEO, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->xy, xy, sizeof(double) * N * 6, cudaMemcpyHostToDevice)) != cudaSuccess ||

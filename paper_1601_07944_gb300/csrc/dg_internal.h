@@ -38,13 +38,16 @@ struct DevTables {
   double *BfT;   // [NP][NF]   phi_j(r_{q,k})                 (edge traces)
   double *Pw;    // [NQ][NP]   w_k phi_j(r_k)                 (L2 projection of data)
   double *vr, *vs;   // [NQ] reference volume points
-  // Sum factorisation on the collapsed grid (point k = ib*ND + ia):
+  // Sum factorisation on the collapsed grid (point k = ib*ND + ia, weight
+  // w_k = wa(ia) wb(ib) / 8):
   //   phi_j(alpha_ia, beta_ib) = P_a(alpha_ia) chi_j(beta_ib),  a = a(j)
   double *SPa;   // [ND][ND]   P_a(alpha_ia)                 (Legendre, standard normalisation)
-  double *SdPa;  // [ND][ND]   P_a'(alpha_ia)
+  double *SPaW;  // [ND][ND]   wa(ia) P_a(alpha_ia)
+  double *SdPaW; // [ND][ND]   wa(ia) P_a'(alpha_ia)
   double *SChi;  // [NP][ND]   chi_j(beta_ib) = N_ab ((1-beta)/2)^a P_b^{(2a+1,0)}(beta)
-  double *SdChi; // [NP][ND]   d chi_j / d beta
-  double *SK;    // [3][NQ]    2w/(1-s), w(1+alpha)/(1-s), 2w: weights of the collapsed chain rule
+  double *SChiA; // [NP][ND]   chi_j(beta_ib) wb(ib) / (4 (1 - s_ib))
+  double *SdChiB;// [NP][ND]   chi_j'(beta_ib) wb(ib) / 4
+  double *SHalf; // [ND]       (1 + alpha_ia) / 2
 };
 
 // One Runge-Kutta stage update of the element kernels (their mode 1), with
