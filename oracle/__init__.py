@@ -70,6 +70,8 @@ def _load():
             "or_ssp_rk3": (I, [P, P, D, I]),
             "or_rk2": (I, [P, P, D, I]),
             "or_rk4": (I, [P, P, D, I]),
+            "or_limit_bj": (I, [P, P]),
+            "or_set_limiter": (I, [P, I]),
             "or_totals": (I, [P, P, P]),
             "or_lax_friedrichs_jacobians": (I, [D, P, P, D, D, P, P]),
             "or_flux_jacobian": (I, [D, P, D, D, P]),
@@ -306,6 +308,16 @@ class OracleDG:
         out = np.array(c, dtype=np.float64, copy=True, order="C")
         _chk(_lib.or_rk4(self._h, _ptr(out), dt, nsteps))
         return out
+
+    def limit(self, c):
+        """Barth-Jespersen limiter (p = 1) applied to a copy of c."""
+        out = np.array(c, dtype=np.float64, copy=True, order="C")
+        _chk(_lib.or_limit_bj(self._h, _ptr(out)))
+        return out
+
+    def set_limiter(self, on: bool):
+        """Limit every stage value and new state of rk2 / ssp_rk3 / rk4 (p = 1)."""
+        _chk(_lib.or_set_limiter(self._h, 1 if on else 0))
 
     def rhs_vjp(self, c, lam):
         """(dR/dc)^T lam."""

@@ -33,7 +33,8 @@
  *     two traces at each quadrature point;
  *   - the surface temporaries are per edge (one left and one right block).
  *   - time integration: the three-stage SSP Runge-Kutta method in Shu-Osher
- *     form, and the paper's own classic RK2 (read as Heun's method) and RK4.
+ *     form, and the paper's own classic RK2 (read as Heun's method) and RK4;
+ *   - the Barth-Jespersen limiter (p = 1) with the standard per-point ratio.
  *
  * Layout of every coefficient array: c[e][m][j], element e, variable m (M=4),
  * mode j (N_p), float64.
@@ -410,6 +411,7 @@ typedef struct {
     /* temporaries of Algorithms 1-3 */
     double *rhs_volume;                       /* [N][M][Np] */
     double *rhs_surface_left, *rhs_surface_right;   /* [Ns][M][Np] */
+    int limit;                                /* limit every stage value (p = 1) */
 } oracle_dg;
 
 static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
@@ -783,6 +785,83 @@ int or_last_volume_term(const oracle_dg *o, double *out)
     return 0;
 }
 
+/* Barth-Jespersen limiter for p = 1 (Section 4.3.5, Eqs. limit, limitmax,
+ * limitmin), variable by variable, in place on C.  The linear approximation is
+ * written U_i(r) = Ubar_i + alpha_i grad U_i . (r - r_i) with Ubar_i = U_i(r_i), the
+ * value at the centroid r_i.  U^max and U^min are the largest and smallest
+ * centroid values of element i and its three neighbours.  At every edge
+ * integration point r_{q,k} of element i, with d = U_i(r_{q,k}) - Ubar_i,
+ *   alpha_{i,k} = min(1, (U^max - Ubar_i) / d)   if d > 0,
+ *               = min(1, (U^min - Ubar_i) / d)   if d < 0,   1 if d = 0,
+ * (reading: the paper names the limiter and its bounds; this per-point ratio is
+ * the standard Barth-Jespersen one), alpha_i = min_k alpha_{i,k}, and the two
+ * linear modes of U_i are multiplied by alpha_i.  Centroid values are taken from
+ * the input state; the limiter does not change them (the linear modes vanish
+ * at the centroid).  Returns 2 unless p = 1. */
+int or_limit_bj(oracle_dg *o, double *C)
+{
+    if (o->p != 1) return 2;
+    const int np = o->np, ne = o->ne;
+    const int64_t N = o->N;
+    double rc = 1.0 / 3.0, sc = 1.0 / 3.0, cphi[3];
+    or_dubiner_eval(1, 1, &rc, &sc, cphi, NULL, NULL);
+    double *ubar = malloc(sizeof(double) * (size_t)N * OM);
+    if (!ubar) return 1;
+    for (int64_t e = 0; e < N; ++e)
+        for (int m = 0; m < OM; ++m) {
+            const double *c = C + ((size_t)e * OM + m) * np;
+            double u = 0.0;
+            for (int j = 0; j < np; ++j) u += c[j] * cphi[j];
+            ubar[e * OM + m] = u;
+        }
+    for (int64_t e = 0; e < N; ++e) {
+        int64_t nb[3];
+        for (int q = 0; q < 3; ++q) {
+            int64_t s = o->elem_edge[3 * e + q];
+            nb[q] = (o->el[s] == e && o->eL[s] == q) ? o->er[s] : o->el[s];
+        }
+        for (int m = 0; m < OM; ++m) {
+            double *c = C + ((size_t)e * OM + m) * np;
+            const double ub = ubar[e * OM + m];
+            double umax = ub, umin = ub;
+            for (int q = 0; q < 3; ++q) {
+                double v = ubar[nb[q] * OM + m];
+                if (v > umax) umax = v;
+                if (v < umin) umin = v;
+            }
+            double alpha = 1.0;
+            for (int q = 0; q < 3; ++q)
+                for (int k = 0; k < ne; ++k) {
+                    const double *ph = o->phif + ((size_t)q * ne + k) * np;
+                    double u = 0.0;
+                    for (int j = 0; j < np; ++j) u += c[j] * ph[j];
+                    double d = u - ub, a = 1.0;
+                    if (d > 0.0) a = fmin(1.0, (umax - ub) / d);
+                    else if (d < 0.0) a = fmin(1.0, (umin - ub) / d);
+                    if (a < alpha) alpha = a;
+                }
+            c[1] *= alpha;
+            c[2] *= alpha;
+        }
+    }
+    free(ubar);
+    return 0;
+}
+
+/* Limit every intermediate stage value and the new state of the time steppers
+ * below (Section 4.3.1), p = 1 only. */
+int or_set_limiter(oracle_dg *o, int on)
+{
+    if (on && o->p != 1) return 2;
+    o->limit = on != 0;
+    return 0;
+}
+
+static void stage_limit(oracle_dg *o, double *C)
+{
+    if (o->limit) or_limit_bj(o, C);
+}
+
 /* Three-stage SSP Runge-Kutta (Shu-Osher form), nsteps steps in place:
  *   u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1)); u <- 1/3 u + 2/3 (u2 + dt L(u2)) */
 int or_ssp_rk3(oracle_dg *o, double *C, double dt, int nsteps)
@@ -793,10 +872,13 @@ int or_ssp_rk3(oracle_dg *o, double *C, double dt, int nsteps)
     for (int it = 0; it < nsteps; ++it) {
         or_rhs(o, C, L);
         for (size_t t = 0; t < n; ++t) u1[t] = C[t] + dt * L[t];
+        stage_limit(o, u1);
         or_rhs(o, u1, L);
         for (size_t t = 0; t < n; ++t) u2[t] = 0.75 * C[t] + 0.25 * (u1[t] + dt * L[t]);
+        stage_limit(o, u2);
         or_rhs(o, u2, L);
         for (size_t t = 0; t < n; ++t) C[t] = C[t] / 3.0 + 2.0 / 3.0 * (u2[t] + dt * L[t]);
+        stage_limit(o, C);
     }
     free(u1); free(u2); free(L);
     return 0;
@@ -818,8 +900,10 @@ int or_rk2(oracle_dg *o, double *C, double dt, int nsteps)
     for (int it = 0; it < nsteps; ++it) {
         or_rhs(o, C, k1);
         for (size_t t = 0; t < n; ++t) y[t] = C[t] + dt * k1[t];
+        stage_limit(o, y);
         or_rhs(o, y, k2);
         for (size_t t = 0; t < n; ++t) C[t] = C[t] + 0.5 * dt * (k1[t] + k2[t]);
+        stage_limit(o, C);
     }
     free(y); free(k1); free(k2);
     return 0;
@@ -839,10 +923,12 @@ int or_rk4(oracle_dg *o, double *C, double dt, int nsteps)
         or_rhs(o, C, k[0]);
         for (int i = 1; i < 4; ++i) {
             for (size_t t = 0; t < n; ++t) y[t] = C[t] + a[i] * dt * k[i - 1][t];
+            stage_limit(o, y);
             or_rhs(o, y, k[i]);
         }
         for (size_t t = 0; t < n; ++t)
             C[t] = C[t] + dt / 6.0 * (k[0][t] + 2.0 * k[1][t] + 2.0 * k[2][t] + k[3][t]);
+        stage_limit(o, C);
     }
     free(y); for (int i = 0; i < 4; ++i) free(k[i]);
     return 0;

@@ -218,6 +218,18 @@ def density_wave(x, y, t: float = 0.0, gamma: float = GAMMA) -> np.ndarray:
     return primitive_to_conserved(rho, one, one, one, gamma)
 
 
+def density_steps(x, y, gamma: float = GAMMA) -> np.ndarray:
+    """Piecewise constant data with jumps (periodic): rho = 1, p = 1 inside the
+    band |x| < 2.5 and rho = 0.125, p = 0.1 outside it, at rest; a discontinuous
+    state of the kind the paper's limiter is for."""
+    x = np.asarray(x, dtype=np.float64)
+    inside = np.abs(x) < 0.25 * DOMAIN_L
+    rho = np.where(inside, 1.0, 0.125)
+    p = np.where(inside, 1.0, 0.1)
+    zero = np.zeros_like(rho)
+    return primitive_to_conserved(rho, zero, zero, p, gamma)
+
+
 def uniform_state(x, y, rho=1.0, u=0.3, v=-0.2, p=0.8, gamma: float = GAMMA) -> np.ndarray:
     x = np.asarray(x, dtype=np.float64)
     one = np.ones_like(x)
