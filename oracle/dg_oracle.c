@@ -887,25 +887,27 @@ int or_ssp_rk3(oracle_dg *o, double *C, double dt, int nsteps)
 /* The paper's own time integrators (Section 4.3.1, classic explicit Runge-Kutta
  * methods of order two and four), in Butcher form with every stage derivative
  * k_i = L(u + dt sum_j a_ij k_j) kept, nsteps steps in place.
- *   RK2 (reading: Heun's method, c = (0, 1), b = (1/2, 1/2)):
- *     k1 = L(u), k2 = L(u + dt k1), u <- u + dt/2 (k1 + k2)
+ *   RK2 (reading: Heun's method, c = (0, 1), b = (1/2, 1/2)), taken in its
+ *     Shu-Osher form, the convex combination the stage limiting of Section
+ *     4.3.1 is applied to (the same method, u + dt/2 (k1 + k2), when nothing
+ *     is limited):  u1 = u + dt L(u),  u <- 1/2 u + 1/2 (u1 + dt L(u1))
  *   RK4 (the classical method, c = (0, 1/2, 1/2, 1), b = (1, 2, 2, 1)/6):
  *     k1 = L(u), k2 = L(u + dt/2 k1), k3 = L(u + dt/2 k2), k4 = L(u + dt k3),
  *     u <- u + dt/6 (k1 + 2 k2 + 2 k3 + k4) */
 int or_rk2(oracle_dg *o, double *C, double dt, int nsteps)
 {
     size_t n = (size_t)o->N * OM * o->np;
-    double *y = malloc(sizeof(double) * n), *k1 = malloc(sizeof(double) * n), *k2 = malloc(sizeof(double) * n);
-    if (!y || !k1 || !k2) { free(y); free(k1); free(k2); return 1; }
+    double *u1 = malloc(sizeof(double) * n), *L = malloc(sizeof(double) * n);
+    if (!u1 || !L) { free(u1); free(L); return 1; }
     for (int it = 0; it < nsteps; ++it) {
-        or_rhs(o, C, k1);
-        for (size_t t = 0; t < n; ++t) y[t] = C[t] + dt * k1[t];
-        stage_limit(o, y);
-        or_rhs(o, y, k2);
-        for (size_t t = 0; t < n; ++t) C[t] = C[t] + 0.5 * dt * (k1[t] + k2[t]);
+        or_rhs(o, C, L);
+        for (size_t t = 0; t < n; ++t) u1[t] = C[t] + dt * L[t];
+        stage_limit(o, u1);
+        or_rhs(o, u1, L);
+        for (size_t t = 0; t < n; ++t) C[t] = 0.5 * C[t] + 0.5 * (u1[t] + dt * L[t]);
         stage_limit(o, C);
     }
-    free(y); free(k1); free(k2);
+    free(u1); free(L);
     return 0;
 }
 

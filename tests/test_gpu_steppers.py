@@ -2,9 +2,10 @@
 read as Heun's method, and the classical RK4) against the oracle, through
 dg_rk_step_method.
 
-The oracle takes the Butcher form with every stage derivative kept; the library
-runs Heun's method in Shu-Osher form and RK4 with a running sum of its stages,
-so the two differ only in rounding order: relative L2 <= 1e-12 over whole runs.
+The oracle takes RK4 in Butcher form with every stage derivative kept, the
+library with a running sum of its stages (Heun's method is in Shu-Osher form on
+both sides), so the two differ only in rounding order: relative L2 <= 1e-12 over
+whole runs.
 Runs of more than 16 steps go through the replayed CUDA graph.
 """
 import numpy as np
