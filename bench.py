@@ -47,22 +47,24 @@ WORKLOAD = dict(name="isentropic vortex, 256x256 jittered periodic triangle mesh
 
 def flops_element_per_elem(p: int, ne: int) -> float:
     """Float64 flops of one element-kernel launch per element, for the algorithm
-    the kernel executes (sum factorisation on the collapsed grid), counting an
-    FMA as 2 flops:
-      W = chi c                2 N_p (p+1) 4
-      U = P W                  2 (p+1)^3 4
-      flux, 1/rho, weights     56 per volume point
-      Xa, Xb                   4 (p+1)^3 4
-      V = chi Xa + chi' Xb     4 N_p (p+1) 4
-      lift                     2 (3 n_e) N_p 4
-      stage update             5 N_p 4
-      next traces              2 (3 n_e) N_p 4"""
+    the kernel executes (sum factorisation on the collapsed volume grid and on
+    the edges), counting an FMA as 2 flops and a multiply or add as 1:
+      W = chi c                          2 N_p (p+1) 4
+      U = P W                            2 (p+1)^3 4
+      per volume point: 1/rho (4 FMA Newton steps), pressure, the Euler flux
+      along the two rows of J^tau, H_alpha = G_r + (1+alpha)/2 G_s      46
+      Xa, Xb                             4 (p+1)^3 4
+      V = chiA Xa + dchiB Xb             4 N_p (p+1) 4
+      lift sums per variable (face 0: omega P_a; faces 1, 2: F1 +/- F2)
+                                         (2 (p+1) n_e + 2 n_e) 4
+      lift per mode                      2 (1 + n_e) N_p 4
+      stage update                       5 N_p 4
+      next traces (face 0 direct; faces 1, 2 through Y_a(xi_k))
+                                         n_e (4 N_p + 2 p) 4"""
     NP = (p + 1) * (p + 2) // 2
     ND = p + 1
-    NQ = ND * ND
-    NF = 3 * ne
-    return (2 * NP * ND * 4 + 2 * ND ** 3 * 4 + 56 * NQ + 4 * ND ** 3 * 4 + 4 * NP * ND * 4
-            + 2 * NF * NP * 4 + 5 * NP * 4 + 2 * NF * NP * 4)
+    return (2 * NP * ND * 4 + 2 * ND ** 3 * 4 + 46 * ND * ND + 4 * ND ** 3 * 4 + 4 * NP * ND * 4
+            + (2 * ND * ne + 2 * ne) * 4 + 2 * (1 + ne) * NP * 4 + 5 * NP * 4 + ne * (4 * NP + 2 * p) * 4)
 
 
 def bytes_element_tc_per_elem(p: int, ne: int) -> float:

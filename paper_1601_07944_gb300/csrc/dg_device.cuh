@@ -28,6 +28,41 @@ struct Cfg {
 
 constexpr int kThreads = 256;
 
+// Edge traces of one variable at edge point k of the three reference faces,
+// factorised on the collapsed coordinates (face 0: alpha = xi, beta = -1;
+// face 1: alpha = 1, beta = xi; face 2: alpha = -1, beta = -xi):
+//   t0 = T0_k = sum_j phi_j(face 0, k) c_j,
+//   t1 = T1_k = sum_a Y_a(xi_k),  t2 = T2_{NE-1-k} = sum_a (-1)^a Y_a(xi_k),
+//   Y_a(xi) = sum_b chi_ab(xi) c_ab.
+// cj: the N_p coefficients; eF0 = phi_j(face 0, k) and eChi = chi_j(xi_k), both
+// [N_p][NE].  Every kernel that writes traces calls this, so traces of the same
+// state agree bit for bit whichever kernel wrote them.
+template <int P, int NE>
+__device__ __forceinline__ void edge_traces_sf(const double *cj, const double *eF0, const double *eChi, int k,
+                                               double &t0, double &t1, double &t2) {
+  constexpr int ND = P + 1;
+  double y[ND];
+#pragma unroll
+  for (int a = 0; a < ND; ++a) y[a] = 0.0;
+  t0 = 0.0;
+#pragma unroll
+  for (int d = 0; d <= P; ++d)
+#pragma unroll
+    for (int b = 0; b <= d; ++b) {
+      const int j = d * (d + 1) / 2 + b;
+      const double cv = cj[j];
+      t0 = fma(eF0[j * NE + k], cv, t0);
+      y[d - b] = fma(eChi[j * NE + k], cv, y[d - b]);
+    }
+  t1 = y[0];
+  t2 = y[0];
+#pragma unroll
+  for (int a = 1; a < ND; ++a) {
+    t1 += y[a];
+    t2 = (a & 1) ? t2 - y[a] : t2 + y[a];
+  }
+}
+
 // 1/x for a positive normal x: Newton-Raphson refinement r <- r + r (1 - x r) of
 // the hardware's approximate float64 reciprocal (rcp.approx.ftz.f64); each step
 // doubles the number of correct bits, two steps reach double precision

@@ -38,8 +38,12 @@ struct SfCfg {
   using C = Cfg<P, NE>;
   static constexpr int NP = C::NP, ND = C::ND, NQ = C::NQ, NF = C::NF;
   static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);
-  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 2 * NF * NP;
-  static constexpr int TILE = EB * (M * NP + 8 * ND * ND + 8 * NQ + NF * M);
+  // per element and variable, the edge-flux buffer holds the NF gathered fluxes,
+  // then (in place) the LW sums of the factorised lift
+  static constexpr int LW = ND + 2 * NE;
+  static constexpr int RS = NF > LW ? NF : LW;
+  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 3 * NP * NE + ND * NE + NP;
+  static constexpr int TILE = EB * (M * NP + 8 * ND * ND + 8 * NQ + RS * M);
   static constexpr int SMEM = (TAB + TILE) * 8;
   static_assert(8 * NQ >= M * NP, "the new state reuses the point buffer");
 };
@@ -52,7 +56,7 @@ __device__ __forceinline__ int mode_a(int j) {
 }
 
 template <int P, int NE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
              const double *__restrict__ fhat, const double *__restrict__ geo,
              const int32_t *__restrict__ elem_face, DevTables tab, int N, StageUpdate su, int mode,
@@ -67,13 +71,17 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   double *sChiA = sChi + NP * ND;      // [NP][ND]   chi_j wb / (4 (1-s))
   double *sdChiB = sChiA + NP * ND;    // [NP][ND]   chi_j' wb / 4
   double *sHalf = sdChiB + NP * ND;    // [ND]       (1 + alpha_ia) / 2
-  double *sLf = sHalf + ND;            // [NF][NP]
-  double *sBfT = sLf + NF * NP;        // [NP][NF]
-  double *sC = sBfT + NP * NF;         // [EB][M][NP]        stage input
+  double *sEChi = sHalf + ND;          // [NP][NE]   chi_j(xi_k)
+  double *sEWChi = sEChi + NP * NE;    // [NP][NE]   omega_k chi_j(xi_k)
+  double *sEWPa = sEWChi + NP * NE;    // [ND][NE]   omega_k P_a(xi_k)
+  double *sEChiM1 = sEWPa + ND * NE;   // [NP]       chi_j(-1)
+  double *sEF0 = sEChiM1 + NP;         // [NP][NE]   phi_j at the points of face 0
+  double *sC = sEF0 + NP * NE;         // [EB][M][NP]        stage input
   double *sX = sC + EB * M * NP;       // [EB][ND][ND][8]    W (first 4), then Xa, Xb
   double *sH = sX + EB * ND * ND * 8;  // [EB][NQ][8]        Ha, Hb; later the new state
-  double *sF = sH + EB * NQ * 8;       // [EB][NF][M]        -F_hat_out * l
+  double *sF = sH + EB * NQ * 8;       // [EB][RS][M]        -F_hat_out * l, then the lift sums
   double *sO = sH;
+  constexpr int RS = S::RS;
 
   for (int i = threadIdx.x; i < ND * ND; i += blockDim.x) {
     sPa[i] = tab.SPa[i]; sPaW[i] = tab.SPaW[i]; sdPaW[i] = tab.SdPaW[i];
@@ -82,7 +90,10 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
     sChi[i] = tab.SChi[i]; sChiA[i] = tab.SChiA[i]; sdChiB[i] = tab.SdChiB[i];
   }
   for (int i = threadIdx.x; i < ND; i += blockDim.x) sHalf[i] = tab.SHalf[i];
-  for (int i = threadIdx.x; i < NF * NP; i += blockDim.x) { sLf[i] = tab.Lf[i]; sBfT[i] = tab.BfT[i]; }
+  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) { sEChi[i] = tab.EChi[i]; sEWChi[i] = tab.EWChi[i]; }
+  for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sEWPa[i] = tab.EWPa[i];
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) sEChiM1[i] = tab.EChiM1[i];
+  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) sEF0[i] = tab.BfT[(i / NE) * NF + i % NE];
 
   const int ntiles = (N + EB - 1) / EB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -104,9 +115,33 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
         for (int m = 0; m < M; ++m) v[m] = side ? fp[m] : tc::neg_bits(fp[m]);
       }
 #pragma unroll
-      for (int m = 0; m < M; ++m) sF[i * M + m] = v[m];
+      for (int m = 0; m < M; ++m) sF[(el * RS + qk) * M + m] = v[m];
     }
     __syncthreads();
+
+    // the lift's edge sums, in place of the element's fluxes of one variable:
+    //   Q_a = sum_k omega_k P_a(xi_k) F0_k                            (face 0)
+    //   G_even,k / G_odd,k = F1_k +/- F2_{NE-1-k}                   (faces 1, 2)
+    // so that the lift of mode j = (a, b) is
+    //   chi_j(-1) Q_a + sum_k omega_k chi_j(xi_k) G_{a mod 2, k}
+    for (int i = threadIdx.x; i < EB * M; i += blockDim.x) {
+      double *fe = sF + (i / M) * RS * M + (i % M);
+      double f[NF];
+#pragma unroll
+      for (int x = 0; x < NF; ++x) f[x] = fe[x * M];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) {
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) q = fma(sEWPa[a * NE + k], f[k], q);
+        fe[a * M] = q;
+      }
+#pragma unroll
+      for (int k = 0; k < NE; ++k) {
+        fe[(ND + k) * M] = f[NE + k] + f[3 * NE - 1 - k];
+        fe[(ND + NE + k) * M] = f[NE + k] - f[3 * NE - 1 - k];
+      }
+    }
 
     // W(a, ib) = sum over the modes with first index a of chi_j(beta_ib) c_j; one
     // item per (element, ib, variable) runs over all modes (the same unrolled
@@ -203,12 +238,18 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 #pragma unroll
         for (int m = 0; m < M; ++m) acc[m] = fma(dch, x[4 + m], fma(ch, x[m], acc[m]));
       }
+      {
+        const double *fl = sF + el * RS * M;
+        const double c1 = sEChiM1[j];
 #pragma unroll
-      for (int qk = 0; qk < NF; ++qk) {
-        const double *fv = sF + (el * NF + qk) * M;
-        const double l = sLf[qk * NP + j];
+        for (int m = 0; m < M; ++m) acc[m] = fma(c1, fl[a * M + m], acc[m]);
+        const double *g = fl + (ND + (a & 1) * NE) * M;
 #pragma unroll
-        for (int m = 0; m < M; ++m) acc[m] += fv[m] * l;
+        for (int k = 0; k < NE; ++k) {
+          const double l = sEWChi[j * NE + k];
+#pragma unroll
+          for (int m = 0; m < M; ++m) acc[m] = fma(l, g[k * M + m], acc[m]);
+        }
       }
       double nv[M] = {0.0, 0.0, 0.0, 0.0};
       if (el < ecount) {
@@ -245,18 +286,19 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 
     if (trace_out) {
       __syncthreads();
-      for (int i = threadIdx.x; i < ecount * NF; i += blockDim.x) {
-        const int el = i / NF, qk = i - el * NF;
-        double T[M] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          const double b = sBfT[j * NF + qk];
-#pragma unroll
-          for (int m = 0; m < M; ++m) T[m] += sO[(el * M + m) * NP + j] * b;
-        }
-        double *dst = trace_out + ((size_t)(e0 + el) * NF + qk) * M;
-#pragma unroll
-        for (int m = 0; m < M; ++m) dst[m] = T[m];
+      // edge traces of the new state, one item per (element, variable, edge point k):
+      //   T0_k = sum_j phi_j(face 0, k) c_j,
+      //   T1_k = sum_a Y_a(xi_k),  T2_{NE-1-k} = sum_a (-1)^a Y_a(xi_k),
+      //   Y_a(xi) = sum_b chi_ab(xi) c_ab
+      for (int i = threadIdx.x; i < ecount * M * NE; i += blockDim.x) {
+        const int el = i / (M * NE), m = (i / NE) % M, k = i % NE;
+        const double *cj = sO + (el * M + m) * NP;
+        double *dst = trace_out + (size_t)(e0 + el) * NF * M + m;
+        double t0, t1, t2;
+        edge_traces_sf<P, NE>(cj, sEF0, sEChi, k, t0, t1, t2);
+        dst[k * M] = t0;
+        dst[(NE + k) * M] = t1;
+        dst[(3 * NE - 1 - k) * M] = t2;
       }
     }
   }

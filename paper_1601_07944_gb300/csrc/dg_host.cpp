@@ -409,6 +409,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
          oBfT = take(np * nf), oPw = take(nq * np), oVr = take(nq), oVs = take(nq);
   size_t oSPa = take(nd * nd), oSPaW = take(nd * nd), oSdPaW = take(nd * nd), oSChi = take(np * nd),
          oSChiA = take(np * nd), oSdChiB = take(np * nd), oSHalf = take(nd);
+  size_t oEChi = take(np * ne), oEWChi = take(np * ne), oEWPa = take(nd * ne), oEChiM1 = take(np);
   std::vector<double> tb(off, 0.0);
   for (int k = 0; k < nq; ++k)
     for (int j = 0; j < np; ++j) {
@@ -456,6 +457,31 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
     }
   }
   for (int ia = 0; ia < nd; ++ia) tb[oSHalf + ia] = (double)(0.5L * (1.0L + xa[ia]));
+  // sum-factorisation tables of the edges.  On the reference edges the collapsed
+  // coordinates are: face 0 (v0 -> v1) alpha = xi, beta = -1; face 1 (v1 -> v2)
+  // alpha = 1, beta = xi; face 2 (v2 -> v0) alpha = -1, beta = -xi.  With
+  // P_a(1) = 1 and P_a(-1) = (-1)^a, the traces of faces 1 and 2 are
+  //   T1_k = sum_a Y_a(xi_k),  T2_k = sum_a (-1)^a Y_a(xi_{ne-1-k}),
+  //   Y_a(xi) = sum_b chi_ab(xi) c_ab
+  // (the Gauss-Legendre nodes are symmetric, -xi_k = xi_{ne-1-k}), and the lift
+  // is the transposed sum with the weights omega_k; on face 0 it is
+  //   chi_j(-1) sum_k omega_k P_a(xi_k) F_k.
+  for (int k = 0; k < ne; ++k) {
+    const real x = (real)(double)ex[k];      // the edge points are formed from the rounded node
+    for (int a = 0; a < nd; ++a) tb[oEWPa + a * ne + k] = (double)(ew[k] * jacobi_p(a, 0, 0, x));
+  }
+  for (int j = 0; j < np; ++j) {
+    int a, b;
+    mode_ab(j, &a, &b);
+    const real N = std::sqrt(2.0L * (2 * a + 1) * (a + b + 1));
+    for (int k = 0; k < ne; ++k) {
+      const real x = (real)(double)ex[k];
+      const real chi = N * std::pow(0.5L * (1.0L - x), (real)a) * jacobi_p(b, 2 * a + 1, 0, x);
+      tb[oEChi + j * ne + k] = (double)chi;
+      tb[oEWChi + j * ne + k] = (double)(ew[k] * chi);
+    }
+    tb[oEChiM1 + j] = (double)(N * jacobi_p(b, 2 * a + 1, 0, -1.0L));
+  }
 
   // --- device upload ---------------------------------------------------------
   dg_mesh *m = new (std::nothrow) dg_mesh();
@@ -501,6 +527,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   m->tab.BfT = T + oBfT; m->tab.Pw = T + oPw; m->tab.vr = T + oVr; m->tab.vs = T + oVs;
   m->tab.SPa = T + oSPa; m->tab.SPaW = T + oSPaW; m->tab.SdPaW = T + oSdPaW; m->tab.SChi = T + oSChi;
   m->tab.SChiA = T + oSChiA; m->tab.SdChiB = T + oSdChiB; m->tab.SHalf = T + oSHalf;
+  m->tab.EChi = T + oEChi; m->tab.EWChi = T + oEWChi; m->tab.EWPa = T + oEWPa;
+  m->tab.EChiM1 = T + oEChiM1;
   cudaError_t ce;
   if ((ce = cudaMemcpy(m->geo, geo.data(), sizeof(double) * N * GEO, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->xy, xy, sizeof(double) * N * 6, cudaMemcpyHostToDevice)) != cudaSuccess ||

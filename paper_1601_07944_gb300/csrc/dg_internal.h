@@ -48,6 +48,11 @@ struct DevTables {
   double *SChiA; // [NP][ND]   chi_j(beta_ib) wb(ib) / (4 (1 - s_ib))
   double *SdChiB;// [NP][ND]   chi_j'(beta_ib) wb(ib) / 4
   double *SHalf; // [ND]       (1 + alpha_ia) / 2
+  // Sum factorisation on the edges (Gauss-Legendre nodes xi_k, weights omega_k):
+  double *EChi;  // [NP][NE]   chi_j(xi_k)
+  double *EWChi; // [NP][NE]   omega_k chi_j(xi_k)
+  double *EWPa;  // [ND][NE]   omega_k P_a(xi_k)
+  double *EChiM1;// [NP]       chi_j(-1)
 };
 
 // One Runge-Kutta stage update of the element kernels (their mode 1), with

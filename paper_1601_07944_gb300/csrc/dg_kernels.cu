@@ -34,17 +34,21 @@ namespace dg {
 namespace {
 
 // ---------------------------------------------------------------------------
-// edge traces of a coefficient array: trace[e][q*NE+k][m] = sum_j c[e][m][j] phi_j(r_{q,k})
+// edge traces of a coefficient array: trace[e][q*NE+k][m] = sum_j c[e][m][j] phi_j(r_{q,k}),
+// by the same factorised sums (edge_traces_sf) as the element kernel's epilogue
 // ---------------------------------------------------------------------------
 template <int P, int NE>
 __global__ void __launch_bounds__(kThreads)
 k_traces(const double *__restrict__ c, double *__restrict__ trace, const double *__restrict__ BfT,
-         int N) {
+         const double *__restrict__ EChi, int N) {
   using C = Cfg<P, NE>;
   constexpr int NP = C::NP, NF = C::NF, EB = C::EB;
-  __shared__ double sB[NP * NF];
+  __shared__ double sF0[NP * NE], sChi[NP * NE];
   __shared__ double sC[EB * M * NP];
-  for (int i = threadIdx.x; i < NP * NF; i += blockDim.x) sB[i] = BfT[i];
+  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) {
+    sF0[i] = BfT[(i / NE) * NF + i % NE];      // face 0 columns of phi_j(r_{q,k})
+    sChi[i] = EChi[i];
+  }
   const int ntiles = (N + EB - 1) / EB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int e0 = tile * EB;
@@ -54,18 +58,14 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
     for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x)
       sC[i] = i < ecount * M * NP ? src[i] : 0.0;
     __syncthreads();
-    for (int i = threadIdx.x; i < ecount * NF; i += blockDim.x) {
-      const int el = i / NF, qk = i - el * NF;
-      double T[M] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const double b = sB[j * NF + qk];
-#pragma unroll
-        for (int m = 0; m < M; ++m) T[m] += sC[(el * M + m) * NP + j] * b;
-      }
-      double *dst = trace + ((size_t)(e0 + el) * NF + qk) * M;
-#pragma unroll
-      for (int m = 0; m < M; ++m) dst[m] = T[m];
+    for (int i = threadIdx.x; i < ecount * M * NE; i += blockDim.x) {
+      const int el = i / (M * NE), m = (i / NE) % M, k = i % NE;
+      double t0, t1, t2;
+      edge_traces_sf<P, NE>(sC + (el * M + m) * NP, sF0, sChi, k, t0, t1, t2);
+      double *dst = trace + (size_t)(e0 + el) * NF * M + m;
+      dst[k * M] = t0;
+      dst[(NE + k) * M] = t1;
+      dst[(3 * NE - 1 - k) * M] = t2;
     }
   }
 }
@@ -298,7 +298,7 @@ int run_traces(const dg_mesh *m, const double *c, double *trace, cudaStream_t s)
   using C = Cfg<P, NE>;
   const int ntiles = (int)((m->N + C::EB - 1) / C::EB);
   const int grid = ntiles < m->num_sms * 4 ? ntiles : m->num_sms * 4;
-  k_traces<P, NE><<<grid, kThreads, 0, s>>>(c, trace, m->tab.BfT, (int)m->N);
+  k_traces<P, NE><<<grid, kThreads, 0, s>>>(c, trace, m->tab.BfT, m->tab.EChi, (int)m->N);
   return (int)cudaGetLastError();
 }
 
