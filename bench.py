@@ -11,7 +11,8 @@ between timed steps, outside the timed events.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp64|tf32x3|tf32x1] [--method ssp_rk3|rk2|rk4]
   python bench.py --configs     the five stated workloads, one JSON line each
-  python bench.py --sweep       mesh-size scaling (RK4, p = 1 and 4, 200 to 184,832 elements)
+  python bench.py --sweep       mesh-size scaling (RK4, p = 1 and 4, 200 to 184,832 elements;
+                                p = 1 also with the limiter)
 
 With N = 1 the line also carries the tensor-core modes on the same workload
 (throughput, speedup over float64 and state error against the float64 run) and
@@ -101,7 +102,7 @@ def _src_hash(*names) -> str:
 # change voids the entry.
 TRAFFIC = {
     # k_element_sf<3,4>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
-    "f1cb4b0e5de84012": 77178624 + 39680768,
+    "77c6b8d7e17ec4c1": 77148928 + 42764032,
 }
 
 
@@ -332,10 +333,12 @@ def paper_steppers(m, c0, dt, steps, flush):
 
 
 def run_sweep(precisions=("fp64",)):
-    """Mesh-size scaling in the manner of the paper's Section 5 scaling runs
-    (p = 1 for 10,000 steps and p = 4 for 1,000 steps, RK4, on meshes of 180 to
+    """Mesh-size scaling in the manner of the paper's scaling runs (Section 7.1:
+    p = 1 for 10,000 steps and p = 4 for 1,000 steps, RK4, on meshes of 180 to
     184,320 elements): jittered periodic meshes of 200 to 184,832 elements, the
-    perturbed vortex, classical RK4, device-timed whole runs (CUDA graphs)."""
+    perturbed vortex, classical RK4, device-timed whole runs (CUDA graphs).  At
+    p = 1 the float64 runs are repeated with every stage limited (Section 7.2:
+    the limiter's cost)."""
     import torch
     from paper_1601_07944_gb300 import _build, dg, inputs as I
     _build.build()
@@ -346,8 +349,14 @@ def run_sweep(precisions=("fp64",)):
             m = dg.Mesh.from_mesh(mesh, p)
             dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
             c0 = m.project_function(I.perturbed_vortex)
-            for prec in precisions:
+            runs = [(prec, False) for prec in precisions]
+            if p == 1 and "fp64" in precisions:
+                runs.append(("fp64", True))
+            for prec, limited in runs:
+                m.set_limiter(limited)
                 c = c0.clone()
+                if limited:
+                    m.limit(c)
                 m.rk_step(c, dt, 17, precision=prec, method="rk4")     # capture + warm the graph
                 a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize(); a.record()
@@ -356,11 +365,36 @@ def run_sweep(precisions=("fp64",)):
                 m.device_status()
                 ms = a.elapsed_time(b)
                 print(json.dumps({"sweep": "mesh size", "method": "rk4", "p": p, "n": n, "n_elem": m.N,
-                                  "precision": prec, "steps": steps, "time_s": ms * 1e-3,
+                                  "precision": prec, "limiter": limited, "steps": steps, "time_s": ms * 1e-3,
                                   "ms_per_step": ms / steps,
                                   "dof_updates_per_s": _dof_per_step(m.N, p, "rk4") * steps / (ms * 1e-3)}),
                       flush=True)
+            m.set_limiter(False)
             del m
+    # the kind of run behind the paper's only absolute throughput figures (its
+    # double Mach reflection table: p = 1, classic RK2, Barth-Jespersen limiter on
+    # 68,622 / 236,964 / 964,338 elements): here on jittered periodic meshes of
+    # about those sizes with discontinuous data (density_steps), every stage limited
+    for n, steps in ((185, 2000), (344, 1000), (694, 400)):
+        mesh = I.periodic_mesh(n)
+        m = dg.Mesh.from_mesh(mesh, 1)
+        dt = I.fixed_dt(mesh, I.density_steps, 1)
+        c = m.project_function(I.density_steps)
+        m.set_limiter(True)
+        m.limit(c)
+        m.rk_step(c, dt, 17, method="rk2")
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(); a.record()
+        m.rk_step(c, dt, steps, method="rk2")
+        b.record(); torch.cuda.synchronize()
+        m.device_status()
+        ms = a.elapsed_time(b)
+        print(json.dumps({"sweep": "p=1 RK2 limited (the paper's DMR kind of run)", "method": "rk2", "p": 1,
+                          "n": n, "n_elem": m.N, "precision": "fp64", "limiter": True, "steps": steps,
+                          "time_s": ms * 1e-3, "ms_per_step": ms / steps,
+                          "dof_updates_per_s": _dof_per_step(m.N, 1, "rk2") * steps / (ms * 1e-3)}),
+              flush=True)
+        del m
 
 
 def vortex_error(steps: int = 200):

@@ -181,6 +181,24 @@ dg_status dg_rk_step(dg_mesh *mesh, double *c, double dt, int nsteps, dg_precisi
 dg_status dg_rk_step_method(dg_mesh *mesh, double *c, double dt, int nsteps, dg_rk_method method,
                             dg_precision prec, void *stream);
 
+/* Barth-Jespersen limiter for p = 1 (Section 4.3.5, Eqs. limit, limitmax,
+ * limitmin), in place on c (DEVICE [N][4][3]), variable by variable:
+ *   U_i(r) = Ubar_i + alpha_i grad U_i . (r - r_i),
+ * Ubar_i the centroid value, U^max / U^min the largest / smallest centroid value
+ * of element i and its three neighbours, and alpha_i the smallest over the edge
+ * integration points of min(1, (U^max - Ubar_i)/d) where d = U_i(r_qk) - Ubar_i > 0,
+ * min(1, (U^min - Ubar_i)/d) where d < 0 (the standard Barth-Jespersen ratio; the
+ * paper names the limiter and its bounds).  The linear modes are multiplied by
+ * alpha_i; the means are unchanged.  Errors: DG_EINVAL unless p = 1.
+ * Asynchronous. */
+dg_status dg_limit(dg_mesh *mesh, double *c, void *stream);
+
+/* enable != 0: dg_rk_step and dg_rk_step_method limit every intermediate stage
+ * value and the new state with dg_limit's limiter, as the paper does (Section
+ * 4.3.1); float64 path only (the mixed modes then return DG_ENOTIMPL, and so does
+ * dg_adjoint_step).  Off by default.  Errors: DG_EINVAL if enable and p != 1. */
+dg_status dg_set_limiter(dg_mesh *mesh, int enable);
+
 /* Same as dg_rk_step with c in HOST memory (pinned memory gives the fastest
  * copies): copies c to the device, takes nsteps steps and copies the result back
  * into c.  Synchronous. */

@@ -491,6 +491,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   m->p = p; m->np = np; m->nq = nq; m->nd = nd; m->ne = ne; m->gamma = d->gamma;
   m->N = N; m->F = F;
   m->rin_min = rin_min;
+  m->phi1 = phi[0];                              // phi_1 at the first volume point: the constant mode
   cudaGetDevice(&m->device);
   if (cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess || m->num_sms < 1) {
     cudaGetLastError();
@@ -659,10 +660,20 @@ static dg_status rk_step_one(dg_mesh *m, double *c, double dt, bool traces_valid
             }), what);
     return DG_OK;
   };
+  // With the limiter on (Section 4.3.5, p = 1) every stage value and the new
+  // state are limited; the limiter, not the element kernel, then writes the
+  // traces the next stage reads.
   auto stage = [&](const double *cin, const double *u0, double *out, const StageUpdate &su,
                    const char *what) -> dg_status {
     dg_status st = face(what);
-    return st != DG_OK ? st : elem(cin, u0, out, su, what);
+    if (st != DG_OK) return st;
+    if (!m->limiter) return elem(cin, u0, out, su, what);
+    DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+              return launch_elem(m, prec, cin, u0, out, false, su, 1, stream);
+            }), what);
+    DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return launch_limit(m, out, m->trace, stream); }),
+            what);
+    return DG_OK;
   };
   dg_status st;
   // mixed modes: the first stage's traces on the tensor cores, like the traces
@@ -748,6 +759,8 @@ extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nst
   dg_status st = check_prec(prec, "dg_rk_step");
   if (st != DG_OK) return st;
   if ((st = check_method(method, "dg_rk_step")) != DG_OK) return st;
+  if (m->limiter && prec != DG_FP64)
+    return fail(DG_ENOTIMPL, "dg_rk_step: the limiter runs with the float64 path only");
   if (method == DG_RK4 && !m->rk_acc && nsteps > 0) {
     cudaError_t e = cudaMalloc(&m->rk_acc, sizeof(double) * m->N * dg::M * m->np);
     if (e != cudaSuccess) { cudaGetLastError(); m->rk_acc = nullptr; return fail(DG_ENOMEM, "dg_rk_step: RK4 buffer"); }
@@ -775,6 +788,25 @@ extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nst
   }
   for (; done < nsteps; ++done)
     if ((st = rk_step_one(m, c, dt, true, method, prec, stream)) != DG_OK) return st;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_set_limiter(dg_mesh *m, int enable) {
+  if (!m) return fail(DG_EINVAL, "dg_set_limiter: null mesh");
+  if (enable && m->p != 1) return fail(DG_EINVAL, "dg_set_limiter: the Barth-Jespersen limiter is for p = 1 (p = %d)", m->p);
+  if ((enable != 0) != (m->limiter != 0) && m->graph && m->graph->exec) {
+    cudaGraphExecDestroy(m->graph->exec);    // captured with the other setting
+    m->graph->exec = nullptr;
+  }
+  m->limiter = enable != 0;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_limit(dg_mesh *m, double *c, void *stream) {
+  if (!m || !c) return fail(DG_EINVAL, "dg_limit: null argument");
+  if (m->p != 1) return fail(DG_EINVAL, "dg_limit: the Barth-Jespersen limiter is for p = 1 (p = %d)", m->p);
+  DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return dg::launch_limit(m, c, nullptr, stream); }),
+          "dg_limit");
   return DG_OK;
 }
 
@@ -848,6 +880,7 @@ extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, c
   if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "dg_adjoint_step: null argument");
   if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
   if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
+  if (m->limiter) return fail(DG_ENOTIMPL, "dg_adjoint_step: the limited step has no adjoint here (the limiter is off by default)");
   dg_status ast = adjoint_buffers(m, "dg_adjoint_step");
   if (ast != DG_OK) return ast;
   const size_t S = (size_t)m->N * M * m->np;           // one state

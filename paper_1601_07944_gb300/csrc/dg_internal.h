@@ -122,6 +122,8 @@ struct dg_mesh {
   int *err_flag;               // device int: bit 0 = a bounded tensor-core wait expired,
                                //             bit 1 = a non-physical state was met
   double rin_min;              // smallest inscribed radius 2 area / perimeter
+  double phi1;                 // the constant basis function (sqrt 2)
+  int limiter;                 // dg_set_limiter: limit every stage (p = 1, float64)
   double *totals_dev;          // [M]
   int totals_blocks;
   // scratch for the adjoint (allocated on first use)
@@ -170,6 +172,9 @@ int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
 int launch_eval_points(const dg_mesh *m, const double *c, const double *tab, int npts, double *out, void *stream);
 int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);
+// Barth-Jespersen limiter (p = 1) in place on c; traces of the limited state to
+// trace when not null
+int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream);
 // largest |v| + c over the volume points -> out_dev[0]
 int launch_wave_speed(const dg_mesh *m, const double *c, double *out_dev, void *stream);
 // (dR/du)^T lam combined as out = x0 X + x1 Y + x2 Z + s (dR/du)^T lam (X, Y, Z may

@@ -291,6 +291,81 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 }
 
 // ---------------------------------------------------------------------------
+// Barth-Jespersen limiter for p = 1 (Section 4.3.5), one thread per element, in
+// place on c; the traces of the limited state go to trace (when not null).
+// Per variable: Ubar = phi_1 c_1 is the centroid value (the linear modes vanish at
+// the centroid), U^max / U^min the extremes of the centroid values of the element
+// and its three neighbours; at each edge integration point, with
+// d = U(r_qk) - Ubar, alpha_k = min(1, (U^max - Ubar)/d) for d > 0 and
+// min(1, (U^min - Ubar)/d) for d < 0; the linear modes are scaled by min_k alpha_k.
+// Threads read only the constant mode of their neighbours and write only the
+// linear modes of their own element, so the in-place update has no race.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ elem_face,
+           const FaceConn *__restrict__ conn, const double *__restrict__ BfT, const double *__restrict__ EChi,
+           double phi1, int64_t N) {
+  constexpr int P = 1, NE = 2, NP = 3, NF = 6;
+  __shared__ double sF0[NP * NE], sChi[NP * NE];
+  if (threadIdx.x < NP * NE) {
+    sF0[threadIdx.x] = BfT[(threadIdx.x / NE) * NF + threadIdx.x % NE];
+    sChi[threadIdx.x] = EChi[threadIdx.x];
+  }
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t nb[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int ef = elem_face[e * 3 + q];
+      const FaceConn cn = conn[ef >> 1];
+      nb[q] = (ef & 1) ? cn.l : cn.r;
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      double *ce = c + (e * M + m) * NP;
+      double cj[NP] = {ce[0], ce[1], ce[2]};
+      const double ub = phi1 * cj[0];
+      double umax = ub, umin = ub;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double v = phi1 * c[(nb[q] * M + m) * NP];
+        umax = fmax(umax, v);
+        umin = fmin(umin, v);
+      }
+      double alpha = 1.0;
+      double t[NF];
+#pragma unroll
+      for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
+#pragma unroll
+      for (int x = 0; x < NF; ++x) {
+        const double d = t[x] - ub;
+        double a = 1.0;
+        if (d > 0.0) a = fmin(1.0, (umax - ub) / d);
+        else if (d < 0.0) a = fmin(1.0, (umin - ub) / d);
+        alpha = fmin(alpha, a);
+      }
+      if (alpha < 1.0) {
+        cj[1] *= alpha;
+        cj[2] *= alpha;
+        ce[1] = cj[1];
+        ce[2] = cj[2];
+      }
+      if (trace) {
+        double *dst = trace + (size_t)e * NF * M + m;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+          double t0, t1, t2;
+          edge_traces_sf<P, NE>(cj, sF0, sChi, k, t0, t1, t2);
+          dst[k * M] = t0;
+          dst[(NE + k) * M] = t1;
+          dst[(3 * NE - 1 - k) * M] = t2;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
 template <int P, int NE>
@@ -331,6 +406,15 @@ int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, 
   }
   const int64_t need = (n + threads - 1) / threads, cap = (int64_t)m->num_sms * *per_sm;
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream) {
+  if (m->p != 1 || m->ne != 2) return (int)cudaErrorInvalidValue;
+  static int per_sm = 0;
+  k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N, &per_sm), kThreads, 0,
+               (cudaStream_t)stream>>>(c, trace, m->elem_face, m->face_conn, m->tab.BfT, m->tab.EChi, m->phi1,
+                                       m->N);
+  return (int)cudaGetLastError();
 }
 
 int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream) {

@@ -27,7 +27,7 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_point
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
            "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt",
-           "dg_rk_step_method")
+           "dg_rk_step_method", "dg_limit", "dg_set_limiter")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -71,6 +71,8 @@ def load(path: str = LIB_PATH):
         "dg_rhs": [P, P, P, I, P],
         "dg_rk_step": [P, P, D, I, I, P],
         "dg_rk_step_method": [P, P, D, I, I, I, P],
+        "dg_limit": [P, P, P],
+        "dg_set_limiter": [P, I],
         "dg_rk_step_host": [P, P, D, I, I, P],
         "dg_adjoint_step": [P, P, D, P, P, P],
         "dg_conserved_totals": [P, P, P, P],
@@ -290,6 +292,15 @@ class Mesh:
         _check(load().dg_rk_step_method(self._h, _dev_ptr(c, "c", self.coef_shape), float(dt), int(nsteps),
                                         METHOD[method], _prec(precision), _stream_ptr(stream)))
         return c
+
+    def limit(self, c, stream=None):
+        """Barth-Jespersen limiter (p = 1) in place on the device tensor c."""
+        _check(load().dg_limit(self._h, _dev_ptr(c, "c", self.coef_shape), _stream_ptr(stream)))
+        return c
+
+    def set_limiter(self, on: bool):
+        """Limit every stage value and new state of rk_step (p = 1, float64)."""
+        _check(load().dg_set_limiter(self._h, 1 if on else 0))
 
     def rk_step_host(self, c_host, dt: float, nsteps: int = 1, precision="fp64", stream=None):
         """nsteps SSP-RK3 steps on a host array (numpy or CPU tensor, ideally pinned), in place."""
