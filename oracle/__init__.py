@@ -71,6 +71,9 @@ def _load():
             "or_rk2": (I, [P, P, D, I]),
             "or_rk4": (I, [P, P, D, I]),
             "or_limit_bj": (I, [P, P]),
+            "or_n_boundary": (L, [P]),
+            "or_boundary_points": (I, [P, P]),
+            "or_set_boundary_state": (I, [P, P]),
             "or_set_limiter": (I, [P, I]),
             "or_totals": (I, [P, P, P]),
             "or_lax_friedrichs_jacobians": (I, [D, P, P, D, D, P, P]),
@@ -308,6 +311,23 @@ class OracleDG:
         out = np.array(c, dtype=np.float64, copy=True, order="C")
         _chk(_lib.or_rk4(self._h, _ptr(out), dt, nsteps))
         return out
+
+    @property
+    def n_boundary(self) -> int:
+        return int(_lib.or_n_boundary(self._h))
+
+    def boundary_points(self):
+        """Physical points of the boundary faces [Nb, ne, 2] (element order, then
+        local face; points counter-clockwise along the element)."""
+        out = np.zeros((self.n_boundary, self.ne, 2))
+        _chk(_lib.or_boundary_points(self._h, _ptr(out)))
+        return out
+
+    def set_boundary_state(self, u):
+        """Conserved state prescribed at the boundary points [Nb, ne, 4]."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.shape == (self.n_boundary, self.ne, M)
+        _chk(_lib.or_set_boundary_state(self._h, _ptr(u)))
 
     def limit(self, c):
         """Barth-Jespersen limiter (p = 1) applied to a copy of c."""

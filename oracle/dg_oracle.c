@@ -34,7 +34,10 @@
  *   - the surface temporaries are per edge (one left and one right block).
  *   - time integration: the three-stage SSP Runge-Kutta method in Shu-Osher
  *     form, and the paper's own classic RK2 (read as Heun's method) and RK4;
- *   - the Barth-Jespersen limiter (p = 1) with the standard per-point ratio.
+ *   - the Barth-Jespersen limiter (p = 1) with the standard per-point ratio;
+ *   - boundary faces (Algorithm 2's ghost state): a solid wall mirrors the
+ *     momentum, U_g = (rho, m - 2 (m.n) n, E); a prescribed boundary takes a
+ *     state the caller gives at each boundary quadrature point.
  *
  * Layout of every coefficient array: c[e][m][j], element e, variable m (M=4),
  * mode j (N_p), float64.
@@ -412,6 +415,11 @@ typedef struct {
     double *rhs_volume;                       /* [N][M][Np] */
     double *rhs_surface_left, *rhs_surface_right;   /* [Ns][M][Np] */
     int limit;                                /* limit every stage value (p = 1) */
+    /* boundary faces (Algorithm 2: the right state is a ghost state): er[s] is the
+     * boundary code (-1 solid wall, -2 prescribed state), bidx[s] the face's index
+     * among the boundary faces (-1 for interior faces); bstate [Nb][ne][M] */
+    int64_t Nb, *bidx;
+    double *bstate;
 } oracle_dg;
 
 static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
@@ -424,6 +432,7 @@ void or_destroy(oracle_dg *o)
     free(o->xy); free(o->detJ); free(o->JT); free(o->el); free(o->er); free(o->eL); free(o->eR);
     free(o->enx); free(o->eny); free(o->elen); free(o->elem_edge);
     free(o->rhs_volume); free(o->rhs_surface_left); free(o->rhs_surface_right);
+    free(o->bidx); free(o->bstate);
     free(o);
 }
 
@@ -440,8 +449,10 @@ static void face_point(int q, double xi, double *r, double *s)
 /*
  * Creates the oracle for a mesh of N counter-clockwise triangles.
  *   xy[N][3][2]      vertex coordinates (unwrapped per element);
- *   nbr[N][3]        element across local face q;
- *   nbr_face[N][3]   the neighbour's local face index of that edge.
+ *   nbr[N][3]        element across local face q, or a boundary code: -1 for a
+ *                    solid wall, -2 for a state prescribed at the face's points;
+ *   nbr_face[N][3]   the neighbour's local face index of that edge (-1 on a
+ *                    boundary).
  * nvol = points per direction of the collapsed volume rule (0: p+1);
  * ne = edge points (0: p+1).  Returns NULL on invalid input.
  */
@@ -499,24 +510,43 @@ oracle_dg *or_create(int p, int ne, int nvol, double gamma, int64_t N, const dou
 
     /* edge list: the pair (e,q) that sorts first is the left element */
     o->elem_edge = xcalloc((size_t)N * 3, sizeof(int64_t));
-    int64_t Ns = 0;
+    int64_t Ns = 0, Nb = 0;
     for (int64_t e = 0; e < N; ++e)
         for (int q = 0; q < 3; ++q) {
             int64_t f = nbr[3 * e + q]; int qf = nbr_face[3 * e + q];
+            if (f == -1 || f == -2) { ++Ns; ++Nb; continue; }
             if (f < 0 || f >= N || qf < 0 || qf > 2) { or_destroy(o); return NULL; }
             if (nbr[3 * f + qf] != e || nbr_face[3 * f + qf] != q) { or_destroy(o); return NULL; }
             if (e < f || (e == f && q < qf)) ++Ns;
         }
     o->Ns = Ns;
+    o->Nb = Nb;
+    o->bidx = xcalloc(Ns, sizeof(int64_t));
+    o->bstate = xcalloc((size_t)Nb * o->ne * OM, sizeof(double));
     o->el = xcalloc(Ns, sizeof(int64_t)); o->er = xcalloc(Ns, sizeof(int64_t));
     o->eL = xcalloc(Ns, sizeof(int)); o->eR = xcalloc(Ns, sizeof(int));
     o->enx = xcalloc(Ns, sizeof(double)); o->eny = xcalloc(Ns, sizeof(double));
     o->elen = xcalloc(Ns, sizeof(double));
-    int64_t s = 0;
+    int64_t s = 0, b = 0;
     for (int64_t e = 0; e < N; ++e)
         for (int q = 0; q < 3; ++q) {
             int64_t f = nbr[3 * e + q]; int qf = nbr_face[3 * e + q];
+            if (f < 0) {
+                /* boundary face: the element is its left side, the code its right */
+                const double *v = xy + 6 * e;
+                int q1 = (q + 1) % 3;
+                double dx = v[2 * q1] - v[2 * q], dy = v[2 * q1 + 1] - v[2 * q + 1];
+                double len = sqrt(dx * dx + dy * dy);
+                o->el[s] = e; o->er[s] = f; o->eL[s] = q; o->eR[s] = -1;
+                o->enx[s] = dy / len; o->eny[s] = -dx / len;
+                o->elen[s] = len;
+                o->elem_edge[3 * e + q] = s;
+                o->bidx[s] = b++;
+                ++s;
+                continue;
+            }
             if (!(e < f || (e == f && q < qf))) continue;
+            o->bidx[s] = -1;
             const double *v = xy + 6 * e;
             int q1 = (q + 1) % 3;
             double dx = v[2 * q1] - v[2 * q], dy = v[2 * q1 + 1] - v[2 * q + 1];
@@ -532,6 +562,36 @@ oracle_dg *or_create(int p, int ne, int nvol, double gamma, int64_t N, const dou
     o->rhs_surface_left = xcalloc((size_t)Ns * OM * np, sizeof(double));
     o->rhs_surface_right = xcalloc((size_t)Ns * OM * np, sizeof(double));
     return o;
+}
+
+/* Number of boundary faces. */
+int64_t or_n_boundary(const oracle_dg *o) { return o->Nb; }
+
+/* Physical points of the boundary faces (Eq. 1dmap): out[Nb][ne][2], faces in
+ * element order (element, then local face), points at the edge nodes in the
+ * element's counter-clockwise direction. */
+int or_boundary_points(const oracle_dg *o, double *out)
+{
+    for (int64_t s = 0; s < o->Ns; ++s) {
+        if (o->bidx[s] < 0) continue;
+        const double *v = o->xy + 6 * o->el[s];
+        int q = o->eL[s], q1 = (q + 1) % 3;
+        for (int k = 0; k < o->ne; ++k) {
+            double t = o->ex[k];
+            double *p = out + ((size_t)o->bidx[s] * o->ne + k) * 2;
+            p[0] = 0.5 * (1.0 - t) * v[2 * q] + 0.5 * (1.0 + t) * v[2 * q1];
+            p[1] = 0.5 * (1.0 - t) * v[2 * q + 1] + 0.5 * (1.0 + t) * v[2 * q1 + 1];
+        }
+    }
+    return 0;
+}
+
+/* The state prescribed at the boundary points (faces with code -2; the entries
+ * of wall faces are not read): u[Nb][ne][M], in or_boundary_points' order. */
+int or_set_boundary_state(oracle_dg *o, const double *u)
+{
+    memcpy(o->bstate, u, sizeof(double) * (size_t)o->Nb * o->ne * OM);
+    return 0;
 }
 
 int or_info(const oracle_dg *o, int64_t *out)
@@ -714,6 +774,25 @@ static void eval_volume(oracle_dg *o, const double *C)
 
 /* Algorithm 2: surface integral, one edge at a time, with the right element's
  * points traversed in reverse (Eq. edgeint and the reversal k -> ne+1-k) */
+/* Ghost state at point k of boundary edge s from the interior trace ul (the
+ * paper's eval_boundary, Algorithm 2): a solid wall mirrors the momentum in the
+ * wall, U_g = (rho, m - 2 (m.n) n, E); a prescribed boundary takes the caller's
+ * state at that point. */
+static void ghost_state(const oracle_dg *o, int64_t s, int k, const double *ul, double *ug)
+{
+    if (o->er[s] == -1) {
+        double nx = o->enx[s], ny = o->eny[s];
+        double mn = ul[1] * nx + ul[2] * ny;
+        ug[0] = ul[0];
+        ug[1] = ul[1] - 2.0 * mn * nx;
+        ug[2] = ul[2] - 2.0 * mn * ny;
+        ug[3] = ul[3];
+    } else {
+        const double *u = o->bstate + ((size_t)o->bidx[s] * o->ne + k) * OM;
+        for (int m = 0; m < OM; ++m) ug[m] = u[m];
+    }
+}
+
 static void eval_surface(oracle_dg *o, const double *C)
 {
     int np = o->np, ne = o->ne;
@@ -721,6 +800,26 @@ static void eval_surface(oracle_dg *o, const double *C)
         double *sl = o->rhs_surface_left + (size_t)s * OM * np;
         double *sr = o->rhs_surface_right + (size_t)s * OM * np;
         for (int t = 0; t < OM * np; ++t) { sl[t] = 0.0; sr[t] = 0.0; }
+        if (o->er[s] < 0) {
+            /* boundary edge: the ghost state takes the right trace's place */
+            const double *cl = C + (size_t)o->el[s] * OM * np;
+            int L = o->eL[s];
+            double len = o->elen[s];
+            for (int k = 0; k < ne; ++k) {
+                const double *phiL = o->phif + ((size_t)L * ne + k) * np;
+                double ul[OM], ug[OM], Fn[OM];
+                for (int m = 0; m < OM; ++m) {
+                    ul[m] = 0.0;
+                    for (int j = 0; j < np; ++j) ul[m] += cl[m * np + j] * phiL[j];
+                }
+                ghost_state(o, s, k, ul, ug);
+                lax_friedrichs(o->gamma, ul, ug, o->enx[s], o->eny[s], Fn);
+                for (int m = 0; m < OM; ++m)
+                    for (int j = 0; j < np; ++j)
+                        sl[m * np + j] -= len * o->ew[k] * Fn[m] * phiL[j] / 2.0;
+            }
+            continue;
+        }
         const double *cl = C + (size_t)o->el[s] * OM * np;
         const double *cr = C + (size_t)o->er[s] * OM * np;
         int L = o->eL[s], R = o->eR[s];
@@ -819,6 +918,7 @@ int or_limit_bj(oracle_dg *o, double *C)
         for (int q = 0; q < 3; ++q) {
             int64_t s = o->elem_edge[3 * e + q];
             nb[q] = (o->el[s] == e && o->eL[s] == q) ? o->er[s] : o->el[s];
+            if (nb[q] < 0) nb[q] = e;                 /* a boundary face adds no neighbour */
         }
         for (int m = 0; m < OM; ++m) {
             double *c = C + ((size_t)e * OM + m) * np;
@@ -1042,6 +1142,7 @@ int or_flux_jacobian(double g, const double *U, double nx, double ny, double *J)
 /* out = (dR/dC)^T lam, following Algorithms 3, 2 and 1 backwards */
 int or_rhs_vjp(oracle_dg *o, const double *C, const double *lam, double *out)
 {
+    if (o->Nb > 0) return 2;                  /* periodic meshes only */
     int np = o->np, nq = o->nq, ne = o->ne;
     size_t n = (size_t)o->N * OM * np;
     for (size_t t = 0; t < n; ++t) out[t] = 0.0;
@@ -1122,6 +1223,7 @@ int or_rhs_vjp(oracle_dg *o, const double *C, const double *lam, double *out)
 /* lam_n = (d C_{n+1} / d C_n)^T lam_np1 for one SSP-RK3 step from C_n */
 int or_ssp_rk3_vjp(oracle_dg *o, const double *Cn, double dt, const double *lam_np1, double *lam_n)
 {
+    if (o->Nb > 0) return 2;                  /* periodic meshes only */
     size_t n = (size_t)o->N * OM * o->np;
     double *u1 = malloc(sizeof(double) * n), *u2 = malloc(sizeof(double) * n);
     double *L = malloc(sizeof(double) * n), *b2 = malloc(sizeof(double) * n);

@@ -137,6 +137,32 @@ def periodic_mesh(n: int, jitter: float = 0.1, seed: int = SEED_MESH) -> Mesh:
     return Mesh(n, xy, nbr.reshape(N, 3), nf.reshape(N, 3), jitter, seed)
 
 
+# boundary codes of nbr (the element "across" a boundary face): a solid wall, or a
+# state prescribed by the caller at the face's quadrature points
+BC_WALL = -1
+BC_STATE = -2
+
+
+def box_mesh(n: int, x_code: int = BC_WALL, y_code: int = BC_WALL, jitter: float = 0.1,
+             seed: int = SEED_MESH) -> Mesh:
+    """The jittered mesh of periodic_mesh (same vertices, triangles and jitter)
+    with the faces on x = -5, 5 given the boundary code x_code and those on
+    y = -5, 5 the code y_code (0 keeps that direction periodic).  A boundary face
+    has nbr = code (< 0) and nbr_face = -1.  The domain-edge vertices are not
+    jittered, so the boundary is the square's sides exactly."""
+    mesh = periodic_mesh(n, jitter, seed)
+    nbr = mesh.nbr.reshape(n, n, 2, 3).copy()
+    nf = mesh.nbr_face.reshape(n, n, 2, 3).copy()
+    if x_code:
+        nbr[:, n - 1, 0, 1] = x_code; nf[:, n - 1, 0, 1] = -1      # right side, face b->c
+        nbr[:, 0, 1, 2] = x_code;     nf[:, 0, 1, 2] = -1          # left side, face d->a
+    if y_code:
+        nbr[0, :, 0, 0] = y_code;     nf[0, :, 0, 0] = -1          # bottom, face a->b
+        nbr[n - 1, :, 1, 1] = y_code; nf[n - 1, :, 1, 1] = -1      # top, face c->d
+    N = mesh.n_elem
+    return Mesh(n, mesh.elem_xy, nbr.reshape(N, 3), nf.reshape(N, 3), jitter, seed)
+
+
 # ----------------------------------------------------------------------------
 # Initial data (functions of physical position), returned as conserved
 # variables (rho, rho*u, rho*v, E) with E = p/(gamma-1) + rho*(u^2+v^2)/2.
@@ -166,6 +192,23 @@ def vortex_primitive(x, y, t: float = 0.0, beta: float = 5.0, gamma: float = GAM
     rho = (1.0 + dT) ** (1.0 / (gamma - 1.0))
     p = rho ** gamma
     return rho, 1.0 + du, 1.0 + dv, p
+
+
+def steady_vortex(x, y, cx: float = 3.0, cy: float = 0.0, beta: float = 5.0,
+                  gamma: float = GAMMA) -> np.ndarray:
+    """The isentropic vortex on a fluid at rest (rho = p = 1 far away, no mean
+    flow): an exact steady solution of the Euler equations.  Centred at (cx, cy),
+    by default near the right side of [-5, 5]^2, where it is far from uniform
+    (no periodic images: for bounded domains with prescribed boundary states)."""
+    xr = np.asarray(x, dtype=np.float64) - cx
+    yr = np.asarray(y, dtype=np.float64) - cy
+    r2 = xr * xr + yr * yr
+    g = np.exp(0.5 * (1.0 - r2))
+    u = -beta / (2.0 * math.pi) * g * yr
+    v = beta / (2.0 * math.pi) * g * xr
+    dT = -(gamma - 1.0) * beta * beta / (8.0 * gamma * math.pi ** 2) * g * g
+    rho = (1.0 + dT) ** (1.0 / (gamma - 1.0))
+    return primitive_to_conserved(rho, u, v, rho ** gamma, gamma)
 
 
 def fourier_coefficients(seed: int = SEED_PERTURB, kmax: int = 4):
