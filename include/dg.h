@@ -77,6 +77,14 @@ typedef enum {
     DG_RK4 = 2          /* the classical four-stage method, fourth order */
 } dg_rk_method;
 
+/* Boundary codes in dg_mesh_desc.nbr (Algorithm 2: on a boundary face a ghost
+ * state takes the right trace's place in the numerical flux). */
+enum {
+    DG_BC_WALL = -1,    /* solid wall: U_g = (rho, m - 2 (m.n) n, E), the interior state mirrored */
+    DG_BC_STATE = -2    /* a state prescribed at each boundary quadrature point (far field,
+                           Dirichlet data), given with dg_set_boundary_state */
+};
+
 /* Host description of a mesh; dg_mesh_create copies everything it needs. */
 typedef struct {
     int64_t n_elem;             /* N >= 1 */
@@ -85,8 +93,10 @@ typedef struct {
                                    unwrapped; the two copies of a shared edge must be
                                    translates of each other. */
     const int64_t *nbr;         /* HOST [N][3]: element across local face q, where local
-                                   face q runs from vertex q to vertex (q+1) mod 3 */
-    const int8_t *nbr_face;     /* HOST [N][3]: that neighbour's local face index */
+                                   face q runs from vertex q to vertex (q+1) mod 3;
+                                   DG_BC_WALL or DG_BC_STATE on a boundary face */
+    const int8_t *nbr_face;     /* HOST [N][3]: that neighbour's local face index
+                                   (ignored on a boundary face) */
     int p;                      /* polynomial degree, 1 <= p <= 5 */
     int n_edge_pts;             /* Gauss-Legendre points per edge; 0 = p+1 (the paper's rule).
                                    Supported: p+1, and p for p = 3 */
@@ -98,12 +108,14 @@ typedef struct {
     int64_t n_face;             /* number of distinct edges */
     int p, n_modes, n_vol_pts, n_edge_pts;
     double gamma;
+    int64_t n_boundary_face;    /* boundary faces (the first ones of the edge list) */
 } dg_mesh_info_t;
 
 /* Validates the mesh (det J > 0; nbr[nbr[e][q]][nbr_face[e][q]] == e and the face
- * index maps back; the shared edge's endpoints are translates), builds the edge
- * list, geometry and basis tables on the host and copies them to the current
- * CUDA device.  Synchronous.  *out receives a handle to free with dg_mesh_destroy.
+ * index maps back; the shared edge's endpoints are translates; boundary codes are
+ * DG_BC_WALL or DG_BC_STATE), builds the edge list (boundary faces first, in
+ * element order, as the paper sorts them), geometry and basis tables on the host
+ * and copies them to the current CUDA device.  Synchronous.  *out receives a handle to free with dg_mesh_destroy.
  * Errors: DG_EINVAL (null pointers, p or n_edge_pts unsupported), DG_EMESH,
  * DG_ENOMEM, DG_ECUDA. */
 dg_status dg_mesh_create(const dg_mesh_desc *desc, dg_mesh **out);
@@ -114,6 +126,19 @@ dg_status dg_mesh_destroy(dg_mesh *mesh);
 
 /* Sizes of the discretisation. */
 dg_status dg_mesh_info(const dg_mesh *mesh, dg_mesh_info_t *info);
+
+/* Physical points of the boundary faces' quadrature points (Eq. 1dmap at the
+ * Gauss-Legendre edge nodes): xy[n_boundary_face][n_edge_pts][2], DEVICE, faces in
+ * element order (element, then local face), points in the element's
+ * counter-clockwise direction along the face.  Asynchronous. */
+dg_status dg_boundary_points(const dg_mesh *mesh, double *xy, void *stream);
+
+/* The state prescribed on the DG_BC_STATE faces: u[n_boundary_face][n_edge_pts][4]
+ * conserved variables at the points of dg_boundary_points (DEVICE; entries of
+ * wall faces are not read), copied into the mesh.  Required before dg_rhs or a
+ * time step on a mesh with DG_BC_STATE faces (DG_EINVAL otherwise); the state is
+ * constant in time.  Asynchronous. */
+dg_status dg_set_boundary_state(dg_mesh *mesh, const double *u, void *stream);
 
 /* Physical coordinates of the volume quadrature points (Eq. 2dmap applied to the
  * reference rule): xy[N][n_vol_pts][2], DEVICE.  Asynchronous. */

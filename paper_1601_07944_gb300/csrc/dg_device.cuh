@@ -124,6 +124,24 @@ __device__ __forceinline__ bool lax_friedrichs_edge(const double ul[M], const do
   return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(PL) & positive_finite(PR);
 }
 
+// Ghost state at a point of a boundary face (Algorithm 2: it takes the right
+// trace's place in the numerical flux).  A solid wall (DG_BC_WALL) mirrors the
+// momentum in the wall, U_g = (rho, m - 2 (m.n) n, E), with n the unit outward
+// normal; a prescribed boundary (DG_BC_STATE) takes the caller's state ub there.
+__device__ __forceinline__ void ghost_state(int code, const double ul[M], double nx, double ny,
+                                            const double *ub, double ug[M]) {
+  if (code == DG_BC_WALL) {
+    const double mn2 = 2.0 * fma(ul[1], nx, ul[2] * ny);
+    ug[0] = ul[0];
+    ug[1] = fma(-mn2, nx, ul[1]);
+    ug[2] = fma(-mn2, ny, ul[2]);
+    ug[3] = ul[3];
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) ug[m] = ub[m];
+  }
+}
+
 // device error flag bits (read by dg_device_status)
 constexpr int kErrTimeout = 1;      // a bounded tensor-core wait expired
 constexpr int kErrNonPhysical = 2;  // rho <= 0 or p <= 0 met at a quadrature point

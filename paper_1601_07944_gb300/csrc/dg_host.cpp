@@ -233,9 +233,10 @@ bool supported(int p, int ne) {
 
 void free_mesh(dg_mesh *m) {
   if (!m) return;
-  cudaFree(m->geo); cudaFree(m->xy); cudaFree(m->elem_face); cudaFree(m->face_conn);
+  cudaFree(m->geo); cudaFree(m->xy); cudaFree(m->elem_face); cudaFree(m->elem_nbr); cudaFree(m->face_conn);
   cudaFree(m->face_geo); cudaFree(m->table_block); cudaFree(m->trace); cudaFree(m->fhat);
   cudaFree(m->stage); cudaFree(m->host_state); cudaFree(m->rk_acc); cudaFree(m->partial); cudaFree(m->totals_dev);
+  cudaFree(m->bstate); cudaFree(m->bxy);
   cudaFree(m->adj_buf);
   cudaFree(m->err_flag);
   if (m->timing) {
@@ -358,13 +359,38 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   std::vector<FaceGeo> fgeo;
   conn.reserve(N * 3 / 2 + 1);
   fgeo.reserve(N * 3 / 2 + 1);
+  auto face_geo = [&](const double *v, int q) {
+    // l = |edge| / 2 (Eq. len); the flux is scaled by h = l / 2 (F_hat's 1/2)
+    const int q1 = (q + 1) % 3;
+    const double dx = v[2 * q1] - v[2 * q], dy = v[2 * q1 + 1] - v[2 * q + 1];
+    const double len = std::sqrt(dx * dx + dy * dy);
+    const double nx = dy / len, ny = -dx / len, l = 0.5 * len, h = 0.5 * l, g1 = d->gamma - 1.0;
+    return FaceGeo{nx, ny, l, h * h * d->gamma * g1, h * nx, h * ny, g1 * (h * nx), g1 * (h * ny)};
+  };
+  // boundary faces first (as the paper sorts its edge list: the warps of the edge
+  // kernels then take one branch), in element order; the element is the left side
+  int64_t n_state = 0;
+  for (int64_t e = 0; e < N; ++e)
+    for (int q = 0; q < 3; ++q) {
+      const int64_t f = d->nbr[3 * e + q];
+      if (f >= 0) continue;
+      if (f != DG_BC_WALL && f != DG_BC_STATE)
+        return fail(DG_EMESH, "element %lld face %d: boundary code %lld is not DG_BC_WALL or DG_BC_STATE",
+                    (long long)e, q, (long long)f);
+      if (f == DG_BC_STATE) ++n_state;
+      elem_face[3 * e + q] = 2 * (int32_t)conn.size();
+      conn.push_back(FaceConn{(int32_t)e, q, (int32_t)f, -1});
+      fgeo.push_back(face_geo(xy + 6 * e, q));
+    }
+  const int64_t Fb = (int64_t)conn.size();
   for (int64_t e = 0; e < N; ++e)
     for (int q = 0; q < 3; ++q) {
       int64_t f = d->nbr[3 * e + q];
       int qf = d->nbr_face[3 * e + q];
-      if (f < 0 || f >= N || qf < 0 || qf > 2)
-        return fail(DG_EMESH, "element %lld face %d: neighbour (%lld, %d) out of range (boundary edges "
-                    "are not supported)", (long long)e, q, (long long)f, qf);
+      if (f < 0) continue;
+      if (f >= N || qf < 0 || qf > 2)
+        return fail(DG_EMESH, "element %lld face %d: neighbour (%lld, %d) out of range", (long long)e, q,
+                    (long long)f, qf);
       if (d->nbr[3 * f + qf] != e || d->nbr_face[3 * f + qf] != q)
         return fail(DG_EMESH, "element %lld face %d: neighbour relation is not symmetric", (long long)e, q);
       if (f == e && qf == q) return fail(DG_EMESH, "element %lld face %d is its own neighbour", (long long)e, q);
@@ -380,11 +406,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
       if (!(e < f || (e == f && q < qf))) continue;
       int32_t fi = (int32_t)conn.size();
       conn.push_back(FaceConn{(int32_t)e, q, (int32_t)f, qf});
-      {
-        // l = |edge| / 2 (Eq. len); the flux is scaled by h = l / 2 (F_hat's 1/2)
-        const double nx = dy / len, ny = -dx / len, l = 0.5 * len, h = 0.5 * l, g1 = d->gamma - 1.0;
-        fgeo.push_back(FaceGeo{nx, ny, l, h * h * d->gamma * g1, h * nx, h * ny, g1 * (h * nx), g1 * (h * ny)});
-      }
+      fgeo.push_back(face_geo(v, q));
       elem_face[3 * e + q] = 2 * fi + 0;
       elem_face[3 * f + qf] = 2 * fi + 1;
     }
@@ -511,6 +533,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   DG_ALLOC(m->geo, sizeof(double) * N * GEO, "geometry");
   DG_ALLOC(m->xy, sizeof(double) * N * 6, "vertices");
   DG_ALLOC(m->elem_face, sizeof(int32_t) * N * 3, "element faces");
+  DG_ALLOC(m->elem_nbr, sizeof(int32_t) * N * 3, "element neighbours");
   DG_ALLOC(m->face_conn, sizeof(FaceConn) * F, "face connectivity");
   DG_ALLOC(m->face_geo, sizeof(FaceGeo) * F, "face geometry");
   DG_ALLOC(m->table_block, sizeof(double) * off, "tables");
@@ -521,6 +544,13 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   DG_ALLOC(m->partial, sizeof(double) * m->totals_blocks * M, "totals partials");
   DG_ALLOC(m->totals_dev, sizeof(double) * M, "totals");
   DG_ALLOC(m->err_flag, sizeof(int), "error flag");
+  m->Fb = Fb;
+  m->n_state_faces = n_state;
+  m->bstate_set = n_state == 0;
+  if (Fb > 0) {
+    DG_ALLOC(m->bstate, sizeof(double) * Fb * ne * M, "boundary states");
+    DG_ALLOC(m->bxy, sizeof(double) * Fb * ne * 2, "boundary points");
+  }
 #undef DG_ALLOC
   m->table_doubles = off;
   double *T = m->table_block;
@@ -530,8 +560,30 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   m->tab.SChiA = T + oSChiA; m->tab.SdChiB = T + oSdChiB; m->tab.SHalf = T + oSHalf;
   m->tab.EChi = T + oEChi; m->tab.EWChi = T + oEWChi; m->tab.EWPa = T + oEWPa;
   m->tab.EChiM1 = T + oEChiM1;
+  // the neighbour across each face; a boundary face adds the element itself
+  std::vector<int32_t> elem_nbr(N * 3);
+  for (int64_t i = 0; i < N * 3; ++i) elem_nbr[i] = d->nbr[i] >= 0 ? (int32_t)d->nbr[i] : (int32_t)(i / 3);
+  // physical points of the boundary faces (Eq. 1dmap at the edge nodes, in the
+  // element's counter-clockwise direction)
+  std::vector<double> bxy(Fb * ne * 2);
+  for (int64_t b = 0; b < Fb; ++b) {
+    const double *v = xy + 6 * conn[b].l;
+    const int q = conn[b].L, q1 = (q + 1) % 3;
+    for (int k = 0; k < ne; ++k) {
+      const double t = (double)ex[k];
+      bxy[(b * ne + k) * 2 + 0] = 0.5 * (1.0 - t) * v[2 * q] + 0.5 * (1.0 + t) * v[2 * q1];
+      bxy[(b * ne + k) * 2 + 1] = 0.5 * (1.0 - t) * v[2 * q + 1] + 0.5 * (1.0 + t) * v[2 * q1 + 1];
+    }
+  }
   cudaError_t ce;
+  if (Fb > 0 &&
+      ((ce = cudaMemcpy(m->bxy, bxy.data(), sizeof(double) * Fb * ne * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
+       (ce = cudaMemset(m->bstate, 0, sizeof(double) * Fb * ne * M)) != cudaSuccess)) {
+    free_mesh(m);
+    return cuda_fail(ce, "dg_mesh_create: boundary upload");
+  }
   if ((ce = cudaMemcpy(m->geo, geo.data(), sizeof(double) * N * GEO, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemcpy(m->elem_nbr, elem_nbr.data(), sizeof(int32_t) * N * 3, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->xy, xy, sizeof(double) * N * 6, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->elem_face, elem_face.data(), sizeof(int32_t) * N * 3, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->face_conn, conn.data(), sizeof(FaceConn) * F, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -557,6 +609,24 @@ extern "C" dg_status dg_mesh_info(const dg_mesh *m, dg_mesh_info_t *info) {
   if (!m || !info) return fail(DG_EINVAL, "dg_mesh_info: null argument");
   info->n_elem = m->N; info->n_face = m->F; info->p = m->p; info->n_modes = m->np;
   info->n_vol_pts = m->nq; info->n_edge_pts = m->ne; info->gamma = m->gamma;
+  info->n_boundary_face = m->Fb;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_boundary_points(const dg_mesh *m, double *xy, void *stream) {
+  if (!m || !xy) return fail(DG_EINVAL, "dg_boundary_points: null argument");
+  if (m->Fb == 0) return DG_OK;
+  DG_CUDA(cudaMemcpyAsync(xy, m->bxy, sizeof(double) * m->Fb * m->ne * 2, cudaMemcpyDeviceToDevice,
+                          (cudaStream_t)stream), "dg_boundary_points");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_set_boundary_state(dg_mesh *m, const double *u, void *stream) {
+  if (!m || !u) return fail(DG_EINVAL, "dg_set_boundary_state: null argument");
+  if (m->Fb == 0) return DG_OK;
+  DG_CUDA(cudaMemcpyAsync(m->bstate, u, sizeof(double) * m->Fb * m->ne * dg::M, cudaMemcpyDeviceToDevice,
+                          (cudaStream_t)stream), "dg_set_boundary_state");
+  m->bstate_set = true;
   return DG_OK;
 }
 
@@ -627,6 +697,7 @@ extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision
   if (c == r) return fail(DG_EINVAL, "dg_rhs: c and r alias");
   dg_status st = check_prec(prec, "dg_rhs");
   if (st != DG_OK) return st;
+  if (!m->bstate_set) return fail(DG_EINVAL, "dg_rhs: the mesh has DG_BC_STATE faces and no boundary state was set");
   DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces_p(m, prec, c, stream); }),
           "dg_rhs traces");
   DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_p(m, prec, stream); }),
@@ -759,6 +830,8 @@ extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nst
   dg_status st = check_prec(prec, "dg_rk_step");
   if (st != DG_OK) return st;
   if ((st = check_method(method, "dg_rk_step")) != DG_OK) return st;
+  if (!m->bstate_set)
+    return fail(DG_EINVAL, "dg_rk_step: the mesh has DG_BC_STATE faces and no boundary state was set");
   if (m->limiter && prec != DG_FP64)
     return fail(DG_ENOTIMPL, "dg_rk_step: the limiter runs with the float64 path only");
   if (method == DG_RK4 && !m->rk_acc && nsteps > 0) {
@@ -863,6 +936,7 @@ extern "C" dg_status dg_rhs_adjoint(dg_mesh *m, const double *c, const double *l
   using namespace dg;
   if (!m || !c || !lam || !out) return fail(DG_EINVAL, "dg_rhs_adjoint: null argument");
   if (out == c || out == lam) return fail(DG_EINVAL, "dg_rhs_adjoint: out aliases an input");
+  if (m->Fb > 0) return fail(DG_ENOTIMPL, "dg_rhs_adjoint: meshes with boundary faces have no adjoint here");
   dg_status st = adjoint_buffers(m, "dg_rhs_adjoint");
   if (st != DG_OK) return st;
   const size_t S = (size_t)m->N * M * m->np, TR = (size_t)m->N * 3 * m->ne * M;
@@ -881,6 +955,7 @@ extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, c
   if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
   if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
   if (m->limiter) return fail(DG_ENOTIMPL, "dg_adjoint_step: the limited step has no adjoint here (the limiter is off by default)");
+  if (m->Fb > 0) return fail(DG_ENOTIMPL, "dg_adjoint_step: meshes with boundary faces have no adjoint here");
   dg_status ast = adjoint_buffers(m, "dg_adjoint_step");
   if (ast != DG_OK) return ast;
   const size_t S = (size_t)m->N * M * m->np;           // one state

@@ -22,7 +22,8 @@ constexpr int PMAX = 5;
 //   flux is G_r = jt0 F1 + jt1 F2, G_s = jt2 F1 + jt3 F2; then 1/det J, det J.
 constexpr int GEO = 8;
 
-// Face record: left element, its local face, right element, its local face.
+// Face record: left element, its local face, right element, its local face; on a
+// boundary face r is the boundary code (DG_BC_WALL, DG_BC_STATE) and R = -1.
 struct FaceConn { int32_t l, L, r, R; };
 // Face geometry (8 doubles): unit normal n (left -> right) and half length l
 // (Eq. len); then the products the edge flux uses, formed once on the host with
@@ -101,13 +102,19 @@ struct dg_mesh {
   int p, np, nq, nd, ne;
   double gamma;
   int64_t N, F;
+  int64_t Fb;                  // boundary faces (the first Fb of the face list)
+  int64_t n_state_faces;       // boundary faces with a prescribed state
+  bool bstate_set;             // dg_set_boundary_state was called (or none is needed)
+  double *bstate;              // [Fb][ne][M] prescribed boundary states (device)
+  double *bxy;                 // [Fb][ne][2] boundary points (device)
   int device;
   int num_sms;
   // device arrays
   double *geo;                 // [N][GEO]
   double *xy;                  // [N][6]
   int32_t *elem_face;          // [N][3]: f*2 + side (0 = left, 1 = right)
-  dg::FaceConn *face_conn;     // [F]
+  int32_t *elem_nbr;           // [N][3]: the element across each local face
+  dg::FaceConn *face_conn;     // [F]: the Fb boundary faces first (r = boundary code < 0)
   dg::FaceGeo *face_geo;       // [F]
   dg::DevTables tab;
   double *table_block;         // one allocation holding every table

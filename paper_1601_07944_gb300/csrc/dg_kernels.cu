@@ -76,7 +76,7 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
 template <int NE>
 __global__ void __launch_bounds__(kThreads)
 k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
-       const FaceGeo *__restrict__ fg, int64_t F, double gamma, int *err) {
+       const FaceGeo *__restrict__ fg, const double *__restrict__ bstate, int64_t F, double gamma, int *err) {
   constexpr int NF = 3 * NE;
   bool ok = true;
   // The grid is what fits on the GPU at once; block b takes the b-th of gridDim.x
@@ -90,10 +90,17 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
     const FaceConn cn = conn[f];
     const FaceGeo g = fg[f];
     const double *pl = trace + ((size_t)cn.l * NF + cn.L * NE + k) * M;
-    const double *pr = trace + ((size_t)cn.r * NF + cn.R * NE + (NE - 1 - k)) * M;
     double ul[M], ur[M], Fh[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) { ul[m] = pl[m]; ur[m] = pr[m]; }
+    for (int m = 0; m < M; ++m) ul[m] = pl[m];
+    if (cn.r < 0) {
+      // boundary face (the first faces of the list): the ghost state at the same point
+      ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
+    } else {
+      const double *pr = trace + ((size_t)cn.r * NF + cn.R * NE + (NE - 1 - k)) * M;
+#pragma unroll
+      for (int m = 0; m < M; ++m) ur[m] = pr[m];
+    }
     // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
     ok &= lax_friedrichs_edge(ul, ur, g, gamma, Fh);
     double *dst = fhat + (size_t)i * M;
@@ -300,11 +307,23 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 // min(1, (U^min - Ubar)/d) for d < 0; the linear modes are scaled by min_k alpha_k.
 // Threads read only the constant mode of their neighbours and write only the
 // linear modes of their own element, so the in-place update has no race.
+// The float64 pipe is spared where the decisions allow it: extremes are found by
+// integer compares of order-preserving keys of the bit patterns, the smallest
+// ratio num_k/|d_k| (both non-negative) by comparing the cross products
+// num_k |d_best| and num_best |d_k| as unsigned integers, and the one division
+// happens only when the element is limited.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ unsigned long long nonneg_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x);   // x >= 0: bits order like values
+}
+
 __global__ void __launch_bounds__(kThreads)
-k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ elem_face,
-           const FaceConn *__restrict__ conn, const double *__restrict__ BfT, const double *__restrict__ EChi,
-           double phi1, int64_t N) {
+k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ elem_nbr,
+           const double *__restrict__ BfT, const double *__restrict__ EChi, double phi1, int64_t N) {
   constexpr int P = 1, NE = 2, NP = 3, NF = 6;
   __shared__ double sF0[NP * NE], sChi[NP * NE];
   if (threadIdx.x < NP * NE) {
@@ -313,53 +332,57 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
   }
   __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t nb[3];
+    const int64_t nb0 = elem_nbr[e * 3], nb1 = elem_nbr[e * 3 + 1], nb2 = elem_nbr[e * 3 + 2];
+    double cn[3][M];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int ef = elem_face[e * 3 + q];
-      const FaceConn cn = conn[ef >> 1];
-      nb[q] = (ef & 1) ? cn.l : cn.r;
+    for (int m = 0; m < M; ++m) {
+      cn[0][m] = c[(nb0 * M + m) * NP];
+      cn[1][m] = c[(nb1 * M + m) * NP];
+      cn[2][m] = c[(nb2 * M + m) * NP];
     }
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       double *ce = c + (e * M + m) * NP;
       double cj[NP] = {ce[0], ce[1], ce[2]};
-      const double ub = phi1 * cj[0];
-      double umax = ub, umin = ub;
+      // extremes of the constant modes (phi_1 > 0 keeps the order)
+      double cmax = cj[0], cmin = cj[0];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const double v = phi1 * c[(nb[q] * M + m) * NP];
-        umax = fmax(umax, v);
-        umin = fmin(umin, v);
+        const double v = cn[q][m];
+        if (order_key(v) > order_key(cmax)) cmax = v;
+        if (order_key(v) < order_key(cmin)) cmin = v;
       }
-      double alpha = 1.0;
+      const double ub = phi1 * cj[0];
+      // U^max - Ubar and Ubar - U^min, formed so that they are exactly >= 0 (an
+      // FMA-contracted phi1 cmax - ub would leave the product's rounding error,
+      // of either sign, where the difference is 0; the comparisons below read
+      // these as non-negative bit patterns)
+      const double up = phi1 * (cmax - cj[0]), dn = phi1 * (cj[0] - cmin);
       double t[NF];
 #pragma unroll
       for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
+      double nbest = 1.0, dbest = 1.0;                                  // ratio 1: no limiting
 #pragma unroll
       for (int x = 0; x < NF; ++x) {
-        const double d = t[x] - ub;
-        double a = 1.0;
-        if (d > 0.0) a = fmin(1.0, (umax - ub) / d);
-        else if (d < 0.0) a = fmin(1.0, (umin - ub) / d);
-        alpha = fmin(alpha, a);
+        const unsigned long long db = (unsigned long long)__double_as_longlong(t[x] - ub);
+        const unsigned long long mag = db & 0x7FFFFFFFFFFFFFFFull;       // |d|
+        const double num = (db >> 63) ? dn : up;
+        const double den = __longlong_as_double((long long)mag);
+        if (mag != 0ull && nonneg_bits(num * dbest) < nonneg_bits(nbest * den)) { nbest = num; dbest = den; }
       }
-      if (alpha < 1.0) {
+      if (nonneg_bits(nbest) < nonneg_bits(dbest)) {
+        const double alpha = nbest / dbest;
         cj[1] *= alpha;
         cj[2] *= alpha;
         ce[1] = cj[1];
         ce[2] = cj[2];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
       }
       if (trace) {
         double *dst = trace + (size_t)e * NF * M + m;
 #pragma unroll
-        for (int k = 0; k < NE; ++k) {
-          double t0, t1, t2;
-          edge_traces_sf<P, NE>(cj, sF0, sChi, k, t0, t1, t2);
-          dst[k * M] = t0;
-          dst[(NE + k) * M] = t1;
-          dst[(3 * NE - 1 - k) * M] = t2;
-        }
+        for (int x = 0; x < NF; ++x) dst[x * M] = t[x];
       }
     }
   }
@@ -412,8 +435,7 @@ int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream) {
   if (m->p != 1 || m->ne != 2) return (int)cudaErrorInvalidValue;
   static int per_sm = 0;
   k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N, &per_sm), kThreads, 0,
-               (cudaStream_t)stream>>>(c, trace, m->elem_face, m->face_conn, m->tab.BfT, m->tab.EChi, m->phi1,
-                                       m->N);
+               (cudaStream_t)stream>>>(c, trace, m->elem_nbr, m->tab.BfT, m->tab.EChi, m->phi1, m->N);
   return (int)cudaGetLastError();
 }
 
@@ -424,7 +446,7 @@ int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *
   do {                                                                                                  \
     static int per_sm = 0;                                                                              \
     k_face<NE><<<resident_grid(m, (const void *)k_face<NE>, kThreads, n, &per_sm), kThreads, 0, s>>>(   \
-        trace, fhat, m->face_conn, m->face_geo, m->F, m->gamma, m->err_flag);                           \
+        trace, fhat, m->face_conn, m->face_geo, m->bstate, m->F, m->gamma, m->err_flag);                \
   } while (0)
   switch (m->ne) {
     case 2: FACE(2); break;

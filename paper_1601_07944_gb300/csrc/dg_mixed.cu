@@ -435,29 +435,41 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
 // the float64 integral of l F_hat against the constant mode,
 // fmean_m = sum_k omega_k phi_1 l F_hat_{k,m} (Algorithm 2 for j = 1; the
 // Gauss-Legendre weights are symmetric, so it is the same from both sides).
-template <int NE>
+// BND: the launch covers the boundary faces [f0, f1) = [0, Fb) (a ghost state on
+// the right, Algorithm 2); otherwise the interior faces [Fb, F), in a separate
+// instantiation so that the common case carries no boundary code.
+template <int NE, bool BND>
 __global__ void __launch_bounds__(256)
 k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *__restrict__ fmean,
              const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg, const double *__restrict__ Lf,
-             int np, int64_t F, double gamma, int *err) {
+             const double *__restrict__ bstate, int np, int64_t f0, int64_t f1, double gamma, int *err) {
   constexpr int NF = 3 * NE;
   bool ok = true;
   // the grid is what is resident at once; block b takes the b-th of gridDim.x
   // equal slices of the edges
-  const int64_t lo = F * blockIdx.x / gridDim.x, hi = F * (blockIdx.x + 1) / gridDim.x;
+  const int64_t F = f1 - f0;
+  const int64_t lo = f0 + F * blockIdx.x / gridDim.x, hi = f0 + F * (blockIdx.x + 1) / gridDim.x;
   for (int64_t f = lo + threadIdx.x; f < hi; f += blockDim.x) {
     const FaceConn cn = conn[f];
     const FaceGeo g = fg[f];
     // [N][NF][M] float32: one point's four values are one aligned float4
+    constexpr bool bnd = BND;
     const float4 *tl = reinterpret_cast<const float4 *>(trace) + (size_t)cn.l * NF + cn.L * NE;
-    const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)cn.r * NF + cn.R * NE;
+    const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)(bnd ? cn.l : cn.r) * NF + (bnd ? 0 : cn.R * NE);
     float4 *dst = reinterpret_cast<float4 *>(fhat) + (size_t)f * NE;
     double sm[M] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
-      const float4 a = tl[k], b = tr[NE - 1 - k];
+      const float4 a = tl[k];
       const double ul[M] = {tc::f32_to_f64(a.x), tc::f32_to_f64(a.y), tc::f32_to_f64(a.z), tc::f32_to_f64(a.w)};
-      const double ur[M] = {tc::f32_to_f64(b.x), tc::f32_to_f64(b.y), tc::f32_to_f64(b.z), tc::f32_to_f64(b.w)};
+      double ur[M];
+      if (bnd) {
+        ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
+      } else {
+        const float4 b = tr[NE - 1 - k];
+        ur[0] = tc::f32_to_f64(b.x); ur[1] = tc::f32_to_f64(b.y);
+        ur[2] = tc::f32_to_f64(b.z); ur[3] = tc::f32_to_f64(b.w);
+      }
       double Fh[M];
       ok &= lax_friedrichs_edge<true>(ul, ur, g, gamma, Fh);
       const double w = Lf[k * np];           // omega_k phi_1, the same on the three faces
@@ -591,9 +603,16 @@ int launch_face_flux_mixed(const dg_mesh *m, const MixedBuffers &b, void *stream
   cudaStream_t s = (cudaStream_t)stream;
 #define FACE(NE)                                                                                          \
   do {                                                                                                    \
-    static int per_sm = 0;                                                                                \
-    k_face_mixed<NE><<<resident_grid(m, (const void *)k_face_mixed<NE>, 256, m->F, &per_sm), 256, 0, s>>>( \
-        b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->np, m->F, m->gamma, m->err_flag); \
+    static int per_sm = 0, per_sm_b = 0;                                                                  \
+    k_face_mixed<NE, false><<<resident_grid(m, (const void *)k_face_mixed<NE, false>, 256, m->F - m->Fb,   \
+                                            &per_sm), 256, 0, s>>>(                                       \
+        b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->bstate, m->np, m->Fb, m->F,    \
+        m->gamma, m->err_flag);                                                                           \
+    if (m->Fb > 0)                                                                                        \
+      k_face_mixed<NE, true><<<resident_grid(m, (const void *)k_face_mixed<NE, true>, 256, m->Fb,         \
+                                             &per_sm_b), 256, 0, s>>>(                                    \
+          b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->bstate, m->np, 0, m->Fb,     \
+          m->gamma, m->err_flag);                                                                         \
   } while (0)
   switch (m->ne) {
     case 2: FACE(2); break;

@@ -41,6 +41,8 @@ extern "C" dg_status dg_rhs_noalloc(dg_mesh *m, const double *c, double *r, dg_p
   if (c == r) return dg::set_error(DG_EINVAL, "dg_rhs_noalloc: c and r alias");
   if (prec != DG_FP64 && prec != DG_TF32X1 && prec != DG_TF32X3)
     return dg::set_error(DG_EINVAL, "dg_rhs_noalloc: unknown precision %d", (int)prec);
+  if (!m->bstate_set)
+    return dg::set_error(DG_EINVAL, "dg_rhs_noalloc: the mesh has DG_BC_STATE faces and no boundary state was set");
   const size_t n_trace = (size_t)m->N * 3 * m->ne * dg::M;
   const size_t n_flux = (size_t)m->F * m->ne * dg::M;
   if (n_trace + n_flux > kScratchDoubles)

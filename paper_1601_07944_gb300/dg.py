@@ -27,7 +27,8 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_point
            "dg_project_ic", "dg_rhs", "dg_rk_step", "dg_rk_step_host", "dg_adjoint_step",
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
            "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt",
-           "dg_rk_step_method", "dg_limit", "dg_set_limiter")
+           "dg_rk_step_method", "dg_limit", "dg_set_limiter", "dg_boundary_points",
+           "dg_set_boundary_state")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -46,7 +47,7 @@ class _Desc(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("n_elem", ctypes.c_int64), ("n_face", ctypes.c_int64), ("p", ctypes.c_int),
                 ("n_modes", ctypes.c_int), ("n_vol_pts", ctypes.c_int), ("n_edge_pts", ctypes.c_int),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("n_boundary_face", ctypes.c_int64)]
 
 
 _lib = None
@@ -72,6 +73,8 @@ def load(path: str = LIB_PATH):
         "dg_rk_step": [P, P, D, I, I, P],
         "dg_rk_step_method": [P, P, D, I, I, I, P],
         "dg_limit": [P, P, P],
+        "dg_boundary_points": [P, P, P],
+        "dg_set_boundary_state": [P, P, P],
         "dg_set_limiter": [P, I],
         "dg_rk_step_host": [P, P, D, I, I, P],
         "dg_adjoint_step": [P, P, D, P, P, P],
@@ -176,6 +179,7 @@ class Mesh:
         _check(lib.dg_mesh_info(h, ctypes.byref(info)))
         self.N, self.n_face, self.p = info.n_elem, info.n_face, info.p
         self.np, self.nq, self.ne, self.gamma = info.n_modes, info.n_vol_pts, info.n_edge_pts, info.gamma
+        self.n_boundary = info.n_boundary_face
 
     @classmethod
     def from_mesh(cls, mesh, p: int, **kw):
@@ -292,6 +296,23 @@ class Mesh:
         _check(load().dg_rk_step_method(self._h, _dev_ptr(c, "c", self.coef_shape), float(dt), int(nsteps),
                                         METHOD[method], _prec(precision), _stream_ptr(stream)))
         return c
+
+    def boundary_points(self, stream=None):
+        """Physical points of the boundary faces, a device tensor [Nb, n_e, 2]."""
+        import torch
+        out = torch.empty((self.n_boundary, self.ne, 2), dtype=torch.float64, device="cuda")
+        if self.n_boundary:
+            _check(load().dg_boundary_points(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def set_boundary_state(self, u, stream=None):
+        """Conserved state prescribed at the boundary points: device tensor [Nb, n_e, 4]."""
+        import torch
+        if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()
+                and tuple(u.shape) == (self.n_boundary, self.ne, 4)):
+            raise TypeError("u must be a contiguous float64 CUDA tensor of shape %s"
+                            % ((self.n_boundary, self.ne, 4),))
+        _check(load().dg_set_boundary_state(self._h, ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream)))
 
     def limit(self, c, stream=None):
         """Barth-Jespersen limiter (p = 1) in place on the device tensor c."""

@@ -89,9 +89,14 @@ def test_mesh_validation_errors(lib):
     st, msg = _create(lib, m.elem_xy, nbr, m.nbr_face)
     assert st == 4 and "symmetric" in msg
     nbr = m.nbr.copy()
-    nbr[0, 0] = -1                                # boundary code: unsupported
-    st, _ = _create(lib, m.elem_xy, nbr, m.nbr_face)
-    assert st == 4
+    nbr[0, 0] = I.BC_WALL                         # a wall on one side of an interior face only
+    st, msg = _create(lib, m.elem_xy, nbr, m.nbr_face)
+    assert st == 4 and "symmetric" in msg
+    b = I.box_mesh(4)
+    nbr = b.nbr.copy()
+    nbr[nbr == I.BC_WALL] = -7                    # not a boundary code
+    st, msg = _create(lib, b.elem_xy, nbr, b.nbr_face)
+    assert st == 4 and "boundary code" in msg
     xy = m.elem_xy.copy()
     xy[7, 1] += 1e-3                              # edge no longer matches its neighbour's
     xy[7, 1] -= 0.0
