@@ -32,7 +32,9 @@
  *     asynchronous on it unless stated; a caller must not reuse an output before
  *     the stream has reached the call.
  *   - The mesh handle owns its geometry, basis tables and work buffers; calls on
- *     one handle must not overlap in time on different streams.
+ *     one handle must not overlap in time on different streams.  Calls that take
+ *     a mesh run on the device it was created on, which must be the calling
+ *     thread's current device (DG_EINVAL otherwise).
  *   - No call aborts.  Every call returns a dg_status; on failure
  *     dg_last_error() returns a message for the calling thread.
  */

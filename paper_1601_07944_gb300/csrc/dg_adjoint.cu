@@ -223,15 +223,15 @@ int run_adj(const dg_mesh *m, const double *u, const double *lam, double *uvol, 
             double s, double *out, cudaStream_t st) {
   using A = AdjCfg<P, NE>;
   using C = Cfg<P, NE>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDevice attr_set;
+  if (!attr_set.test(m->device)) {
     cudaError_t e = cudaFuncSetAttribute(k_adj_element<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, A::SMEM);
     if (e != cudaSuccess) return (int)e;
     // all of the SM's unified L1/shared storage as shared memory, so that the
     // occupancy query and the launch see every CTA that fits
     e = cudaFuncSetAttribute(k_adj_element<P, NE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
-    attr_set = true;
+    attr_set.set(m->device);
   }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_element<P, NE>, kThreads, A::SMEM);

@@ -309,13 +309,13 @@ template <int P, int NE>
 int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
                    const double *fhat, const StageUpdate &su, int mode, cudaStream_t s) {
   using S = SfCfg<P, NE>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDevice attr_set;
+  if (!attr_set.test(m->device)) {
     cudaError_t e = cudaFuncSetAttribute(k_element_sf<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_element_sf<P, NE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
-    attr_set = true;
+    attr_set.set(m->device);
   }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element_sf<P, NE>, kThreads, S::SMEM);

@@ -295,6 +295,19 @@ dg_status set_error(dg_status st, const char *fmt, ...) {
 
 extern "C" const char *dg_last_error(void) { return g_err.c_str(); }
 
+// Kernels launch on the current device; the mesh's arrays live on the device it
+// was created on.
+static dg_status check_device(const dg_mesh *m, const char *who) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DG_ECUDA, "%s: cudaGetDevice failed", who);
+  }
+  if (dev != m->device)
+    return fail(DG_EINVAL, "%s: the current device is %d, the mesh lives on device %d", who, dev, m->device);
+  return DG_OK;
+}
+
 extern "C" dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s, double *vol_w,
                                     double *edge_x, double *edge_w, double *phi, double *dphi_r,
                                     double *dphi_s, double *phi_face) {
@@ -615,6 +628,7 @@ extern "C" dg_status dg_mesh_info(const dg_mesh *m, dg_mesh_info_t *info) {
 
 extern "C" dg_status dg_boundary_points(const dg_mesh *m, double *xy, void *stream) {
   if (!m || !xy) return fail(DG_EINVAL, "dg_boundary_points: null argument");
+  if (dg_status dst = check_device(m, "dg_boundary_points")) return dst;
   if (m->Fb == 0) return DG_OK;
   DG_CUDA(cudaMemcpyAsync(xy, m->bxy, sizeof(double) * m->Fb * m->ne * 2, cudaMemcpyDeviceToDevice,
                           (cudaStream_t)stream), "dg_boundary_points");
@@ -623,6 +637,7 @@ extern "C" dg_status dg_boundary_points(const dg_mesh *m, double *xy, void *stre
 
 extern "C" dg_status dg_set_boundary_state(dg_mesh *m, const double *u, void *stream) {
   if (!m || !u) return fail(DG_EINVAL, "dg_set_boundary_state: null argument");
+  if (dg_status dst = check_device(m, "dg_set_boundary_state")) return dst;
   if (m->Fb == 0) return DG_OK;
   DG_CUDA(cudaMemcpyAsync(m->bstate, u, sizeof(double) * m->Fb * m->ne * dg::M, cudaMemcpyDeviceToDevice,
                           (cudaStream_t)stream), "dg_set_boundary_state");
@@ -632,6 +647,7 @@ extern "C" dg_status dg_set_boundary_state(dg_mesh *m, const double *u, void *st
 
 extern "C" dg_status dg_volume_points(const dg_mesh *m, double *xy, void *stream) {
   if (!m || !xy) return fail(DG_EINVAL, "dg_volume_points: null argument");
+  if (dg_status dst = check_device(m, "dg_volume_points")) return dst;
   DG_CUDA((cudaError_t)dg::launch_volume_points(m, xy, stream), "dg_volume_points");
   return DG_OK;
 }
@@ -639,6 +655,7 @@ extern "C" dg_status dg_volume_points(const dg_mesh *m, double *xy, void *stream
 extern "C" dg_status dg_eval_points(dg_mesh *m, int npts, const double *r, const double *s, const double *c,
                                     double *out, void *stream) {
   if (!m || !r || !s || !c || !out) return fail(DG_EINVAL, "dg_eval_points: null argument");
+  if (dg_status dst = check_device(m, "dg_eval_points")) return dst;
   if (npts < 1 || npts > 1 << 20) return fail(DG_EINVAL, "dg_eval_points: npts=%d", npts);
   std::vector<double> tab((size_t)npts * m->np);
   for (int k = 0; k < npts; ++k) {
@@ -659,6 +676,7 @@ extern "C" dg_status dg_eval_points(dg_mesh *m, int npts, const double *r, const
 
 extern "C" dg_status dg_project_ic(dg_mesh *m, const double *u, double *c, void *stream) {
   if (!m || !u || !c) return fail(DG_EINVAL, "dg_project_ic: null argument");
+  if (dg_status dst = check_device(m, "dg_project_ic")) return dst;
   DG_CUDA((cudaError_t)timed(m, DG_K_PROJECT, stream, [&] { return dg::launch_project(m, u, c, stream); }),
           "dg_project_ic");
   return DG_OK;
@@ -694,6 +712,7 @@ static int launch_elem(dg_mesh *m, dg_precision prec, const double *c, const dou
 
 extern "C" dg_status dg_rhs(dg_mesh *m, const double *c, double *r, dg_precision prec, void *stream) {
   if (!m || !c || !r) return fail(DG_EINVAL, "dg_rhs: null argument");
+  if (dg_status dst = check_device(m, "dg_rhs")) return dst;
   if (c == r) return fail(DG_EINVAL, "dg_rhs: c and r alias");
   dg_status st = check_prec(prec, "dg_rhs");
   if (st != DG_OK) return st;
@@ -825,6 +844,7 @@ static cudaGraphExec_t step_graph(dg_mesh *m, double *c, double dt, dg_rk_method
 extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nsteps, dg_rk_method method,
                                        dg_precision prec, void *stream) {
   if (!m || !c) return fail(DG_EINVAL, "dg_rk_step: null argument");
+  if (dg_status dst = check_device(m, "dg_rk_step")) return dst;
   if (nsteps < 0) return fail(DG_EINVAL, "dg_rk_step: nsteps < 0");
   if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_rk_step: dt is not finite");
   dg_status st = check_prec(prec, "dg_rk_step");
@@ -877,6 +897,7 @@ extern "C" dg_status dg_set_limiter(dg_mesh *m, int enable) {
 
 extern "C" dg_status dg_limit(dg_mesh *m, double *c, void *stream) {
   if (!m || !c) return fail(DG_EINVAL, "dg_limit: null argument");
+  if (dg_status dst = check_device(m, "dg_limit")) return dst;
   if (m->p != 1) return fail(DG_EINVAL, "dg_limit: the Barth-Jespersen limiter is for p = 1 (p = %d)", m->p);
   DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return dg::launch_limit(m, c, nullptr, stream); }),
           "dg_limit");
@@ -891,6 +912,7 @@ extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg
 extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int nsteps,
                                      dg_precision prec, void *stream) {
   if (!m || !c_host) return fail(DG_EINVAL, "dg_rk_step_host: null argument");
+  if (dg_status dst = check_device(m, "dg_rk_step_host")) return dst;
   size_t bytes = sizeof(double) * m->N * dg::M * m->np;
   if (!m->host_state) {
     cudaError_t e = cudaMalloc(&m->host_state, bytes);
@@ -907,6 +929,7 @@ extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int 
 
 extern "C" dg_status dg_conserved_totals(dg_mesh *m, const double *c, double out[4], void *stream) {
   if (!m || !c || !out) return fail(DG_EINVAL, "dg_conserved_totals: null argument");
+  if (dg_status dst = check_device(m, "dg_conserved_totals")) return dst;
   cudaStream_t s = (cudaStream_t)stream;
   DG_CUDA((cudaError_t)timed(m, DG_K_TOTALS, stream, [&] { return dg::launch_totals(m, c, m->totals_dev, stream); }),
           "dg_conserved_totals");
@@ -935,6 +958,7 @@ static dg_status adjoint_buffers(dg_mesh *m, const char *who) {
 extern "C" dg_status dg_rhs_adjoint(dg_mesh *m, const double *c, const double *lam, double *out, void *stream) {
   using namespace dg;
   if (!m || !c || !lam || !out) return fail(DG_EINVAL, "dg_rhs_adjoint: null argument");
+  if (dg_status dst = check_device(m, "dg_rhs_adjoint")) return dst;
   if (out == c || out == lam) return fail(DG_EINVAL, "dg_rhs_adjoint: out aliases an input");
   if (m->Fb > 0) return fail(DG_ENOTIMPL, "dg_rhs_adjoint: meshes with boundary faces have no adjoint here");
   dg_status st = adjoint_buffers(m, "dg_rhs_adjoint");
@@ -952,6 +976,7 @@ extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, c
                                      double *lam_n, void *stream) {
   using namespace dg;
   if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "dg_adjoint_step: null argument");
+  if (dg_status dst = check_device(m, "dg_adjoint_step")) return dst;
   if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
   if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
   if (m->limiter) return fail(DG_ENOTIMPL, "dg_adjoint_step: the limited step has no adjoint here (the limiter is off by default)");
@@ -1092,6 +1117,7 @@ extern "C" dg_status dg_self_test(int64_t mismatches[3], void *stream) {
 
 extern "C" dg_status dg_stable_dt(dg_mesh *m, const double *c, double cfl, double *dt_out, void *stream) {
   if (!m || !c || !dt_out) return fail(DG_EINVAL, "dg_stable_dt: null argument");
+  if (dg_status dst = check_device(m, "dg_stable_dt")) return dst;
   if (!(cfl > 0.0)) return fail(DG_EINVAL, "dg_stable_dt: cfl must be positive");
   cudaStream_t s = (cudaStream_t)stream;
   double smax = 0.0;

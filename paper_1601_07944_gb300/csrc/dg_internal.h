@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -72,6 +73,17 @@ struct StageUpdate {
 inline StageUpdate shu_osher(double dt, double a0, double b0) {
   return StageUpdate{dt, a0, b0, b0, nullptr, nullptr, 0.0, 0.0, 0.0};
 }
+
+// Which devices a one-time setting of a kernel (cudaFuncSetAttribute, a per-device
+// property) has been applied on: bit d for device d < 64; larger device numbers
+// apply it on every launch.
+struct PerDevice {
+  std::atomic<unsigned long long> done{0};
+  bool test(int dev) const { return dev >= 0 && dev < 64 && ((done.load() >> dev) & 1ull); }
+  void set(int dev) {
+    if (dev >= 0 && dev < 64) done.fetch_or(1ull << dev);
+  }
+};
 
 // Per-kernel CUDA-event timing (dg_set_timing / dg_kernel_times).
 struct Timing {

@@ -489,8 +489,8 @@ template <int P, int NE, bool X3, bool OUT2>
 int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, float *trace_out, const float *fhat,
            const double *fmean, const StageUpdate &su, int mode, cudaStream_t s) {
   using T = Tc<P, NE, X3>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDevice attr_set;
+  if (!attr_set.test(m->device)) {
     cudaError_t e = cudaFuncSetAttribute(k_element_tc<P, NE, X3, OUT2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          T::SMEM);
     if (e != cudaSuccess) return (int)e;
@@ -498,7 +498,7 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, flo
     // occupancy query and the launch see every CTA that fits
     e = cudaFuncSetAttribute(k_element_tc<P, NE, X3, OUT2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
-    attr_set = true;
+    attr_set.set(m->device);
   }
   // CTAs per SM from the shared memory and registers each needs (the occupancy
   // query under-reports for this kernel), at most 8 (TMEM: 512 columns per SM)
