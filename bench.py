@@ -651,7 +651,9 @@ def run_ours(args, world, rank, local):
 
     line = None
     if rank == 0:
-        launches = sum(n for n, _ in ktimes.values())
+        # each timed library call is one kernel, except dg_conserved_totals: two
+        # kernels (per-block partial sums, then the fixed-order final sum)
+        launches = sum(n for n, _ in ktimes.values()) + ktimes.get("totals", (0, 0.0))[0]
         el_n, el_ms = ktimes.get("element", (0, 0.0))
         avg_el_ms = el_ms / max(1, el_n)
         if prec == "fp64":
