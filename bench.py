@@ -102,7 +102,7 @@ def _src_hash(*names) -> str:
 # change voids the entry.
 TRAFFIC = {
     # k_element_sf<3,4>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
-    "5b9a255c8a6015ef": 77150976 + 42258944,
+    "e64e929d29b32da3": 77161984 + 42322944,
 }
 
 
