@@ -1142,7 +1142,6 @@ int or_flux_jacobian(double g, const double *U, double nx, double ny, double *J)
 /* out = (dR/dC)^T lam, following Algorithms 3, 2 and 1 backwards */
 int or_rhs_vjp(oracle_dg *o, const double *C, const double *lam, double *out)
 {
-    if (o->Nb > 0) return 2;                  /* periodic meshes only */
     int np = o->np, nq = o->nq, ne = o->ne;
     size_t n = (size_t)o->N * OM * np;
     for (size_t t = 0; t < n; ++t) out[t] = 0.0;
@@ -1154,6 +1153,47 @@ int or_rhs_vjp(oracle_dg *o, const double *C, const double *lam, double *out)
 
     /* Algorithm 2 backwards, edge by edge */
     for (int64_t s = 0; s < o->Ns; ++s) {
+        if (o->er[s] < 0) {
+            /* boundary edge: F_hat(U_l, U_g(U_l)); a wall's ghost is the reflection
+             * U_g = Rf U_l, Rf = diag(1, I - 2 n n^T, 1) (symmetric), so the left
+             * trace's cotangent is Jl^T fb + Rf Jr^T fb; a prescribed ghost does not
+             * depend on U_l */
+            int64_t l = o->el[s];
+            const double *cl = C + (size_t)l * OM * np, *bl = lb + (size_t)l * OM * np;
+            double *ol = out + (size_t)l * OM * np;
+            int L = o->eL[s];
+            double len = o->elen[s], nx = o->enx[s], ny = o->eny[s];
+            for (int k = 0; k < ne; ++k) {
+                const double *phiL = o->phif + ((size_t)L * ne + k) * np;
+                double ul[OM], ug[OM], fb[OM];
+                for (int m = 0; m < OM; ++m) {
+                    ul[m] = 0.0;
+                    for (int j = 0; j < np; ++j) ul[m] += cl[m * np + j] * phiL[j];
+                }
+                ghost_state(o, s, k, ul, ug);
+                for (int m = 0; m < OM; ++m) {
+                    double a = 0.0;
+                    for (int j = 0; j < np; ++j) a += -bl[m * np + j] * len * o->ew[k] * phiL[j] / 2.0;
+                    fb[m] = a;
+                }
+                double Jl[OM][OM], Jr[OM][OM], gl[OM], gr[OM];
+                lax_friedrichs_jacobians(o->gamma, ul, ug, nx, ny, Jl, Jr);
+                for (int b = 0; b < OM; ++b) {
+                    gl[b] = 0.0; gr[b] = 0.0;
+                    for (int a = 0; a < OM; ++a) { gl[b] += Jl[a][b] * fb[a]; gr[b] += Jr[a][b] * fb[a]; }
+                }
+                if (o->er[s] == -1) {
+                    double gn = gr[1] * nx + gr[2] * ny;
+                    gl[0] += gr[0];
+                    gl[1] += gr[1] - 2.0 * gn * nx;
+                    gl[2] += gr[2] - 2.0 * gn * ny;
+                    gl[3] += gr[3];
+                }
+                for (int b = 0; b < OM; ++b)
+                    for (int j = 0; j < np; ++j) ol[b * np + j] += gl[b] * phiL[j];
+            }
+            continue;
+        }
         int64_t l = o->el[s], r = o->er[s];
         const double *cl = C + (size_t)l * OM * np, *cr = C + (size_t)r * OM * np;
         const double *bl = lb + (size_t)l * OM * np, *br = lb + (size_t)r * OM * np;
@@ -1223,7 +1263,6 @@ int or_rhs_vjp(oracle_dg *o, const double *C, const double *lam, double *out)
 /* lam_n = (d C_{n+1} / d C_n)^T lam_np1 for one SSP-RK3 step from C_n */
 int or_ssp_rk3_vjp(oracle_dg *o, const double *Cn, double dt, const double *lam_np1, double *lam_n)
 {
-    if (o->Nb > 0) return 2;                  /* periodic meshes only */
     size_t n = (size_t)o->N * OM * o->np;
     double *u1 = malloc(sizeof(double) * n), *u2 = malloc(sizeof(double) * n);
     double *L = malloc(sizeof(double) * n), *b2 = malloc(sizeof(double) * n);

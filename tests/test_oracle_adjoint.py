@@ -68,6 +68,29 @@ def test_rhs_jacobian_transpose(oracle_mod, p):
     assert np.abs(Jfd - Jad).max() < 1e-8 * np.abs(Jfd).max()
 
 
+@pytest.mark.parametrize("p", [1, 2])
+def test_rhs_jacobian_transpose_with_boundaries(oracle_mod, p):
+    """Walls on x = +-5 (the ghost is the reflected interior trace) and prescribed
+    states on y = +-5 (a ghost independent of the solution)."""
+    mesh = I.box_mesh(3, x_code=I.BC_WALL, y_code=I.BC_STATE)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    xy = o.boundary_points()
+    o.set_boundary_state(I.steady_vortex(xy[..., 0], xy[..., 1]))
+    c = _rough(o, mesh, 8)
+    n = c.size
+    eps = 1e-6
+    Jfd = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n); e[i] = eps
+        e = e.reshape(c.shape)
+        Jfd[:, i] = ((o.rhs(c + e) - o.rhs(c - e)) / (2 * eps)).ravel()
+    Jad = np.zeros((n, n))
+    for i in range(n):
+        lam = np.zeros(n); lam[i] = 1.0
+        Jad[i, :] = o.rhs_vjp(c, lam.reshape(c.shape)).ravel()
+    assert np.abs(Jfd - Jad).max() < 1e-8 * np.abs(Jfd).max()
+
+
 def test_rk_step_dot_product(oracle_mod):
     mesh = I.periodic_mesh(6)
     o = oracle_mod.OracleDG.from_mesh(mesh, 2)
