@@ -102,7 +102,7 @@ def _src_hash(*names) -> str:
 # change voids the entry.
 TRAFFIC = {
     # k_element_sf<3,4>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
-    "e64e929d29b32da3": 77161984 + 42322944,
+    "3618e85697765c25": 77377280 + 42241536,
 }
 
 
@@ -344,7 +344,7 @@ def run_sweep(precisions=("fp64",)):
     _build.build()
     dg.load()
     for p, steps in ((1, 10000), (4, 1000)):
-        for n in (10, 20, 40, 80, 160, 304):
+        for n in (10, 20, 40, 80, 152, 160, 304):
             mesh = I.periodic_mesh(n)
             m = dg.Mesh.from_mesh(mesh, p)
             dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
@@ -370,6 +370,18 @@ def run_sweep(precisions=("fp64",)):
                                   "dof_updates_per_s": _dof_per_step(m.N, p, "rk4") * steps / (ms * 1e-3)}),
                       flush=True)
             m.set_limiter(False)
+            if n == 152:
+                # the paper's kernel runtime distribution of an RK4 step (its mesh E,
+                # 46,080 elements): per-kernel CUDA-event times (plain launches, no graph)
+                c = c0.clone()
+                m.set_timing(True)
+                m.rk_step(c, dt, 100, method="rk4")
+                kt = m.kernel_times()
+                m.set_timing(False)
+                tot = sum(ms for _, ms in kt.values())
+                print(json.dumps({"sweep": "kernel time split", "method": "rk4", "p": p, "n_elem": m.N,
+                                  "steps": 100, "ms_per_step": tot / 100,
+                                  "share": {k: round(ms / tot, 4) for k, (_, ms) in kt.items()}}), flush=True)
             del m
     # the kind of run behind the paper's only absolute throughput figures (its
     # double Mach reflection table: p = 1, classic RK2, Barth-Jespersen limiter on

@@ -234,15 +234,18 @@ dg_status dg_rk_step_host(dg_mesh *mesh, double *c_host, double dt, int nsteps,
 
 /* Discrete adjoint of dg_rhs (float64): out = (dR/dc)^T lam, the transpose of the
  * RHS Jacobian at c applied to lam, taken backwards through the edge traces,
- * the Lax-Friedrichs flux (same kink conventions as dg_adjoint_step), the lift,
- * the volume integral and the 1/det J scaling.  All arrays DEVICE [N][4][N_p];
- * out must not alias c or lam.  Asynchronous. */
+ * the Lax-Friedrichs flux (same kink conventions as dg_adjoint_step; on a
+ * boundary face through the ghost state: a wall's ghost is the reflected trace,
+ * a prescribed ghost is constant), the lift, the volume integral and the 1/det J
+ * scaling.  All arrays DEVICE [N][4][N_p]; out must not alias c or lam.
+ * Asynchronous. */
 dg_status dg_rhs_adjoint(dg_mesh *mesh, const double *c, const double *lam, double *out, void *stream);
 
 /* Discrete adjoint of one SSP-RK3 step (float64): given the state c_n at the start
  * of the step and lam_np1 = dJ/dc_{n+1}, writes lam_n = dJ/dc_n = (d c_{n+1}/d c_n)^T
  * lam_np1.  The stages are recomputed from c_n.  At a tie of the two wave speeds in
- * alpha the derivative follows the left trace, and d|x|/dx at x = 0 is taken as 0.
+ * alpha the derivative follows the left trace (at a wall the two always tie), and
+ * d|x|/dx at x = 0 is taken as 0.  Not with the limiter on (DG_ENOTIMPL).
  * All arrays DEVICE [N][4][N_p]; lam_n must not alias the others.  Asynchronous. */
 dg_status dg_adjoint_step(dg_mesh *mesh, const double *c_n, double dt, const double *lam_np1,
                           double *lam_n, void *stream);
@@ -293,8 +296,10 @@ dg_status dg_kernel_times(dg_mesh *mesh, double ms[8], int64_t launches[8]);
 dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stream);
 
 /* Synchronises stream and reports device-side failures recorded since the last
- * call: DG_ETIMEOUT if a bounded wait of the mixed-precision kernels expired
- * (the kernel then skipped its remaining work and released its resources);
+ * call: DG_EMESH if a kernel of a library built with DG_DEBUG read a connectivity
+ * index out of range (it then used index 0 instead; other builds do not check);
+ * DG_ETIMEOUT if a bounded wait of the mixed-precision kernels expired (the
+ * kernel then skipped its remaining work and released its resources);
  * DG_ENONPHYS if a kernel met rho <= 0 or p <= 0 (or NaN) at a volume or edge
  * quadrature point (the results of that call are then meaningless).  The record
  * is cleared.  Synchronous. */

@@ -5,6 +5,11 @@ Each translation unit is compiled in parallel to an object file under
 ``paper_1601_07944_gb300/libdg.so``, and a stamp beside the objects records
 that the library was linked on this machine type.
 A unit is recompiled only when it, or a header, is newer than its object.
+
+``build(debug=True)`` makes ``libdg_debug.so`` (objects under
+``_build/<machine>-debug/``) with ``-DDG_DEBUG``: every kernel then checks each
+connectivity index it reads before using it and reports a bad one through
+``dg_device_status`` (a stand-in for a memory checker).
 """
 from __future__ import annotations
 
@@ -19,6 +24,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build", platform.machine())
 LIB = os.path.join(PKG, "libdg.so")
+LIB_DEBUG = os.path.join(PKG, "libdg_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
@@ -35,19 +41,22 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+    build_dir = BUILD + "-debug" if debug else BUILD
+    lib = LIB_DEBUG if debug else LIB
+    flags = ["-DDG_DEBUG"] if debug else []
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     newest_hdr = max((os.path.getmtime(h) for h in headers), default=0.0)
     jobs, objs = [], []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         if (not force and os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
                 and os.path.getmtime(obj) >= newest_hdr):
             continue
-        cmd = [nvcc] + ARCH + COMMON + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + COMMON + flags + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         jobs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -61,16 +70,16 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if failed:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    stamp = os.path.join(BUILD, "libdg.stamp")
-    if (force or jobs or not os.path.exists(LIB) or not os.path.exists(stamp)
-            or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    stamp = os.path.join(build_dir, "libdg.stamp")
+    if (force or jobs or not os.path.exists(lib) or not os.path.exists(stamp)
+            or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs)):
+        tmp = lib + ".tmp%d" % os.getpid()
         subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
         with open(stamp, "w") as f:
-            f.write(LIB + "\n")
-    return LIB
+            f.write(lib + "\n")
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, debug="--debug" in sys.argv))

@@ -16,7 +16,8 @@
  *                   elements (with the same signs and reversed right-side order
  *                   as the forward gather) and applies the transposed
  *                   Lax-Friedrichs Jacobians, writing one trace cotangent per
- *                   element face point (each slot has exactly one writer).
+ *                   element face point (each slot has exactly one writer); on a
+ *                   boundary face through the ghost state (a wall's reflection).
  *   k_adj_combine   per element: transposed trace interpolation, plus the linear
  *                   combination of the Runge-Kutta adjoint
  *                   out = x0 X + x1 Y + x2 Z + s (dR/du)^T lam.
@@ -150,7 +151,8 @@ k_adj_element(const double *__restrict__ u, const double *__restrict__ lam, doub
 template <int NE>
 __global__ void __launch_bounds__(kThreads)
 k_adj_face(const double *__restrict__ T, const double *__restrict__ G, double *__restrict__ TB,
-           const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg, int64_t F, double gamma) {
+           const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg, const double *__restrict__ bstate,
+           int64_t N, int64_t F, double gamma, int *err) {
   constexpr int NF = 3 * NE;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F * NE) return;
@@ -158,9 +160,31 @@ k_adj_face(const double *__restrict__ T, const double *__restrict__ G, double *_
   const int k = (int)(i - f * NE);
   const FaceConn cn = conn[f];
   const FaceGeo g = fg[f];
-  const size_t ol = ((size_t)cn.l * NF + cn.L * NE + k) * M;
-  const size_t orr = ((size_t)cn.r * NF + cn.R * NE + (NE - 1 - k)) * M;
+  const size_t ol = ((size_t)checked(cn.l, N, err) * NF + checked(cn.L, 3, err) * NE + k) * M;
   double ul[M], ur[M], fb[M], gl[M], gr[M];
+  if (cn.r < 0) {
+    // boundary face: F_hat(U_l, U_g(U_l)).  A wall's ghost is the reflection
+    // U_g = Rf U_l, Rf = diag(1, I - 2 n n^T, 1) (symmetric), so the trace's
+    // cotangent is gl + Rf gr; a prescribed ghost does not depend on U_l.  Only
+    // the left element lifts the flux (with -1).
+#pragma unroll
+    for (int m = 0; m < M; ++m) ul[m] = T[ol + m];
+    ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
+#pragma unroll
+    for (int m = 0; m < M; ++m) fb[m] = -g.hl * G[ol + m];
+    lax_friedrichs_vjp(ul, ur, g.nx, g.ny, gamma, fb, gl, gr);
+    if (cn.r == DG_BC_WALL) {
+      const double gn2 = 2.0 * fma(gr[1], g.nx, gr[2] * g.ny);
+      gl[0] += gr[0];
+      gl[1] += fma(-gn2, g.nx, gr[1]);
+      gl[2] += fma(-gn2, g.ny, gr[2]);
+      gl[3] += gr[3];
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) TB[ol + m] = gl[m];
+    return;
+  }
+  const size_t orr = ((size_t)checked(cn.r, N, err) * NF + checked(cn.R, 3, err) * NE + (NE - 1 - k)) * M;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     ul[m] = T[ol + m];
@@ -243,7 +267,8 @@ int run_adj(const dg_mesh *m, const double *u, const double *lam, double *uvol, 
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   const int64_t nf = m->F * NE;
   k_adj_face<NE><<<(int)((nf + kThreads - 1) / kThreads), kThreads, 0, st>>>(T, G, TB, m->face_conn, m->face_geo,
-                                                                             m->F, m->gamma);
+                                                                             m->bstate, m->N, m->F, m->gamma,
+                                                                             m->err_flag);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   grid = ntiles < m->num_sms * 4 ? ntiles : m->num_sms * 4;
   k_adj_combine<P, NE><<<grid, kThreads, 0, st>>>(uvol, TB, m->tab.BfT, X, Y, Z, x0, x1, x2, s, out, (int)m->N);

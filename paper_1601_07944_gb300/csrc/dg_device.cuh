@@ -145,6 +145,23 @@ __device__ __forceinline__ void ghost_state(int code, const double ul[M], double
 // device error flag bits (read by dg_device_status)
 constexpr int kErrTimeout = 1;      // a bounded tensor-core wait expired
 constexpr int kErrNonPhysical = 2;  // rho <= 0 or p <= 0 met at a quadrature point
+constexpr int kErrIndex = 4;        // (DG_DEBUG builds) a connectivity index was out of range
+
+// An index read from the mesh's connectivity (an element, a face, a local face).
+// DG_DEBUG builds check it against [0, n) before it is used: outside, the flag
+// kErrIndex is set and 0 is returned, so the access stays in bounds (a stand-in
+// for a memory checker).  Other builds return i unchanged.
+__device__ __forceinline__ int64_t checked(int64_t i, int64_t n, int *err) {
+#ifdef DG_DEBUG
+  if (i < 0 || i >= n) {
+    atomicOr(err, kErrIndex);
+    return 0;
+  }
+#else
+  (void)n; (void)err;
+#endif
+  return i;
+}
 
 // out = (d(F(U).n)/dU)^T b for the Euler flux F.n = (rho vn, mx vn + p nx,
 // my vn + p ny, (E+p) vn), using d vn/dU = (-vn, nx, ny, 0)/rho and

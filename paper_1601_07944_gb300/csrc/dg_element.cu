@@ -59,7 +59,7 @@ template <int P, int NE>
 __global__ void __launch_bounds__(kThreads, 2)
 k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
              const double *__restrict__ fhat, const double *__restrict__ geo,
-             const int32_t *__restrict__ elem_face, DevTables tab, int N, StageUpdate su, int mode,
+             const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
              double gamma, int *err) {
   using S = SfCfg<P, NE>;
   constexpr int NP = S::NP, ND = S::ND, NQ = S::NQ, NF = S::NF, EB = S::EB;
@@ -109,7 +109,8 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
       if (el < ecount) {
         const int q = qk / NE, k = qk - q * NE;
         const int ef = elem_face[(size_t)(e0 + el) * 3 + q];
-        const int f = ef >> 1, side = ef & 1;
+        const int64_t f = checked(ef >> 1, F, err);
+        const int side = ef & 1;
         const double *fp = fhat + ((size_t)f * NE + (side ? NE - 1 - k : k)) * M;
 #pragma unroll
         for (int m = 0; m < M; ++m) v[m] = side ? fp[m] : tc::neg_bits(fp[m]);
@@ -324,7 +325,7 @@ int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *
   const int ntiles = (int)((m->N + S::EB - 1) / S::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
   k_element_sf<P, NE><<<grid, kThreads, S::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
-                                                      (int)m->N, su, mode, m->gamma, m->err_flag);
+                                                      (int)m->N, m->F, su, mode, m->gamma, m->err_flag);
   return (int)cudaGetLastError();
 }
 

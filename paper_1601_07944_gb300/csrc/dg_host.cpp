@@ -960,7 +960,6 @@ extern "C" dg_status dg_rhs_adjoint(dg_mesh *m, const double *c, const double *l
   if (!m || !c || !lam || !out) return fail(DG_EINVAL, "dg_rhs_adjoint: null argument");
   if (dg_status dst = check_device(m, "dg_rhs_adjoint")) return dst;
   if (out == c || out == lam) return fail(DG_EINVAL, "dg_rhs_adjoint: out aliases an input");
-  if (m->Fb > 0) return fail(DG_ENOTIMPL, "dg_rhs_adjoint: meshes with boundary faces have no adjoint here");
   dg_status st = adjoint_buffers(m, "dg_rhs_adjoint");
   if (st != DG_OK) return st;
   const size_t S = (size_t)m->N * M * m->np, TR = (size_t)m->N * 3 * m->ne * M;
@@ -980,7 +979,6 @@ extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, c
   if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
   if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
   if (m->limiter) return fail(DG_ENOTIMPL, "dg_adjoint_step: the limited step has no adjoint here (the limiter is off by default)");
-  if (m->Fb > 0) return fail(DG_ENOTIMPL, "dg_adjoint_step: meshes with boundary faces have no adjoint here");
   dg_status ast = adjoint_buffers(m, "dg_adjoint_step");
   if (ast != DG_OK) return ast;
   const size_t S = (size_t)m->N * M * m->np;           // one state
@@ -1089,6 +1087,8 @@ extern "C" dg_status dg_device_status(dg_mesh *m, void *stream) {
   if (flag) {
     DG_CUDA(cudaMemsetAsync(m->err_flag, 0, sizeof(int), s), "dg_device_status reset");
     DG_CUDA(cudaStreamSynchronize(s), "dg_device_status sync");
+    if (flag & 4)
+      return fail(DG_EMESH, "a kernel read a connectivity index out of range (checked in DG_DEBUG builds)");
     if (flag & 1)
       return fail(DG_ETIMEOUT, "a tensor-core wait in the mixed-precision kernel expired%s",
                   (flag & 2) ? "; a non-physical state was also met" : "");

@@ -76,7 +76,8 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
 template <int NE>
 __global__ void __launch_bounds__(kThreads)
 k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
-       const FaceGeo *__restrict__ fg, const double *__restrict__ bstate, int64_t F, double gamma, int *err) {
+       const FaceGeo *__restrict__ fg, const double *__restrict__ bstate, int64_t N, int64_t F, double gamma,
+       int *err) {
   constexpr int NF = 3 * NE;
   bool ok = true;
   // The grid is what fits on the GPU at once; block b takes the b-th of gridDim.x
@@ -89,7 +90,7 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
     const int k = (int)(i - f * NE);
     const FaceConn cn = conn[f];
     const FaceGeo g = fg[f];
-    const double *pl = trace + ((size_t)cn.l * NF + cn.L * NE + k) * M;
+    const double *pl = trace + ((size_t)checked(cn.l, N, err) * NF + checked(cn.L, 3, err) * NE + k) * M;
     double ul[M], ur[M], Fh[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) ul[m] = pl[m];
@@ -97,7 +98,8 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
       // boundary face (the first faces of the list): the ghost state at the same point
       ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
     } else {
-      const double *pr = trace + ((size_t)cn.r * NF + cn.R * NE + (NE - 1 - k)) * M;
+      const double *pr =
+          trace + ((size_t)checked(cn.r, N, err) * NF + checked(cn.R, 3, err) * NE + (NE - 1 - k)) * M;
 #pragma unroll
       for (int m = 0; m < M; ++m) ur[m] = pr[m];
     }
@@ -323,7 +325,7 @@ __device__ __forceinline__ unsigned long long nonneg_bits(double x) {
 
 __global__ void __launch_bounds__(kThreads)
 k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ elem_nbr,
-           const double *__restrict__ BfT, const double *__restrict__ EChi, double phi1, int64_t N) {
+           const double *__restrict__ BfT, const double *__restrict__ EChi, double phi1, int64_t N, int *err) {
   constexpr int P = 1, NE = 2, NP = 3, NF = 6;
   __shared__ double sF0[NP * NE], sChi[NP * NE];
   if (threadIdx.x < NP * NE) {
@@ -332,7 +334,8 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
   }
   __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t nb0 = elem_nbr[e * 3], nb1 = elem_nbr[e * 3 + 1], nb2 = elem_nbr[e * 3 + 2];
+    const int64_t nb0 = checked(elem_nbr[e * 3], N, err), nb1 = checked(elem_nbr[e * 3 + 1], N, err),
+                  nb2 = checked(elem_nbr[e * 3 + 2], N, err);
     double cn[3][M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -435,7 +438,8 @@ int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream) {
   if (m->p != 1 || m->ne != 2) return (int)cudaErrorInvalidValue;
   static int per_sm = 0;
   k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N, &per_sm), kThreads, 0,
-               (cudaStream_t)stream>>>(c, trace, m->elem_nbr, m->tab.BfT, m->tab.EChi, m->phi1, m->N);
+               (cudaStream_t)stream>>>(c, trace, m->elem_nbr, m->tab.BfT, m->tab.EChi, m->phi1, m->N,
+                                       m->err_flag);
   return (int)cudaGetLastError();
 }
 
@@ -446,7 +450,7 @@ int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *
   do {                                                                                                  \
     static int per_sm = 0;                                                                              \
     k_face<NE><<<resident_grid(m, (const void *)k_face<NE>, kThreads, n, &per_sm), kThreads, 0, s>>>(   \
-        trace, fhat, m->face_conn, m->face_geo, m->bstate, m->F, m->gamma, m->err_flag);                \
+        trace, fhat, m->face_conn, m->face_geo, m->bstate, m->N, m->F, m->gamma, m->err_flag);          \
   } while (0)
   switch (m->ne) {
     case 2: FACE(2); break;

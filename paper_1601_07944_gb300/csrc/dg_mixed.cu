@@ -132,7 +132,7 @@ template <int P, int NE, bool X3, bool OUT2>
 __global__ void __launch_bounds__(kTcThreads)
 k_element_tc(const double *c, const double *u0, double *out, float *__restrict__ trace_out,
              const float *__restrict__ fhat, const double *__restrict__ fmean, const double *__restrict__ geo,
-             const int32_t *__restrict__ elem_face, DevTables tab, int N, StageUpdate su, int mode,
+             const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
              double gamma, int *err) {
   using T = Tc<P, NE, X3>;
   constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB;
@@ -252,7 +252,8 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     const bool lv = t < ntiles && rel < N - t * EB && mode != 2;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const int f = r.ef[q] >> 1, side = r.ef[q] & 1;
+      const int64_t f = checked(r.ef[q] >> 1, F, err);      // ef = 0 on rows past the mesh
+      const int side = r.ef[q] & 1;
       r.s[q] = lv ? fmean[(size_t)f * M + rm] : 0.0;
 #pragma unroll
       for (int k = 0; k < NE; ++k)
@@ -442,7 +443,8 @@ template <int NE, bool BND>
 __global__ void __launch_bounds__(256)
 k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *__restrict__ fmean,
              const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg, const double *__restrict__ Lf,
-             const double *__restrict__ bstate, int np, int64_t f0, int64_t f1, double gamma, int *err) {
+             const double *__restrict__ bstate, int np, int64_t N, int64_t f0, int64_t f1, double gamma,
+             int *err) {
   constexpr int NF = 3 * NE;
   bool ok = true;
   // the grid is what is resident at once; block b takes the b-th of gridDim.x
@@ -454,8 +456,10 @@ k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *
     const FaceGeo g = fg[f];
     // [N][NF][M] float32: one point's four values are one aligned float4
     constexpr bool bnd = BND;
-    const float4 *tl = reinterpret_cast<const float4 *>(trace) + (size_t)cn.l * NF + cn.L * NE;
-    const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)(bnd ? cn.l : cn.r) * NF + (bnd ? 0 : cn.R * NE);
+    const int64_t el = checked(cn.l, N, err);
+    const float4 *tl = reinterpret_cast<const float4 *>(trace) + (size_t)el * NF + checked(cn.L, 3, err) * NE;
+    const float4 *tr = reinterpret_cast<const float4 *>(trace) + (size_t)(bnd ? el : checked(cn.r, N, err)) * NF +
+                       (bnd ? 0 : checked(cn.R, 3, err) * NE);
     float4 *dst = reinterpret_cast<float4 *>(fhat) + (size_t)f * NE;
     double sm[M] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -526,7 +530,7 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, flo
   const int ntiles = (int)((m->N + T::EB - 1) / T::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
   k_element_tc<P, NE, X3, OUT2><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face,
-                                                            m->tab, (int)m->N, su, mode, m->gamma,
+                                                            m->tab, (int)m->N, m->F, su, mode, m->gamma,
                                                             m->err_flag);
   return (int)cudaGetLastError();
 }
@@ -606,12 +610,12 @@ int launch_face_flux_mixed(const dg_mesh *m, const MixedBuffers &b, void *stream
     static int per_sm = 0, per_sm_b = 0;                                                                  \
     k_face_mixed<NE, false><<<resident_grid(m, (const void *)k_face_mixed<NE, false>, 256, m->F - m->Fb,   \
                                             &per_sm), 256, 0, s>>>(                                       \
-        b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->bstate, m->np, m->Fb, m->F,    \
+        b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->bstate, m->np, m->N, m->Fb, m->F, \
         m->gamma, m->err_flag);                                                                           \
     if (m->Fb > 0)                                                                                        \
       k_face_mixed<NE, true><<<resident_grid(m, (const void *)k_face_mixed<NE, true>, 256, m->Fb,         \
                                              &per_sm_b), 256, 0, s>>>(                                    \
-          b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->bstate, m->np, 0, m->Fb,     \
+          b.trace, b.fhat, b.fmean, m->face_conn, m->face_geo, m->tab.Lf, m->bstate, m->np, m->N, 0, m->Fb, \
           m->gamma, m->err_flag);                                                                         \
   } while (0)
   switch (m->ne) {

@@ -53,11 +53,15 @@ class _Info(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Loads libdg.so (raises if it has not been built)."""
+def load(path: str = None):
+    """Loads libdg.so (raises if it has not been built).  The environment variable
+    DG_LIB names another build of the library to load instead (for example the
+    index-checking libdg_debug.so of ``_build.build(debug=True)``)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("DG_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError("libdg.so not found at %s: run __graft_entry__.build() (or "
                            "python -m paper_1601_07944_gb300._build) first" % path)
