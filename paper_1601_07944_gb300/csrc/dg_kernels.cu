@@ -300,8 +300,9 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 }
 
 // ---------------------------------------------------------------------------
-// Barth-Jespersen limiter for p = 1 (Section 4.3.5), one thread per element, in
-// place on c; the traces of the limited state go to trace (when not null).
+// Barth-Jespersen limiter for p = 1 (Section 4.3.5), one thread per element and
+// variable, in place on c; the traces of the limited state go to trace (when not
+// null).
 // Per variable: Ubar = phi_1 c_1 is the centroid value (the linear modes vanish at
 // the centroid), U^max / U^min the extremes of the centroid values of the element
 // and its three neighbours; at each edge integration point, with
@@ -333,60 +334,55 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
     sChi[threadIdx.x] = EChi[threadIdx.x];
   }
   __syncthreads();
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+  // one item per (element, variable): four independent chains per element, and
+  // a warp's loads and trace stores cover contiguous runs
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < N * M;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = it >> 2;
+    const int m = (int)(it & 3);
     const int64_t nb0 = checked(elem_nbr[e * 3], N, err), nb1 = checked(elem_nbr[e * 3 + 1], N, err),
                   nb2 = checked(elem_nbr[e * 3 + 2], N, err);
-    double cn[3][M];
+    double *ce = c + (e * M + m) * NP;
+    double cj[NP] = {ce[0], ce[1], ce[2]};
+    const double cn[3] = {c[(nb0 * M + m) * NP], c[(nb1 * M + m) * NP], c[(nb2 * M + m) * NP]};
+    // extremes of the constant modes (phi_1 > 0 keeps the order)
+    double cmax = cj[0], cmin = cj[0];
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      cn[0][m] = c[(nb0 * M + m) * NP];
-      cn[1][m] = c[(nb1 * M + m) * NP];
-      cn[2][m] = c[(nb2 * M + m) * NP];
+    for (int q = 0; q < 3; ++q) {
+      if (order_key(cn[q]) > order_key(cmax)) cmax = cn[q];
+      if (order_key(cn[q]) < order_key(cmin)) cmin = cn[q];
     }
+    const double ub = phi1 * cj[0];
+    // U^max - Ubar and Ubar - U^min, formed so that they are exactly >= 0 (an
+    // FMA-contracted phi1 cmax - ub would leave the product's rounding error,
+    // of either sign, where the difference is 0; the comparisons below read
+    // these as non-negative bit patterns)
+    const double up = phi1 * (cmax - cj[0]), dn = phi1 * (cj[0] - cmin);
+    double t[NF];
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      double *ce = c + (e * M + m) * NP;
-      double cj[NP] = {ce[0], ce[1], ce[2]};
-      // extremes of the constant modes (phi_1 > 0 keeps the order)
-      double cmax = cj[0], cmin = cj[0];
+    for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
+    double nbest = 1.0, dbest = 1.0;                                  // ratio 1: no limiting
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const double v = cn[q][m];
-        if (order_key(v) > order_key(cmax)) cmax = v;
-        if (order_key(v) < order_key(cmin)) cmin = v;
-      }
-      const double ub = phi1 * cj[0];
-      // U^max - Ubar and Ubar - U^min, formed so that they are exactly >= 0 (an
-      // FMA-contracted phi1 cmax - ub would leave the product's rounding error,
-      // of either sign, where the difference is 0; the comparisons below read
-      // these as non-negative bit patterns)
-      const double up = phi1 * (cmax - cj[0]), dn = phi1 * (cj[0] - cmin);
-      double t[NF];
+    for (int x = 0; x < NF; ++x) {
+      const unsigned long long db = (unsigned long long)__double_as_longlong(t[x] - ub);
+      const unsigned long long mag = db & 0x7FFFFFFFFFFFFFFFull;       // |d|
+      const double num = (db >> 63) ? dn : up;
+      const double den = __longlong_as_double((long long)mag);
+      if (mag != 0ull && nonneg_bits(num * dbest) < nonneg_bits(nbest * den)) { nbest = num; dbest = den; }
+    }
+    if (nonneg_bits(nbest) < nonneg_bits(dbest)) {
+      const double alpha = nbest / dbest;
+      cj[1] *= alpha;
+      cj[2] *= alpha;
+      ce[1] = cj[1];
+      ce[2] = cj[2];
 #pragma unroll
       for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
-      double nbest = 1.0, dbest = 1.0;                                  // ratio 1: no limiting
+    }
+    if (trace) {
+      double *dst = trace + (size_t)e * NF * M + m;
 #pragma unroll
-      for (int x = 0; x < NF; ++x) {
-        const unsigned long long db = (unsigned long long)__double_as_longlong(t[x] - ub);
-        const unsigned long long mag = db & 0x7FFFFFFFFFFFFFFFull;       // |d|
-        const double num = (db >> 63) ? dn : up;
-        const double den = __longlong_as_double((long long)mag);
-        if (mag != 0ull && nonneg_bits(num * dbest) < nonneg_bits(nbest * den)) { nbest = num; dbest = den; }
-      }
-      if (nonneg_bits(nbest) < nonneg_bits(dbest)) {
-        const double alpha = nbest / dbest;
-        cj[1] *= alpha;
-        cj[2] *= alpha;
-        ce[1] = cj[1];
-        ce[2] = cj[2];
-#pragma unroll
-        for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
-      }
-      if (trace) {
-        double *dst = trace + (size_t)e * NF * M + m;
-#pragma unroll
-        for (int x = 0; x < NF; ++x) dst[x * M] = t[x];
-      }
+      for (int x = 0; x < NF; ++x) dst[x * M] = t[x];
     }
   }
 }
@@ -437,7 +433,7 @@ int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, 
 int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream) {
   if (m->p != 1 || m->ne != 2) return (int)cudaErrorInvalidValue;
   static int per_sm = 0;
-  k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N, &per_sm), kThreads, 0,
+  k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N * M, &per_sm), kThreads, 0,
                (cudaStream_t)stream>>>(c, trace, m->elem_nbr, m->tab.BfT, m->tab.EChi, m->phi1, m->N,
                                        m->err_flag);
   return (int)cudaGetLastError();
