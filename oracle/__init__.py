@@ -55,6 +55,7 @@ def _load():
             "or_destroy": (None, [P]),
             "or_info": (I, [P, P]),
             "or_volume_rule": (I, [P, P, P, P]),
+            "or_set_volume_rule": (I, [P, I, P, P, P]),
             "or_volume_tables": (I, [P, P, P, P]),
             "or_edge_rule": (I, [P, P, P]),
             "or_edges": (I, [P, P, P, P, P, P, P, P]),
@@ -189,7 +190,10 @@ class OracleDG:
     """FP64 CPU DG solver on one mesh (coefficients c[N, M, Np])."""
 
     def __init__(self, elem_xy, nbr, nbr_face, p: int, n_edge_pts: int = 0, n_vol_dir: int = 0,
-                 gamma: float = 1.4):
+                 gamma: float = 1.4, vol_rule: str = "collapsed"):
+        """vol_rule: "collapsed" (the (p+1)^2-point collapsed Gauss grid, or
+        n_vol_dir^2 points) or "symmetric" (the fully symmetric degree-2p rule
+        of oracle/symmetric_rules.py)."""
         lib = _load()
         self._xy = np.ascontiguousarray(elem_xy, dtype=np.float64)
         self._nbr = np.ascontiguousarray(nbr, dtype=np.int64)
@@ -200,6 +204,13 @@ class OracleDG:
         if not h:
             raise ValueError("oracle rejected the mesh or the order")
         self._h = h
+        if vol_rule == "symmetric":
+            from .symmetric_rules import symmetric_rule
+            r, s, w = (np.ascontiguousarray(v) for v in symmetric_rule(p))
+            _chk(lib.or_set_volume_rule(h, r.size, _ptr(r), _ptr(s), _ptr(w)))
+        elif vol_rule != "collapsed":
+            raise ValueError("vol_rule must be 'collapsed' or 'symmetric'")
+        self.vol_rule = vol_rule
         info = np.zeros(5, dtype=np.int64)
         lib.or_info(h, _ptr(info))
         self.N, self.np, self.nq, self.ne, self.n_edges = (int(v) for v in info)

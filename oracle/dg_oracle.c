@@ -609,6 +609,35 @@ int or_volume_rule(const oracle_dg *o, double *r, double *s, double *w)
     return 0;
 }
 
+/* Replaces the volume rule by nq points (r, s) with weights w, and the volume
+ * tables by the basis evaluated at those points: the symmetric rules of degree
+ * 2p of Section 4.1 in place of the collapsed grid.  Every volume sum of the
+ * solver runs over whatever rule is installed.  Returns 0, or 1 on invalid input. */
+int or_set_volume_rule(oracle_dg *o, int nq, const double *r, const double *s, const double *w)
+{
+    if (nq < 1 || nq > 4096) return 1;
+    int np = o->np;
+    double *vr = xcalloc(nq, sizeof(double)), *vs = xcalloc(nq, sizeof(double)), *vw = xcalloc(nq, sizeof(double));
+    double *phi = xcalloc((size_t)nq * np, sizeof(double));
+    double *phir = xcalloc((size_t)nq * np, sizeof(double));
+    double *phis = xcalloc((size_t)nq * np, sizeof(double));
+    long double *rl = xcalloc(nq, sizeof(long double)), *sl = xcalloc(nq, sizeof(long double));
+    if (!vr || !vs || !vw || !phi || !phir || !phis || !rl || !sl) {
+        free(vr); free(vs); free(vw); free(phi); free(phir); free(phis); free(rl); free(sl);
+        return 1;
+    }
+    for (int k = 0; k < nq; ++k) {
+        vr[k] = r[k]; vs[k] = s[k]; vw[k] = w[k];
+        rl[k] = r[k]; sl[k] = s[k];
+    }
+    dubiner_eval_l(o->p, nq, rl, sl, phi, phir, phis);
+    free(rl); free(sl);
+    free(o->vr); free(o->vs); free(o->vw); free(o->phi); free(o->phir); free(o->phis);
+    o->vr = vr; o->vs = vs; o->vw = vw; o->phi = phi; o->phir = phir; o->phis = phis;
+    o->nq = nq;
+    return 0;
+}
+
 /* the volume tables phi, dphi/dr, dphi/ds at the volume points, [nq][np] each */
 int or_volume_tables(const oracle_dg *o, double *phi, double *dr, double *ds)
 {
