@@ -68,6 +68,16 @@ def flops_element_per_elem(p: int, ne: int) -> float:
             + (2 * ND * ne + 2 * ne) * 4 + 2 * (1 + ne) * NP * 4 + 5 * NP * 4 + ne * (4 * NP + 2 * p) * 4)
 
 
+def flops_element_direct_per_elem(p: int, ne: int, nq: int) -> float:
+    """The same for the direct form on a rule of nq points (the symmetric
+    rules): U = Phi c 2 nq N_p 4, per point 38 (the flux without H_alpha),
+    V = Dr G_r + Ds G_s 4 nq N_p 4, the lift, update and traces as above."""
+    NP = (p + 1) * (p + 2) // 2
+    ND = p + 1
+    return (2 * nq * NP * 4 + 38 * nq + 4 * nq * NP * 4
+            + (2 * ND * ne + 2 * ne) * 4 + 2 * (1 + ne) * NP * 4 + 5 * NP * 4 + ne * (4 * NP + 2 * p) * 4)
+
+
 def bytes_element_tc_per_elem(p: int, ne: int) -> float:
     """Algorithmic HBM bytes of one mixed-precision element-kernel launch per
     element, averaged over the three stages: stage input 8*4*N_p, u^n in two of
@@ -98,11 +108,13 @@ def _src_hash(*names) -> str:
 
 # DRAM bytes per launch of the element kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum) from one ncu capture, keyed by the hash of the kernel's
-# source files (dg_element.cu and the device headers) it was taken on; a source
-# change voids the entry.
+# source files (dg_element.cu and the device headers) it was taken on, and the
+# volume rule when it is not the collapsed grid; a source change voids the entry.
 TRAFFIC = {
-    # k_element_sf<3,4>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
-    "3618e85697765c25": 77377280 + 42241536,
+    # k_element_sf<3,4,0>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
+    "7330af2e39508d0f": 77150208 + 42102528,
+    # k_element_sf<3,4,12>: the same launch on the symmetric volume rule (--vol-rule symmetric)
+    "7330af2e39508d0f:symmetric": 77159168 + 42025728,
 }
 
 
@@ -253,7 +265,7 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds: float = 12.0):
+def cpu_baseline(seconds: float = 12.0, vol_rule: str = "collapsed"):
     """The oracle on the full workload mesh for as many whole steps as fit in about
     `seconds` (at least one), single-threaded."""
     import oracle
@@ -261,7 +273,7 @@ def cpu_baseline(seconds: float = 12.0):
     oracle.build()
     mesh = I.periodic_mesh(WORKLOAD["n"])
     p = WORKLOAD["p"]
-    o = oracle.OracleDG.from_mesh(mesh, p, n_edge_pts=WORKLOAD["ne"])
+    o = oracle.OracleDG.from_mesh(mesh, p, n_edge_pts=WORKLOAD["ne"], vol_rule=vol_rule)
     c = o.project_ic(I.vortex)
     dt = I.fixed_dt(mesh, I.vortex, p, WORKLOAD["cfl"])
     steps, el = 0, 0.0
@@ -272,8 +284,8 @@ def cpu_baseline(seconds: float = 12.0):
         steps += 1
     return {"value": _dof_per_step(mesh.n_elem, p) * steps / el, "unit": UNIT, "cores": 1,
             "kind": "oracle",
-            "sample": "%d full SSP-RK3 step(s) of the 256x256 p=3 workload on 1 host thread "
-                      "(%.1f s)" % (steps, el)}
+            "sample": "%d full SSP-RK3 step(s) of the 256x256 p=3 workload (%s volume rule) on 1 host "
+                      "thread (%.1f s)" % (steps, vol_rule, el)}
 
 
 def mixed_modes(m, c0, dt, steps, flush, fp64_ms_per_step):
@@ -466,6 +478,57 @@ def adjoint_ratio(steps: int = 20, every: int = 10):
             "rk_step_ms": fwd / steps, "adjoint_step_ms": adj / steps}
 
 
+def run_rules(n: int = 256, steps: int = 100):
+    """The two volume rules side by side (the collapsed (p+1)^2 grid and the
+    symmetric degree-2p rule with the paper's point counts, Sections 4.3.2, 6.1): the
+    perturbed vortex on the n x n mesh, p = 1..5, SSP-RK3, every precision,
+    device-timed whole runs (CUDA graphs), plus the element kernel's time per
+    launch from per-kernel events over 5 plain steps and the state difference
+    between the rules after the run (float64)."""
+    import torch
+    from paper_1601_07944_gb300 import _build, dg, inputs as I
+    _build.build()
+    dg.load()
+    mesh = I.periodic_mesh(n)
+    for p in (1, 2, 3, 4, 5):
+        dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+        finals = {}
+        for rule in ("collapsed", "symmetric"):
+            m = dg.Mesh.from_mesh(mesh, p, vol_rule=rule)
+            c0 = m.project_function(I.perturbed_vortex)
+            for prec in ("fp64", "tf32x3", "tf32x1"):
+                c = c0.clone()
+                m.rk_step(c, dt, 17, precision=prec)                   # capture + warm the graph
+                c = c0.clone()
+                a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(); a.record()
+                m.rk_step(c, dt, steps, precision=prec)
+                b.record(); torch.cuda.synchronize()
+                m.device_status()
+                ms = a.elapsed_time(b)
+                if prec == "fp64":
+                    finals[rule] = c
+                w = c0.clone()
+                m.set_timing(True)
+                m.rk_step(w, dt, 5, precision=prec)
+                kt = m.kernel_times()
+                m.set_timing(False)
+                el_n, el_ms = kt.get("element", (0, 0.0))
+                line = {"rules": "volume rule", "p": p, "n_elem": m.N, "vol_rule": rule, "n_vol_pts": m.nq,
+                        "precision": prec, "steps": steps, "ms_per_step": ms / steps,
+                        "dof_updates_per_s": _dof_per_step(m.N, p) * steps / (ms * 1e-3),
+                        "element_ms_per_launch": el_ms / max(1, el_n)}
+                if prec == "fp64":
+                    fl = (flops_element_direct_per_elem(p, m.ne, m.nq) if rule == "symmetric"
+                          else flops_element_per_elem(p, m.ne)) * m.N
+                    line["element_fp64_tflops"] = fl / (line["element_ms_per_launch"] * 1e-3) / 1e12
+                print(json.dumps(line), flush=True)
+            del m
+        d = float(torch.linalg.norm(finals["symmetric"] - finals["collapsed"]) / torch.linalg.norm(finals["collapsed"]))
+        print(json.dumps({"rules": "state difference", "p": p, "steps": steps,
+                          "rel_l2_symmetric_vs_collapsed_fp64": d}), flush=True)
+
+
 def run_configs():
     """Every workload of the five configurations as stated, one JSON line each
     (device-timed full runs; parity with the oracle is the tests' job)."""
@@ -599,7 +662,7 @@ def run_ours(args, world, rank, local):
     p, ne = WORKLOAD["p"], WORKLOAD["ne"]
     method = args.method
     mesh = I.periodic_mesh(WORKLOAD["n"])
-    m = dg.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    m = dg.Mesh.from_mesh(mesh, p, n_edge_pts=ne, vol_rule=args.vol_rule)
     ne = m.ne
     c = m.project_function(I.vortex)
     dt = I.fixed_dt(mesh, I.vortex, p, WORKLOAD["cfl"])
@@ -669,9 +732,14 @@ def run_ours(args, world, rank, local):
         el_n, el_ms = ktimes.get("element", (0, 0.0))
         avg_el_ms = el_ms / max(1, el_n)
         if prec == "fp64":
-            flops = flops_element_per_elem(p, ne) * m.N
+            if args.vol_rule == "symmetric":
+                flops = flops_element_direct_per_elem(p, ne, m.nq) * m.N
+            else:
+                flops = flops_element_per_elem(p, ne) * m.N
             achieved = flops / (avg_el_ms * 1e-3) / 1e12
             khash = _src_hash("dg_element.cu", "dg_device.cuh", "dg_tcgen05.cuh")
+            if args.vol_rule != "collapsed":
+                khash += ":" + args.vol_rule
             roofline = {"bound": "alu", "kernel": "k_element_sf (float64 FMA pipe)",
                         "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                         "frac": achieved / fp64_peak if fp64_peak else None, "traffic": TRAFFIC.get(khash),
@@ -696,7 +764,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD["name"] if method == "ssp_rk3"
                        else WORKLOAD["name"].replace("SSP-RK3", method.upper()),
                        "n_elem": m.N, "p": p, "n_edge_pts": ne, "method": method,
-                       "n_vol_pts": m.nq, "precision": prec, "dt": dt,
+                       "n_vol_pts": m.nq, "vol_rule": args.vol_rule, "precision": prec, "dt": dt,
                        "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
@@ -721,7 +789,7 @@ def run_ours(args, world, rank, local):
             line["adjoint"] = adjoint_ratio()
             line["vortex_200_steps"] = vortex_error()
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(vol_rule=args.vol_rule)
     if world > 1:
         import torch.distributed as tdist
         tdist.barrier()
@@ -745,6 +813,10 @@ def main():
                     help="skip the mixed-precision and adjoint measurements")
     ap.add_argument("--method", choices=sorted(STAGES), default="ssp_rk3",
                     help="time integrator of the timed steps (the headline line is ssp_rk3)")
+    ap.add_argument("--vol-rule", choices=["collapsed", "symmetric"], default="collapsed",
+                    help="volume rule of the timed workload (the headline line uses the collapsed grid)")
+    ap.add_argument("--rules", action="store_true",
+                    help="both volume rules at p=1..5 in every precision instead of the benchmark")
     ap.add_argument("--sweep", action="store_true",
                     help="mesh-size scaling runs (p=1 x 10000 and p=4 x 1000 RK4 steps) instead of the benchmark")
     args = ap.parse_args()
@@ -758,6 +830,10 @@ def main():
     if args.sweep:
         if rank == 0:
             run_sweep((args.precision,))
+        return
+    if args.rules:
+        if rank == 0:
+            run_rules()
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

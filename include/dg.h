@@ -87,6 +87,18 @@ enum {
                            Dirichlet data), given with dg_set_boundary_state */
 };
 
+/* Volume quadrature (Section 4.3.2: the volume integrals of Eq. volume are
+ * evaluated with a rule exact for polynomials of degree 2p). */
+typedef enum {
+    DG_RULE_COLLAPSED = 0,  /* (p+1)^2-point collapsed Gauss grid (Gauss-Legendre x
+                               Gauss-Jacobi(1,0)), exact to degree 2p+1; the float64
+                               element kernel sum-factorises on it */
+    DG_RULE_SYMMETRIC = 1   /* fully symmetric rule of degree 2p with the paper's point
+                               counts, 3 / 6 / 12 / 16 / 25 points at p = 1..5 (positive
+                               weights, interior points), derived at mesh creation from
+                               its moment conditions; contracted directly */
+} dg_vol_rule;
+
 /* Host description of a mesh; dg_mesh_create copies everything it needs. */
 typedef struct {
     int64_t n_elem;             /* N >= 1 */
@@ -103,6 +115,7 @@ typedef struct {
     int n_edge_pts;             /* Gauss-Legendre points per edge; 0 = p+1 (the paper's rule).
                                    Supported: p+1, and p for p = 3 */
     double gamma;               /* ratio of specific heats (1.4 for air) */
+    int vol_rule;               /* dg_vol_rule; 0 (DG_RULE_COLLAPSED) for a zeroed struct */
 } dg_mesh_desc;
 
 typedef struct {
@@ -327,6 +340,16 @@ const char *dg_last_error(void);
 dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s, double *vol_w,
                          double *edge_x, double *edge_w, double *phi, double *dphi_r,
                          double *dphi_s, double *phi_face);
+
+/* Host-only (needs no GPU): the volume rule of kind `rule` (dg_vol_rule) for
+ * degree p, as dg_mesh_create builds it.  *nq receives the point count (may be
+ * read first with r = s = w = NULL); r, s, w [*nq] receive the reference points
+ * and weights (sum 1/2), and phi [*nq][N_p] the basis at the points (any of them
+ * may be NULL).  Symmetric rule point order: the orbits S3, S21, S111 in the
+ * library's order, an S21 orbit with parameter a as (a, a), (a, 1-2a), (1-2a, a),
+ * an S111 orbit (a, b), c = 1-a-b, as (a, b), (b, a), (a, c), (c, a), (b, c), (c, b).
+ * Errors: DG_EINVAL (p outside 1..5, unknown rule, nq null). */
+dg_status dg_volume_rule(int p, int rule, int *nq, double *r, double *s, double *w, double *phi);
 
 #ifdef __cplusplus
 }

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (part of the oracle): the tests, ``smoke()`` and the
 benchmark's CPU-baseline leg are the only callers.
 
 The paper evaluates its volume integrals with symmetric rules of degree 2p
-(Section 4.1; 3 points at p = 1 and 16 at p = 4 in Section 7.1) and does not
+(Section 4.3.2; 3 points at p = 1 and 16 at p = 4 in Section 6.1) and does not
 print them.  This module derives rules of that kind from their defining
 conditions.  A rule invariant under the six symmetries of the triangle
 T = {(0,0), (1,0), (0,1)} is a union of orbits in barycentric coordinates

@@ -47,7 +47,8 @@ def build(verbose: bool = False, force: bool = False, debug: bool = False) -> st
     flags = ["-DDG_DEBUG"] if debug else []
     os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+               + glob.glob(os.path.join(ROOT, "include", "*.h")))
     newest_hdr = max((os.path.getmtime(h) for h in headers), default=0.0)
     jobs, objs = [], []
     for src in sources():

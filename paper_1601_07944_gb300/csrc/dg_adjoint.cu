@@ -32,19 +32,19 @@
 namespace dg {
 namespace {
 
-template <int P, int NE>
+template <int P, int NE, int Q>
 struct AdjCfg {
-  using C = Cfg<P, NE>;
+  using C = Cfg<P, NE, Q>;
   static constexpr int TILE = C::EB * (2 * M * C::NP + C::NQ * M);
   static constexpr int SMEM = (C::TAB + TILE) * 8;
 };
 
-template <int P, int NE>
+template <int P, int NE, int Q>
 __global__ void __launch_bounds__(kThreads)
 k_adj_element(const double *__restrict__ u, const double *__restrict__ lam, double *__restrict__ uvol,
               double *__restrict__ G, double *__restrict__ T, const double *__restrict__ geo,
               DevTables tab, int N, double gamma) {
-  using C = Cfg<P, NE>;
+  using C = Cfg<P, NE, Q>;
   constexpr int NP = C::NP, NQ = C::NQ, NF = C::NF, EB = C::EB;
   extern __shared__ double smem[];
   double *sBvT = smem;                 // [NP][NQ]
@@ -241,29 +241,29 @@ k_adj_combine(const double *__restrict__ uvol, const double *__restrict__ TB, co
   }
 }
 
-template <int P, int NE>
+template <int P, int NE, int Q>
 int run_adj(const dg_mesh *m, const double *u, const double *lam, double *uvol, double *G, double *T,
             double *TB, const double *X, const double *Y, const double *Z, double x0, double x1, double x2,
             double s, double *out, cudaStream_t st) {
-  using A = AdjCfg<P, NE>;
-  using C = Cfg<P, NE>;
+  using A = AdjCfg<P, NE, Q>;
+  using C = Cfg<P, NE, Q>;
   static PerDevice attr_set;
   if (!attr_set.test(m->device)) {
-    cudaError_t e = cudaFuncSetAttribute(k_adj_element<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, A::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_element<P, NE, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, A::SMEM);
     if (e != cudaSuccess) return (int)e;
     // all of the SM's unified L1/shared storage as shared memory, so that the
     // occupancy query and the launch see every CTA that fits
-    e = cudaFuncSetAttribute(k_adj_element<P, NE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(k_adj_element<P, NE, Q>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
     attr_set.set(m->device);
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_element<P, NE>, kThreads, A::SMEM);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_element<P, NE, Q>, kThreads, A::SMEM);
   if (e != cudaSuccess) return (int)e;
   if (per_sm < 1) per_sm = 1;
   const int ntiles = (int)((m->N + C::EB - 1) / C::EB);
   int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_adj_element<P, NE><<<grid, kThreads, A::SMEM, st>>>(u, lam, uvol, G, T, m->geo, m->tab, (int)m->N, m->gamma);
+  k_adj_element<P, NE, Q><<<grid, kThreads, A::SMEM, st>>>(u, lam, uvol, G, T, m->geo, m->tab, (int)m->N, m->gamma);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   const int64_t nf = m->F * NE;
   k_adj_face<NE><<<(int)((nf + kThreads - 1) / kThreads), kThreads, 0, st>>>(T, G, TB, m->face_conn, m->face_geo,
@@ -281,7 +281,10 @@ int launch_rhs_vjp(const dg_mesh *m, const double *u, const double *lam, double 
                    double *TB, const double *X, const double *Y, const double *Z, double x0, double x1,
                    double x2, double s, double *out, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
-#define CALL(P, NE) run_adj<P, NE>(m, u, lam, uvol, G, T, TB, X, Y, Z, x0, x1, x2, s, out, st)
+#define CALL(P, NE)                                                                                  \
+  (m->rule == DG_RULE_SYMMETRIC                                                                      \
+       ? run_adj<P, NE, sym_points(P)>(m, u, lam, uvol, G, T, TB, X, Y, Z, x0, x1, x2, s, out, st)  \
+       : run_adj<P, NE, 0>(m, u, lam, uvol, G, T, TB, X, Y, Z, x0, x1, x2, s, out, st))
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);

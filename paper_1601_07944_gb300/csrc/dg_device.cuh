@@ -16,11 +16,17 @@ namespace dg {
 __device__ __forceinline__ float f64_to_f32_dev(double x) { return tc::f64_to_f32(x); }
 __device__ __forceinline__ double f32_to_f64_dev(float f) { return tc::f32_to_f64(f); }
 
-template <int P, int NE>
+// points of the fully symmetric volume rule of degree 2p (p = 1..5)
+__host__ __device__ constexpr int sym_points(int p) {
+  return p == 1 ? 3 : p == 2 ? 6 : p == 3 ? 12 : p == 4 ? 16 : 25;
+}
+
+// Q = 0: the collapsed (p+1)^2 grid; Q > 0: a rule of Q points (the symmetric one)
+template <int P, int NE, int Q = 0>
 struct Cfg {
   static constexpr int NP = (P + 1) * (P + 2) / 2;
   static constexpr int ND = P + 1;
-  static constexpr int NQ = ND * ND;
+  static constexpr int NQ = Q > 0 ? Q : ND * ND;
   static constexpr int NF = 3 * NE;
   static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);   // elements per tile
   static constexpr int TAB = NP * NQ * 3 + NF * NP * 2;          // direct tables, doubles

@@ -33,20 +33,50 @@ namespace {
 // reference fluxes (G_r, G_s) = J^tau (F1, F2) are formed as the Euler flux
 // along the two rows of J^tau, which are constant on the element.
 // ---------------------------------------------------------------------------
-template <int P, int NE>
+//
+// Q > 0 (a volume rule of Q points without tensor structure: the symmetric
+// rules) contracts the volume term directly instead,
+//   U(k) = sum_j phi_j(r_k) c_j,   V_j = sum_k w_k (d_r phi_j(r_k) G_r(k) + d_s phi_j(r_k) G_s(k)),
+// Q N_p products per variable for each; the lift, the stage update and the
+// traces are the same in both forms.
+// ---------------------------------------------------------------------------
+template <int P, int NE, int Q>
 struct SfCfg {
-  using C = Cfg<P, NE>;
+  using C = Cfg<P, NE, Q>;
+  static constexpr bool DIRECT = Q > 0;
   static constexpr int NP = C::NP, ND = C::ND, NQ = C::NQ, NF = C::NF;
   static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);
   // per element and variable, the edge-flux buffer holds the NF gathered fluxes,
   // then (in place) the LW sums of the factorised lift
   static constexpr int LW = ND + 2 * NE;
   static constexpr int RS = NF > LW ? NF : LW;
-  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 3 * NP * NE + ND * NE + NP;
-  static constexpr int TILE = EB * (M * NP + 8 * ND * ND + 8 * NQ + RS * M);
+  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 3 * NP * NE + ND * NE + NP + (DIRECT ? 3 * NP * NQ : 0);
+  // per element: the sum-factorisation buffer (8 ND^2), or for the direct form
+  // the new state (its point buffer is read until the last mode is done)
+  static constexpr int XS = DIRECT ? M * NP : 8 * ND * ND;
+  static constexpr int TILE = EB * (M * NP + XS + 8 * NQ + RS * M);
   static constexpr int SMEM = (TAB + TILE) * 8;
-  static_assert(8 * NQ >= M * NP, "the new state reuses the point buffer");
+  static_assert(DIRECT || 8 * NQ >= M * NP, "the new state reuses the point buffer");
 };
+
+// Reference fluxes at one volume point: G_r = J^tau row 0 . (F1, F2), G_s = row 1
+// . (F1, F2).  The Euler flux along a direction d is (rho v_d, rho u v_d + p d_x,
+// rho v v_d + p d_y, (E + p) v_d) with v_d = (rho u d_x + rho v d_y) / rho.
+__device__ __forceinline__ void ref_flux(const double U[M], const double *g, double gamma, int *err, double Gr[M],
+                                         double Gs[M]) {
+  const double inv = recip(U[0]);
+  const double p = (gamma - 1.0) * fma(fma(U[1], U[1], U[2] * U[2]), -0.5 * inv, U[3]);
+  if (!(positive_finite(U[0]) & positive_finite(p))) atomicOr(err, kErrNonPhysical);
+  const double Ep = U[3] + p;
+  {
+    const double mn = fma(U[1], g[0], U[2] * g[1]), vd = mn * inv;
+    Gr[0] = mn; Gr[1] = fma(U[1], vd, p * g[0]); Gr[2] = fma(U[2], vd, p * g[1]); Gr[3] = Ep * vd;
+  }
+  {
+    const double mn = fma(U[1], g[2], U[2] * g[3]), vd = mn * inv;
+    Gs[0] = mn; Gs[1] = fma(U[1], vd, p * g[2]); Gs[2] = fma(U[2], vd, p * g[3]); Gs[3] = Ep * vd;
+  }
+}
 
 // mode j -> a (first Dubiner index); modes are ordered by degree d = a+b, then b
 __device__ __forceinline__ int mode_a(int j) {
@@ -55,13 +85,13 @@ __device__ __forceinline__ int mode_a(int j) {
   return d - (j - d * (d + 1) / 2);
 }
 
-template <int P, int NE>
+template <int P, int NE, int Q>
 __global__ void __launch_bounds__(kThreads, 2)
 k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
              const double *__restrict__ fhat, const double *__restrict__ geo,
              const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
              double gamma, int *err) {
-  using S = SfCfg<P, NE>;
+  using S = SfCfg<P, NE, Q>;
   constexpr int NP = S::NP, ND = S::ND, NQ = S::NQ, NF = S::NF, EB = S::EB;
   extern __shared__ double smem[];
   double *sPa = smem;                  // [ND][ND]   P_a(alpha_ia)
@@ -76,11 +106,14 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   double *sEWPa = sEWChi + NP * NE;    // [ND][NE]   omega_k P_a(xi_k)
   double *sEChiM1 = sEWPa + ND * NE;   // [NP]       chi_j(-1)
   double *sEF0 = sEChiM1 + NP;         // [NP][NE]   phi_j at the points of face 0
-  double *sC = sEF0 + NP * NE;         // [EB][M][NP]        stage input
-  double *sX = sC + EB * M * NP;       // [EB][ND][ND][8]    W (first 4), then Xa, Xb
-  double *sH = sX + EB * ND * ND * 8;  // [EB][NQ][8]        Ha, Hb; later the new state
+  double *sBvT = sEF0 + NP * NE;       // direct form: [NP][NQ] phi_j(r_k)
+  double *sDr = sBvT + (S::DIRECT ? NP * NQ : 0);   //  [NQ][NP] w_k d_r phi_j(r_k)
+  double *sDs = sDr + (S::DIRECT ? NQ * NP : 0);    //  [NQ][NP] w_k d_s phi_j(r_k)
+  double *sC = sDs + (S::DIRECT ? NQ * NP : 0);     // [EB][M][NP]        stage input
+  double *sX = sC + EB * M * NP;       // [EB][ND][ND][8]    W (first 4), then Xa, Xb (direct: the new state)
+  double *sH = sX + EB * S::XS;        // [EB][NQ][8]        Ha, Hb (direct: G_r, G_s); later the new state
   double *sF = sH + EB * NQ * 8;       // [EB][RS][M]        -F_hat_out * l, then the lift sums
-  double *sO = sH;
+  double *sO = S::DIRECT ? sX : sH;
   constexpr int RS = S::RS;
 
   for (int i = threadIdx.x; i < ND * ND; i += blockDim.x) {
@@ -94,6 +127,11 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sEWPa[i] = tab.EWPa[i];
   for (int i = threadIdx.x; i < NP; i += blockDim.x) sEChiM1[i] = tab.EChiM1[i];
   for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) sEF0[i] = tab.BfT[(i / NE) * NF + i % NE];
+  if constexpr (S::DIRECT) {
+    for (int i = threadIdx.x; i < NP * NQ; i += blockDim.x) {
+      sBvT[i] = tab.BvT[i]; sDr[i] = tab.Dr[i]; sDs[i] = tab.Ds[i];
+    }
+  }
 
   const int ntiles = (N + EB - 1) / EB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -144,100 +182,116 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
       }
     }
 
-    // W(a, ib) = sum over the modes with first index a of chi_j(beta_ib) c_j; one
-    // item per (element, ib, variable) runs over all modes (the same unrolled
-    // sequence in every lane)
-    for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
-      const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
-      const double *cm = sC + (el * M + m) * NP;
-      double w[ND];
+    if constexpr (S::DIRECT) {
+      // volume points: U = sum_j phi_j c_j, then G_r, G_s; one item per (element, point)
+      for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
+        const int el = i / NQ, k = i - el * NQ;
+        double U[M] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int a = 0; a < ND; ++a) w[a] = 0.0;
+        for (int j = 0; j < NP; ++j) {
+          const double b = sBvT[j * NQ + k];
 #pragma unroll
-      for (int d = 0; d <= P; ++d)
-#pragma unroll
-        for (int b = 0; b <= d; ++b) {
-          const int j = d * (d + 1) / 2 + b;
-          w[d - b] = fma(sChi[j * ND + ib], cm[j], w[d - b]);
+          for (int m = 0; m < M; ++m) U[m] = fma(b, sC[(el * M + m) * NP + j], U[m]);
         }
+        double Gr[M] = {0.0, 0.0, 0.0, 0.0}, Gs[M] = {0.0, 0.0, 0.0, 0.0};
+        if (el < ecount) ref_flux(U, geo + (size_t)(e0 + el) * GEO, gamma, err, Gr, Gs);
+        double *h = sH + (size_t)i * 8;
 #pragma unroll
-      for (int a = 0; a < ND; ++a) sX[((el * ND + a) * ND + ib) * 8 + m] = w[a];
-    }
-    __syncthreads();
+        for (int m = 0; m < M; ++m) { h[m] = Gr[m]; h[4 + m] = Gs[m]; }
+      }
+      __syncthreads();
+    } else {
+      // W(a, ib) = sum over the modes with first index a of chi_j(beta_ib) c_j; one
+      // item per (element, ib, variable) runs over all modes (the same unrolled
+      // sequence in every lane)
+      for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
+        const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
+        const double *cm = sC + (el * M + m) * NP;
+        double w[ND];
+  #pragma unroll
+        for (int a = 0; a < ND; ++a) w[a] = 0.0;
+  #pragma unroll
+        for (int d = 0; d <= P; ++d)
+  #pragma unroll
+          for (int b = 0; b <= d; ++b) {
+            const int j = d * (d + 1) / 2 + b;
+            w[d - b] = fma(sChi[j * ND + ib], cm[j], w[d - b]);
+          }
+  #pragma unroll
+        for (int a = 0; a < ND; ++a) sX[((el * ND + a) * ND + ib) * 8 + m] = w[a];
+      }
+      __syncthreads();
 
-    // volume points: U = sum_a P_a W; Euler flux; Ha, Hb
-    for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
-      const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
-      double U[M] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int a = 0; a < ND; ++a) {
-        const double pa = sPa[a * ND + ia];
-        const double *w = sX + ((el * ND + a) * ND + ib) * 8;
-#pragma unroll
-        for (int m = 0; m < M; ++m) U[m] += pa * w[m];
+      // volume points: U = sum_a P_a W; Euler flux; Ha, Hb
+      for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
+        const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
+        double U[M] = {0.0, 0.0, 0.0, 0.0};
+  #pragma unroll
+        for (int a = 0; a < ND; ++a) {
+          const double pa = sPa[a * ND + ia];
+          const double *w = sX + ((el * ND + a) * ND + ib) * 8;
+  #pragma unroll
+          for (int m = 0; m < M; ++m) U[m] += pa * w[m];
+        }
+        double Ha[M], Hb[M];
+        if (el < ecount) {
+          double Gr[M], Gs[M];
+          ref_flux(U, geo + (size_t)(e0 + el) * GEO, gamma, err, Gr, Gs);
+          const double half = sHalf[ia];
+  #pragma unroll
+          for (int m = 0; m < M; ++m) {
+            Ha[m] = fma(half, Gs[m], Gr[m]);
+            Hb[m] = Gs[m];
+          }
+        } else {
+  #pragma unroll
+          for (int m = 0; m < M; ++m) { Ha[m] = 0.0; Hb[m] = 0.0; }
+        }
+        double *h = sH + (size_t)i * 8;
+  #pragma unroll
+        for (int m = 0; m < M; ++m) { h[m] = Ha[m]; h[4 + m] = Hb[m]; }
       }
-      double Ha[M], Hb[M];
-      if (el < ecount) {
-        const double *g = geo + (size_t)(e0 + el) * GEO;
-        // G_r = J^tau row 0 . (F1, F2), G_s = row 1 . (F1, F2): the Euler flux along
-        // a direction d is (rho v_d, rho u v_d + p d_x, rho v v_d + p d_y, (E + p) v_d)
-        // with v_d = (rho u d_x + rho v d_y) / rho
-        const double inv = recip(U[0]);
-        const double p = (gamma - 1.0) * fma(fma(U[1], U[1], U[2] * U[2]), -0.5 * inv, U[3]);
-        if (!(positive_finite(U[0]) & positive_finite(p))) atomicOr(err, kErrNonPhysical);
-        const double Ep = U[3] + p;
-        double Gr[M], Gs[M];
-        {
-          const double mn = fma(U[1], g[0], U[2] * g[1]), vd = mn * inv;
-          Gr[0] = mn; Gr[1] = fma(U[1], vd, p * g[0]); Gr[2] = fma(U[2], vd, p * g[1]); Gr[3] = Ep * vd;
-        }
-        {
-          const double mn = fma(U[1], g[2], U[2] * g[3]), vd = mn * inv;
-          Gs[0] = mn; Gs[1] = fma(U[1], vd, p * g[2]); Gs[2] = fma(U[2], vd, p * g[3]); Gs[3] = Ep * vd;
-        }
-        const double half = sHalf[ia];
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          Ha[m] = fma(half, Gs[m], Gr[m]);
-          Hb[m] = Gs[m];
-        }
-      } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) { Ha[m] = 0.0; Hb[m] = 0.0; }
-      }
-      double *h = sH + (size_t)i * 8;
-#pragma unroll
-      for (int m = 0; m < M; ++m) { h[m] = Ha[m]; h[4 + m] = Hb[m]; }
-    }
-    __syncthreads();
+      __syncthreads();
 
-    // Xa(a, ib) = sum_ia Ha wa P_a', Xb(a, ib) = sum_ia Hb wa P_a
-    for (int i = threadIdx.x; i < EB * ND * ND; i += blockDim.x) {
-      const int el = i / (ND * ND), a = (i / ND) % ND, ib = i % ND;
-      double xa[M] = {0.0, 0.0, 0.0, 0.0}, xb[M] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int ia = 0; ia < ND; ++ia) {
-        const double dp = sdPaW[a * ND + ia], pa = sPaW[a * ND + ia];
-        const double *h = sH + ((el * NQ) + ib * ND + ia) * 8;
-#pragma unroll
-        for (int m = 0; m < M; ++m) { xa[m] += h[m] * dp; xb[m] += h[4 + m] * pa; }
+      // Xa(a, ib) = sum_ia Ha wa P_a', Xb(a, ib) = sum_ia Hb wa P_a
+      for (int i = threadIdx.x; i < EB * ND * ND; i += blockDim.x) {
+        const int el = i / (ND * ND), a = (i / ND) % ND, ib = i % ND;
+        double xa[M] = {0.0, 0.0, 0.0, 0.0}, xb[M] = {0.0, 0.0, 0.0, 0.0};
+  #pragma unroll
+        for (int ia = 0; ia < ND; ++ia) {
+          const double dp = sdPaW[a * ND + ia], pa = sPaW[a * ND + ia];
+          const double *h = sH + ((el * NQ) + ib * ND + ia) * 8;
+  #pragma unroll
+          for (int m = 0; m < M; ++m) { xa[m] += h[m] * dp; xb[m] += h[4 + m] * pa; }
+        }
+        double *x = sX + (size_t)i * 8;
+  #pragma unroll
+        for (int m = 0; m < M; ++m) { x[m] = xa[m]; x[4 + m] = xb[m]; }
       }
-      double *x = sX + (size_t)i * 8;
-#pragma unroll
-      for (int m = 0; m < M; ++m) { x[m] = xa[m]; x[4 + m] = xb[m]; }
+      __syncthreads();
+
     }
-    __syncthreads();
 
     // modes: V_j + lifted edge fluxes, 1/det J, stage update
     for (int i = threadIdx.x; i < EB * NP; i += blockDim.x) {
       const int el = i / NP, j = i - el * NP, a = mode_a(j);
       double acc[M] = {0.0, 0.0, 0.0, 0.0};
+      if constexpr (S::DIRECT) {
 #pragma unroll
-      for (int ib = 0; ib < ND; ++ib) {
-        const double ch = sChiA[j * ND + ib], dch = sdChiB[j * ND + ib];
-        const double *x = sX + ((el * ND + a) * ND + ib) * 8;
+        for (int k = 0; k < NQ; ++k) {
+          const double dr = sDr[k * NP + j], ds = sDs[k * NP + j];
+          const double *h = sH + (el * NQ + k) * 8;
 #pragma unroll
-        for (int m = 0; m < M; ++m) acc[m] = fma(dch, x[4 + m], fma(ch, x[m], acc[m]));
+          for (int m = 0; m < M; ++m) acc[m] = fma(ds, h[4 + m], fma(dr, h[m], acc[m]));
+        }
+      } else {
+#pragma unroll
+        for (int ib = 0; ib < ND; ++ib) {
+          const double ch = sChiA[j * ND + ib], dch = sdChiB[j * ND + ib];
+          const double *x = sX + ((el * ND + a) * ND + ib) * 8;
+#pragma unroll
+          for (int m = 0; m < M; ++m) acc[m] = fma(dch, x[4 + m], fma(ch, x[m], acc[m]));
+        }
       }
       {
         const double *fl = sF + el * RS * M;
@@ -279,8 +333,9 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
           nv[m] = v;
         }
       }
-      // the new state, for the next stage's traces (sH is free: every thread has
-      // passed the barrier after the X phase, the last reader of sH)
+      // the new state, for the next stage's traces (sum-factorised: sH is free,
+      // every thread has passed the barrier after the X phase, the last reader of
+      // sH; direct: a buffer of its own, the modes still read sH)
 #pragma unroll
       for (int m = 0; m < M; ++m) sO[(el * M + m) * NP + j] = nv[m];
     }
@@ -306,25 +361,25 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 }
 
 
-template <int P, int NE>
+template <int P, int NE, int Q>
 int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
                    const double *fhat, const StageUpdate &su, int mode, cudaStream_t s) {
-  using S = SfCfg<P, NE>;
+  using S = SfCfg<P, NE, Q>;
   static PerDevice attr_set;
   if (!attr_set.test(m->device)) {
-    cudaError_t e = cudaFuncSetAttribute(k_element_sf<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_element_sf<P, NE, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
     if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_element_sf<P, NE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(k_element_sf<P, NE, Q>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
     attr_set.set(m->device);
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element_sf<P, NE>, kThreads, S::SMEM);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element_sf<P, NE, Q>, kThreads, S::SMEM);
   if (e != cudaSuccess) return (int)e;
   if (per_sm < 1) per_sm = 1;
   const int ntiles = (int)((m->N + S::EB - 1) / S::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_element_sf<P, NE><<<grid, kThreads, S::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
+  k_element_sf<P, NE, Q><<<grid, kThreads, S::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
                                                       (int)m->N, m->F, su, mode, m->gamma, m->err_flag);
   return (int)cudaGetLastError();
 }
@@ -334,7 +389,9 @@ int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
                    const double *fhat, const StageUpdate &su, int mode, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
-#define CALL(P, NE) run_element_sf<P, NE>(m, c, u0, out, trace_out, fhat, su, mode, s)
+#define CALL(P, NE)                                                                       \
+  (m->rule == DG_RULE_SYMMETRIC ? run_element_sf<P, NE, sym_points(P)>(m, c, u0, out, trace_out, fhat, su, mode, s) \
+                                : run_element_sf<P, NE, 0>(m, c, u0, out, trace_out, fhat, su, mode, s))
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);

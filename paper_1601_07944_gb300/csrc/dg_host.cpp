@@ -193,7 +193,8 @@ void mode_ab(int j, int *a, int *b) {
 }
 
 // phi_j and its reference gradient at (r, s) for every mode j of degree <= p
-void dubiner(int p, real r, real s, double *phi, double *dr, double *ds) {
+template <class T>
+void dubiner_t(int p, real r, real s, T *phi, T *dr, T *ds) {
   int np = (p + 1) * (p + 2) / 2;
   real oms = 1.0L - s;
   real al = 2.0L * r / oms - 1.0L, be = 2.0L * s - 1.0L;
@@ -205,12 +206,183 @@ void dubiner(int p, real r, real s, double *phi, double *dr, double *ds) {
     real Pb = jacobi_p(b, 2 * a + 1, 0, be), dPb = jacobi_dp(b, 2 * a + 1, 0, be);
     real oa = std::pow(oms, (real)a);
     real oa1 = a > 0 ? std::pow(oms, (real)(a - 1)) : 0.0L;
-    if (phi) phi[j] = (double)(N * Pa * oa * Pb);
+    if (phi) phi[j] = (T)(N * Pa * oa * Pb);
     // d/dr: d alpha/dr = 2/(1-s)
-    if (dr) dr[j] = (double)(N * 2.0L * dPa * oa1 * Pb);
+    if (dr) dr[j] = (T)(N * 2.0L * dPa * oa1 * Pb);
     // d/ds: d alpha/ds = (1+alpha)/(1-s), d beta/ds = 2
-    if (ds) ds[j] = (double)(N * (oa1 * (dPa * (1.0L + al) - a * Pa) * Pb + 2.0L * Pa * oa * dPb));
+    if (ds) ds[j] = (T)(N * (oa1 * (dPa * (1.0L + al) - a * Pa) * Pb + 2.0L * Pa * oa * dPb));
   }
+}
+
+void dubiner(int p, real r, real s, double *phi, double *dr, double *ds) { dubiner_t<double>(p, r, s, phi, dr, ds); }
+
+// ---------------------------------------------------------------------------
+// Fully symmetric volume rules of degree 2p (Section 4.3.2 evaluates the volume
+// integrals with rules of degree 2p; Section 6.1 gives their point counts, 3 at
+// p = 1 and 16 at p = 4).  A rule invariant under the symmetries of the triangle is a
+// union of orbits in barycentric coordinates, one weight per orbit:
+//   S3    the centroid,                         1 point,  parameters (w)
+//   S21   (a, a, 1-2a) and its permutations,    3 points, parameters (w, a)
+//   S111  (a, b, 1-a-b) and its permutations,   6 points, parameters (w, a, b)
+// (w is the weight of each point; (r, s) = the 2nd and 3rd barycentric
+// coordinates).  The rule is exact to degree d when it integrates every
+// orthonormal Dubiner polynomial of degree <= d exactly: sum_k w_k phi_j(x_k) =
+// int phi_j = delta_j0 / sqrt(2).  The orbit structure for each p has as many
+// parameters as there are independent symmetric conditions; they are solved by
+// Gauss-Newton on all (2p+1)(2p+2)/2 conditions (normal equations, Gaussian
+// elimination, extended precision, gradients from the basis derivatives) from
+// the start values below.  Where several positive-interior rules of a structure
+// exist (p = 3, p = 5), the start values pick the one whose points lie farthest
+// from the edges.
+// ---------------------------------------------------------------------------
+struct SymOrbit {
+  int kind;          // 0 = S3, 1 = S21, 2 = S111
+  double prm[3];     // start values (w, a, b)
+};
+const SymOrbit kSym1[] = {{1, {0.167, 0.167}}};
+const SymOrbit kSym2[] = {{1, {0.0550, 0.0916}}, {1, {0.112, 0.446}}};
+const SymOrbit kSym3[] = {{1, {0.0254, 0.0631}}, {1, {0.0584, 0.249}}, {2, {0.0414, 0.0531, 0.310}}};
+const SymOrbit kSym4[] = {{0, {0.0722}}, {1, {0.0162, 0.0505}}, {1, {0.0516, 0.171}}, {1, {0.0475, 0.459}},
+                          {2, {0.0136, 0.00839, 0.263}}};
+const SymOrbit kSym5[] = {{0, {0.0416}}, {1, {0.00548, 0.0285}}, {1, {0.0263, 0.163}},
+                          {2, {0.0177, 0.0293, 0.363}}, {2, {0.0147, 0.0337, 0.153}},
+                          {2, {0.0281, 0.147, 0.337}}};
+
+struct SymPoint {
+  real r, s, w;
+  int iw, ia, ib;        // parameter indices of w, a, b (-1: none)
+  real dra, drb, dsa, dsb;  // d r / d a, d r / d b, d s / d a, d s / d b
+};
+
+void sym_points(const SymOrbit *orb, int norb, const std::vector<real> &x, std::vector<SymPoint> &pts) {
+  pts.clear();
+  int off = 0;
+  for (int o = 0; o < norb; ++o) {
+    const real w = x[off];
+    if (orb[o].kind == 0) {
+      pts.push_back({1.0L / 3.0L, 1.0L / 3.0L, w, off, -1, -1, 0, 0, 0, 0});
+      off += 1;
+    } else if (orb[o].kind == 1) {
+      const real a = x[off + 1], c = 1.0L - 2.0L * a;
+      const int ia = off + 1;
+      pts.push_back({a, a, w, off, ia, -1, 1, 0, 1, 0});
+      pts.push_back({a, c, w, off, ia, -1, 1, 0, -2, 0});
+      pts.push_back({c, a, w, off, ia, -1, -2, 0, 1, 0});
+      off += 2;
+    } else {
+      const real a = x[off + 1], b = x[off + 2], c = 1.0L - a - b;
+      const int ia = off + 1, ib = off + 2;
+      // (value, d/da, d/db) of a, b, c
+      const real v[3][3] = {{a, 1, 0}, {b, 0, 1}, {c, -1, -1}};
+      const int order[6][2] = {{0, 1}, {1, 0}, {0, 2}, {2, 0}, {1, 2}, {2, 1}};
+      for (auto &q : order)
+        pts.push_back({v[q[0]][0], v[q[1]][0], w, off, ia, ib, v[q[0]][1], v[q[0]][2], v[q[1]][1], v[q[1]][2]});
+      off += 3;
+    }
+  }
+}
+
+// solves A x = b in place (n x n, row-major; partial pivoting); false if singular
+bool solve_dense(int n, std::vector<real> &A, std::vector<real> &b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0L) return false;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const real f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    real t = b[r];
+    for (int k = r + 1; k < n; ++k) t -= A[r * n + k] * b[k];
+    b[r] = t / A[r * n + r];
+  }
+  return true;
+}
+
+// The symmetric rule of degree 2p, rounded to double (r, s, w hold the rounded
+// values).  false if p is unsupported or the iteration fails.
+bool symmetric_rule(int p, std::vector<real> &r, std::vector<real> &s, std::vector<real> &w) {
+  const SymOrbit *orb = nullptr;
+  int norb = 0;
+  switch (p) {
+    case 1: orb = kSym1; norb = 1; break;
+    case 2: orb = kSym2; norb = 2; break;
+    case 3: orb = kSym3; norb = 3; break;
+    case 4: orb = kSym4; norb = 5; break;
+    case 5: orb = kSym5; norb = 6; break;
+    default: return false;
+  }
+  std::vector<real> x;
+  for (int o = 0; o < norb; ++o) {
+    const int np_ = orb[o].kind == 0 ? 1 : orb[o].kind == 1 ? 2 : 3;
+    for (int k = 0; k < np_; ++k) x.push_back((real)orb[o].prm[k]);
+  }
+  const int n = (int)x.size(), d = 2 * p, nm = (d + 1) * (d + 2) / 2;
+  std::vector<SymPoint> pts;
+  std::vector<real> phi(nm), dr(nm), ds(nm), res(nm), jac((size_t)nm * n);
+  const real target0 = 1.0L / std::sqrt(2.0L);
+  real worst = 0.0L;
+  for (int it = 0; it < 60; ++it) {
+    sym_points(orb, norb, x, pts);
+    std::fill(res.begin(), res.end(), 0.0L);
+    std::fill(jac.begin(), jac.end(), 0.0L);
+    res[0] = -target0;
+    for (const SymPoint &q : pts) {
+      dubiner_t<real>(d, q.r, q.s, phi.data(), dr.data(), ds.data());
+      for (int j = 0; j < nm; ++j) {
+        res[j] += q.w * phi[j];
+        real *g = &jac[(size_t)j * n];
+        g[q.iw] += phi[j];
+        if (q.ia >= 0) g[q.ia] += q.w * (dr[j] * q.dra + ds[j] * q.dsa);
+        if (q.ib >= 0) g[q.ib] += q.w * (dr[j] * q.drb + ds[j] * q.dsb);
+      }
+    }
+    worst = 0.0L;
+    for (int j = 0; j < nm; ++j) worst = std::max(worst, std::fabs(res[j]));
+    std::vector<real> A((size_t)n * n, 0.0L), b(n, 0.0L);
+    for (int j = 0; j < nm; ++j) {
+      const real *g = &jac[(size_t)j * n];
+      for (int a = 0; a < n; ++a) {
+        b[a] -= g[a] * res[j];
+        for (int c = 0; c < n; ++c) A[a * n + c] += g[a] * g[c];
+      }
+    }
+    if (!solve_dense(n, A, b)) return false;
+    real step = 0.0L;
+    for (int k = 0; k < n; ++k) {
+      x[k] += b[k];
+      step = std::max(step, std::fabs(b[k]));
+    }
+    if (step < std::max(64.0L * std::numeric_limits<real>::epsilon(), 1e-28L)) break;
+  }
+  if (!(worst < 1e-15L)) return false;
+  sym_points(orb, norb, x, pts);
+  r.resize(pts.size()); s.resize(pts.size()); w.resize(pts.size());
+  for (size_t k = 0; k < pts.size(); ++k) {
+    r[k] = (real)(double)pts[k].r;
+    s[k] = (real)(double)pts[k].s;
+    w[k] = (real)(double)pts[k].w;
+    if (!(pts[k].w > 0.0L && pts[k].r > 0.0L && pts[k].s > 0.0L && pts[k].r + pts[k].s < 1.0L)) return false;
+  }
+  return true;
+}
+
+// The volume rule of a mesh: the collapsed grid or the symmetric rule.
+bool volume_rule(int p, int rule, std::vector<real> &r, std::vector<real> &s, std::vector<real> &w) {
+  if (rule == DG_RULE_COLLAPSED) {
+    collapsed_rule(p + 1, r, s, w);
+    return true;
+  }
+  if (rule == DG_RULE_SYMMETRIC) return symmetric_rule(p, r, s, w);
+  return false;
 }
 
 // Reference point of edge coordinate xi on local face q (running from reference
@@ -339,6 +511,23 @@ extern "C" dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s,
   return DG_OK;
 }
 
+extern "C" dg_status dg_volume_rule(int p, int rule, int *nq, double *r, double *s, double *w, double *phi) {
+  if (!nq || p < 1 || p > dg::PMAX) return fail(DG_EINVAL, "dg_volume_rule: p=%d", p);
+  std::vector<real> vr, vs, vw;
+  if (rule != DG_RULE_COLLAPSED && rule != DG_RULE_SYMMETRIC) return fail(DG_EINVAL, "dg_volume_rule: rule=%d", rule);
+  if (!volume_rule(p, rule, vr, vs, vw)) return fail(DG_EINVAL, "dg_volume_rule: no rule for p=%d", p);
+  const int n = (int)vr.size(), np = (p + 1) * (p + 2) / 2;
+  *nq = n;
+  for (int k = 0; k < n; ++k) {
+    if (r) r[k] = (double)vr[k];
+    if (s) s[k] = (double)vs[k];
+    if (w) w[k] = (double)vw[k];
+    if (phi) dubiner(p, vr[k], vs[k], phi + (size_t)k * np, nullptr, nullptr);
+  }
+  g_err.clear();
+  return DG_OK;
+}
+
 extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   using namespace dg;
   if (!d || !out) return fail(DG_EINVAL, "dg_mesh_create: null argument");
@@ -350,6 +539,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   const int ne = d->n_edge_pts ? d->n_edge_pts : p + 1;
   if (!supported(p, ne)) return fail(DG_EINVAL, "dg_mesh_create: unsupported p=%d n_edge_pts=%d", p, ne);
   if (!(d->gamma > 1.0)) return fail(DG_EINVAL, "dg_mesh_create: gamma must exceed 1");
+  if (d->vol_rule != DG_RULE_COLLAPSED && d->vol_rule != DG_RULE_SYMMETRIC)
+    return fail(DG_EINVAL, "dg_mesh_create: unknown vol_rule %d", d->vol_rule);
 
   const double *xy = d->elem_xy;
   // --- validation and edge list ------------------------------------------
@@ -426,9 +617,14 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   const int64_t F = (int64_t)conn.size();
 
   // --- tables ----------------------------------------------------------------
-  const int np = (p + 1) * (p + 2) / 2, nd = p + 1, nq = nd * nd, nf = 3 * ne;
+  const int np = (p + 1) * (p + 2) / 2, nd = p + 1, nf = 3 * ne;
   std::vector<real> r, s, w, ex, ew, xa, xb, wa_, wb_;
+  // the collapsed grid's 1D rules feed the sum-factorisation tables whichever
+  // volume rule the mesh uses (the edge tables need them too)
   collapsed_rule(nd, r, s, w, &xa, &xb, &wa_, &wb_);
+  if (d->vol_rule == DG_RULE_SYMMETRIC && !symmetric_rule(p, r, s, w))
+    return fail(DG_EINVAL, "dg_mesh_create: the symmetric rule for p=%d did not converge", p);
+  const int nq = (int)r.size();
   gauss_rule(ne, 0.0L, 0.0L, ex, ew);
   std::vector<double> phi(nq * np), dr(nq * np), ds(nq * np), phif(nf * np);
   for (int k = 0; k < nq; ++k) dubiner(p, r[k], s[k], &phi[k * np], &dr[k * np], &ds[k * np]);
@@ -523,7 +719,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   if (!m) return fail(DG_ENOMEM, "dg_mesh_create: host allocation");
   m->timing = new (std::nothrow) dg::Timing();
   if (!m->timing) { delete m; return fail(DG_ENOMEM, "dg_mesh_create: host allocation"); }
-  m->p = p; m->np = np; m->nq = nq; m->nd = nd; m->ne = ne; m->gamma = d->gamma;
+  m->p = p; m->np = np; m->nq = nq; m->nd = nd; m->ne = ne; m->gamma = d->gamma; m->rule = d->vol_rule;
   m->N = N; m->F = F;
   m->rin_min = rin_min;
   m->phi1 = phi[0];                              // phi_1 at the first volume point: the constant mode

@@ -112,6 +112,7 @@ struct GraphCache {
 
 struct dg_mesh {
   int p, np, nq, nd, ne;
+  int rule;               // dg_vol_rule: the collapsed grid or the symmetric rule
   double gamma;
   int64_t N, F;
   int64_t Fb;                  // boundary faces (the first Fb of the face list)
@@ -185,7 +186,10 @@ inline int launch_element_tc(const dg_mesh *m, int split3, const double *c, cons
                              double b0, int mode, void *stream) {
   return launch_element_tc(m, split3, c, u0, out, trace_out, fhat, fmean, shu_osher(dt, a0, b0), mode, stream);
 }
-int tc_smem_bytes(int p, int ne, int split3);
+// launch_element_tc for a mesh on the symmetric volume rule (dg_mixed_sym.cu)
+int launch_element_tc_sym(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
+                          float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
+                          int mode, void *stream);
 int launch_convert_check(int n, unsigned long long *bad, void *stream);
 int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);

@@ -115,10 +115,10 @@ k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceCo
 // ---------------------------------------------------------------------------
 // projection of point data and volume point coordinates
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, int NQ>
 __global__ void __launch_bounds__(kThreads)
 k_project(const double *__restrict__ u, double *__restrict__ c, const double *__restrict__ Pw, int N) {
-  constexpr int NP = (P + 1) * (P + 2) / 2, NQ = (P + 1) * (P + 1);
+  constexpr int NP = (P + 1) * (P + 2) / 2;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)N * NP) return;
   const int64_t e = i / NP;
@@ -231,11 +231,11 @@ k_totals_final(const double *__restrict__ partial, int nb, double *__restrict__ 
 // largest wave speed |v| + c over the volume points (max is exact, so the result
 // does not depend on the order)
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, int NQ>
 __global__ void __launch_bounds__(kThreads)
 k_wave_partial(const double *__restrict__ c, const double *__restrict__ BvT, int N, double gamma,
                double *__restrict__ partial, int *err) {
-  constexpr int NP = (P + 1) * (P + 2) / 2, NQ = (P + 1) * (P + 1);
+  constexpr int NP = (P + 1) * (P + 2) / 2;
   __shared__ double red[kThreads / 32];
   double smax = 0.0;
   const int64_t chunk = ((int64_t)N * NQ + gridDim.x - 1) / gridDim.x;
@@ -464,14 +464,18 @@ int launch_project(const dg_mesh *m, const double *u, double *c, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = m->N * m->np;
   const int grid = (int)((n + kThreads - 1) / kThreads);
+#define PROJ(P)                                                                                       \
+  (m->rule == DG_RULE_SYMMETRIC ? k_project<P, sym_points(P)><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N) \
+                                : k_project<P, (P + 1) * (P + 1)><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N))
   switch (m->p) {
-    case 1: k_project<1><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
-    case 2: k_project<2><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
-    case 3: k_project<3><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
-    case 4: k_project<4><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
-    case 5: k_project<5><<<grid, kThreads, 0, s>>>(u, c, m->tab.Pw, (int)m->N); break;
+    case 1: PROJ(1); break;
+    case 2: PROJ(2); break;
+    case 3: PROJ(3); break;
+    case 4: PROJ(4); break;
+    case 5: PROJ(5); break;
     default: return (int)cudaErrorInvalidValue;
   }
+#undef PROJ
   return (int)cudaGetLastError();
 }
 
@@ -501,14 +505,21 @@ int launch_fma_probe(int fp64, int blocks, int threads, int iters, double *out, 
 int launch_wave_speed(const dg_mesh *m, const double *c, double *out_dev, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = m->totals_blocks;
+#define WAVE(P)                                                                                        \
+  (m->rule == DG_RULE_SYMMETRIC                                                                        \
+       ? k_wave_partial<P, sym_points(P)><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma,      \
+                                                                  m->partial, m->err_flag)             \
+       : k_wave_partial<P, (P + 1) * (P + 1)><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, \
+                                                                      m->partial, m->err_flag))
   switch (m->p) {
-    case 1: k_wave_partial<1><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
-    case 2: k_wave_partial<2><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
-    case 3: k_wave_partial<3><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
-    case 4: k_wave_partial<4><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
-    case 5: k_wave_partial<5><<<nb, kThreads, 0, s>>>(c, m->tab.BvT, (int)m->N, m->gamma, m->partial, m->err_flag); break;
+    case 1: WAVE(1); break;
+    case 2: WAVE(2); break;
+    case 3: WAVE(3); break;
+    case 4: WAVE(4); break;
+    case 5: WAVE(5); break;
     default: return (int)cudaErrorInvalidValue;
   }
+#undef WAVE
   k_wave_final<<<1, 32, 0, s>>>(m->partial, nb, out_dev);
   return (int)cudaGetLastError();
 }

@@ -21,6 +21,7 @@ STATUS = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EMES
           5: "DG_ENONPHYS", 6: "DG_ETIMEOUT", 7: "DG_ENOTIMPL"}
 PRECISION = {"fp64": 0, "tf32x1": 1, "tf32x3": 2}
 METHOD = {"ssp_rk3": 0, "rk2": 1, "rk4": 2}
+VOL_RULE = {"collapsed": 0, "symmetric": 1}
 
 # every entry point declared in include/dg.h
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_points",
@@ -28,7 +29,7 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_point
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
            "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt",
            "dg_rk_step_method", "dg_limit", "dg_set_limiter", "dg_boundary_points",
-           "dg_set_boundary_state")
+           "dg_set_boundary_state", "dg_volume_rule")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
 
 
@@ -41,7 +42,7 @@ class DGError(RuntimeError):
 class _Desc(ctypes.Structure):
     _fields_ = [("n_elem", ctypes.c_int64), ("elem_xy", ctypes.c_void_p), ("nbr", ctypes.c_void_p),
                 ("nbr_face", ctypes.c_void_p), ("p", ctypes.c_int), ("n_edge_pts", ctypes.c_int),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("vol_rule", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -93,6 +94,7 @@ def load(path: str = None):
         "dg_eval_points": [P, I, P, P, P, P, P],
         "dg_rhs_adjoint": [P, P, P, P, P],
         "dg_stable_dt": [P, P, D, P, P],
+        "dg_volume_rule": [I, I, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -164,17 +166,38 @@ def host_tables(p: int, ne: int = 0):
     return out
 
 
-class Mesh:
-    """A mesh handle (geometry, tables and work buffers on the current GPU)."""
+def volume_rule(p: int, rule: str = "collapsed"):
+    """The library's volume rule for degree p (no GPU needed): points r, s,
+    weights w and the basis phi [nq, N_p] at the points."""
+    lib = load()
+    nq = ctypes.c_int()
+    _check(lib.dg_volume_rule(p, VOL_RULE[rule], ctypes.byref(nq), None, None, None, None))
+    n, np_ = nq.value, (p + 1) * (p + 2) // 2
+    r, s, w, phi = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros((n, np_))
+    _check(lib.dg_volume_rule(p, VOL_RULE[rule], ctypes.byref(nq), _np_ptr(r), _np_ptr(s), _np_ptr(w),
+                              _np_ptr(phi)))
+    return r, s, w, phi
 
-    def __init__(self, elem_xy, nbr, nbr_face, p: int, n_edge_pts: int = 0, gamma: float = 1.4):
+
+class Mesh:
+    """A mesh handle (geometry, tables and work buffers on the current GPU).
+
+    vol_rule: "collapsed" (the (p+1)^2-point collapsed Gauss grid, the default)
+    or "symmetric" (the fully symmetric degree-2p rule with the paper's point
+    counts, 3 / 6 / 12 / 16 / 25 at p = 1..5)."""
+
+    def __init__(self, elem_xy, nbr, nbr_face, p: int, n_edge_pts: int = 0, gamma: float = 1.4,
+                 vol_rule: str = "collapsed"):
+        if vol_rule not in VOL_RULE:
+            raise ValueError("vol_rule must be one of %s" % sorted(VOL_RULE))
         lib = load()
         xy = np.ascontiguousarray(elem_xy, dtype=np.float64)
         nb = np.ascontiguousarray(nbr, dtype=np.int64)
         nf = np.ascontiguousarray(nbr_face, dtype=np.int8)
         if xy.ndim != 3 or xy.shape[1:] != (3, 2) or nb.shape != (xy.shape[0], 3) or nf.shape != nb.shape:
             raise ValueError("mesh arrays must be elem_xy[N,3,2], nbr[N,3], nbr_face[N,3]")
-        desc = _Desc(xy.shape[0], xy.ctypes.data, nb.ctypes.data, nf.ctypes.data, p, n_edge_pts, gamma)
+        desc = _Desc(xy.shape[0], xy.ctypes.data, nb.ctypes.data, nf.ctypes.data, p, n_edge_pts, gamma,
+                     VOL_RULE[vol_rule])
         h = ctypes.c_void_p()
         _check(lib.dg_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
         self._h = h
@@ -184,6 +207,7 @@ class Mesh:
         self.N, self.n_face, self.p = info.n_elem, info.n_face, info.p
         self.np, self.nq, self.ne, self.gamma = info.n_modes, info.n_vol_pts, info.n_edge_pts, info.gamma
         self.n_boundary = info.n_boundary_face
+        self.vol_rule = vol_rule
 
     @classmethod
     def from_mesh(cls, mesh, p: int, **kw):

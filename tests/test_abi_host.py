@@ -68,11 +68,11 @@ def test_host_tables_p3_three_edge_points(lib, oracle_mod):
     assert np.abs(T["edge_x"] - x).max() < 1e-15 and np.abs(T["edge_w"] - w).max() < 1e-15
 
 
-def _create(lib, xy, nbr, nf, p=2, ne=0):
+def _create(lib, xy, nbr, nf, p=2, ne=0, rule=0):
     xy = np.ascontiguousarray(xy, np.float64)
     nbr = np.ascontiguousarray(nbr, np.int64)
     nf = np.ascontiguousarray(nf, np.int8)
-    desc = dg._Desc(xy.shape[0], xy.ctypes.data, nbr.ctypes.data, nf.ctypes.data, p, ne, 1.4)
+    desc = dg._Desc(xy.shape[0], xy.ctypes.data, nbr.ctypes.data, nf.ctypes.data, p, ne, 1.4, rule)
     h = ctypes.c_void_p()
     st = lib.dg_mesh_create(ctypes.byref(desc), ctypes.byref(h))
     return st, lib.dg_last_error().decode()
@@ -106,6 +106,35 @@ def test_mesh_validation_errors(lib):
     assert st == 1 and "unsupported" in msg
     st, msg = _create(lib, m.elem_xy, m.nbr, m.nbr_face, p=2, ne=5)
     assert st == 1
+    st, msg = _create(lib, m.elem_xy, m.nbr, m.nbr_face, rule=2)
+    assert st == 1 and "vol_rule" in msg
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_symmetric_rule_matches_oracle(lib, p):
+    """The library derives the symmetric rule on its own (extended precision,
+    orthonormal-basis moments) and must land on the oracle's rule (50-digit
+    decimal, monomial moments) in the same point order."""
+    from oracle.symmetric_rules import symmetric_rule
+    r, s, w, phi = dg.volume_rule(p, "symmetric")
+    R, S, W = symmetric_rule(p)
+    assert r.size == {1: 3, 2: 6, 3: 12, 4: 16, 5: 25}[p]
+    assert np.abs(r - R).max() <= 2e-16 and np.abs(s - S).max() <= 2e-16 and np.abs(w - W).max() <= 3e-17
+    # the basis values at the points agree with the oracle's evaluation there
+    o_phi = oracle_basis(p, r, s)
+    assert np.abs(phi - o_phi).max() < 1e-13
+    # and the collapsed grid is the one dg_host_tables reports
+    rc, sc, wc, _ = dg.volume_rule(p, "collapsed")
+    T = dg.host_tables(p)
+    assert np.array_equal(rc, T["vol_r"]) and np.array_equal(wc, T["vol_w"])
+    nq = ctypes.c_int()
+    assert lib.dg_volume_rule(p, 5, ctypes.byref(nq), None, None, None, None) == 1
+    assert lib.dg_volume_rule(9, 1, ctypes.byref(nq), None, None, None, None) == 1
+
+
+def oracle_basis(p, r, s):
+    import oracle
+    return oracle.dubiner(p, r, s)[0]
 
 
 def test_null_arguments(lib):

@@ -1,5 +1,5 @@
-"""Pins of the fully symmetric degree-2p volume rules (Section 4.1: the paper's
-volume rules have 3 points at p = 1 and 16 at p = 4) and of the oracle's
+"""Pins of the fully symmetric degree-2p volume rules (Section 4.3.2 asks for
+rules of degree 2p; Section 6.1 counts 3 points at p = 1 and 16 at p = 4) and of the oracle's
 solver running on them.
 
 Facts checked, none of them a re-run of the derivation:
