@@ -3,7 +3,8 @@ connectivity index it reads before using it and records a bad one, which
 dg_device_status reports as DG_EMESH (compute-sanitizer is not available, so this
 build stands in for a memory checker).  A fresh process loads that build and runs
 every kind of call -- all precisions, steppers, the limiter, boundary faces, the
-adjoint and the no-allocation RHS -- on meshes with ragged last tiles, then
+adjoint and the no-allocation RHS, on both volume rules -- on meshes with ragged
+last tiles, then
 requires a clean device record and parity with the oracle.
 """
 import os
@@ -31,9 +32,9 @@ def rel(a, b):
 
 for mesh, ic in ((I.periodic_mesh(6), I.perturbed_vortex),
                  (I.box_mesh(6, x_code=I.BC_WALL, y_code=I.BC_STATE), I.steady_vortex)):
-    for p in (1, 3, 5):
-        m = dg.Mesh.from_mesh(mesh, p)
-        o = oracle.OracleDG.from_mesh(mesh, p)
+    for p, rule in ((1, "collapsed"), (3, "collapsed"), (5, "collapsed"), (2, "symmetric"), (5, "symmetric")):
+        m = dg.Mesh.from_mesh(mesh, p, vol_rule=rule)
+        o = oracle.OracleDG.from_mesh(mesh, p, vol_rule=rule)
         if m.n_boundary:
             xy = m.boundary_points().cpu().numpy()
             m.set_boundary_state(torch.from_numpy(ic(xy[..., 0], xy[..., 1])).cuda())
