@@ -131,8 +131,10 @@ typedef struct {
  * DG_BC_WALL or DG_BC_STATE), builds the edge list (boundary faces first, in
  * element order, as the paper sorts them), geometry and basis tables on the host
  * and copies them to the current CUDA device.  Synchronous.  *out receives a handle to free with dg_mesh_destroy.
- * Errors: DG_EINVAL (null pointers, p or n_edge_pts unsupported), DG_EMESH,
- * DG_ENOMEM, DG_ECUDA. */
+ * The volume rule (vol_rule) is built here; a symmetric rule is derived from its
+ * moment conditions (milliseconds).
+ * Errors: DG_EINVAL (null pointers, p, n_edge_pts or vol_rule unsupported),
+ * DG_EMESH, DG_ENOMEM, DG_ECUDA. */
 dg_status dg_mesh_create(const dg_mesh_desc *desc, dg_mesh **out);
 
 /* Frees the handle and its device memory (synchronises the device first).

@@ -1,7 +1,8 @@
 /*
  * dg_element.cu -- the float64 element kernel of one stage (k_element_sf): the
  * volume integral (Eq. volume, Algorithm 1) sum-factorised on the collapsed
- * volume grid, the lift of the three edge fluxes (Algorithms 2-3), the 1/det J
+ * volume grid (or contracted directly on a symmetric rule of Q points), the lift
+ * of the three edge fluxes (Algorithms 2-3), the 1/det J
  * scaling (Eq. 2ddg0), the Runge-Kutta stage update (with, for the classical
  * RK4, the running sum of its stages as a second output) and the next stage's
  * edge traces, for one tile of elements per CTA.

@@ -254,6 +254,41 @@ def test_full_size_parity_1024_p5(dgmod, oracle_mod):
     assert rel_l2(_host(cd), o.ssp_rk3(c, dt, 1)) < TOL
 
 
+def _full_run_samples():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_run_samples.json")
+    with open(path) as fh:
+        return json.load(fh)["runs"]
+
+
+@pytest.mark.parametrize("run", [0, 1])
+def test_full_run_parity(dgmod, run):
+    """Whole runs at full size against the oracle (tests/golden/full_run_samples.json,
+    written by make_full_run_samples.py from the oracle alone): the 256^2 p=3
+    vortex after its 200 steps and the 256^2 p=2 perturbed vortex after the 400
+    steps of the adjoint workload's forward run; the GPU run replays the 16-step
+    CUDA graph.  Sampled coefficients (1024 seeded indices) within 1e-12 relative
+    L2, the whole state's norm within 1e-12, the totals within 1e-13."""
+    r = _full_run_samples()[run]
+    mesh = I.periodic_mesh(r["n"])
+    f = getattr(I, r["ic"])
+    m = dgmod.Mesh.from_mesh(mesh, r["p"])
+    assert list(m.coef_shape) == r["shape"]
+    dt = r["dt"]                              # the oracle run's step (libm may differ in the last bit)
+    assert abs(I.fixed_dt(mesh, f, r["p"]) - dt) <= 1e-14 * dt
+    c = m.project_function(f)
+    m.rk_step(c, dt, r["steps"])
+    m.device_status()
+    got = _host(c).reshape(-1)
+    ref = np.array(r["value"])
+    sample = got[np.array(r["index"])]
+    assert rel_l2(sample, ref) < TOL, rel_l2(sample, ref)
+    assert abs(np.linalg.norm(got) - r["l2_norm"]) <= 1e-12 * r["l2_norm"]
+    tot = m.conserved_totals(c)
+    assert np.all(np.abs(tot - np.array(r["totals"])) <= 1e-13 * np.abs(np.array(r["totals"])))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
 def test_graph_replay_matches_plain_launches(dgmod, prec):
     """A 40-step call (one plain step, two replays of the 16-step CUDA graph, seven
