@@ -39,17 +39,17 @@ constexpr int kThreads = 256;
 // face 1: alpha = 1, beta = xi; face 2: alpha = -1, beta = -xi):
 //   t0 = T0_k = sum_j phi_j(face 0, k) c_j,
 //   t1 = T1_k = sum_a Y_a(xi_k),  t2 = T2_{NE-1-k} = sum_a (-1)^a Y_a(xi_k),
-//   Y_a(xi) = sum_b chi_ab(xi) c_ab.
+//   Y_a(xi) = sum_b chi_ab(xi) c_ab,
+// formed as t1 = E + O and t2 = E - O from the sums over the modes of even and of
+// odd first index, E = sum_{a even} Y_a and O = sum_{a odd} Y_a (one FMA per mode
+// into one of two accumulators, then two additions).
 // cj: the N_p coefficients; eF0 = phi_j(face 0, k) and eChi = chi_j(xi_k), both
 // [N_p][NE].  Every kernel that writes traces calls this, so traces of the same
 // state agree bit for bit whichever kernel wrote them.
 template <int P, int NE>
 __device__ __forceinline__ void edge_traces_sf(const double *cj, const double *eF0, const double *eChi, int k,
                                                double &t0, double &t1, double &t2) {
-  constexpr int ND = P + 1;
-  double y[ND];
-#pragma unroll
-  for (int a = 0; a < ND; ++a) y[a] = 0.0;
+  double ev = 0.0, od = 0.0;
   t0 = 0.0;
 #pragma unroll
   for (int d = 0; d <= P; ++d)
@@ -58,15 +58,11 @@ __device__ __forceinline__ void edge_traces_sf(const double *cj, const double *e
       const int j = d * (d + 1) / 2 + b;
       const double cv = cj[j];
       t0 = fma(eF0[j * NE + k], cv, t0);
-      y[d - b] = fma(eChi[j * NE + k], cv, y[d - b]);
+      if ((d - b) & 1) od = fma(eChi[j * NE + k], cv, od);
+      else ev = fma(eChi[j * NE + k], cv, ev);
     }
-  t1 = y[0];
-  t2 = y[0];
-#pragma unroll
-  for (int a = 1; a < ND; ++a) {
-    t1 += y[a];
-    t2 = (a & 1) ? t2 - y[a] : t2 + y[a];
-  }
+  t1 = ev + od;
+  t2 = ev - od;
 }
 
 // 1/x for a positive normal x: Newton-Raphson refinement r <- r + r (1 - x r) of
