@@ -209,16 +209,16 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
         const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
         const double *cm = sC + (el * M + m) * NP;
         double w[ND];
-  #pragma unroll
+#pragma unroll
         for (int a = 0; a < ND; ++a) w[a] = 0.0;
-  #pragma unroll
+#pragma unroll
         for (int d = 0; d <= P; ++d)
-  #pragma unroll
+#pragma unroll
           for (int b = 0; b <= d; ++b) {
             const int j = d * (d + 1) / 2 + b;
             w[d - b] = fma(sChi[j * ND + ib], cm[j], w[d - b]);
           }
-  #pragma unroll
+#pragma unroll
         for (int a = 0; a < ND; ++a) sX[((el * ND + a) * ND + ib) * 8 + m] = w[a];
       }
       __syncthreads();
@@ -226,12 +226,14 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
       // volume points: U = sum_a P_a W; Euler flux; Ha, Hb
       for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
         const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
-        double U[M] = {0.0, 0.0, 0.0, 0.0};
-  #pragma unroll
-        for (int a = 0; a < ND; ++a) {
+        // P_0 = 1: the a = 0 term is W(0, ib) itself
+        const double *w0 = sX + ((el * ND) * ND + ib) * 8;
+        double U[M] = {w0[0], w0[1], w0[2], w0[3]};
+#pragma unroll
+        for (int a = 1; a < ND; ++a) {
           const double pa = sPa[a * ND + ia];
           const double *w = sX + ((el * ND + a) * ND + ib) * 8;
-  #pragma unroll
+#pragma unroll
           for (int m = 0; m < M; ++m) U[m] += pa * w[m];
         }
         double Ha[M], Hb[M];
@@ -239,35 +241,63 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
           double Gr[M], Gs[M];
           ref_flux(U, geo + (size_t)(e0 + el) * GEO, gamma, err, Gr, Gs);
           const double half = sHalf[ia];
-  #pragma unroll
+#pragma unroll
           for (int m = 0; m < M; ++m) {
             Ha[m] = fma(half, Gs[m], Gr[m]);
             Hb[m] = Gs[m];
           }
         } else {
-  #pragma unroll
+#pragma unroll
           for (int m = 0; m < M; ++m) { Ha[m] = 0.0; Hb[m] = 0.0; }
         }
         double *h = sH + (size_t)i * 8;
-  #pragma unroll
+#pragma unroll
         for (int m = 0; m < M; ++m) { h[m] = Ha[m]; h[4 + m] = Hb[m]; }
       }
       __syncthreads();
 
-      // Xa(a, ib) = sum_ia Ha wa P_a', Xb(a, ib) = sum_ia Hb wa P_a
-      for (int i = threadIdx.x; i < EB * ND * ND; i += blockDim.x) {
-        const int el = i / (ND * ND), a = (i / ND) % ND, ib = i % ND;
-        double xa[M] = {0.0, 0.0, 0.0, 0.0}, xb[M] = {0.0, 0.0, 0.0, 0.0};
-  #pragma unroll
-        for (int ia = 0; ia < ND; ++ia) {
-          const double dp = sdPaW[a * ND + ia], pa = sPaW[a * ND + ia];
-          const double *h = sH + ((el * NQ) + ib * ND + ia) * 8;
-  #pragma unroll
-          for (int m = 0; m < M; ++m) { xa[m] += h[m] * dp; xb[m] += h[4 + m] * pa; }
+      if constexpr (P <= 4) {
+        // Xa(a, ib) = sum_ia Ha wa P_a', Xb(a, ib) = sum_ia Hb wa P_a; one item per
+        // (element, ib, variable) runs over every a, so that Xa(0, ib) = 0 (P_0' = 0)
+        // costs no arithmetic
+        for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
+          const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
+          double xa[ND], xb[ND];
+#pragma unroll
+          for (int a = 0; a < ND; ++a) { xa[a] = 0.0; xb[a] = 0.0; }
+#pragma unroll
+          for (int ia = 0; ia < ND; ++ia) {
+            const double *h = sH + ((el * NQ) + ib * ND + ia) * 8;
+            const double ha = h[m], hb = h[4 + m];
+#pragma unroll
+            for (int a = 1; a < ND; ++a) xa[a] = fma(ha, sdPaW[a * ND + ia], xa[a]);
+#pragma unroll
+            for (int a = 0; a < ND; ++a) xb[a] = fma(hb, sPaW[a * ND + ia], xb[a]);
+          }
+#pragma unroll
+          for (int a = 0; a < ND; ++a) {
+            double *x = sX + ((el * ND + a) * ND + ib) * 8;
+            x[m] = xa[a];
+            x[4 + m] = xb[a];
+          }
         }
-        double *x = sX + (size_t)i * 8;
-  #pragma unroll
-        for (int m = 0; m < M; ++m) { x[m] = xa[m]; x[4 + m] = xb[m]; }
+      } else {
+        // p = 5: one item per (element, a, ib) for all four variables (the
+        // per-variable form above would spill at this size)
+        for (int i = threadIdx.x; i < EB * ND * ND; i += blockDim.x) {
+          const int el = i / (ND * ND), a = (i / ND) % ND, ib = i % ND;
+          double xa[M] = {0.0, 0.0, 0.0, 0.0}, xb[M] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+          for (int ia = 0; ia < ND; ++ia) {
+            const double dp = sdPaW[a * ND + ia], pa = sPaW[a * ND + ia];
+            const double *h = sH + ((el * NQ) + ib * ND + ia) * 8;
+#pragma unroll
+            for (int m = 0; m < M; ++m) { xa[m] += h[m] * dp; xb[m] += h[4 + m] * pa; }
+          }
+          double *x = sX + (size_t)i * 8;
+#pragma unroll
+          for (int m = 0; m < M; ++m) { x[m] = xa[m]; x[4 + m] = xb[m]; }
+        }
       }
       __syncthreads();
 
