@@ -86,6 +86,14 @@ __device__ __forceinline__ int mode_a(int j) {
   return d - (j - d * (d + 1) / 2);
 }
 
+// the r-th mode (in mode order) whose first index a is >= 1: degree d holds d of
+// them (b = 0 .. d-1), so it lies in the degree d with d(d-1)/2 <= r < d(d+1)/2
+__device__ __forceinline__ int mode_a_ge1(int r) {
+  int d = 1;
+  while (d * (d + 1) / 2 <= r) ++d;
+  return d * (d + 1) / 2 + (r - d * (d - 1) / 2);
+}
+
 template <int P, int NE, int Q>
 __global__ void __launch_bounds__(kThreads, 2)
 k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
@@ -303,9 +311,28 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 
     }
 
-    // modes: V_j + lifted edge fluxes, 1/det J, stage update
+    // modes: V_j + lifted edge fluxes, 1/det J, stage update.  Sum-factorised:
+    // the items of the modes with a >= 1 come first and those of the modes with
+    // a = 0 (b = d) last, so that warps take one branch of the projection (for
+    // a = 0, Xa(0, .) = 0 and only the Xb term is formed)
     for (int i = threadIdx.x; i < EB * NP; i += blockDim.x) {
-      const int el = i / NP, j = i - el * NP, a = mode_a(j);
+      int el, j;
+      if constexpr (S::DIRECT) {
+        el = i / NP;
+        j = i - el * NP;
+      } else {
+        constexpr int NB = NP - ND;                   // modes with a >= 1
+        if (i < EB * NB) {
+          el = i / NB;
+          j = mode_a_ge1(i - el * NB);
+        } else {
+          const int i2 = i - EB * NB;
+          el = i2 / ND;
+          const int d = i2 - el * ND;
+          j = d * (d + 1) / 2 + d;
+        }
+      }
+      const int a = mode_a(j);
       double acc[M] = {0.0, 0.0, 0.0, 0.0};
       if constexpr (S::DIRECT) {
 #pragma unroll
@@ -315,13 +342,21 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 #pragma unroll
           for (int m = 0; m < M; ++m) acc[m] = fma(ds, h[4 + m], fma(dr, h[m], acc[m]));
         }
-      } else {
+      } else if (a > 0) {
 #pragma unroll
         for (int ib = 0; ib < ND; ++ib) {
           const double ch = sChiA[j * ND + ib], dch = sdChiB[j * ND + ib];
           const double *x = sX + ((el * ND + a) * ND + ib) * 8;
 #pragma unroll
           for (int m = 0; m < M; ++m) acc[m] = fma(dch, x[4 + m], fma(ch, x[m], acc[m]));
+        }
+      } else {
+#pragma unroll
+        for (int ib = 0; ib < ND; ++ib) {
+          const double dch = sdChiB[j * ND + ib];
+          const double *x = sX + (el * ND * ND + ib) * 8;
+#pragma unroll
+          for (int m = 0; m < M; ++m) acc[m] = fma(dch, x[4 + m], acc[m]);
         }
       }
       {
