@@ -125,6 +125,8 @@ def _src_hash(*names) -> str:
 TRAFFIC = {
     # k_element_sf<3,4,0>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
     "4299d84dc7600e00": 77149696 + 40798464,
+    # k_element_sf<3,4,12>: the same launch on the symmetric volume rule (--vol-rule symmetric)
+    "4299d84dc7600e00:symmetric": 77157888 + 42121728,
 }
 
 
