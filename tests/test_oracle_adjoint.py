@@ -49,10 +49,13 @@ def test_lax_friedrichs_jacobians_fd(oracle_mod):
         assert np.abs(fr - Jr).max() < 1e-7 * max(1, np.abs(Jr).max())
 
 
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
 @pytest.mark.parametrize("p", [1, 2])
-def test_rhs_jacobian_transpose(oracle_mod, p):
+def test_rhs_jacobian_transpose(oracle_mod, p, rule):
+    """Central-difference Jacobian of the RHS against the reverse sweep, on both
+    volume rules (the sweep's volume term runs over whatever rule is installed)."""
     mesh = I.periodic_mesh(3)
-    o = oracle_mod.OracleDG.from_mesh(mesh, p)
+    o = oracle_mod.OracleDG.from_mesh(mesh, p, vol_rule=rule)
     c = _rough(o, mesh, 7)
     n = c.size
     eps = 1e-6
