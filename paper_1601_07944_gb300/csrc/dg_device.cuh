@@ -37,27 +37,43 @@ constexpr int kThreads = 256;
 // Edge traces of one variable at edge point k of the three reference faces,
 // factorised on the collapsed coordinates (face 0: alpha = xi, beta = -1;
 // face 1: alpha = 1, beta = xi; face 2: alpha = -1, beta = -xi):
-//   t0 = T0_k = sum_j phi_j(face 0, k) c_j,
+//   t0 = T0_k = sum_a P_a(xi_k) Z_a,  Z_a = sum_b chi_ab(-1) c_ab,
 //   t1 = T1_k = sum_a Y_a(xi_k),  t2 = T2_{NE-1-k} = sum_a (-1)^a Y_a(xi_k),
 //   Y_a(xi) = sum_b chi_ab(xi) c_ab,
-// formed as t1 = E + O and t2 = E - O from the sums over the modes of even and of
-// odd first index, E = sum_{a even} Y_a and O = sum_{a odd} Y_a (one FMA per mode
-// into one of two accumulators, then two additions).
-// cj: the N_p coefficients; eF0 = phi_j(face 0, k) and eChi = chi_j(xi_k), both
-// [N_p][NE].  Every kernel that writes traces calls this, so traces of the same
-// state agree bit for bit whichever kernel wrote them.
+// with t1 = E + O and t2 = E - O formed from the sums over the modes of even and
+// of odd first index, E = sum_{a even} Y_a and O = sum_{a odd} Y_a (one FMA per
+// mode into one of two accumulators, then two additions).
+// face0_z forms the Z_a of a coefficient set (they do not depend on k);
+// edge_traces_sf takes them with cj, the N_p coefficients; ePa = P_a(xi_k)
+// [ND][NE], eChi = chi_j(xi_k) [N_p][NE], eChiM1 = chi_j(-1) [N_p].  Every kernel
+// that writes traces goes through these two, in this order of operations, so
+// traces of the same state agree bit for bit whichever kernel wrote them.
+template <int P>
+__device__ __forceinline__ void face0_z(const double *cj, const double *eChiM1, double z[P + 1]) {
+#pragma unroll
+  for (int a = 0; a <= P; ++a) z[a] = 0.0;
+#pragma unroll
+  for (int d = 0; d <= P; ++d)
+#pragma unroll
+    for (int b = 0; b <= d; ++b) {
+      const int j = d * (d + 1) / 2 + b;
+      z[d - b] = fma(eChiM1[j], cj[j], z[d - b]);
+    }
+}
+
 template <int P, int NE>
-__device__ __forceinline__ void edge_traces_sf(const double *cj, const double *eF0, const double *eChi, int k,
-                                               double &t0, double &t1, double &t2) {
+__device__ __forceinline__ void edge_traces_sf(const double *cj, const double *z, const double *ePa,
+                                               const double *eChi, int k, double &t0, double &t1, double &t2) {
   double ev = 0.0, od = 0.0;
   t0 = 0.0;
+#pragma unroll
+  for (int a = 0; a <= P; ++a) t0 = fma(ePa[a * NE + k], z[a], t0);
 #pragma unroll
   for (int d = 0; d <= P; ++d)
 #pragma unroll
     for (int b = 0; b <= d; ++b) {
       const int j = d * (d + 1) / 2 + b;
       const double cv = cj[j];
-      t0 = fma(eF0[j * NE + k], cv, t0);
       if ((d - b) & 1) od = fma(eChi[j * NE + k], cv, od);
       else ev = fma(eChi[j * NE + k], cv, ev);
     }

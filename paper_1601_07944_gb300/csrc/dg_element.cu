@@ -51,7 +51,7 @@ struct SfCfg {
   // then (in place) the LW sums of the factorised lift
   static constexpr int LW = ND + 2 * NE;
   static constexpr int RS = NF > LW ? NF : LW;
-  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 3 * NP * NE + ND * NE + NP + (DIRECT ? 3 * NP * NQ : 0);
+  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 2 * NP * NE + 2 * ND * NE + NP + (DIRECT ? 3 * NP * NQ : 0);
   // per element: the sum-factorisation buffer (8 ND^2), or for the direct form
   // the new state (its point buffer is read until the last mode is done)
   static constexpr int XS = DIRECT ? M * NP : 8 * ND * ND;
@@ -114,8 +114,8 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   double *sEWChi = sEChi + NP * NE;    // [NP][NE]   omega_k chi_j(xi_k)
   double *sEWPa = sEWChi + NP * NE;    // [ND][NE]   omega_k P_a(xi_k)
   double *sEChiM1 = sEWPa + ND * NE;   // [NP]       chi_j(-1)
-  double *sEF0 = sEChiM1 + NP;         // [NP][NE]   phi_j at the points of face 0
-  double *sBvT = sEF0 + NP * NE;       // direct form: [NP][NQ] phi_j(r_k)
+  double *sEPa = sEChiM1 + NP;         // [ND][NE]   P_a(xi_k)
+  double *sBvT = sEPa + ND * NE;       // direct form: [NP][NQ] phi_j(r_k)
   double *sDr = sBvT + (S::DIRECT ? NP * NQ : 0);   //  [NQ][NP] w_k d_r phi_j(r_k)
   double *sDs = sDr + (S::DIRECT ? NQ * NP : 0);    //  [NQ][NP] w_k d_s phi_j(r_k)
   double *sC = sDs + (S::DIRECT ? NQ * NP : 0);     // [EB][M][NP]        stage input
@@ -135,7 +135,7 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) { sEChi[i] = tab.EChi[i]; sEWChi[i] = tab.EWChi[i]; }
   for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sEWPa[i] = tab.EWPa[i];
   for (int i = threadIdx.x; i < NP; i += blockDim.x) sEChiM1[i] = tab.EChiM1[i];
-  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) sEF0[i] = tab.BfT[(i / NE) * NF + i % NE];
+  for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sEPa[i] = tab.EPa[i];
   if constexpr (S::DIRECT) {
     for (int i = threadIdx.x; i < NP * NQ; i += blockDim.x) {
       sBvT[i] = tab.BvT[i]; sDr[i] = tab.Dr[i]; sDs[i] = tab.Ds[i];
@@ -408,8 +408,18 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 
     if (trace_out) {
       __syncthreads();
+      // Z_a of the new state (face 0 lies on beta = -1), one item per (element,
+      // variable), in the buffer the modes have finished reading (sX; direct: sH)
+      double *sZ = S::DIRECT ? sH : sX;
+      for (int i = threadIdx.x; i < ecount * M; i += blockDim.x) {
+        double z[ND];
+        face0_z<P>(sO + i * NP, sEChiM1, z);
+#pragma unroll
+        for (int a = 0; a < ND; ++a) sZ[i * ND + a] = z[a];
+      }
+      __syncthreads();
       // edge traces of the new state, one item per (element, variable, edge point k):
-      //   T0_k = sum_j phi_j(face 0, k) c_j,
+      //   T0_k = sum_a P_a(xi_k) Z_a,
       //   T1_k = sum_a Y_a(xi_k),  T2_{NE-1-k} = sum_a (-1)^a Y_a(xi_k),
       //   Y_a(xi) = sum_b chi_ab(xi) c_ab
       for (int i = threadIdx.x; i < ecount * M * NE; i += blockDim.x) {
@@ -417,7 +427,7 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
         const double *cj = sO + (el * M + m) * NP;
         double *dst = trace_out + (size_t)(e0 + el) * NF * M + m;
         double t0, t1, t2;
-        edge_traces_sf<P, NE>(cj, sEF0, sEChi, k, t0, t1, t2);
+        edge_traces_sf<P, NE>(cj, sZ + (el * M + m) * ND, sEPa, sEChi, k, t0, t1, t2);
         dst[k * M] = t0;
         dst[(NE + k) * M] = t1;
         dst[(3 * NE - 1 - k) * M] = t2;

@@ -640,7 +640,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
          oBfT = take(np * nf), oPw = take(nq * np), oVr = take(nq), oVs = take(nq);
   size_t oSPa = take(nd * nd), oSPaW = take(nd * nd), oSdPaW = take(nd * nd), oSChi = take(np * nd),
          oSChiA = take(np * nd), oSdChiB = take(np * nd), oSHalf = take(nd);
-  size_t oEChi = take(np * ne), oEWChi = take(np * ne), oEWPa = take(nd * ne), oEChiM1 = take(np);
+  size_t oEChi = take(np * ne), oEWChi = take(np * ne), oEWPa = take(nd * ne), oEChiM1 = take(np),
+         oEPa = take(nd * ne);
   std::vector<double> tb(off, 0.0);
   for (int k = 0; k < nq; ++k)
     for (int j = 0; j < np; ++j) {
@@ -699,7 +700,10 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   //   chi_j(-1) sum_k omega_k P_a(xi_k) F_k.
   for (int k = 0; k < ne; ++k) {
     const real x = (real)(double)ex[k];      // the edge points are formed from the rounded node
-    for (int a = 0; a < nd; ++a) tb[oEWPa + a * ne + k] = (double)(ew[k] * jacobi_p(a, 0, 0, x));
+    for (int a = 0; a < nd; ++a) {
+      tb[oEWPa + a * ne + k] = (double)(ew[k] * jacobi_p(a, 0, 0, x));
+      tb[oEPa + a * ne + k] = (double)jacobi_p(a, 0, 0, x);
+    }
   }
   for (int j = 0; j < np; ++j) {
     int a, b;
@@ -769,6 +773,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   m->tab.SChiA = T + oSChiA; m->tab.SdChiB = T + oSdChiB; m->tab.SHalf = T + oSHalf;
   m->tab.EChi = T + oEChi; m->tab.EWChi = T + oEWChi; m->tab.EWPa = T + oEWPa;
   m->tab.EChiM1 = T + oEChiM1;
+  m->tab.EPa = T + oEPa;
   // the neighbour across each face; a boundary face adds the element itself
   std::vector<int32_t> elem_nbr(N * 3);
   for (int64_t i = 0; i < N * 3; ++i) elem_nbr[i] = d->nbr[i] >= 0 ? (int32_t)d->nbr[i] : (int32_t)(i / 3);

@@ -55,6 +55,7 @@ struct DevTables {
   double *EWChi; // [NP][NE]   omega_k chi_j(xi_k)
   double *EWPa;  // [ND][NE]   omega_k P_a(xi_k)
   double *EChiM1;// [NP]       chi_j(-1)
+  double *EPa;   // [ND][NE]   P_a(xi_k)
 };
 
 // One Runge-Kutta stage update of the element kernels (their mode 1), with

@@ -39,16 +39,15 @@ namespace {
 // ---------------------------------------------------------------------------
 template <int P, int NE>
 __global__ void __launch_bounds__(kThreads)
-k_traces(const double *__restrict__ c, double *__restrict__ trace, const double *__restrict__ BfT,
-         const double *__restrict__ EChi, int N) {
+k_traces(const double *__restrict__ c, double *__restrict__ trace, const double *__restrict__ EPa,
+         const double *__restrict__ EChiM1, const double *__restrict__ EChi, int N) {
   using C = Cfg<P, NE>;
-  constexpr int NP = C::NP, NF = C::NF, EB = C::EB;
-  __shared__ double sF0[NP * NE], sChi[NP * NE];
+  constexpr int NP = C::NP, ND = C::ND, NF = C::NF, EB = C::EB;
+  __shared__ double sPa[ND * NE], sChiM1[NP], sChi[NP * NE];
   __shared__ double sC[EB * M * NP];
-  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) {
-    sF0[i] = BfT[(i / NE) * NF + i % NE];      // face 0 columns of phi_j(r_{q,k})
-    sChi[i] = EChi[i];
-  }
+  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) sChi[i] = EChi[i];
+  for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sPa[i] = EPa[i];
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) sChiM1[i] = EChiM1[i];
   const int ntiles = (N + EB - 1) / EB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int e0 = tile * EB;
@@ -60,8 +59,10 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
     __syncthreads();
     for (int i = threadIdx.x; i < ecount * M * NE; i += blockDim.x) {
       const int el = i / (M * NE), m = (i / NE) % M, k = i % NE;
-      double t0, t1, t2;
-      edge_traces_sf<P, NE>(sC + (el * M + m) * NP, sF0, sChi, k, t0, t1, t2);
+      const double *cj = sC + (el * M + m) * NP;
+      double z[ND], t0, t1, t2;
+      face0_z<P>(cj, sChiM1, z);
+      edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t0, t1, t2);
       double *dst = trace + (size_t)(e0 + el) * NF * M + m;
       dst[k * M] = t0;
       dst[(NE + k) * M] = t1;
@@ -326,13 +327,13 @@ __device__ __forceinline__ unsigned long long nonneg_bits(double x) {
 
 __global__ void __launch_bounds__(kThreads)
 k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ elem_nbr,
-           const double *__restrict__ BfT, const double *__restrict__ EChi, double phi1, int64_t N, int *err) {
-  constexpr int P = 1, NE = 2, NP = 3, NF = 6;
-  __shared__ double sF0[NP * NE], sChi[NP * NE];
-  if (threadIdx.x < NP * NE) {
-    sF0[threadIdx.x] = BfT[(threadIdx.x / NE) * NF + threadIdx.x % NE];
-    sChi[threadIdx.x] = EChi[threadIdx.x];
-  }
+           const double *__restrict__ EPa, const double *__restrict__ EChiM1, const double *__restrict__ EChi,
+           double phi1, int64_t N, int *err) {
+  constexpr int P = 1, NE = 2, ND = 2, NP = 3, NF = 6;
+  __shared__ double sPa[ND * NE], sChiM1[NP], sChi[NP * NE];
+  if (threadIdx.x < NP * NE) sChi[threadIdx.x] = EChi[threadIdx.x];
+  if (threadIdx.x < ND * NE) sPa[threadIdx.x] = EPa[threadIdx.x];
+  if (threadIdx.x < NP) sChiM1[threadIdx.x] = EChiM1[threadIdx.x];
   __syncthreads();
   // one item per (element, variable): four independent chains per element, and
   // a warp's loads and trace stores cover contiguous runs
@@ -358,9 +359,10 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
     // of either sign, where the difference is 0; the comparisons below read
     // these as non-negative bit patterns)
     const double up = phi1 * (cmax - cj[0]), dn = phi1 * (cj[0] - cmin);
-    double t[NF];
+    double t[NF], z[ND];
+    face0_z<P>(cj, sChiM1, z);
 #pragma unroll
-    for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
+    for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
     double nbest = 1.0, dbest = 1.0;                                  // ratio 1: no limiting
 #pragma unroll
     for (int x = 0; x < NF; ++x) {
@@ -376,8 +378,9 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
       cj[2] *= alpha;
       ce[1] = cj[1];
       ce[2] = cj[2];
+      face0_z<P>(cj, sChiM1, z);
 #pragma unroll
-      for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, sF0, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
+      for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
     }
     if (trace) {
       double *dst = trace + (size_t)e * NF * M + m;
@@ -395,7 +398,7 @@ int run_traces(const dg_mesh *m, const double *c, double *trace, cudaStream_t s)
   using C = Cfg<P, NE>;
   const int ntiles = (int)((m->N + C::EB - 1) / C::EB);
   const int grid = ntiles < m->num_sms * 4 ? ntiles : m->num_sms * 4;
-  k_traces<P, NE><<<grid, kThreads, 0, s>>>(c, trace, m->tab.BfT, m->tab.EChi, (int)m->N);
+  k_traces<P, NE><<<grid, kThreads, 0, s>>>(c, trace, m->tab.EPa, m->tab.EChiM1, m->tab.EChi, (int)m->N);
   return (int)cudaGetLastError();
 }
 
@@ -434,8 +437,8 @@ int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream) {
   if (m->p != 1 || m->ne != 2) return (int)cudaErrorInvalidValue;
   static int per_sm = 0;
   k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N * M, &per_sm), kThreads, 0,
-               (cudaStream_t)stream>>>(c, trace, m->elem_nbr, m->tab.BfT, m->tab.EChi, m->phi1, m->N,
-                                       m->err_flag);
+               (cudaStream_t)stream>>>(c, trace, m->elem_nbr, m->tab.EPa, m->tab.EChiM1, m->tab.EChi, m->phi1,
+                                       m->N, m->err_flag);
   return (int)cudaGetLastError();
 }
 
