@@ -126,7 +126,8 @@ typedef struct {
     int64_t n_boundary_face;    /* boundary faces (the first ones of the edge list) */
 } dg_mesh_info_t;
 
-/* Validates the mesh (det J > 0; nbr[nbr[e][q]][nbr_face[e][q]] == e and the face
+/* The mesh and its connectivity (Section 4.2; element maps Eq. 2dmap, edge lengths
+ * Eq. len).  Validates the mesh (det J > 0; nbr[nbr[e][q]][nbr_face[e][q]] == e and the face
  * index maps back; the shared edge's endpoints are translates; boundary codes are
  * DG_BC_WALL or DG_BC_STATE), builds the edge list (boundary faces first, in
  * element order, as the paper sorts them), geometry and basis tables on the host
@@ -138,10 +139,12 @@ typedef struct {
 dg_status dg_mesh_create(const dg_mesh_desc *desc, dg_mesh **out);
 
 /* Frees the handle and its device memory (synchronises the device first).
- * A NULL handle is accepted. */
+ * A NULL handle is accepted.  (Resource management: no passage of the paper.) */
 dg_status dg_mesh_destroy(dg_mesh *mesh);
 
-/* Sizes of the discretisation. */
+/* Sizes of the discretisation (N_p of Eq. np, the volume and edge rules of
+ * Sections 4.3.2-4.3.3, the edge count of Section 4.2).  info: HOST, written on
+ * DG_OK.  Errors: DG_EINVAL (null pointers). */
 dg_status dg_mesh_info(const dg_mesh *mesh, dg_mesh_info_t *info);
 
 /* Physical points of the boundary faces' quadrature points (Eq. 1dmap at the
@@ -150,7 +153,8 @@ dg_status dg_mesh_info(const dg_mesh *mesh, dg_mesh_info_t *info);
  * counter-clockwise direction along the face.  Asynchronous. */
 dg_status dg_boundary_points(const dg_mesh *mesh, double *xy, void *stream);
 
-/* The state prescribed on the DG_BC_STATE faces: u[n_boundary_face][n_edge_pts][4]
+/* The state prescribed on the DG_BC_STATE faces (Algorithm 2's ghost state for
+ * Dirichlet and far-field boundaries, Section 4.3.3): u[n_boundary_face][n_edge_pts][4]
  * conserved variables at the points of dg_boundary_points (DEVICE; entries of
  * wall faces are not read), copied into the mesh.  Required before dg_rhs or a
  * time step on a mesh with DG_BC_STATE faces (DG_EINVAL otherwise); the state is
@@ -183,7 +187,7 @@ dg_status dg_project_ic(dg_mesh *mesh, const double *u, double *c, void *stream)
  * Asynchronous. */
 dg_status dg_rhs(dg_mesh *mesh, const double *c, double *r, dg_precision prec, void *stream);
 
-/* Same result as dg_rhs, for callers that cannot allocate device memory when they
+/* Same result as dg_rhs (Eq. 2ddg0, Algorithms 1-3), for callers that cannot allocate device memory when they
  * call it (for example a host whose device memory is all reserved by another
  * allocator, or a time-critical loop that must not allocate).  The paper has no
  * counterpart: this is a service of the library, not a step of the method.
@@ -200,7 +204,9 @@ dg_status dg_rhs(dg_mesh *mesh, const double *c, double *r, dg_precision prec, v
  * [N][4][N_p], must not alias.  Asynchronous. */
 dg_status dg_rhs_noalloc(dg_mesh *mesh, const double *c, double *r, dg_precision prec, void *stream);
 
-/* nsteps steps of the three-stage SSP Runge-Kutta method (Shu-Osher form),
+/* Time integration of Eq. 2ddg0 (Section 4.3.1; the paper uses classic RK2/RK4,
+ * this entry point the SSP method, dg_rk_step_method the paper's): nsteps steps
+ * of the three-stage SSP Runge-Kutta method (Shu-Osher form),
  *   u1 = u + dt L(u),  u2 = 3/4 u + 1/4 (u1 + dt L(u1)),
  *   u <- 1/3 u + 2/3 (u2 + dt L(u2)),
  * in place on c (DEVICE [N][4][N_p]).  The stage accumulation is float64 in every
@@ -241,13 +247,15 @@ dg_status dg_limit(dg_mesh *mesh, double *c, void *stream);
  * dg_adjoint_step).  Off by default.  Errors: DG_EINVAL if enable and p != 1. */
 dg_status dg_set_limiter(dg_mesh *mesh, int enable);
 
-/* Same as dg_rk_step with c in HOST memory (pinned memory gives the fastest
- * copies): copies c to the device, takes nsteps steps and copies the result back
- * into c.  Synchronous. */
+/* Same as dg_rk_step (Section 4.3.1) with c in HOST memory (pinned memory gives
+ * the fastest copies): copies c to the device, takes nsteps steps and copies the
+ * result back into c.  Errors as dg_rk_step, and DG_ENOMEM if the device copy of
+ * the state cannot be allocated (first call on the handle).  Synchronous. */
 dg_status dg_rk_step_host(dg_mesh *mesh, double *c_host, double dt, int nsteps,
                           dg_precision prec, void *stream);
 
-/* Discrete adjoint of dg_rhs (float64): out = (dR/dc)^T lam, the transpose of the
+/* Discrete adjoint of dg_rhs (float64; the transpose, step by step, of Eq. 2ddg0
+ * and Algorithms 1-3 -- the paper has no adjoint): out = (dR/dc)^T lam, the transpose of the
  * RHS Jacobian at c applied to lam, taken backwards through the edge traces,
  * the Lax-Friedrichs flux (same kink conventions as dg_adjoint_step; on a
  * boundary face through the ghost state: a wall's ghost is the reflected trace,
@@ -256,7 +264,8 @@ dg_status dg_rk_step_host(dg_mesh *mesh, double *c_host, double dt, int nsteps,
  * Asynchronous. */
 dg_status dg_rhs_adjoint(dg_mesh *mesh, const double *c, const double *lam, double *out, void *stream);
 
-/* Discrete adjoint of one SSP-RK3 step (float64): given the state c_n at the start
+/* Discrete adjoint of one SSP-RK3 step (float64; the transpose of dg_rk_step's
+ * stages, Section 4.3.1, and of dg_rhs_adjoint's RHS): given the state c_n at the start
  * of the step and lam_np1 = dJ/dc_{n+1}, writes lam_n = dJ/dc_n = (d c_{n+1}/d c_n)^T
  * lam_np1.  The stages are recomputed from c_n.  At a tie of the two wave speeds in
  * alpha the derivative follows the left trace (at a wall the two always tie), and
@@ -273,7 +282,8 @@ dg_status dg_adjoint_step(dg_mesh *mesh, const double *c_n, double dt, const dou
  * p <= 0 at a point.  Synchronous. */
 dg_status dg_stable_dt(dg_mesh *mesh, const double *c, double cfl, double *dt_out, void *stream);
 
-/* Domain integrals of the conserved variables,
+/* Domain integrals of the conserved variables (Section 2: the basis of Eq. np is
+ * orthonormal with phi_1 = sqrt(2) constant),
  *   T_m = sum_e int_{Omega_e} U_m = sum_e det J_e c[e][m][0] / sqrt(2)
  * (only the constant mode has a non-zero mean), as a fixed-order float64
  * reduction, so repeated calls give bitwise equal results.  c: DEVICE.
@@ -294,24 +304,28 @@ enum {
     DG_NKINDS = 8
 };
 
-/* When enable != 0, every kernel this library launches for the mesh is
- * bracketed by a pair of CUDA events recorded on the launch's own stream.
- * Enabling or disabling clears the accumulated times. */
+/* Per-kernel timing, for the kernel runtime distribution of Section 6.1: when
+ * enable != 0, every kernel this library launches for the mesh is bracketed by a
+ * pair of CUDA events recorded on the launch's own stream.  Enabling or
+ * disabling clears the accumulated times.  Errors: DG_EINVAL (null mesh). */
 dg_status dg_set_timing(dg_mesh *mesh, int enable);
 
-/* Waits for the recorded events and adds their durations, per kernel kind, to
- * ms[DG_NKINDS] and launches[DG_NKINDS] (HOST arrays, overwritten with the
- * totals since timing was enabled).  Synchronous. */
+/* The runtime distribution of Section 6.1: waits for the recorded events and adds
+ * their durations, per kernel kind, to ms[DG_NKINDS] and launches[DG_NKINDS] (HOST
+ * arrays, overwritten with the totals since timing was enabled).  Errors:
+ * DG_EINVAL (null pointers), DG_ECUDA.  Synchronous. */
 dg_status dg_kernel_times(dg_mesh *mesh, double ms[8], int64_t launches[8]);
 
-/* Measures the device's sustained fused multiply-add rate in float64 and
- * float32 (TFLOP/s, 2 flops per FMA) with a register-resident FMA chain over
- * every SM, timed with CUDA events on stream.  Either output may be NULL.
- * Synchronous; allocates a small scratch buffer. */
+/* The arithmetic peak that Section 6.4's throughput figures are measured against:
+ * the device's sustained fused multiply-add rate in float64 and float32
+ * (TFLOP/s, 2 flops per FMA) with a register-resident FMA chain over every SM,
+ * timed with CUDA events on stream.  Either output may be NULL.  Errors:
+ * DG_ECUDA (including a failed scratch allocation).  Synchronous; allocates a
+ * small scratch buffer. */
 dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stream);
 
-/* Synchronises stream and reports device-side failures recorded since the last
- * call: DG_EMESH if a kernel of a library built with DG_DEBUG read a connectivity
+/* Failure detection (no passage of the paper): synchronises stream and reports
+ * device-side failures recorded since the last call: DG_EMESH if a kernel of a library built with DG_DEBUG read a connectivity
  * index out of range (it then used index 0 instead; other builds do not check);
  * DG_ETIMEOUT if a bounded wait of the mixed-precision kernels expired (the
  * kernel then skipped its remaining work and released its resources);
@@ -320,8 +334,8 @@ dg_status dg_probe_fma_rate(double *fp64_tflops, double *fp32_tflops, void *stre
  * is cleared.  Synchronous. */
 dg_status dg_device_status(dg_mesh *mesh, void *stream);
 
-/* Device self-check of two arithmetic helpers the kernels use to spare the
- * narrow float64 pipe: on 2^20 values over the float32 normal range (both signs,
+/* Device self-check (no passage of the paper) of two arithmetic helpers the
+ * kernels use to spare the narrow float64 pipe: on 2^20 values over the float32 normal range (both signs,
  * exact rounding ties, zeros) it counts
  *   mismatches[0]: integer float64 -> float32 conversions (round to nearest even)
  *                  that differ bit for bit from the hardware conversion,
@@ -333,8 +347,10 @@ dg_status dg_self_test(int64_t mismatches[3], void *stream);
 /* Message for the last failing call on this thread ("" if none). */
 const char *dg_last_error(void);
 
-/* Host-only (needs no GPU): the reference rules and basis tables this library
- * uses for degree p with ne edge points.  Any pointer may be NULL.
+/* Host-only (needs no GPU): the reference rules (the collapsed volume grid and
+ * the Gauss-Legendre edge rule of Sections 4.3.2-4.3.3) and the basis tables of
+ * Eq. np this library uses for degree p with ne edge points.  Any pointer may be
+ * NULL.  Errors: DG_EINVAL (p outside 0..8, ne outside 1..16).
  *   vol_r, vol_s, vol_w [nq] with nq = (p+1)^2;  edge_x, edge_w [ne];
  *   phi, dphi_r, dphi_s [nq][N_p] at the volume points;  phi_face [3][ne][N_p]
  *   at the edge points of local faces 0, 1, 2 (edge point order: xi ascending,
@@ -343,8 +359,9 @@ dg_status dg_host_tables(int p, int ne, double *vol_r, double *vol_s, double *vo
                          double *edge_x, double *edge_w, double *phi, double *dphi_r,
                          double *dphi_s, double *phi_face);
 
-/* Host-only (needs no GPU): the volume rule of kind `rule` (dg_vol_rule) for
- * degree p, as dg_mesh_create builds it.  *nq receives the point count (may be
+/* Host-only (needs no GPU): the volume rule of kind `rule` (dg_vol_rule; the
+ * degree-2p rules of Section 4.3.2 with Section 6.1's point counts for
+ * DG_RULE_SYMMETRIC) for degree p, as dg_mesh_create builds it.  *nq receives the point count (may be
  * read first with r = s = w = NULL); r, s, w [*nq] receive the reference points
  * and weights (sum 1/2), and phi [*nq][N_p] the basis at the points (any of them
  * may be NULL).  Symmetric rule point order: the orbits S3, S21, S111 in the
