@@ -611,8 +611,9 @@ int or_volume_rule(const oracle_dg *o, double *r, double *s, double *w)
 
 /* Replaces the volume rule by nq points (r, s) with weights w, and the volume
  * tables by the basis evaluated at those points: the symmetric rules of degree
- * 2p of Section 4.1 in place of the collapsed grid.  Every volume sum of the
- * solver runs over whatever rule is installed.  Returns 0, or 1 on invalid input. */
+ * 2p of Section 4.3.2 (point counts in Section 6.1) in place of the collapsed
+ * grid.  Every volume sum of the solver runs over whatever rule is installed.
+ * Returns 0, or 1 on invalid input. */
 int or_set_volume_rule(oracle_dg *o, int nq, const double *r, const double *s, const double *w)
 {
     if (nq < 1 || nq > 4096) return 1;
