@@ -187,8 +187,8 @@ dg_status dg_project_ic(dg_mesh *mesh, const double *u, double *c, void *stream)
  * Asynchronous. */
 dg_status dg_rhs(dg_mesh *mesh, const double *c, double *r, dg_precision prec, void *stream);
 
-/* Same result as dg_rhs (Eq. 2ddg0, Algorithms 1-3), for callers that cannot allocate device memory when they
- * call it (for example a host whose device memory is all reserved by another
+/* Same result as dg_rhs, for callers that cannot allocate device memory when
+ * they call it (for example a host whose device memory is all reserved by another
  * allocator, or a time-critical loop that must not allocate).  The paper has no
  * counterpart: this is a service of the library, not a step of the method.
  * The call allocates nothing.  Its work space (edge traces and edge fluxes,
@@ -200,8 +200,10 @@ dg_status dg_rhs(dg_mesh *mesh, const double *c, double *r, dg_precision prec, v
  * before any stream capture.  All calls share the one array and it keeps the
  * last call's contents (every slot is written before it is read, so nothing
  * needs clearing); calls that overlap on the GPU, on any stream or thread, race
- * on it.  The current device must be the mesh's device.  c, r: DEVICE
- * [N][4][N_p], must not alias.  Asynchronous. */
+ * on it.  The current device must be the mesh's device.  The cached address
+ * assumes that the device's context is not reset (cudaDeviceReset) while the
+ * library stays loaded.  Its launches are not recorded by dg_set_timing.
+ * c, r: DEVICE [N][4][N_p], must not alias.  Asynchronous. */
 dg_status dg_rhs_noalloc(dg_mesh *mesh, const double *c, double *r, dg_precision prec, void *stream);
 
 /* Time integration of Eq. 2ddg0 (Section 4.3.1; the paper uses classic RK2/RK4,

@@ -52,7 +52,10 @@ extern "C" dg_status dg_rhs_noalloc(dg_mesh *m, const double *c, double *r, dg_p
                          n_trace + n_flux, n_trace, n_flux, kScratchDoubles);
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return dg::set_error(DG_ECUDA, "dg_rhs_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    cudaGetLastError();     // leave no stale error for the next launch check
+    return dg::set_error(DG_ECUDA, "dg_rhs_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+  }
   if (dev != m->device)
     return dg::set_error(DG_EINVAL, "dg_rhs_noalloc: current device %d is not the mesh's device %d", dev, m->device);
   if (dev < 0 || dev >= kMaxDevices) return dg::set_error(DG_EINVAL, "dg_rhs_noalloc: device %d out of range", dev);
@@ -62,8 +65,10 @@ extern "C" dg_status dg_rhs_noalloc(dg_mesh *m, const double *c, double *r, dg_p
     if (!g_scratch_ptr[dev]) {
       double *ptr = nullptr;
       e = cudaGetSymbolAddress((void **)&ptr, g_scratch);
-      if (e != cudaSuccess || !ptr)
+      if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();   // leave no stale error for the next launch check
         return dg::set_error(DG_ECUDA, "dg_rhs_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      }
       g_scratch_ptr[dev] = ptr;
     }
     scratch = g_scratch_ptr[dev];

@@ -99,3 +99,64 @@ def test_mixed_state_vs_fp64(dgmod, p, prec, tol):
     m.device_status()
     A, B = _host(a), _host(b)
     assert np.linalg.norm(B - A) / np.linalg.norm(A) < tol
+
+
+# -- full size: more tiles than resident CTAs ---------------------------------
+# The tensor-core element kernel runs a resident grid (at most 8 CTAs per SM, so
+# at most 1,216 CTAs on 152 SMs) whose CTAs loop over 32-element tiles, loading
+# the next tile's inputs one tile ahead and carrying the mbarrier phase across
+# tiles; the edge-flux kernel gives each block an equal slice of the edges.  The
+# 256^2 (4,096 tiles) and 512^2 (16,384 tiles) meshes make every CTA run many
+# tiles, in the launch configuration the benchmark times.
+
+_ORACLE = {}
+
+
+def _oracle_rhs(oracle_mod, n, p, rule):
+    key = (n, p, rule)
+    if key not in _ORACLE:
+        _ORACLE.clear()
+        mesh = I.periodic_mesh(n)
+        o = oracle_mod.OracleDG.from_mesh(mesh, p, vol_rule=rule)
+        ic = I.vortex if (n, p) == (256, 3) else I.perturbed_vortex
+        c = o.project_ic(ic)
+        ref, vol = o.rhs_and_volume(c)
+        _ORACLE[key] = (mesh, o, ic, c, ref, vol)
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
+@pytest.mark.parametrize("n,p,rule", [(256, 3, "collapsed"), (512, 4, "collapsed"), (256, 3, "symmetric")])
+def test_mixed_full_size_rhs_vs_oracle(dgmod, oracle_mod, n, p, rule, prec):
+    mesh, o, _, c, ref, vol = _oracle_rhs(oracle_mod, n, p, rule)
+    m = dgmod.Mesh.from_mesh(mesh, p, vol_rule=rule)
+    assert (m.N + 31) // 32 > 152 * 8                 # many tiles per CTA
+    got = _host(m.rhs(_dev(c), precision=prec))
+    m.device_status()
+    err = np.linalg.norm(got - ref)
+    assert err <= TOL[prec] * (np.linalg.norm(ref) + np.linalg.norm(vol)), err / np.linalg.norm(ref)
+    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= TOL[prec] * np.abs(vol - ref).max()
+    # the same call again: bit for bit (one writer per output slot, no atomics)
+    assert np.array_equal(got, _host(m.rhs(_dev(c), precision=prec)))
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32x1"])
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+def test_mixed_full_size_step_vs_oracle(dgmod, oracle_mod, rule, prec):
+    """One SSP-RK3 step of the 256^2 p=3 vortex in a tensor-core mode against the
+    oracle's float64 step: the increment c1 - c0 = dt (k1/6 + k2/6 + 2 k3/3) carries
+    each stage's RHS error with weights summing to one, so it is bounded by dt
+    times the RHS bound (twice, for the stages' inputs differing from the
+    oracle's); the state itself within the mode's state bound."""
+    mesh, o, ic, c, ref, vol = _oracle_rhs(oracle_mod, 256, 3, rule)
+    m = dgmod.Mesh.from_mesh(mesh, 3, vol_rule=rule)
+    dt = I.fixed_dt(mesh, ic, 3)
+    want = o.ssp_rk3(c, dt, 1)
+    cd = _dev(c)
+    m.rk_step(cd, dt, 1, precision=prec)
+    m.device_status()
+    got = _host(cd)
+    inc_err = np.linalg.norm((got - c) - (want - c))
+    assert inc_err <= 2 * TOL[prec] * dt * (np.linalg.norm(ref) + np.linalg.norm(vol)), inc_err
+    state_tol = {"tf32x3": 1e-6, "tf32x1": 1e-3}[prec]
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < state_tol
