@@ -342,9 +342,11 @@ dg_status dg_device_status(dg_mesh *mesh, void *stream);
  *   mismatches[0]: integer float64 -> float32 conversions (round to nearest even)
  *                  that differ bit for bit from the hardware conversion,
  *   mismatches[1]: integer float32 -> float64 conversions that differ,
- *   mismatches[2]: Newton-refined reciprocals more than 1 ulp from 1/x.
- * HOST int64_t[3].  Synchronous; allocates 24 bytes. */
-dg_status dg_self_test(int64_t mismatches[3], void *stream);
+ *   mismatches[2]: Newton-refined reciprocals more than 1 ulp from 1/x,
+ *   mismatches[3]: Newton-refined square roots (of the mixed-precision edge
+ *                  flux's sound speeds) more than 1 ulp from sqrt(x).
+ * HOST int64_t[4].  Synchronous; allocates 32 bytes. */
+dg_status dg_self_test(int64_t mismatches[4], void *stream);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char *dg_last_error(void);

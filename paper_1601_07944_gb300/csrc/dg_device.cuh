@@ -101,6 +101,31 @@ __device__ __forceinline__ bool positive_finite(double x) {
   return hi < 0x7FF00000u && (hi | lo) != 0u;      // sign clear, exponent not all ones, not zero
 }
 
+// sqrt(x) for a finite x >= 0 in float64 by Newton-Raphson (Heron) refinement of
+// a float32 estimate r of 1/sqrt(x) (rsqrt.approx.ftz.f32 on x rounded to
+// float32): y = x r, then twice y <- y + (x - y^2) r / 2.  The estimate is good to
+// about 2^-22; the first step leaves a relative error of about 1.5 (2^-22)^2, the
+// second one of about its cube, below float64 rounding (dg_self_test checks the
+// result against the correctly rounded square root: at most 1 ulp apart).  Five
+// float64 operations.  x below the float32 normal range gives 0; x < 0 gives NaN.
+__device__ __forceinline__ double sqrt_nr(double x) {
+  const float xf = f64_to_f32_dev(x);
+  float rf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  if (xf == 0.0f) rf = 0.0f;
+  const double r = f32_to_f64_dev(rf), hr = f32_to_f64_dev(0.5f * rf);
+  double y = x * r;
+  y = fma(fma(-y, y, x), hr, y);
+  return fma(fma(-y, y, x), hr, y);
+}
+
+// max(a, b) of two non-negative float64 values on their bit patterns (integer
+// order equals numeric order there); a NaN with the sign bit clear wins.
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double(ia > ib ? ia : ib);
+}
+
 // Local Lax-Friedrichs flux times the edge's half length l (Eq. len), at one edge
 // point:  out = l F_hat = h (F(Ul).n + F(Ur).n - alpha (Ur - Ul)),  h = l / 2,
 //         alpha = max(|v_l.n| + c_l, |v_r.n| + c_r),  c = sqrt(gamma p / rho).
@@ -109,10 +134,7 @@ __device__ __forceinline__ bool positive_finite(double x) {
 // P = E - |rho u|^2 / (2 rho) = p / (gamma - 1),
 //   h F(U).n = (mn, rho u w + P (gamma-1) s_x, rho v w + P (gamma-1) s_y, (E + (gamma-1) P) w)
 // and h alpha = max(|w_l| + h c_l, |w_r| + h c_r), h c = sqrt(hk P / rho).
-// FAST_ALPHA (mixed-precision modes only): h alpha, a dissipation coefficient, is
-// formed in float32; the fluxes and the jump stay float64.
 // Returns false if either side is non-physical (rho <= 0 or p <= 0, or NaN).
-template <bool FAST_ALPHA = false>
 __device__ __forceinline__ bool lax_friedrichs_edge(const double ul[M], const double ur[M], const FaceGeo &g,
                                                     double gamma, double out[M]) {
   const double g1 = gamma - 1.0;
@@ -121,17 +143,9 @@ __device__ __forceinline__ bool lax_friedrichs_edge(const double ul[M], const do
   const double wL = mL * il, wR = mR * ir;
   const double PL = fma(-0.5 * fma(ul[1], ul[1], ul[2] * ul[2]), il, ul[3]);
   const double PR = fma(-0.5 * fma(ur[1], ur[1], ur[2] * ur[2]), ir, ur[3]);
-  double la;
-  if (FAST_ALPHA) {
-    const float k = f64_to_f32_dev(g.hk);
-    const float aL = fabsf(f64_to_f32_dev(wL)) + sqrtf(k * f64_to_f32_dev(PL) * f64_to_f32_dev(il));
-    const float aR = fabsf(f64_to_f32_dev(wR)) + sqrtf(k * f64_to_f32_dev(PR) * f64_to_f32_dev(ir));
-    la = f32_to_f64_dev(fmaxf(aL, aR));
-  } else {
-    const double aL = fabs(wL) + sqrt(g.hk * PL * il);
-    const double aR = fabs(wR) + sqrt(g.hk * PR * ir);
-    la = fmax(aL, aR);
-  }
+  const double aL = fabs(wL) + sqrt(g.hk * PL * il);
+  const double aR = fabs(wR) + sqrt(g.hk * PR * ir);
+  const double la = fmax(aL, aR);
   double fL[M], fR[M];
   fL[0] = mL;                             fR[0] = mR;
   fL[1] = fma(ul[1], wL, PL * g.gsx);     fR[1] = fma(ur[1], wR, PR * g.gsx);
@@ -139,6 +153,35 @@ __device__ __forceinline__ bool lax_friedrichs_edge(const double ul[M], const do
   fL[3] = fma(g1, PL, ul[3]) * wL;        fR[3] = fma(g1, PR, ur[3]) * wR;
 #pragma unroll
   for (int m = 0; m < M; ++m) out[m] = fma(-la, ur[m] - ul[m], fL[m] + fR[m]);
+  return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(PL) & positive_finite(PR);
+}
+
+// The same flux, float64 throughout, in the form the mixed-precision edge kernel
+// evaluates (about 54 float64 operations per point instead of about 70): the
+// dissipation term moves into the normal velocities, wa = w_l + h alpha and
+// wb = w_r - h alpha, so that
+//   l F_hat = (rho_l wa + rho_r wb,
+//              mx_l wa + mx_r wb + (P_l + P_r) (gamma-1) s_x,
+//              my_l wa + my_r wb + (P_l + P_r) (gamma-1) s_y,
+//              E_l wa + E_r wb + (gamma-1) (P_l w_l + P_r w_r)),
+// (rho w = mn); the square roots of the sound speeds are sqrt_nr, and the larger
+// wave speed is picked on the bit patterns.  The two forms differ by float64
+// rounding only.  Returns false if either side is non-physical.
+__device__ __forceinline__ bool lax_friedrichs_edge_jf(const double ul[M], const double ur[M], const FaceGeo &g,
+                                                       double gamma, double out[M]) {
+  const double g1 = gamma - 1.0;
+  const double il = recip(ul[0]), ir = recip(ur[0]);
+  const double wL = fma(ul[1], g.sx, ul[2] * g.sy) * il, wR = fma(ur[1], g.sx, ur[2] * g.sy) * ir;
+  const double PL = fma(-0.5 * fma(ul[1], ul[1], ul[2] * ul[2]), il, ul[3]);
+  const double PR = fma(-0.5 * fma(ur[1], ur[1], ur[2] * ur[2]), ir, ur[3]);
+  const double aL = fabs(wL) + sqrt_nr(g.hk * PL * il);
+  const double aR = fabs(wR) + sqrt_nr(g.hk * PR * ir);
+  const double la = max_nonneg(aL, aR);
+  const double wa = wL + la, wb = wR - la, Ps = PL + PR;
+  out[0] = fma(ul[0], wa, ur[0] * wb);
+  out[1] = fma(ul[1], wa, fma(ur[1], wb, Ps * g.gsx));
+  out[2] = fma(ul[2], wa, fma(ur[2], wb, Ps * g.gsy));
+  out[3] = fma(ul[3], wa, fma(ur[3], wb, g1 * fma(PL, wL, PR * wR)));
   return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(PL) & positive_finite(PR);
 }
 

@@ -1298,21 +1298,19 @@ extern "C" dg_status dg_device_status(dg_mesh *m, void *stream) {
   return DG_OK;
 }
 
-extern "C" dg_status dg_self_test(int64_t mismatches[3], void *stream) {
+extern "C" dg_status dg_self_test(int64_t mismatches[4], void *stream) {
   if (!mismatches) return fail(DG_EINVAL, "dg_self_test: null argument");
   unsigned long long *bad = nullptr;
-  DG_CUDA(cudaMalloc(&bad, 3 * sizeof(unsigned long long)), "dg_self_test alloc");
+  DG_CUDA(cudaMalloc(&bad, 4 * sizeof(unsigned long long)), "dg_self_test alloc");
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned long long h[3] = {0, 0, 0};
+  unsigned long long h[4] = {0, 0, 0, 0};
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof h, s);
   if (e == cudaSuccess) e = (cudaError_t)dg::launch_convert_check(1 << 20, bad, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, bad, sizeof h, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(bad);
   if (e != cudaSuccess) return cuda_fail(e, "dg_self_test");
-  mismatches[0] = (int64_t)h[0];
-  mismatches[1] = (int64_t)h[1];
-  mismatches[2] = (int64_t)h[2];
+  for (int i = 0; i < 4; ++i) mismatches[i] = (int64_t)h[i];
   return DG_OK;
 }
 

@@ -33,8 +33,9 @@ namespace {
 // Edge flux of the mixed-precision modes, one thread per edge.  The two traces
 // are float32 (exact results of the tensor-core contraction) and are widened
 // exactly; the local Lax-Friedrichs flux is evaluated in float64 at the NE edge
-// points as in k_face (only its dissipation coefficient alpha in float32), with
-// the right element's trace at the reversed point (Eq. edgeint).  Written per
+// points (lax_friedrichs_edge_jf: the flux of k_face, alpha included, in a form
+// with fewer float64 operations), with the right element's trace at the
+// reversed point (Eq. edgeint).  Written per
 // edge: l F_hat at the points rounded to float32 (the lift columns of GEMM 2), and
 // the float64 integral of l F_hat against the constant mode,
 // fmean_m = sum_k omega_k phi_1 l F_hat_{k,m} (Algorithm 2 for j = 1; the
@@ -78,7 +79,7 @@ k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *
         ur[2] = tc::f32_to_f64(b.z); ur[3] = tc::f32_to_f64(b.w);
       }
       double Fh[M];
-      ok &= lax_friedrichs_edge<true>(ul, ur, g, gamma, Fh);
+      ok &= lax_friedrichs_edge_jf(ul, ur, g, gamma, Fh);
       const double w = Lf[k * np];           // omega_k phi_1, the same on the three faces
 #pragma unroll
       for (int m = 0; m < M; ++m) sm[m] = fma(w, Fh[m], sm[m]);
@@ -112,12 +113,16 @@ __global__ void k_convert_check(int n, unsigned long long *bad) {
   const double d_hw = (double)f_hw, d_int = tc::f32_to_f64(f_hw);
   if (__float_as_uint(f_hw) != __float_as_uint(f_int)) atomicAdd(bad, 1ull);
   if (__double_as_longlong(d_hw) != __double_as_longlong(d_int)) atomicAdd(bad + 1, 1ull);
-  // Newton-refined reciprocal against the correctly rounded 1/x: at most 1 ulp apart
+  // Newton-refined reciprocal and square root against the correctly rounded
+  // 1/x and sqrt(x): at most 1 ulp apart
   const double ax = fabs(x);
   if (ax != 0.0) {
     const long long q = __double_as_longlong(1.0 / ax), r = __double_as_longlong(recip(ax));
     const long long d = q > r ? q - r : r - q;
     if (d > 1) atomicAdd(bad + 2, 1ull);
+    const long long qs = __double_as_longlong(sqrt(ax)), rs = __double_as_longlong(sqrt_nr(ax));
+    const long long ds = qs > rs ? qs - rs : rs - qs;
+    if (ds > 1) atomicAdd(bad + 3, 1ull);
   }
 }
 

@@ -5,7 +5,7 @@
  * units, so that the two sets of instantiations compile in parallel).
  *
  * A tile is 32 elements = 128 accumulator rows, row r = 4 e + m (element e,
- * variable m).  Per tile:
+ * variable m); thread r of the CTA owns row r.  Per tile:
  *   GEMM 1  U[128 x NQ]   = C[128 x NP] Phi[NP x NQ]            interpolation
  *           FP32 Euler flux and G = J^tau F at every volume point (SIMT)
  *   GEMM 2  D[128 x NP]   = [G_r | G_s | F_hat] [Dr; Ds; Lf]     projection on
@@ -17,6 +17,21 @@
  * (mode 2 runs GEMM 3 alone on the stage input: the first stage's traces.)
  * The volume rule enters only through its point count Q (0: the collapsed
  * (p+1)^2 grid) and the tables Phi, Dr, Ds built for it on the host.
+ *
+ * Operands.  The A operands of the three GEMMs live in tensor memory: row r of A
+ * is TMEM lane r, so the thread that owns a row writes it with tcgen05.st straight
+ * from its registers (TF32 planes hi and, for 3xTF32, lo; one column per
+ * element along K).  The B operands (the tables, split likewise) sit in shared
+ * memory, K-major without swizzle, written once per CTA.  The accumulator D takes
+ * the first columns of the CTA's TMEM allocation and the A planes the next ones;
+ * GEMM 1's operand shares columns with GEMM 2's (its result has been read back by
+ * the time GEMM 2's operand is written), and GEMM 3's with both.
+ *
+ * Only the flux step moves data between the threads of an element (its four
+ * rows are four lanes of one warp): the interpolated state goes through shared
+ * memory from the row layout [variable][point] to the point layout, and the
+ * reference fluxes back, with warp-level synchronisation only.  The CTA
+ * synchronises three times per tile, before each GEMM is issued.
  */
 #pragma once
 
@@ -34,9 +49,12 @@ namespace {
 constexpr int pad8(int x) { return (x + 7) / 8 * 8; }
 constexpr int pad16(int x) { return (x + 15) / 16 * 16; }
 constexpr int align1k(int x) { return (x + 1023) / 1024 * 1024; }
+constexpr int imax(int a, int b) { return a > b ? a : b; }
+// TMEM is allocated in powers of two of at least 32 columns
+constexpr int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
 constexpr int kTcThreads = 128;
-constexpr int kTmemCols = 64;
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per MMA batch before giving up
+constexpr uint32_t kSuspendNs = 2000;         // suspend-time hint of one mbarrier try
 
 template <int P, int NE, bool X3, int Q>
 struct Tc {
@@ -45,52 +63,76 @@ struct Tc {
   static constexpr int EB = 32, ROWS = 128;
   static constexpr int K1 = pad8(NP), N1 = pad16(NQ), K2 = pad8(2 * NQ + NF), N2 = pad16(NP), N4 = pad16(NF);
   static constexpr int NS = X3 ? 2 : 1;                     // TF32 planes: hi (, lo)
-  static constexpr int A1P = ROWS * K1 * 4, A2P = ROWS * K2 * 4;
+  // TMEM columns: D [0, ND), A hi [ND, ND + K2), A lo [ND + K2, ND + 2 K2)
+  static constexpr int ND = imax(imax(N1, N2), N4);
+  static constexpr int COLS = tmem_cols(ND + NS * K2);
+  static constexpr int PER_SM = 512 / COLS;                   // CTAs whose TMEM fits on one SM
+  // shared memory: B operands (split), then per-warp staging
   static constexpr int B1P = N1 * K1 * 4, B2P = N2 * K2 * 4, B4P = N4 * K1 * 4;
-  static constexpr int oA1 = 0;
-  static constexpr int oA2 = align1k(oA1 + A1P * NS);
-  static constexpr int oB1 = align1k(oA2 + A2P * NS);
+  static constexpr int oB1 = 0;
   static constexpr int oB2 = align1k(oB1 + B1P * NS);
   static constexpr int oB4 = align1k(oB2 + B2P * NS);
   static constexpr int endB = align1k(oB4 + B4P * NS);
-  static constexpr int SU = EB * NQ * M * 4;                 // float [EB][NQ][M]
-  static constexpr bool U_IN_A1 = SU <= A1P * NS;            // reuse GEMM 1's A planes
-  static constexpr int oU = U_IN_A1 ? oA1 : endB;
-  static constexpr int oJ = U_IN_A1 ? endB : endB + SU;      // float [EB][4]  J^tau
-  static constexpr int oBar = oJ + EB * 16;                  // mbarrier, TMEM slot
+  // U staging [EB][SE] floats, point k of element e at e SE + 4 k (its four
+  // variables); SE / 4 is odd, so the row threads' scalar writes hit 32 banks.
+  // The edge traces [NF][4] are staged in the same place.
+  static constexpr int SE4 = imax((NQ & 1) ? NQ : NQ + 1, (NF & 1) ? NF : NF + 1);
+  static constexpr int SE = 4 * SE4;
+  static constexpr int oU = endB;
+  // reference-flux staging [EB][M][RG] floats (row 4 e + m, column k of G_r,
+  // NQ + k of G_s); RG odd
+  static constexpr int RG = (2 * NQ) | 1;
+  static constexpr int oG = oU + EB * SE * 4;
+  static constexpr int oJ = oG + EB * M * RG * 4;             // float [EB][4]  J^tau
+  static constexpr int oBar = (oJ + EB * 16 + 15) / 16 * 16;  // mbarrier, TMEM slot
   static constexpr int SMEM = oBar + 16;
-  // the new state and the new traces are staged for coalesced stores in GEMM 2's
-  // A planes, which are free once GEMM 2 has completed
-  static_assert(EB * M * NP * 8 <= A2P * NS && EB * NF * M * 4 <= A2P * NS, "staging");
-  static_assert(N1 <= kTmemCols && N2 <= kTmemCols && N4 <= kTmemCols, "TMEM columns");
+  static_assert(K1 <= K2, "GEMM 1's operand shares GEMM 2's columns");
+  static_assert(N1 <= 256 && N2 <= 256 && N4 <= 256, "MMA N");
+  static_assert(ND + NS * K2 <= 512, "TMEM columns");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 // writes v (rounded to TF32, and its TF32 remainder for the split product) at
-// (row, k) of a K-major operand with ktot columns
+// (row, k) of a K-major shared-memory operand with ktot columns (the B tables)
 template <bool X3>
-__device__ __forceinline__ void put_at(unsigned char *base, int plane_bytes, int off, float v) {
+__device__ __forceinline__ void put(unsigned char *base, int plane_bytes, int row, int k, int ktot, float v) {
+  const int off = tc::kmaj(row, k, ktot);
   const float hi = tc::to_tf32(v);
   *reinterpret_cast<float *>(base + off) = hi;
   if (X3) *reinterpret_cast<float *>(base + plane_bytes + off) = tc::to_tf32(v - hi);
 }
-template <bool X3>
-__device__ __forceinline__ void put(unsigned char *base, int plane_bytes, int row, int k, int ktot, float v) {
-  put_at<X3>(base, plane_bytes, tc::kmaj(row, k, ktot), v);
+
+// this thread's TMEM lane, columns [c0, c0 + N) (N a multiple of 8) <- v split
+// into TF32 planes: hi at tHi, the remainder lo at tLo (3xTF32)
+template <bool X3, int N>
+__device__ __forceinline__ void st_split(uint32_t tHi, uint32_t tLo, const float *v) {
+#pragma unroll
+  for (int c = 0; c < N; c += 8) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      hi[i] = tc::tf32_bits(__float_as_uint(v[c + i]));
+      if (X3) lo[i] = tc::tf32_bits(__float_as_uint(v[c + i] - __uint_as_float(hi[i])));
+    }
+    tc::st8(tHi + (uint32_t)c, hi);
+    if (X3) tc::st8(tLo + (uint32_t)c, lo);
+  }
 }
 
-// D (TMEM) = sum over k-steps of A B^T, split products when X3
+// D (TMEM) = sum over k-steps of A B^T with A in TMEM (columns aHi, aLo) and B in
+// shared memory; split products a_lo b_hi + a_hi b_lo + a_hi b_hi when X3
 template <bool X3, int KT>
-__device__ __forceinline__ void gemm(uint32_t d, uint32_t a, int a_plane, uint32_t b, int b_plane, uint32_t idesc) {
+__device__ __forceinline__ void gemm_ts(uint32_t d, uint32_t aHi, uint32_t aLo, uint32_t b, int b_plane,
+                                        uint32_t idesc) {
 #pragma unroll
   for (int s = 0; s < KT / 8; ++s) {
-    const uint32_t off = (uint32_t)s * 256u;
+    const uint32_t off = (uint32_t)s * 256u, ac = (uint32_t)s * 8u;
     if (X3) {
-      tc::mma_tf32(d, tc::desc(a + a_plane + off, KT), tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
-      tc::mma_tf32(d, tc::desc(a + off, KT), tc::desc(b + b_plane + off, KT), idesc, 1u);
-      tc::mma_tf32(d, tc::desc(a + off, KT), tc::desc(b + off, KT), idesc, 1u);
+      tc::mma_tf32_ts(d, aLo + ac, tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
+      tc::mma_tf32_ts(d, aHi + ac, tc::desc(b + b_plane + off, KT), idesc, 1u);
+      tc::mma_tf32_ts(d, aHi + ac, tc::desc(b + off, KT), idesc, 1u);
     } else {
-      tc::mma_tf32(d, tc::desc(a + off, KT), tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
+      tc::mma_tf32_ts(d, aHi + ac, tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
     }
   }
 }
@@ -105,7 +147,8 @@ __device__ __forceinline__ void tmem_row(uint32_t taddr, float *v) {
 // float32 reference flux G = J^tau F at one point (Euler flux, Eq. euler)
 __device__ __forceinline__ bool ref_flux_f32(const float U[M], const float *jt, float gamma, float Gr[M],
                                              float Gs[M]) {
-  const float inv = 1.0f / U[0];
+  float inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(U[0]));
   const float u = U[1] * inv, v = U[2] * inv;
   const float p = (gamma - 1.0f) * (U[3] - 0.5f * (U[1] * u + U[2] * v));
   float F1[M], F2[M];
@@ -124,28 +167,26 @@ __device__ __forceinline__ bool ref_flux_f32(const float U[M], const float *jt, 
 // OUT2: the stage also writes the classical RK4's running sum (StageUpdate::out2);
 // a separate instantiation, so that the kernels without it keep their registers.
 template <int P, int NE, bool X3, bool OUT2, int Q>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, Tc<P, NE, X3, Q>::PER_SM < 4 ? Tc<P, NE, X3, Q>::PER_SM : 4)
 k_element_tc(const double *c, const double *u0, double *out, float *__restrict__ trace_out,
              const float *__restrict__ fhat, const double *__restrict__ fmean, const double *__restrict__ geo,
              const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
              double gamma, int *err) {
   using T = Tc<P, NE, X3, Q>;
-  constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB;
+  constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB, SE = T::SE, RG = T::RG;
   constexpr int K1 = T::K1, N1 = T::N1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char *A1 = sm + T::oA1, *A2 = sm + T::oA2, *B1 = sm + T::oB1, *B2 = sm + T::oB2, *B4 = sm + T::oB4;
-  double *sStage = reinterpret_cast<double *>(sm + T::oA2);   // after GEMM 2 only
+  unsigned char *B1 = sm + T::oB1, *B2 = sm + T::oB2, *B4 = sm + T::oB4;
   float *sU = reinterpret_cast<float *>(sm + T::oU);
+  float *sG = reinterpret_cast<float *>(sm + T::oG);
   float *sJ = reinterpret_cast<float *>(sm + T::oJ);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + T::oBar);
   uint32_t *slot = reinterpret_cast<uint32_t *>(sm + T::oBar + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t mbar = tc::smem_u32(bar);
 
-  // ---- once per CTA: zeroed A planes, B operands (split), TMEM, mbarrier ----
-  for (int i = tid; i < (T::A1P * T::NS) / 16; i += kTcThreads) reinterpret_cast<int4 *>(A1)[i] = make_int4(0, 0, 0, 0);
-  for (int i = tid; i < (T::A2P * T::NS) / 16; i += kTcThreads) reinterpret_cast<int4 *>(A2)[i] = make_int4(0, 0, 0, 0);
-  for (int i = tid; i < N1 * K1; i += kTcThreads) {
+  // ---- once per CTA: B operands (split), TMEM, mbarrier ----
+  for (int i = tid; i < T::N1 * K1; i += kTcThreads) {
     const int n = i / K1, k = i - n * K1;
     const double v = (n < NQ && k < NP) ? tab.BvT[k * NQ + n] : 0.0;
     put<X3>(B1, T::B1P, n, k, K1, (float)v);
@@ -165,306 +206,301 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     const double v = (n < NF && k < NP) ? tab.BfT[k * NF + n] : 0.0;
     put<X3>(B4, T::B4P, n, k, K1, (float)v);
   }
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(slot), kTmemCols);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(slot), T::COLS);
   if (tid == 0) tc::mbar_init(mbar, 1);
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);       // this warp's 32 TMEM lanes
-  const uint32_t uA1 = tc::smem_u32(A1), uA2 = tc::smem_u32(A2);
+  const uint32_t tD = tmem + ((uint32_t)(warp * 32) << 16);          // this warp's 32 lanes
+  const uint32_t tHi = tD + (uint32_t)T::ND, tLo = tHi + (uint32_t)K2;
+  const uint32_t aHi = tmem + (uint32_t)T::ND, aLo = aHi + (uint32_t)K2;
   const uint32_t uB1 = tc::smem_u32(B1), uB2 = tc::smem_u32(B2), uB4 = tc::smem_u32(B4);
   const float g32 = (float)gamma;
   const int row = tid, rel = row >> 2, rm = row & 3;                 // accumulator row = 4 e + m
   uint32_t phase = 0;
+  bool failed = false;
 
-  int e0 = 0, ecount = 0;
-  // GEMM 3: edge traces of the state held in A1's planes -> trace_out (float64),
-  // staged through GEMM 2's A planes.  Returns false if the tensor-core wait
-  // expired (recorded in *err).
-  auto traces_of_A1 = [&]() -> bool {
-    if (tid == 0) {
-      gemm<X3, K1>(tmem, uA1, T::A1P, uB4, T::B4P, tc::idesc_tf32(128, N4));
-      tc::commit(mbar);
-    }
-    const bool done = tc::mbar_wait(mbar, phase, kWaitNs);
+  // the rows' tcgen05.st complete and are ordered before the MMA issue
+  auto sync_operands = [&]() {
+    tc::wait_st();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  // waits for the issued MMAs; false if the bounded wait expired (recorded)
+  auto mma_done = [&]() -> bool {
+    const bool done = tc::mbar_wait_sleep(mbar, phase, kWaitNs, kSuspendNs);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {
       if (tid == 0) atomicOr(err, kErrTimeout);
+      failed = true;
       return false;
     }
     tc::fence_after_sync();
-    float *sT = reinterpret_cast<float *>(sStage);
-    {
-      float v[N4];
-      tmem_row<N4>(trow, v);
-#pragma unroll
-      for (int qk = 0; qk < NF; ++qk) sT[(rel * NF + qk) * M + rm] = v[qk];
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // [EB][NF][M] float32 is whole float4s: NF * M is a multiple of 4
-    const float4 *src4 = reinterpret_cast<const float4 *>(sT);
-    float4 *dst4 = reinterpret_cast<float4 *>(trace_out + (size_t)e0 * NF * M);
-    for (int i = tid; i < ecount * NF; i += kTcThreads) dst4[i] = src4[i];
     return true;
+  };
+  // GEMM 3 has completed: edge traces of the state in the A columns [0, K1) ->
+  // trace_out, staged through this warp's part of sU for float4 stores
+  auto store_traces = [&](int e0, bool live) {
+    float v[N4];
+    tmem_row<N4>(tD, v);
+    float *t = sU + rel * SE + rm;
+#pragma unroll
+    for (int qk = 0; qk < NF; ++qk) t[4 * qk] = v[qk];
+    __syncwarp();
+    float4 *dst = reinterpret_cast<float4 *>(trace_out + (size_t)(e0 + rel) * NF * M);
+#pragma unroll
+    for (int i = 0; i < (NF + 3) / 4; ++i) {
+      const int qk = rm + 4 * i;
+      if (qk < NF && live) dst[qk] = *reinterpret_cast<const float4 *>(sU + rel * SE + 4 * qk);
+    }
+    __syncwarp();
   };
 
   const int ntiles = (N + EB - 1) / EB;
-  // Per-row inputs of a tile, loaded one tile ahead: while tile t runs through
-  // its GEMMs and updates, the loads of tile t + gridDim.x are in flight.  The
-  // edge-flux values depend on the edge records, so they are requested later in
-  // the tile than the rest.  The second register set costs resident CTAs where
-  // registers, not shared memory, bound them: at p = 5 it does not fit at all,
-  // and for the 1xTF32 kernels at p = 2 and 4 (small shared memory) the CTAs it
-  // displaces hide more latency than it does (measured); there the loads are
-  // issued at the start of the tile itself.
-  constexpr bool AHEAD = P <= 4 && (X3 || P == 3);
-  struct RowIn {
-    double c[NP], u[NP], s[3], inv;            // s: the three edges' mean-mode integrals
-    double jt;                                 // entry rm of this row's element's J^tau
-    float f[NF];
-    int ef[3];
-  };
   const bool need_u0 = mode == 1 && su.a0 != 0.0;
-  auto load_head = [&](int t, RowIn &r) {
-    const int base = t * EB;
-    const bool lv = t < ntiles && rel < N - base;
-    const size_t o = ((size_t)(base + rel) * M + rm) * NP;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) r.ef[q] = lv && mode != 2 ? elem_face[(size_t)(base + rel) * 3 + q] : 0;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      r.c[j] = lv ? c[o + j] : 0.0;
-      r.u[j] = lv && need_u0 ? u0[o + j] : 0.0;
-    }
-    r.inv = lv && mode != 2 ? geo[(size_t)(base + rel) * GEO + 4] : 0.0;
-    r.jt = lv && mode != 2 ? geo[(size_t)(base + rel) * GEO + rm] : 0.0;
-  };
-  auto load_flux = [&](int t, RowIn &r) {
-    const bool lv = t < ntiles && rel < N - t * EB && mode != 2;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int64_t f = checked(r.ef[q] >> 1, F, err);      // ef = 0 on rows past the mesh
-      const int side = r.ef[q] & 1;
-      r.s[q] = lv ? fmean[(size_t)f * M + rm] : 0.0;
-#pragma unroll
-      for (int k = 0; k < NE; ++k)
-        r.f[q * NE + k] = lv ? fhat[((size_t)f * NE + (side ? NE - 1 - k : k)) * M + rm] : 0.0f;
-    }
-  };
-  static_assert(EB * 4 == kTcThreads, "one J^tau entry per row");
-
-  RowIn cur, nxt;
-  if (AHEAD) { load_head(blockIdx.x, cur); load_flux(blockIdx.x, cur); }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    e0 = tile * EB;
-    ecount = min(EB, N - e0);
+    const int e0 = tile * EB;
+    const int ecount = min(EB, N - e0);
     const bool live = rel < ecount;
-    const int tnext = tile + gridDim.x;
-    if (!AHEAD) { load_head(tile, cur); load_flux(tile, cur); }
-    sJ[row] = tc::f64_to_f32(cur.jt);      // sJ[4 e + i]: entry i of element e's J^tau
-    for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cur.c[k]) : 0.0f);
+    const size_t o = ((size_t)(e0 + rel) * M + rm) * NP;
+    // ---- the stage input: GEMM 1's operand (A columns [0, K1)) ----
+    // (scalar loads and stores of the caller's arrays: they need only the
+    // alignment of a double; a warp's rows are contiguous, so they coalesce)
+    double cv[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) cv[j] = live ? c[o + j] : 0.0;
+    {
+      float v[K1];
+#pragma unroll
+      for (int k = 0; k < K1; ++k) v[k] = k < NP ? __uint_as_float(tc::f64_to_f32_rz_bits(cv[k])) : 0.0f;
+      st_split<X3, K1>(tHi, tLo, v);
+    }
     if (mode == 2) {
       // ---- traces only: GEMM 3 on the stage input ----
-      if (AHEAD) load_head(tnext, nxt);
-      tc::fence_proxy_async();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-      if (!traces_of_A1()) break;
-      __syncthreads();
-      if (AHEAD) cur = nxt;
+      sync_operands();
+      if (tid == 0) {
+        gemm_ts<X3, K1>(tmem, aHi, aLo, uB4, T::B4P, tc::idesc_tf32(128, N4));
+        tc::commit(mbar);
+      }
+      if (!mma_done()) break;
+      store_traces(e0, live);
       continue;
     }
-    // ---- its edge fluxes in the element's orientation and point order: the lift
-    // columns of GEMM 2, and the mean mode's lift in float64 ----
+    // ---- the row's edge fluxes in the element's orientation and point order
+    // (the lift columns of GEMM 2) and their float64 mean-mode integrals ----
+    float fl[NF];
     double sq[3];
+    {
+      const int32_t *efp = elem_face + (size_t)(e0 + rel) * 3;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int side = cur.ef[q] & 1;
-      sq[q] = side ? cur.s[q] : tc::neg_bits(cur.s[q]);
+      for (int q = 0; q < 3; ++q) {
+        const int ef = live ? efp[q] : 0;
+        const int64_t f = checked(ef >> 1, F, err);
+        const int side = ef & 1;
+        const double s = live ? fmean[(size_t)f * M + rm] : 0.0;
+        sq[q] = side ? s : tc::neg_bits(s);
+        const float *fp = fhat + (size_t)f * NE * M + rm;
 #pragma unroll
-      for (int k = 0; k < NE; ++k) {
-        const float v = side ? cur.f[q * NE + k] : -cur.f[q * NE + k];
-        put<X3>(A2, T::A2P, row, 2 * NQ + q * NE + k, K2, v);
+        for (int k = 0; k < NE; ++k) {
+          const float x = live ? fp[(side ? NE - 1 - k : k) * M] : 0.0f;
+          fl[q * NE + k] = side ? x : -x;
+        }
       }
     }
     const double s0 = (sq[0] + sq[1]) + sq[2];
-    for (int qk = 2 * NQ + NF; qk < K2; ++qk) put<X3>(A2, T::A2P, row, qk, K2, 0.0f);
-    if (AHEAD) load_head(tnext, nxt);
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
+    double inv = 0.0;
+    {
+      const double *ge = geo + (size_t)(e0 + rel) * GEO;
+      inv = live ? ge[4] : 0.0;
+      sJ[row] = __uint_as_float(tc::f64_to_f32_rz_bits(live ? ge[rm] : 0.0));
+    }
+    sync_operands();
     // ---- GEMM 1: interpolation to the volume points ----
     if (tid == 0) {
-      gemm<X3, K1>(tmem, uA1, T::A1P, uB1, T::B1P, tc::idesc_tf32(128, N1));
+      gemm_ts<X3, K1>(tmem, aHi, aLo, uB1, T::B1P, tc::idesc_tf32(128, N1));
       tc::commit(mbar);
     }
     // the part of the stage update that does not depend on the RHS, b0 c + a0 u0,
     // in float64 while the tensor core runs GEMM 1:
     // a0 u0 + b0 c + g dt R with R = D / det J is b0 c + a0 u0 + (g dt / det J) D
     double tb[NP];
-    const double kap = su.g * su.dt * cur.inv;
+    const double kap = su.g * su.dt * inv;
     if (mode == 1) {
+      if (need_u0) {
 #pragma unroll
-      for (int j = 0; j < NP; ++j) tb[j] = need_u0 ? fma(su.a0, cur.u[j], su.b0 * cur.c[j]) : su.b0 * cur.c[j];
+        for (int j = 0; j < NP; ++j) tb[j] = fma(su.a0, live ? u0[o + j] : 0.0, su.b0 * cv[j]);
+      } else if (su.b0 == 1.0) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) tb[j] = cv[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) tb[j] = su.b0 * cv[j];
+      }
     }
-    bool ok = tc::mbar_wait(mbar, phase, kWaitNs);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, kErrTimeout); break; }
-    tc::fence_after_sync();
+    if (!mma_done()) break;
+    // ---- U (this row: variable rm at the NQ points) -> point layout ----
     {
       float v[N1];
-      tmem_row<N1>(trow, v);
+      tmem_row<N1>(tD, v);
+      float *u = sU + rel * SE + rm;
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) sU[(rel * NQ + k) * M + rm] = v[k];
+      for (int k = 0; k < NQ; ++k) u[4 * k] = v[k];
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // ---- float32 flux at the volume points -> G_r, G_s columns of GEMM 2 ----
-    // Thread (element rel, kk = rm) takes the points k = kk + 4 i of its element.
-    // Column C0 + kk + 4 i of row 4 rel + m sits at byte kmaj(4 rel, C0 + kk) +
-    // 16 m + 128 i, so every store below is a fixed offset from two bases.
+    __syncwarp();
+    // ---- float32 flux at the points k = rm + 4 i of element rel ----
     {
-      const int oGr = tc::kmaj(4 * rel, rm, K2), oGs = tc::kmaj(4 * rel, NQ + rm, K2);
+      const float4 J = *reinterpret_cast<const float4 *>(sJ + rel * 4);
+      const float jt[4] = {J.x, J.y, J.z, J.w};
+      float *g = sG + rel * (M * RG);
       bool phys = true;
 #pragma unroll
       for (int i = 0; i < (NQ + 3) / 4; ++i) {
         const int k = rm + 4 * i;
         if (k < NQ) {
-          const float4 U4 = *reinterpret_cast<const float4 *>(sU + (rel * NQ + k) * M);
+          const float4 U4 = *reinterpret_cast<const float4 *>(sU + rel * SE + 4 * k);
           const float U[M] = {U4.x, U4.y, U4.z, U4.w};
           float Gr[M], Gs[M];
           if (live) {
-            phys &= ref_flux_f32(U, sJ + rel * 4, g32, Gr, Gs);
+            phys &= ref_flux_f32(U, jt, g32, Gr, Gs);
           } else {
 #pragma unroll
             for (int m = 0; m < M; ++m) { Gr[m] = 0.0f; Gs[m] = 0.0f; }
           }
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            put_at<X3>(A2, T::A2P, oGr + 16 * m + 128 * i, Gr[m]);
-            put_at<X3>(A2, T::A2P, oGs + 16 * m + 128 * i, Gs[m]);
+            g[m * RG + k] = Gr[m];
+            g[m * RG + NQ + k] = Gs[m];
           }
         }
       }
       if (!phys) atomicOr(err, kErrNonPhysical);
     }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
+    __syncwarp();
+    // ---- GEMM 2's operand: [G_r | G_s | lifted fluxes | 0] in A columns [0, K2) ----
+    {
+      const float *g = sG + row * RG;
+#pragma unroll
+      for (int c0 = 0; c0 < K2; c0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int col = c0 + i;
+          v[i] = col < 2 * NQ ? g[col] : (col < 2 * NQ + NF ? fl[col - 2 * NQ < NF ? col - 2 * NQ : 0] : 0.0f);
+        }
+        st_split<X3, 8>(tHi + (uint32_t)c0, tLo + (uint32_t)c0, v);
+      }
+    }
+    sync_operands();
     // ---- GEMM 2: volume projection + lift ----
     if (tid == 0) {
-      gemm<X3, K2>(tmem, uA2, T::A2P, uB2, T::B2P, tc::idesc_tf32(128, N2));
+      gemm_ts<X3, K2>(tmem, aHi, aLo, uB2, T::B2P, tc::idesc_tf32(128, N2));
       tc::commit(mbar);
     }
-    if (AHEAD) load_flux(tnext, nxt);
-    ok = tc::mbar_wait(mbar, phase, kWaitNs);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) { if (tid == 0) atomicOr(err, kErrTimeout); break; }
-    tc::fence_after_sync();
+    if (!mma_done()) break;
+    double cr[NP];
     {
       float v[N2];
-      tmem_row<N2>(trow, v);
-      double cr[NP];
-      if (live) {
-        const double inv = cur.inv;
-        if (mode == 0) {
+      tmem_row<N2>(tD, v);
+      if (mode == 0) {
 #pragma unroll
-          for (int j = 0; j < NP; ++j) cr[j] = (j == 0 ? s0 : tc::f32_to_f64(v[j])) * inv;
-        } else {
-          // with the second output (the classical RK4's running sum)
-          // x acc + y out + (w dt / det J) D beside it
-          const size_t o = ((size_t)(e0 + rel) * M + rm) * NP;
-          const double kw = su.w * su.dt * inv;
+        for (int j = 0; j < NP; ++j) cr[j] = (j == 0 ? s0 : tc::f32_to_f64_fast(v[j])) * inv;
+      } else {
+        // with the second output (the classical RK4's running sum)
+        // x acc + y out + (w dt / det J) D beside it
+        const double kw = su.w * su.dt * inv;
 #pragma unroll
-          for (int j = 0; j < NP; ++j) {
-            const double D = j == 0 ? s0 : tc::f32_to_f64(v[j]);
-            cr[j] = fma(kap, D, tb[j]);
-            if (OUT2) {
-              double t2 = su.y * cr[j];
-              if (su.x != 0.0) t2 = fma(su.x, su.acc[o + j], t2);
-              su.out2[o + j] = fma(kw, D, t2);
-            }
+        for (int j = 0; j < NP; ++j) {
+          const double D = j == 0 ? s0 : tc::f32_to_f64_fast(v[j]);
+          cr[j] = fma(kap, D, tb[j]);
+          if (OUT2 && live) {
+            double t2 = su.y * cr[j];
+            if (su.x != 0.0) t2 = fma(su.x, su.acc[o + j], t2);
+            su.out2[o + j] = fma(kw, D, t2);
           }
         }
-      } else {
-#pragma unroll
-        for (int j = 0; j < NP; ++j) cr[j] = 0.0;
       }
-      // GEMM 2 has completed: its A planes stage the new state
+      if (live) {
 #pragma unroll
-      for (int j = 0; j < NP; ++j) sStage[(rel * M + rm) * NP + j] = cr[j];
-      if (trace_out)
-        for (int k = 0; k < K1; ++k) put<X3>(A1, T::A1P, row, k, K1, k < NP ? tc::f64_to_f32(cr[k]) : 0.0f);
+        for (int j = 0; j < NP; ++j) out[o + j] = cr[j];
+      }
     }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    {
-      double *dst = out + (size_t)e0 * M * NP;
-      for (int i = tid; i < ecount * M * NP; i += kTcThreads) dst[i] = sStage[i];
+    if (trace_out) {
+      // ---- GEMM 3: edge traces of the new state ----
+      float v[K1];
+#pragma unroll
+      for (int k = 0; k < K1; ++k) v[k] = k < NP ? __uint_as_float(tc::f64_to_f32_rz_bits(cr[k])) : 0.0f;
+      st_split<X3, K1>(tHi, tLo, v);
+      sync_operands();
+      if (tid == 0) {
+        gemm_ts<X3, K1>(tmem, aHi, aLo, uB4, T::B4P, tc::idesc_tf32(128, N4));
+        tc::commit(mbar);
+      }
+      if (!mma_done()) break;
+      store_traces(e0, live);
     }
-    if (trace_out && !traces_of_A1()) break;
-    __syncthreads();
-    if (AHEAD) cur = nxt;
+  }
+  if (failed) {
+    // a bounded wait expired: wait (bounded again) for the MMAs of that batch, so
+    // that the columns freed below are no longer written
+    tc::mbar_wait_sleep(mbar, phase ^ 1u, kWaitNs, kSuspendNs);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0) tc::tmem_dealloc(tmem, T::COLS);
 }
 
 template <int P, int NE, bool X3, bool OUT2, int Q>
 int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, float *trace_out, const float *fhat,
            const double *fmean, const StageUpdate &su, int mode, cudaStream_t s) {
   using T = Tc<P, NE, X3, Q>;
-  static PerDevice attr_set;
-  if (!attr_set.test(m->device)) {
-    cudaError_t e = cudaFuncSetAttribute(k_element_tc<P, NE, X3, OUT2, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         T::SMEM);
-    if (e != cudaSuccess) return (int)e;
-    // all of the SM's unified L1/shared storage as shared memory, so that the
-    // occupancy query and the launch see every CTA that fits
-    e = cudaFuncSetAttribute(k_element_tc<P, NE, X3, OUT2, Q>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return (int)e;
-    attr_set.set(m->device);
-  }
-  // CTAs per SM from the shared memory and registers each needs (the occupancy
-  // query under-reports for this kernel), at most 8 (TMEM: 512 columns per SM)
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    int smem_sm = 0, reserved = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device);
-    if (e != cudaSuccess) return (int)e;
-    per_sm = smem_sm / (T::SMEM + reserved);
-    // and from the registers (allocated per warp in units of 256)
-    int regs_sm = 0;
-    e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, m->device);
-    if (e != cudaSuccess) return (int)e;
+  auto kern = k_element_tc<P, NE, X3, OUT2, Q>;
+  // per device: CTAs per SM from TMEM (512 columns per SM), shared memory and
+  // registers, and the dynamic shared memory that keeps the SM at that count
+  struct Launch { int per_sm, smem; };
+  static Launch cfg[64];
+  static PerDevice ready;
+  const int dev = m->device;
+  Launch L{0, 0};
+  if (dev >= 0 && dev < 64 && ready.test(dev)) {
+    L = cfg[dev];
+  } else {
+    int smem_sm = 0, reserved = 0, regs_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, k_element_tc<P, NE, X3, OUT2, Q>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return (int)e;
+    int per_sm = T::PER_SM;
+    const int by_smem = smem_sm / (T::SMEM + reserved);
     const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
     const int by_regs = regs_sm / (warp_regs * (kTcThreads / 32));
+    if (per_sm > by_smem) per_sm = by_smem;
     if (per_sm > by_regs) per_sm = by_regs;
-    if (per_sm > 512 / kTmemCols) per_sm = 512 / kTmemCols;
     if (per_sm < 1) per_sm = 1;
+    // ask for as much shared memory as leaves room for per_sm CTAs only, so that
+    // no more CTAs than their TMEM allows share an SM
+    int smem = smem_sm / per_sm - reserved;
+    smem = smem / 128 * 128;
+    if (smem > 227 * 1024) smem = 227 * 1024;
+    if (smem < T::SMEM) smem = T::SMEM;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return (int)e;
+    L = Launch{per_sm, smem};
+    if (dev >= 0 && dev < 64) {
+      cfg[dev] = L;
+      ready.set(dev);
+    }
   }
   const int ntiles = (int)((m->N + T::EB - 1) / T::EB);
-  const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_element_tc<P, NE, X3, OUT2, Q><<<grid, kTcThreads, T::SMEM, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face,
-                                                            m->tab, (int)m->N, m->F, su, mode, m->gamma,
-                                                            m->err_flag);
+  const int grid = ntiles < m->num_sms * L.per_sm ? ntiles : m->num_sms * L.per_sm;
+  kern<<<grid, kTcThreads, L.smem, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face, m->tab, (int)m->N,
+                                        m->F, su, mode, m->gamma, m->err_flag);
   return (int)cudaGetLastError();
 }
 

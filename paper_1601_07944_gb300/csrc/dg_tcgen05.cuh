@@ -6,9 +6,12 @@
  *   tcgen05.mma.cta_group::1.kind::tf32
  *                                  D[128 x N] (+)= A[128 x 8] B[8 x N], A and B in
  *                                  shared memory, D in TMEM, FP32 accumulation
+ *   tcgen05.mma ... [a-tmem]       the same with A read from TMEM (lane = row of
+ *                                  A, one column per TF32 element along K)
  *   tcgen05.commit -> mbarrier     completion of the issued MMAs
  *   tcgen05.ld.32x32b              TMEM -> registers (each warp reads its own
  *                                  32-lane quarter; lane = accumulator row)
+ *   tcgen05.st.32x32b              registers -> TMEM (the same lane mapping)
  *
  * Operand layout: K-major without swizzle.  The tile is made of core matrices of
  * 8 rows x 16 bytes (8 rows x 4 TF32 values) stored as 128 contiguous bytes; the
@@ -57,6 +60,16 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// A operand in tensor memory: A[row][k] at lane row, column a_tmem + k (K-major;
+// one K = 8 step reads eight consecutive columns)
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
 }
@@ -88,6 +101,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64
   }
 }
 
+// The same, with the waiting threads suspended (up to suspend_ns per try) instead
+// of polling, so that they take no issue slots from the other warps of the SM.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t parity, uint64_t limit_ns,
+                                                uint32_t suspend_ns) {
+  uint32_t done = 0;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity), "r"(suspend_ns));
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
@@ -114,6 +144,42 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
+
+// 8 consecutive 32-bit columns of this thread's TMEM lane from v (warp-collective)
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// TF32 rounding of a float32 bit pattern, to nearest with ties away from zero
+// (an add on the magnitude bits, then the 13 low bits cleared)
+__device__ __forceinline__ uint32_t tf32_bits(uint32_t b) { return (b + 0x1000u) & 0xFFFFE000u; }
+
+// float64 -> float32 truncated toward zero, branchless, on the bit patterns:
+// magnitudes below the float32 normal range give signed zero, magnitudes of 2^128
+// and above (and non-finite values) give signed infinity.  (The tensor-core
+// operands round this value to TF32 again, so truncation costs nothing there.)
+__device__ __forceinline__ uint32_t f64_to_f32_rz_bits(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t ah = hi & 0x7FFFFFFFu;
+  uint32_t f = __funnelshift_l(lo, ah - 0x38000000u, 3);   // exponent rebias, 23 mantissa bits
+  f = ah < 0x38100000u ? 0u : f;
+  f = ah >= 0x47F00000u ? 0x7F800000u : f;
+  return f | (hi & 0x80000000u);
+}
+
+// float32 -> float64, exact for zeros and normal values, branchless; float32
+// subnormals (below 2^-126) come out within 2^-126 of their value, non-finite
+// values as finite values of magnitude 2^128 or more.
+__device__ __forceinline__ double f32_to_f64_fast(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ab = b & 0x7FFFFFFFu;
+  uint32_t hi = (ab >> 3) + 0x38000000u;
+  hi = ab == 0u ? 0u : hi;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(b << 29));
+}
 
 // round an FP32 value to TF32 (10 mantissa bits, round to nearest, ties away)
 __device__ __forceinline__ float to_tf32(float x) {

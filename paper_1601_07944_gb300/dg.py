@@ -147,11 +147,11 @@ def probe_fma_rate(stream=None):
 
 def self_test(stream=None):
     """(float64->float32, float32->float64) bit mismatches of the integer
-    conversions against the hardware's, and reciprocals more than 1 ulp from
-    1/x, over 2^20 values."""
-    out = np.zeros(3, dtype=np.int64)
+    conversions against the hardware's, and reciprocals and square roots more
+    than 1 ulp from 1/x and sqrt(x), over 2^20 values."""
+    out = np.zeros(4, dtype=np.int64)
     _check(load().dg_self_test(_np_ptr(out), _stream_ptr(stream)))
-    return int(out[0]), int(out[1]), int(out[2])
+    return tuple(int(v) for v in out)
 
 
 def host_tables(p: int, ne: int = 0):
