@@ -78,14 +78,24 @@ struct Tc {
   // The edge traces [NF][4] are staged in the same place.
   static constexpr int SE4 = imax((NQ & 1) ? NQ : NQ + 1, (NF & 1) ? NF : NF + 1);
   static constexpr int SE = 4 * SE4;
-  static constexpr int oU = endB;
   // reference-flux staging [EB][M][RG] floats (row 4 e + m, column k of G_r,
-  // NQ + k of G_s); RG odd
+  // NQ + k of G_s); RG odd.  Each warp (8 elements) has a region of WS floats
+  // holding its U staging and, in the same place, its G staging: a thread has
+  // read its points' U before the warp writes G.
   static constexpr int RG = (2 * NQ) | 1;
-  static constexpr int oG = oU + EB * SE * 4;
-  static constexpr int oJ = oG + EB * M * RG * 4;             // float [EB][4]  J^tau
-  static constexpr int oBar = (oJ + EB * 16 + 15) / 16 * 16;  // mbarrier, TMEM slot
-  static constexpr int SMEM = oBar + 16;
+  static constexpr int WS = imax(8 * SE, 8 * M * RG);
+  static constexpr int oW = endB;
+  static constexpr int oJ = oW + 4 * WS * 4;                         // float [EB][4]  J^tau
+  static constexpr int oBar = (oJ + EB * 16 + 15) / 16 * 16;        // 2 mbarriers, TMEM slot
+  static constexpr int SMEM_NOPF = oBar + 32;
+  // the next tile's stage input, u^n [EB][M][NP] and geometry [EB][GEO] (bulk
+  // copies one tile ahead), where the shared memory of the CTAs an SM holds allows
+  static constexpr int PC = EB * M * NP * 8, PG = EB * GEO * 8;
+  static constexpr int oPC = (SMEM_NOPF + 127) / 128 * 128, oPU = oPC + PC, oPG = oPU + PC;
+  static constexpr int SMEM_PF = oPG + PG;
+  static constexpr int CTAS = PER_SM < 4 ? PER_SM : 4;              // the launch bound
+  static constexpr bool PF = SMEM_PF + 1024 <= 233472 / CTAS;
+  static constexpr int SMEM = PF ? SMEM_PF : SMEM_NOPF;
   static_assert(K1 <= K2, "GEMM 1's operand shares GEMM 2's columns");
   static_assert(N1 <= 256 && N2 <= 256 && N4 <= 256, "MMA N");
   static_assert(ND + NS * K2 <= 512, "TMEM columns");
@@ -103,7 +113,9 @@ __device__ __forceinline__ void put(unsigned char *base, int plane_bytes, int ro
 }
 
 // this thread's TMEM lane, columns [c0, c0 + N) (N a multiple of 8) <- v split
-// into TF32 planes: hi at tHi, the remainder lo at tLo (3xTF32)
+// into TF32 planes: hi = v rounded to TF32 at tHi, and (3xTF32) the remainder
+// lo = v - hi at tLo, exact in float32; the tensor core takes lo's leading TF32
+// bits, so hi + lo carries v to within 2^-22 of |v|.
 template <bool X3, int N>
 __device__ __forceinline__ void st_split(uint32_t tHi, uint32_t tLo, const float *v) {
 #pragma unroll
@@ -112,7 +124,7 @@ __device__ __forceinline__ void st_split(uint32_t tHi, uint32_t tLo, const float
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       hi[i] = tc::tf32_bits(__float_as_uint(v[c + i]));
-      if (X3) lo[i] = tc::tf32_bits(__float_as_uint(v[c + i] - __uint_as_float(hi[i])));
+      if (X3) lo[i] = __float_as_uint(v[c + i] - __uint_as_float(hi[i]));
     }
     tc::st8(tHi + (uint32_t)c, hi);
     if (X3) tc::st8(tLo + (uint32_t)c, lo);
@@ -167,23 +179,28 @@ __device__ __forceinline__ bool ref_flux_f32(const float U[M], const float *jt, 
 // OUT2: the stage also writes the classical RK4's running sum (StageUpdate::out2);
 // a separate instantiation, so that the kernels without it keep their registers.
 template <int P, int NE, bool X3, bool OUT2, int Q>
-__global__ void __launch_bounds__(kTcThreads, Tc<P, NE, X3, Q>::PER_SM < 4 ? Tc<P, NE, X3, Q>::PER_SM : 4)
+__global__ void __launch_bounds__(kTcThreads, Tc<P, NE, X3, Q>::CTAS)
 k_element_tc(const double *c, const double *u0, double *out, float *__restrict__ trace_out,
              const float *__restrict__ fhat, const double *__restrict__ fmean, const double *__restrict__ geo,
              const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
-             double gamma, int *err) {
+             double gamma, int bulk, int *err) {
   using T = Tc<P, NE, X3, Q>;
   constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB, SE = T::SE, RG = T::RG;
   constexpr int K1 = T::K1, N1 = T::N1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char *B1 = sm + T::oB1, *B2 = sm + T::oB2, *B4 = sm + T::oB4;
-  float *sU = reinterpret_cast<float *>(sm + T::oU);
-  float *sG = reinterpret_cast<float *>(sm + T::oG);
+  // this warp's staging region: element e (its e & 7) at sU + (e & 7) SE, sG + (e & 7) M RG
+  float *sU = reinterpret_cast<float *>(sm + T::oW) + (threadIdx.x >> 5) * T::WS;
+  float *sG = sU;
   float *sJ = reinterpret_cast<float *>(sm + T::oJ);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + T::oBar);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + T::oBar + 8);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + T::oBar);         // [0] MMAs, [1] bulk copies
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + T::oBar + 16);
+  const double *sPC = reinterpret_cast<const double *>(sm + T::oPC);
+  const double *sPU = reinterpret_cast<const double *>(sm + T::oPU);
+  const double *sPG = reinterpret_cast<const double *>(sm + T::oPG);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const uint32_t mbar = tc::smem_u32(bar);
+  const uint32_t mbar = tc::smem_u32(bar), mbar_in = tc::smem_u32(bar + 1);
+  const bool pf = T::PF && bulk;
 
   // ---- once per CTA: B operands (split), TMEM, mbarrier ----
   for (int i = tid; i < T::N1 * K1; i += kTcThreads) {
@@ -207,7 +224,10 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     put<X3>(B4, T::B4P, n, k, K1, (float)v);
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(slot), T::COLS);
-  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    tc::mbar_init(mbar_in, 1);
+  }
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
@@ -219,8 +239,9 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   const uint32_t uB1 = tc::smem_u32(B1), uB2 = tc::smem_u32(B2), uB4 = tc::smem_u32(B4);
   const float g32 = (float)gamma;
   const int row = tid, rel = row >> 2, rm = row & 3;                 // accumulator row = 4 e + m
-  uint32_t phase = 0;
-  bool failed = false;
+  const int le = rel & 7;                                            // element within the warp
+  uint32_t phase = 0, phase_in = 0;
+  bool failed = false, copies = false;        // copies: a bulk copy is in flight
 
   // the rows' tcgen05.st complete and are ordered before the MMA issue
   auto sync_operands = [&]() {
@@ -246,7 +267,7 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   auto store_traces = [&](int e0, bool live) {
     float v[N4];
     tmem_row<N4>(tD, v);
-    float *t = sU + rel * SE + rm;
+    float *t = sU + le * SE + rm;
 #pragma unroll
     for (int qk = 0; qk < NF; ++qk) t[4 * qk] = v[qk];
     __syncwarp();
@@ -254,24 +275,118 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
 #pragma unroll
     for (int i = 0; i < (NF + 3) / 4; ++i) {
       const int qk = rm + 4 * i;
-      if (qk < NF && live) dst[qk] = *reinterpret_cast<const float4 *>(sU + rel * SE + 4 * qk);
+      if (qk < NF && live) dst[qk] = *reinterpret_cast<const float4 *>(sU + le * SE + 4 * qk);
     }
     __syncwarp();
   };
 
   const int ntiles = (N + EB - 1) / EB;
   const bool need_u0 = mode == 1 && su.a0 != 0.0;
+  // one thread: bulk copies of tile t's stage input, u^n and geometry into the
+  // prefetch buffers (the CTA has finished reading them)
+  auto prefetch = [&](int t) {
+    const int e0 = t * EB, ec = min(EB, N - e0);
+    const uint32_t bc = (uint32_t)ec * M * NP * 8, bg = (uint32_t)ec * GEO * 8;
+    tc::fence_proxy_async();
+    tc::mbar_arrive_expect_tx(mbar_in, bc + (need_u0 ? bc : 0u) + (mode != 2 ? bg : 0u));
+    tc::bulk_g2s(tc::smem_u32(sPC), c + (size_t)e0 * M * NP, bc, mbar_in);
+    if (need_u0) tc::bulk_g2s(tc::smem_u32(sPU), u0 + (size_t)e0 * M * NP, bc, mbar_in);
+    if (mode != 2) tc::bulk_g2s(tc::smem_u32(sPG), geo + (size_t)e0 * GEO, bg, mbar_in);
+  };
+  if (pf && blockIdx.x < ntiles) {
+    if (tid == 0) prefetch(blockIdx.x);
+    copies = true;
+  }
+  // the element's three edges (2 f + side), loaded one tile ahead
+  auto load_ef = [&](int t, int *ef) {
+    const int r = t * EB + rel;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) ef[q] = mode != 2 && t < ntiles && r < N ? elem_face[(size_t)r * 3 + q] : 0;
+  };
+  int ef[3];
+  load_ef(blockIdx.x, ef);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int e0 = tile * EB;
     const int ecount = min(EB, N - e0);
     const bool live = rel < ecount;
     const size_t o = ((size_t)(e0 + rel) * M + rm) * NP;
-    // ---- the stage input: GEMM 1's operand (A columns [0, K1)) ----
-    // (scalar loads and stores of the caller's arrays: they need only the
-    // alignment of a double; a warp's rows are contiguous, so they coalesce)
-    double cv[NP];
+    const int tnext = tile + gridDim.x;
+    // ---- the row's edge fluxes in the element's point order (the lift columns
+    // of GEMM 2) and their float64 mean-mode integrals; the loads stay in flight
+    // until GEMM 2's operand is written, where the sign of the element's
+    // orientation is applied (on the bit patterns) ----
+    float fl[NF];
+    double sq[3];
+    uint32_t sgn[3];
+    if (mode != 2) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) cv[j] = live ? c[o + j] : 0.0;
+      for (int q = 0; q < 3; ++q) {
+        const int64_t f = checked(ef[q] >> 1, F, err);
+        const int side = ef[q] & 1;
+        sgn[q] = side ? 0u : 0x80000000u;
+        sq[q] = live ? fmean[(size_t)f * M + rm] : 0.0;
+        const float *fp = fhat + (size_t)f * NE * M + rm;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) fl[q * NE + k] = live ? fp[(side ? NE - 1 - k : k) * M] : 0.0f;
+      }
+      load_ef(tnext, ef);
+    }
+    if (pf) {
+      const bool ok = tc::mbar_wait_sleep(mbar_in, phase_in, kWaitNs, kSuspendNs);
+      phase_in ^= 1u;
+      copies = false;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(err, kErrTimeout);
+        failed = true;
+        copies = true;
+        break;
+      }
+    }
+    // ---- the stage input: GEMM 1's operand (A columns [0, K1)) ----
+    // (without the bulk copies: scalar loads of the caller's array, which then
+    // needs only the alignment of a double; a warp's rows are contiguous)
+    double cv[NP];
+    if (pf && NP % 2 == 0) {
+      const double2 *r2 = reinterpret_cast<const double2 *>(sPC + row * NP);
+#pragma unroll
+      for (int j = 0; j < NP / 2; ++j) {
+        const double2 x = r2[j];
+        cv[2 * j] = live ? x.x : 0.0;
+        cv[2 * j + 1] = live ? x.y : 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) cv[j] = live ? (pf ? sPC[row * NP + j] : c[o + j]) : 0.0;
+    }
+    // the part of the stage update that does not depend on the RHS, b0 c + a0 u0,
+    // in float64 among the integer work of the operand conversion:
+    // a0 u0 + b0 c + g dt R with R = D / det J is b0 c + a0 u0 + (g dt / det J) D
+    double tb[NP];
+    if (mode == 1) {
+      if (need_u0) {
+        double uv[NP];
+        if (pf && NP % 2 == 0) {
+          const double2 *r2 = reinterpret_cast<const double2 *>(sPU + row * NP);
+#pragma unroll
+          for (int j = 0; j < NP / 2; ++j) {
+            const double2 x = r2[j];
+            uv[2 * j] = live ? x.x : 0.0;
+            uv[2 * j + 1] = live ? x.y : 0.0;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NP; ++j) uv[j] = live ? (pf ? sPU[row * NP + j] : u0[o + j]) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) tb[j] = fma(su.a0, uv[j], su.b0 * cv[j]);
+      } else if (su.b0 == 1.0) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) tb[j] = cv[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) tb[j] = su.b0 * cv[j];
+      }
+    }
     {
       float v[K1];
 #pragma unroll
@@ -286,66 +401,37 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
         tc::commit(mbar);
       }
       if (!mma_done()) break;
+      if (pf && tnext < ntiles) {
+        if (tid == 0) prefetch(tnext);
+        copies = true;
+      }
       store_traces(e0, live);
       continue;
     }
-    // ---- the row's edge fluxes in the element's orientation and point order
-    // (the lift columns of GEMM 2) and their float64 mean-mode integrals ----
-    float fl[NF];
-    double sq[3];
-    {
-      const int32_t *efp = elem_face + (size_t)(e0 + rel) * 3;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int ef = live ? efp[q] : 0;
-        const int64_t f = checked(ef >> 1, F, err);
-        const int side = ef & 1;
-        const double s = live ? fmean[(size_t)f * M + rm] : 0.0;
-        sq[q] = side ? s : tc::neg_bits(s);
-        const float *fp = fhat + (size_t)f * NE * M + rm;
-#pragma unroll
-        for (int k = 0; k < NE; ++k) {
-          const float x = live ? fp[(side ? NE - 1 - k : k) * M] : 0.0f;
-          fl[q * NE + k] = side ? x : -x;
-        }
-      }
-    }
-    const double s0 = (sq[0] + sq[1]) + sq[2];
     double inv = 0.0;
     {
-      const double *ge = geo + (size_t)(e0 + rel) * GEO;
+      const double *ge = pf ? sPG + rel * GEO : geo + (size_t)(e0 + rel) * GEO;
       inv = live ? ge[4] : 0.0;
       sJ[row] = __uint_as_float(tc::f64_to_f32_rz_bits(live ? ge[rm] : 0.0));
     }
+    const double kap = su.g * su.dt * inv;
     sync_operands();
     // ---- GEMM 1: interpolation to the volume points ----
     if (tid == 0) {
       gemm_ts<X3, K1>(tmem, aHi, aLo, uB1, T::B1P, tc::idesc_tf32(128, N1));
       tc::commit(mbar);
     }
-    // the part of the stage update that does not depend on the RHS, b0 c + a0 u0,
-    // in float64 while the tensor core runs GEMM 1:
-    // a0 u0 + b0 c + g dt R with R = D / det J is b0 c + a0 u0 + (g dt / det J) D
-    double tb[NP];
-    const double kap = su.g * su.dt * inv;
-    if (mode == 1) {
-      if (need_u0) {
-#pragma unroll
-        for (int j = 0; j < NP; ++j) tb[j] = fma(su.a0, live ? u0[o + j] : 0.0, su.b0 * cv[j]);
-      } else if (su.b0 == 1.0) {
-#pragma unroll
-        for (int j = 0; j < NP; ++j) tb[j] = cv[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < NP; ++j) tb[j] = su.b0 * cv[j];
-      }
-    }
     if (!mma_done()) break;
+    // every thread has read the prefetch buffers: the next tile's copies
+    if (pf && tnext < ntiles) {
+      if (tid == 0) prefetch(tnext);
+      copies = true;
+    }
     // ---- U (this row: variable rm at the NQ points) -> point layout ----
     {
       float v[N1];
       tmem_row<N1>(tD, v);
-      float *u = sU + rel * SE + rm;
+      float *u = sU + le * SE + rm;
 #pragma unroll
       for (int k = 0; k < NQ; ++k) u[4 * k] = v[k];
     }
@@ -354,14 +440,20 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     {
       const float4 J = *reinterpret_cast<const float4 *>(sJ + rel * 4);
       const float jt[4] = {J.x, J.y, J.z, J.w};
-      float *g = sG + rel * (M * RG);
+      float4 Up[(NQ + 3) / 4];
+#pragma unroll
+      for (int i = 0; i < (NQ + 3) / 4; ++i) {
+        const int k = rm + 4 * i;
+        Up[i] = k < NQ ? *reinterpret_cast<const float4 *>(sU + le * SE + 4 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncwarp();          // the G staging below overwrites the U staging
+      float *g = sG + le * (M * RG);
       bool phys = true;
 #pragma unroll
       for (int i = 0; i < (NQ + 3) / 4; ++i) {
         const int k = rm + 4 * i;
         if (k < NQ) {
-          const float4 U4 = *reinterpret_cast<const float4 *>(sU + rel * SE + 4 * k);
-          const float U[M] = {U4.x, U4.y, U4.z, U4.w};
+          const float U[M] = {Up[i].x, Up[i].y, Up[i].z, Up[i].w};
           float Gr[M], Gs[M];
           if (live) {
             phys &= ref_flux_f32(U, jt, g32, Gr, Gs);
@@ -381,14 +473,16 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     __syncwarp();
     // ---- GEMM 2's operand: [G_r | G_s | lifted fluxes | 0] in A columns [0, K2) ----
     {
-      const float *g = sG + row * RG;
+      const float *g = sG + (row & 31) * RG;
 #pragma unroll
       for (int c0 = 0; c0 < K2; c0 += 8) {
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int col = c0 + i;
-          v[i] = col < 2 * NQ ? g[col] : (col < 2 * NQ + NF ? fl[col - 2 * NQ < NF ? col - 2 * NQ : 0] : 0.0f);
+          const int li = col - 2 * NQ >= 0 && col - 2 * NQ < NF ? col - 2 * NQ : 0;
+          v[i] = col < 2 * NQ ? g[col]
+                              : (col < 2 * NQ + NF ? __uint_as_float(__float_as_uint(fl[li]) ^ sgn[li / NE]) : 0.0f);
         }
         st_split<X3, 8>(tHi + (uint32_t)c0, tLo + (uint32_t)c0, v);
       }
@@ -402,6 +496,13 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     if (!mma_done()) break;
     double cr[NP];
     {
+      // the mean mode's lift: the three edges' float64 integrals, signed by the
+      // element's orientation
+      double sqs[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        sqs[q] = __hiloint2double(__double2hiint(sq[q]) ^ (int)sgn[q], __double2loint(sq[q]));
+      const double s0 = (sqs[0] + sqs[1]) + sqs[2];
       float v[N2];
       tmem_row<N2>(tD, v);
       if (mode == 0) {
@@ -444,8 +545,10 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   }
   if (failed) {
     // a bounded wait expired: wait (bounded again) for the MMAs of that batch, so
-    // that the columns freed below are no longer written
+    // that the columns freed below are no longer written, and for a bulk copy
+    // still in flight, so that no copy lands after the CTA has left
     tc::mbar_wait_sleep(mbar, phase ^ 1u, kWaitNs, kSuspendNs);
+    if (copies) tc::mbar_wait_sleep(mbar_in, phase_in, kWaitNs, kSuspendNs);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -499,8 +602,12 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, flo
   }
   const int ntiles = (int)((m->N + T::EB - 1) / T::EB);
   const int grid = ntiles < m->num_sms * L.per_sm ? ntiles : m->num_sms * L.per_sm;
+  // the bulk copies need 16-byte aligned sources (the mesh's arrays are; the
+  // caller's state arrays usually are, else the kernel loads them directly)
+  const bool need_u0 = mode == 1 && su.a0 != 0.0;
+  const int bulk = ((uintptr_t)c % 16 == 0 && (!need_u0 || (uintptr_t)u0 % 16 == 0)) ? 1 : 0;
   kern<<<grid, kTcThreads, L.smem, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face, m->tab, (int)m->N,
-                                        m->F, su, mode, m->gamma, m->err_flag);
+                                        m->F, su, mode, m->gamma, bulk, m->err_flag);
   return (int)cudaGetLastError();
 }
 

@@ -102,20 +102,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64
 }
 
 // The same, with the waiting threads suspended (up to suspend_ns per try) instead
-// of polling, so that they take no issue slots from the other warps of the SM.
+// of polling, so that they take fewer issue slots from the other warps of the
+// SM; the clock is read on every eighth try.
 __device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t parity, uint64_t limit_ns,
                                                 uint32_t suspend_ns) {
   uint32_t done = 0;
-  const uint64_t t0 = global_ns();
-  while (true) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         "selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
         : "r"(mbar), "r"(parity), "r"(suspend_ns));
     if (done) return true;
-    if (global_ns() - t0 > limit_ns) return false;
+    if ((it & 7u) == 0u) {
+      const uint64_t t = global_ns();
+      if (it == 0u) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
   }
+}
+
+// the calling thread arrives on the mbarrier and adds tx_bytes to the bytes the
+// current phase waits for (the bulk copies below complete them)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t tx_bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(tx_bytes) : "memory");
+}
+
+// bulk copy (TMA, not tiled) of `bytes` bytes global -> shared memory, completing
+// on the mbarrier; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst_smem),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
