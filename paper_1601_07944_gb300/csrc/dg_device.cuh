@@ -127,53 +127,58 @@ __device__ __forceinline__ double max_nonneg(double a, double b) {
 }
 
 // Local Lax-Friedrichs flux times the edge's half length l (Eq. len), at one edge
-// point:  out = l F_hat = h (F(Ul).n + F(Ur).n - alpha (Ur - Ul)),  h = l / 2,
-//         alpha = max(|v_l.n| + c_l, |v_r.n| + c_r),  c = sqrt(gamma p / rho).
+// point, float64 throughout:
+//   out = l F_hat = h (F(Ul).n + F(Ur).n - alpha (Ur - Ul)),  h = l / 2,
+//   alpha = max(|v_l.n| + c_l, |v_r.n| + c_r),  c = sqrt(gamma p / rho).
 // The scaled normal s = h n of the face record is folded into the physical
-// fluxes: with mn = s.(rho u) = h rho v.n, w = mn / rho and
-// P = E - |rho u|^2 / (2 rho) = p / (gamma - 1),
-//   h F(U).n = (mn, rho u w + P (gamma-1) s_x, rho v w + P (gamma-1) s_y, (E + (gamma-1) P) w)
-// and h alpha = max(|w_l| + h c_l, |w_r| + h c_r), h c = sqrt(hk P / rho).
+// fluxes: with w = s.(rho u) / rho = h v.n and P = E - |rho u|^2 / (2 rho) =
+// p / (gamma - 1),
+//   h F(U).n = (rho w, mx w + P (gamma-1) s_x, my w + P (gamma-1) s_y, (E + (gamma-1) P) w),
+//   h alpha = max(|w_l| + h c_l, |w_r| + h c_r),  h c = sqrt(hk P / rho).
+// The dissipation term moves into the normal velocities, wa = w_l + h alpha and
+// wb = w_r - h alpha, so that
+//   l F_hat = (rho_l wa + rho_r wb,
+//              mx_l wa + mx_r wb + (P_l + P_r) (gamma-1) s_x,
+//              my_l wa + my_r wb + (P_l + P_r) (gamma-1) s_y,
+//              E_l wa + E_r wb + (gamma-1) (P_l w_l + P_r w_r))
+// (about 56 float64 operations per point).  The square roots of the sound speeds
+// are sqrt_nr; the larger wave speed is picked on the bit patterns.
 // Returns false if either side is non-physical (rho <= 0 or p <= 0, or NaN).
 __device__ __forceinline__ bool lax_friedrichs_edge(const double ul[M], const double ur[M], const FaceGeo &g,
                                                     double gamma, double out[M]) {
   const double g1 = gamma - 1.0;
   const double il = recip(ul[0]), ir = recip(ur[0]);
-  const double mL = fma(ul[1], g.sx, ul[2] * g.sy), mR = fma(ur[1], g.sx, ur[2] * g.sy);
-  const double wL = mL * il, wR = mR * ir;
-  const double PL = fma(-0.5 * fma(ul[1], ul[1], ul[2] * ul[2]), il, ul[3]);
-  const double PR = fma(-0.5 * fma(ur[1], ur[1], ur[2] * ur[2]), ir, ur[3]);
-  const double aL = fabs(wL) + sqrt(g.hk * PL * il);
-  const double aR = fabs(wR) + sqrt(g.hk * PR * ir);
-  const double la = fmax(aL, aR);
-  double fL[M], fR[M];
-  fL[0] = mL;                             fR[0] = mR;
-  fL[1] = fma(ul[1], wL, PL * g.gsx);     fR[1] = fma(ur[1], wR, PR * g.gsx);
-  fL[2] = fma(ul[2], wL, PL * g.gsy);     fR[2] = fma(ur[2], wR, PR * g.gsy);
-  fL[3] = fma(g1, PL, ul[3]) * wL;        fR[3] = fma(g1, PR, ur[3]) * wR;
-#pragma unroll
-  for (int m = 0; m < M; ++m) out[m] = fma(-la, ur[m] - ul[m], fL[m] + fR[m]);
-  return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(PL) & positive_finite(PR);
-}
-
-// The same flux, float64 throughout, in the form the mixed-precision edge kernel
-// evaluates (about 54 float64 operations per point instead of about 70): the
-// dissipation term moves into the normal velocities, wa = w_l + h alpha and
-// wb = w_r - h alpha, so that
-//   l F_hat = (rho_l wa + rho_r wb,
-//              mx_l wa + mx_r wb + (P_l + P_r) (gamma-1) s_x,
-//              my_l wa + my_r wb + (P_l + P_r) (gamma-1) s_y,
-//              E_l wa + E_r wb + (gamma-1) (P_l w_l + P_r w_r)),
-// (rho w = mn); the square roots of the sound speeds are sqrt_nr, and the larger
-// wave speed is picked on the bit patterns.  The two forms differ by float64
-// rounding only.  Returns false if either side is non-physical.
-__device__ __forceinline__ bool lax_friedrichs_edge_jf(const double ul[M], const double ur[M], const FaceGeo &g,
-                                                       double gamma, double out[M]) {
-  const double g1 = gamma - 1.0;
-  const double il = recip(ul[0]), ir = recip(ur[0]);
   const double wL = fma(ul[1], g.sx, ul[2] * g.sy) * il, wR = fma(ur[1], g.sx, ur[2] * g.sy) * ir;
   const double PL = fma(-0.5 * fma(ul[1], ul[1], ul[2] * ul[2]), il, ul[3]);
   const double PR = fma(-0.5 * fma(ur[1], ur[1], ur[2] * ur[2]), ir, ur[3]);
+  const double aL = fabs(wL) + sqrt_nr(g.hk * PL * il);
+  const double aR = fabs(wR) + sqrt_nr(g.hk * PR * ir);
+  const double la = max_nonneg(aL, aR);
+  const double wa = wL + la, wb = wR - la, Ps = PL + PR;
+  out[0] = fma(ul[0], wa, ur[0] * wb);
+  out[1] = fma(ul[1], wa, fma(ur[1], wb, Ps * g.gsx));
+  out[2] = fma(ul[2], wa, fma(ur[2], wb, Ps * g.gsy));
+  out[3] = fma(ul[3], wa, fma(ur[3], wb, g1 * fma(PL, wL, PR * wR)));
+  return positive_finite(ul[0]) & positive_finite(ur[0]) & positive_finite(PL) & positive_finite(PR);
+}
+
+// lax_friedrichs_edge for two float32 traces (an interior face of the mixed
+// modes: the values widen exactly), with two float64 operations fewer per point:
+// one reciprocal serves both sides (1/rho_l = rho_r / (rho_l rho_r), the product
+// of two float32 values being exact in float64), and |rho u|^2 / 2 is formed
+// from the momenta halved in float32 (exact) instead of a multiply by 1/2.
+__device__ __forceinline__ bool lax_friedrichs_edge_f32(const float4 a, const float4 b, const FaceGeo &g,
+                                                        double gamma, double out[M]) {
+  const double g1 = gamma - 1.0;
+  const double ul[M] = {f32_to_f64_dev(a.x), f32_to_f64_dev(a.y), f32_to_f64_dev(a.z), f32_to_f64_dev(a.w)};
+  const double ur[M] = {f32_to_f64_dev(b.x), f32_to_f64_dev(b.y), f32_to_f64_dev(b.z), f32_to_f64_dev(b.w)};
+  const double hxL = f32_to_f64_dev(0.5f * a.y), hyL = f32_to_f64_dev(0.5f * a.z);
+  const double hxR = f32_to_f64_dev(0.5f * b.y), hyR = f32_to_f64_dev(0.5f * b.z);
+  const double ilr = recip(ul[0] * ur[0]);
+  const double il = ur[0] * ilr, ir = ul[0] * ilr;
+  const double wL = fma(ul[1], g.sx, ul[2] * g.sy) * il, wR = fma(ur[1], g.sx, ur[2] * g.sy) * ir;
+  const double PL = fma(-fma(hxL, ul[1], hyL * ul[2]), il, ul[3]);
+  const double PR = fma(-fma(hxR, ur[1], hyR * ur[2]), ir, ur[3]);
   const double aL = fabs(wL) + sqrt_nr(g.hk * PL * il);
   const double aR = fabs(wR) + sqrt_nr(g.hk * PR * ir);
   const double la = max_nonneg(aL, aR);

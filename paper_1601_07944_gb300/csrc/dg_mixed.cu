@@ -33,9 +33,9 @@ namespace {
 // Edge flux of the mixed-precision modes, one thread per edge.  The two traces
 // are float32 (exact results of the tensor-core contraction) and are widened
 // exactly; the local Lax-Friedrichs flux is evaluated in float64 at the NE edge
-// points (lax_friedrichs_edge_jf: the flux of k_face, alpha included, in a form
-// with fewer float64 operations), with the right element's trace at the
-// reversed point (Eq. edgeint).  Written per
+// points (lax_friedrichs_edge_f32: the flux of k_face, alpha included, with two
+// float64 operations fewer for float32 inputs), with the right element's trace
+// at the reversed point (Eq. edgeint).  Written per
 // edge: l F_hat at the points rounded to float32 (the lift columns of GEMM 2), and
 // the float64 integral of l F_hat against the constant mode,
 // fmean_m = sum_k omega_k phi_1 l F_hat_{k,m} (Algorithm 2 for j = 1; the
@@ -69,17 +69,15 @@ k_face_mixed(const float *__restrict__ trace, float *__restrict__ fhat, double *
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
       const float4 a = tl[k];
-      const double ul[M] = {tc::f32_to_f64(a.x), tc::f32_to_f64(a.y), tc::f32_to_f64(a.z), tc::f32_to_f64(a.w)};
-      double ur[M];
-      if (bnd) {
-        ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
-      } else {
-        const float4 b = tr[NE - 1 - k];
-        ur[0] = tc::f32_to_f64(b.x); ur[1] = tc::f32_to_f64(b.y);
-        ur[2] = tc::f32_to_f64(b.z); ur[3] = tc::f32_to_f64(b.w);
-      }
       double Fh[M];
-      ok &= lax_friedrichs_edge_jf(ul, ur, g, gamma, Fh);
+      if (bnd) {
+        const double ul[M] = {tc::f32_to_f64(a.x), tc::f32_to_f64(a.y), tc::f32_to_f64(a.z), tc::f32_to_f64(a.w)};
+        double ur[M];
+        ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
+        ok &= lax_friedrichs_edge(ul, ur, g, gamma, Fh);
+      } else {
+        ok &= lax_friedrichs_edge_f32(a, tr[NE - 1 - k], g, gamma, Fh);
+      }
       const double w = Lf[k * np];           // omega_k phi_1, the same on the three faces
 #pragma unroll
       for (int m = 0; m < M; ++m) sm[m] = fma(w, Fh[m], sm[m]);
