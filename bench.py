@@ -21,7 +21,13 @@ the adjoint/forward cost ratio on the 256 x 256, p = 2 workload.
 Under torchrun (N > 1) every rank runs an independent replica of the workload on
 its own GPU (the path is replicated, not sharded): value = all ranks' DOF
 updates / the slowest rank's time.  --impl reference times the CPU oracle on
-the host cores (rank 0 only).
+the host cores (rank 0 only): on one thread (the line's value) and as one
+independent replica per core (cpu_all_cores).
+
+With N = 1 the headline line also carries mixed_512_p4: the mixed-precision
+workload (512 x 512 mesh, p = 4, perturbed vortex) in float64 and both
+tensor-core modes, steady-state over 100 steps, with the state error of each
+mode against float64 and the tensor-core element kernel's HBM roofline.
 """
 from __future__ import annotations
 
@@ -124,7 +130,7 @@ def _src_hash(*names) -> str:
 # aside) it was taken on, and the volume rule when it is not the collapsed grid;
 # a code change voids the entry.
 TRAFFIC = {
-    # k_element_sf<3,4,0>, stage-1 launch, 256x256 p=3 vortex (profiles/k_element_sf_vortex256_p3_fp64.md)
+    # k_element_sf<3,4,0>, stage-1 launch, 256x256 p=3 vortex (one ncu capture)
     "fc0afafb13edafeb": 77147136 + 40573184,
 }
 
@@ -272,8 +278,63 @@ def run_reference(args, world, rank):
         "config": {"workload": WORKLOAD["name"], "sample": sample, "precision": "fp64"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        # the same oracle on every host core (one independent replica per core)
+        "cpu_all_cores": cpu_all_cores(n, seconds=10.0),
     }
     print(json.dumps(line), flush=True)
+
+
+def _oracle_worker(n, p, ne, cfl, vol_rule, seconds, q):
+    """One replica of the oracle in its own process: whole SSP-RK3 steps of the
+    n x n vortex workload for about `seconds`; puts (steps, elapsed) on q."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1601_07944_gb300 import inputs as I
+    mesh = I.periodic_mesh(n)
+    o = oracle.OracleDG.from_mesh(mesh, p, n_edge_pts=ne, vol_rule=vol_rule)
+    c = o.project_ic(I.vortex)
+    dt = I.fixed_dt(mesh, I.vortex, p, cfl)
+    q.put("ready")
+    steps, el = 0, 0.0
+    while el < seconds or steps == 0:
+        t = time.perf_counter()
+        c = o.ssp_rk3(c, dt, 1)
+        el += time.perf_counter() - t
+        steps += 1
+    q.put((steps, el))
+
+
+def cpu_all_cores(n: int, seconds: float = 8.0, vol_rule: str = "collapsed"):
+    """The oracle as it stands (single-threaded C) run as one independent replica
+    per host core, in spawned processes (a process forked after the first CUDA call
+    could hang): the whole host's throughput on the n x n workload, DOF-updates/s
+    summed over the replicas, each timed over its own steps."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(n, WORKLOAD["p"], WORKLOAD["ne"], WORKLOAD["cfl"], vol_rule,
+                                                       seconds, q)) for _ in range(cores)]
+    for pr in procs:
+        pr.start()
+    got, ready = [], 0
+    while len(got) < cores:
+        item = q.get(timeout=600)
+        if item == "ready":
+            ready += 1
+        else:
+            got.append(item)
+    for pr in procs:
+        pr.join(timeout=60)
+    dof = _dof_per_step(2 * n * n, WORKLOAD["p"])
+    value = sum(dof * st / el for st, el in got)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d independent replicas (one per host core, spawned processes) of the single-threaded "
+                      "oracle, each %d-%d whole SSP-RK3 steps of the %dx%d p=%d vortex (%s volume rule), "
+                      "about %.0f s each" % (cores, min(g[0] for g in got), max(g[0] for g in got), n, n,
+                                             WORKLOAD["p"], vol_rule, seconds)}
 
 
 def cpu_baseline(seconds: float = 12.0, vol_rule: str = "collapsed"):
@@ -328,6 +389,65 @@ def mixed_modes(m, c0, dt, steps, flush, fp64_ms_per_step):
                      "speedup_vs_fp64": fp64_ms_per_step / (ms / steps),
                      "rel_l2_vs_fp64": float(np.linalg.norm(X - R) / np.linalg.norm(R)),
                      "error_after_steps": steps}
+    return out
+
+
+def mixed_config3(steps: int = 100):
+    """The mixed-precision workload as stated: the perturbed vortex on the 512x512
+    mesh (524,288 elements) at p = 4, SSP-RK3.  For float64, 3xTF32 and 1xTF32: the
+    steady-state rate over `steps` steps in one call (CUDA-graph replay; the
+    252 MB state and its work arrays exceed L2, so nothing is flushed), the state
+    error of each tensor-core mode against the float64 run after the same steps,
+    and the per-launch times of the element and edge kernels from the library's
+    CUDA events over 5 plain steps; for the tensor-core modes the element kernel's
+    roofline against the measured HBM copy rate (algorithmic bytes per launch,
+    bytes_element_tc_per_elem)."""
+    import torch
+    from paper_1601_07944_gb300 import dg, inputs as I
+    n, p = 512, 4
+    mesh = I.periodic_mesh(n)
+    m = dg.Mesh.from_mesh(mesh, p)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    c0 = m.project_function(I.perturbed_vortex)
+    hbm, src = hbm_peak()
+    out = {"workload": "perturbed vortex (Fourier perturbations 1e-2, wavenumbers 1-4), 512x512 jittered "
+                       "periodic mesh (524288 elements), p=4, 5-point Gauss edges, SSP-RK3",
+           "steps": steps, "timing": "one %d-step call (CUDA-graph replay), CUDA events; inputs exceed L2" % steps}
+    ref = None
+    fp64_ms = None
+    for prec in ("fp64", "tf32x3", "tf32x1"):
+        c = c0.clone()
+        m.rk_step(c, dt, 17, precision=prec)                       # capture + warm the graph
+        c = c0.clone()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(); a.record()
+        m.rk_step(c, dt, steps, precision=prec)
+        b.record(); torch.cuda.synchronize()
+        m.device_status()
+        ms = a.elapsed_time(b) / steps
+        if ref is None:
+            ref, fp64_ms = c.clone(), ms
+        w = c0.clone()
+        m.set_timing(True)
+        m.rk_step(w, dt, 5, precision=prec)
+        kt = m.kernel_times()
+        m.set_timing(False)
+        el_n, el_ms = kt.get("element", (1, 0.0))
+        fa_n, fa_ms = kt.get("face", (1, 0.0))
+        rec = {"value": _dof_per_step(m.N, p) * steps / (ms * steps * 1e-3), "unit": UNIT, "ms_per_step": ms,
+               "element_ms_per_launch": el_ms / el_n, "face_ms_per_launch": fa_ms / fa_n}
+        if prec != "fp64":
+            nbytes = bytes_element_tc_per_elem(p, m.ne) * m.N
+            ach = nbytes / (el_ms / el_n * 1e-3) / 1e9
+            rec.update({"speedup_vs_fp64": fp64_ms / ms,
+                        "rel_l2_vs_fp64": float(torch.linalg.norm(c - ref) / torch.linalg.norm(ref)),
+                        "error_after_steps": steps,
+                        "roofline": {"bound": "hbm", "kernel": "k_element_tc (tcgen05, %s)" % prec,
+                                     "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                     "traffic": None, "peak_source": src, "bytes_per_launch": nbytes,
+                                     "avg_launch_ms": el_ms / el_n}})
+        out[prec] = rec
+    del m
     return out
 
 
@@ -799,8 +919,10 @@ def run_ours(args, world, rank, local):
             line["paper_steppers"] = paper_steppers(m, c0, dt, max(5, min(args.steps, 20)), flush)
             line["adjoint"] = adjoint_ratio()
             line["vortex_200_steps"] = vortex_error()
+            line["mixed_512_p4"] = mixed_config3()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(vol_rule=args.vol_rule)
+            line["cpu_all_cores"] = cpu_all_cores(WORKLOAD["n"] // 2, vol_rule=args.vol_rule)
     if world > 1:
         import torch.distributed as tdist
         tdist.barrier()
