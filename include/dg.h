@@ -343,8 +343,9 @@ dg_status dg_device_status(dg_mesh *mesh, void *stream);
  *                  that differ bit for bit from the hardware conversion,
  *   mismatches[1]: integer float32 -> float64 conversions that differ,
  *   mismatches[2]: Newton-refined reciprocals more than 1 ulp from 1/x,
- *   mismatches[3]: Newton-refined square roots (of the mixed-precision edge
- *                  flux's sound speeds) more than 1 ulp from sqrt(x).
+ *   mismatches[3]: Newton-refined square roots more than 1 ulp from sqrt(x),
+ *                  or reciprocal square roots more than 2 ulp from 1/sqrt(x)
+ *                  (the sound speeds of the edge flux and of its adjoint).
  * HOST int64_t[4].  Synchronous; allocates 32 bytes. */
 dg_status dg_self_test(int64_t mismatches[4], void *stream);
 

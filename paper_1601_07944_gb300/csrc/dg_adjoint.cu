@@ -21,6 +21,13 @@
  *   k_adj_combine   per element: transposed trace interpolation, plus the linear
  *                   combination of the Runge-Kutta adjoint
  *                   out = x0 X + x1 Y + x2 Z + s (dR/du)^T lam.
+ *
+ * On the collapsed volume grid (the default rule) the element pieces are
+ * sum-factorised as the forward kernel is (k_adj_element_sf, k_adj_combine_sf):
+ * every contraction with a basis table is the transpose, in reverse order, of a
+ * factorised forward contraction with the same table (the collapsed grid is a
+ * tensor grid and phi_j(alpha, beta) = P_a(alpha) chi_j(beta)).  The direct
+ * kernels above serve the symmetric rules.
  */
 #include <cuda_runtime.h>
 
@@ -98,16 +105,13 @@ k_adj_element(const double *__restrict__ u, const double *__restrict__ lam, doub
       double ub[M] = {0.0, 0.0, 0.0, 0.0};
       if (el < ecount) {
         const double *g = geo + (size_t)(e0 + el) * GEO;
-        double b1[M], b2[M], o1[M], o2[M];
+        double b1[M], b2[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          b1[m] = ar[m] * g[0] + as[m] * g[2];
-          b2[m] = ar[m] * g[1] + as[m] * g[3];
+          b1[m] = fma(ar[m], g[0], as[m] * g[2]);
+          b2[m] = fma(ar[m], g[1], as[m] * g[3]);
         }
-        flux_jac_t(U, 1.0, 0.0, gamma, b1, o1);
-        flux_jac_t(U, 0.0, 1.0, gamma, b2, o2);
-#pragma unroll
-        for (int m = 0; m < M; ++m) ub[m] = o1[m] + o2[m];
+        flux_jac_t_xy(U, gamma, b1, b2, ub);
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) sU[i * M + m] = ub[m];
@@ -241,6 +245,317 @@ k_adj_combine(const double *__restrict__ uvol, const double *__restrict__ TB, co
   }
 }
 
+// ---------------------------------------------------------------------------
+// sum-factorised transpose on the collapsed grid
+//
+// Forward (k_element_sf), per variable: W(a,ib) = sum_{j: a(j)=a} chi_j(ib) c_j,
+// U(ia,ib) = sum_a P_a(ia) W(a,ib); at the points Ha = G_r + half(ia) G_s,
+// Hb = G_s; Xa(a,ib) = sum_ia wa P_a'(ia) Ha, Xb(a,ib) = sum_ia wa P_a(ia) Hb;
+// V_j = sum_ib chiA_j(ib) Xa(a_j,ib) + dchiB_j(ib) Xb(a_j,ib).  For a cotangent
+// lb = lam / det J of V the transpose is, per variable,
+//   Xa~(a,ib) = sum_{j: a(j)=a} chiA_j(ib) lb_j,   Xb~(a,ib) = sum_{j: a(j)=a} dchiB_j(ib) lb_j,
+//   Ha~(ia,ib) = sum_a wa P_a'(ia) Xa~(a,ib),      Hb~(ia,ib) = sum_a wa P_a(ia) Xb~(a,ib),
+//   G_r~ = Ha~,  G_s~ = half(ia) Ha~ + Hb~   (the cotangents of G_r, G_s at the point),
+// then through J^tau and the Euler flux Jacobians at U to ub (flux_jac_t_xy), and
+// back to modes by the transposed interpolation
+//   U~(a,ib) = sum_ia P_a(ia) ub(ia,ib),   uvol_j = sum_ib chi_j(ib) U~(a_j,ib).
+// The edge pieces: the transposed lift is the traces of lb weighted by the edge
+// weights (Lf[qk][j] = omega_k phi_j(r_qk)), formed by edge_traces_sf with the
+// weighted tables; the transposed trace interpolation is the forward lift with
+// the unweighted ones.
+// ---------------------------------------------------------------------------
+template <int P, int NE>
+struct AdjSf {
+  static constexpr int NP = (P + 1) * (P + 2) / 2, ND = P + 1, NQ = ND * ND, NF = 3 * NE;
+  static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);
+  static constexpr int TAB = 3 * ND * ND + 3 * NP * ND + ND + 2 * NP * NE + 2 * ND * NE + NP;
+  // per element: u, lb [M][NP] each; the factorisation buffer [ND][ND][12]
+  // (W, Xa~, Xb~ at (a, ib), later U~ with stride 4); ub at the points [NQ][4];
+  // Z_a of u and of lb [M][ND] each
+  static constexpr int XS = 12 * ND * ND;
+  static constexpr int TILE = EB * (2 * M * NP + XS + 4 * NQ + 2 * M * ND);
+  static constexpr int SMEM = (TAB + TILE) * 8;
+};
+
+template <int P, int NE>
+__global__ void __launch_bounds__(kThreads, 2)
+k_adj_element_sf(const double *__restrict__ u, const double *__restrict__ lam, double *__restrict__ uvol,
+                 double *__restrict__ G, double *__restrict__ T, const double *__restrict__ geo, DevTables tab, int N,
+                 double gamma) {
+  using A = AdjSf<P, NE>;
+  constexpr int NP = A::NP, ND = A::ND, NQ = A::NQ, NF = A::NF, EB = A::EB;
+  extern __shared__ double smem[];
+  double *sPa = smem;                  // [ND][ND]   P_a(alpha_ia)
+  double *sPaW = sPa + ND * ND;        // [ND][ND]   wa P_a
+  double *sdPaW = sPaW + ND * ND;      // [ND][ND]   wa P_a'
+  double *sChi = sdPaW + ND * ND;      // [NP][ND]   chi_j(beta_ib)
+  double *sChiA = sChi + NP * ND;      // [NP][ND]   chi_j wb / (4 (1-s))
+  double *sdChiB = sChiA + NP * ND;    // [NP][ND]   chi_j' wb / 4
+  double *sHalf = sdChiB + NP * ND;    // [ND]       (1 + alpha_ia) / 2
+  double *sEChi = sHalf + ND;          // [NP][NE]   chi_j(xi_k)
+  double *sEWChi = sEChi + NP * NE;    // [NP][NE]   omega_k chi_j(xi_k)
+  double *sEWPa = sEWChi + NP * NE;    // [ND][NE]   omega_k P_a(xi_k)
+  double *sEPa = sEWPa + ND * NE;      // [ND][NE]   P_a(xi_k)
+  double *sEChiM1 = sEPa + ND * NE;    // [NP]       chi_j(-1)
+  double *sC = sEChiM1 + NP;           // [EB][M][NP]      u
+  double *sL = sC + EB * M * NP;       // [EB][M][NP]      lam / det J
+  double *sX = sL + EB * M * NP;       // [EB][ND][ND][12] W, Xa~, Xb~; then U~ [EB][ND][ND][4]
+  double *sB = sX + EB * A::XS;        // [EB][NQ][4]      ub
+  double *sZ = sB + EB * NQ * 4;       // [EB][M][2][ND]   Z_a of u, of lb
+
+  for (int i = threadIdx.x; i < ND * ND; i += blockDim.x) {
+    sPa[i] = tab.SPa[i]; sPaW[i] = tab.SPaW[i]; sdPaW[i] = tab.SdPaW[i];
+  }
+  for (int i = threadIdx.x; i < NP * ND; i += blockDim.x) {
+    sChi[i] = tab.SChi[i]; sChiA[i] = tab.SChiA[i]; sdChiB[i] = tab.SdChiB[i];
+  }
+  for (int i = threadIdx.x; i < ND; i += blockDim.x) sHalf[i] = tab.SHalf[i];
+  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) { sEChi[i] = tab.EChi[i]; sEWChi[i] = tab.EWChi[i]; }
+  for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) { sEWPa[i] = tab.EWPa[i]; sEPa[i] = tab.EPa[i]; }
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) sEChiM1[i] = tab.EChiM1[i];
+
+  const int ntiles = (N + EB - 1) / EB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e0 = tile * EB;
+    const int ecount = min(EB, N - e0);
+    __syncthreads();
+    const double *su = u + (size_t)e0 * M * NP;
+    const double *sl = lam + (size_t)e0 * M * NP;
+    for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x) {
+      const bool in = i < ecount * M * NP;
+      const int el = i / (M * NP);
+      sC[i] = in ? su[i] : 0.0;
+      sL[i] = in ? sl[i] * geo[(size_t)(e0 + el) * GEO + 4] : 0.0;
+    }
+    __syncthreads();
+
+    // W, Xa~, Xb~ at (a, ib); one item per (element, ib, variable) over all modes
+    // (Xa~(0, .) is not formed: wa P_0' = 0 takes it out of Ha~)
+    for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
+      const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
+      const double *cm = sC + (el * M + m) * NP, *lm = sL + (el * M + m) * NP;
+      double w[ND], xa[ND], xb[ND];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) { w[a] = 0.0; xa[a] = 0.0; xb[a] = 0.0; }
+#pragma unroll
+      for (int d = 0; d <= P; ++d)
+#pragma unroll
+        for (int b = 0; b <= d; ++b) {
+          const int j = d * (d + 1) / 2 + b, a = d - b;
+          w[a] = fma(sChi[j * ND + ib], cm[j], w[a]);
+          if (a > 0) xa[a] = fma(sChiA[j * ND + ib], lm[j], xa[a]);
+          xb[a] = fma(sdChiB[j * ND + ib], lm[j], xb[a]);
+        }
+#pragma unroll
+      for (int a = 0; a < ND; ++a) {
+        double *x = sX + ((el * ND + a) * ND + ib) * 12;
+        x[m] = w[a];
+        x[4 + m] = xa[a];
+        x[8 + m] = xb[a];
+      }
+    }
+    __syncthreads();
+
+    // points: U, the cotangents of G_r and G_s, through J^tau and the flux
+    // Jacobians to ub; one item per (element, point)
+    for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
+      const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
+      const double *x0 = sX + ((el * ND) * ND + ib) * 12;
+      double U[M], ha[M], hb[M];
+      const double pw0 = sPaW[ia];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        U[m] = x0[m];                                   // P_0 = 1
+        ha[m] = 0.0;
+        hb[m] = pw0 * x0[8 + m];
+      }
+#pragma unroll
+      for (int a = 1; a < ND; ++a) {
+        const double pa = sPa[a * ND + ia], dpw = sdPaW[a * ND + ia], pw = sPaW[a * ND + ia];
+        const double *x = sX + ((el * ND + a) * ND + ib) * 12;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          U[m] = fma(pa, x[m], U[m]);
+          ha[m] = fma(dpw, x[4 + m], ha[m]);
+          hb[m] = fma(pw, x[8 + m], hb[m]);
+        }
+      }
+      double ub[M] = {0.0, 0.0, 0.0, 0.0};
+      if (el < ecount) {
+        const double *g = geo + (size_t)(e0 + el) * GEO;
+        const double half = sHalf[ia];
+        double bx[M], by[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const double ar = ha[m], as = fma(half, ha[m], hb[m]);
+          bx[m] = fma(ar, g[0], as * g[2]);
+          by[m] = fma(ar, g[1], as * g[3]);
+        }
+        flux_jac_t_xy(U, gamma, bx, by, ub);
+      }
+      double *b = sB + (size_t)i * 4;
+#pragma unroll
+      for (int m = 0; m < M; ++m) b[m] = ub[m];
+    }
+    __syncthreads();
+
+    // U~(a, ib) = sum_ia P_a(ia) ub(ia, ib); one item per (element, ib, variable)
+    for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
+      const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
+      double ut[ND];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) ut[a] = 0.0;
+#pragma unroll
+      for (int ia = 0; ia < ND; ++ia) {
+        const double b = sB[((el * NQ) + ib * ND + ia) * 4 + m];
+        ut[0] += b;
+#pragma unroll
+        for (int a = 1; a < ND; ++a) ut[a] = fma(sPa[a * ND + ia], b, ut[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < ND; ++a) sX[((el * ND + a) * ND + ib) * 4 + m] = ut[a];
+    }
+    // Z_a of u and of lb (face 0 lies on beta = -1), one item per (element, variable)
+    for (int i = threadIdx.x; i < EB * M; i += blockDim.x) {
+      double z[ND];
+      face0_z<P>(sC + i * NP, sEChiM1, z);
+#pragma unroll
+      for (int a = 0; a < ND; ++a) sZ[i * 2 * ND + a] = z[a];
+      face0_z<P>(sL + i * NP, sEChiM1, z);
+#pragma unroll
+      for (int a = 0; a < ND; ++a) sZ[i * 2 * ND + ND + a] = z[a];
+    }
+    __syncthreads();
+
+    // modes: uvol_j = sum_ib chi_j(ib) U~(a_j, ib)
+    for (int i = threadIdx.x; i < ecount * NP; i += blockDim.x) {
+      const int el = i / NP, j = i - el * NP;
+      int d = 0;
+      while ((d + 1) * (d + 2) / 2 <= j) ++d;
+      const int a = d - (j - d * (d + 1) / 2);
+      double acc[M] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int ib = 0; ib < ND; ++ib) {
+        const double ch = sChi[j * ND + ib];
+        const double *x = sX + ((el * ND + a) * ND + ib) * 4;
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m] = fma(ch, x[m], acc[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) uvol[((size_t)(e0 + el) * M + m) * NP + j] = acc[m];
+    }
+    // edges: traces of u (T) and the weighted traces of lb (G, the transposed
+    // lift); one item per (element, variable, edge point k)
+    for (int i = threadIdx.x; i < ecount * M * NE; i += blockDim.x) {
+      const int el = i / (M * NE), m = (i / NE) % M, k = i % NE;
+      const int em = el * M + m;
+      const size_t o = (size_t)(e0 + el) * NF * M + m;
+      double t0, t1, t2;
+      edge_traces_sf<P, NE>(sC + em * NP, sZ + em * 2 * ND, sEPa, sEChi, k, t0, t1, t2);
+      T[o + k * M] = t0;
+      T[o + (NE + k) * M] = t1;
+      T[o + (3 * NE - 1 - k) * M] = t2;
+      edge_traces_sf<P, NE>(sL + em * NP, sZ + em * 2 * ND + ND, sEWPa, sEWChi, k, t0, t1, t2);
+      G[o + k * M] = t0;
+      G[o + (NE + k) * M] = t1;
+      G[o + (3 * NE - 1 - k) * M] = t2;
+    }
+  }
+}
+
+// Transposed trace interpolation, sum-factorised (the forward lift of
+// k_element_sf with the unweighted edge tables), and the Runge-Kutta adjoint's
+// combination out = x0 X + x1 Y + x2 Z + s (uvol + B_f^T TB).
+template <int P, int NE>
+__global__ void __launch_bounds__(kThreads)
+k_adj_combine_sf(const double *__restrict__ uvol, const double *__restrict__ TB, DevTables tab, const double *X,
+                 const double *Y, const double *Z, double x0, double x1, double x2, double s, double *out, int N) {
+  constexpr int NP = (P + 1) * (P + 2) / 2, ND = P + 1, NF = 3 * NE;
+  constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);
+  constexpr int LW = ND + 2 * NE;                  // Q_a, then G_even,k, G_odd,k
+  __shared__ double sEPa[ND * NE], sEChi[NP * NE], sEChiM1[NP];
+  __shared__ double sW[EB * M * LW];
+  for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sEPa[i] = tab.EPa[i];
+  for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) sEChi[i] = tab.EChi[i];
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) sEChiM1[i] = tab.EChiM1[i];
+  const int ntiles = (N + EB - 1) / EB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e0 = tile * EB;
+    const int ecount = min(EB, N - e0);
+    __syncthreads();
+    // per (element, variable): Q_a = sum_k P_a(xi_k) TB0_k, G_even/odd,k = TB1_k +/- TB2_{NE-1-k}
+    for (int i = threadIdx.x; i < ecount * M; i += blockDim.x) {
+      const int el = i / M, m = i % M;
+      const double *tb = TB + (size_t)(e0 + el) * NF * M + m;
+      double f[NF];
+#pragma unroll
+      for (int x = 0; x < NF; ++x) f[x] = tb[x * M];
+      double *w = sW + i * LW;
+#pragma unroll
+      for (int a = 0; a < ND; ++a) {
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) q = fma(sEPa[a * NE + k], f[k], q);
+        w[a] = q;
+      }
+#pragma unroll
+      for (int k = 0; k < NE; ++k) {
+        w[ND + k] = f[NE + k] + f[3 * NE - 1 - k];
+        w[ND + NE + k] = f[NE + k] - f[3 * NE - 1 - k];
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ecount * M * NP; i += blockDim.x) {
+      const int em = i / NP, j = i - em * NP;
+      int d = 0;
+      while ((d + 1) * (d + 2) / 2 <= j) ++d;
+      const int a = d - (j - d * (d + 1) / 2);
+      const double *w = sW + em * LW;
+      double acc = sEChiM1[j] * w[a];
+      const double *g = w + ND + (a & 1) * NE;
+#pragma unroll
+      for (int k = 0; k < NE; ++k) acc = fma(sEChi[j * NE + k], g[k], acc);
+      const size_t idx = (size_t)e0 * M * NP + i;
+      double v = s * (uvol[idx] + acc);
+      if (X) v = fma(x0, X[idx], v);
+      if (Y) v = fma(x1, Y[idx], v);
+      if (Z) v = fma(x2, Z[idx], v);
+      out[idx] = v;
+    }
+  }
+}
+
+template <int P, int NE>
+int run_adj_sf(const dg_mesh *m, const double *u, const double *lam, double *uvol, double *G, double *T, double *TB,
+               const double *X, const double *Y, const double *Z, double x0, double x1, double x2, double s,
+               double *out, cudaStream_t st) {
+  using A = AdjSf<P, NE>;
+  static PerDevice attr_set;
+  if (!attr_set.test(m->device)) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_element_sf<P, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, A::SMEM);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_adj_element_sf<P, NE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return (int)e;
+    attr_set.set(m->device);
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_element_sf<P, NE>, kThreads, A::SMEM);
+  if (e != cudaSuccess) return (int)e;
+  if (per_sm < 1) per_sm = 1;
+  const int ntiles = (int)((m->N + A::EB - 1) / A::EB);
+  int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
+  k_adj_element_sf<P, NE><<<grid, kThreads, A::SMEM, st>>>(u, lam, uvol, G, T, m->geo, m->tab, (int)m->N, m->gamma);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  const int64_t nf = m->F * NE;
+  k_adj_face<NE><<<(int)((nf + kThreads - 1) / kThreads), kThreads, 0, st>>>(T, G, TB, m->face_conn, m->face_geo,
+                                                                             m->bstate, m->N, m->F, m->gamma,
+                                                                             m->err_flag);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  grid = ntiles < m->num_sms * 4 ? ntiles : m->num_sms * 4;
+  k_adj_combine_sf<P, NE><<<grid, kThreads, 0, st>>>(uvol, TB, m->tab, X, Y, Z, x0, x1, x2, s, out, (int)m->N);
+  return (int)cudaGetLastError();
+}
+
 template <int P, int NE, int Q>
 int run_adj(const dg_mesh *m, const double *u, const double *lam, double *uvol, double *G, double *T,
             double *TB, const double *X, const double *Y, const double *Z, double x0, double x1, double x2,
@@ -284,7 +599,7 @@ int launch_rhs_vjp(const dg_mesh *m, const double *u, const double *lam, double 
 #define CALL(P, NE)                                                                                  \
   (m->rule == DG_RULE_SYMMETRIC                                                                      \
        ? run_adj<P, NE, sym_points(P)>(m, u, lam, uvol, G, T, TB, X, Y, Z, x0, x1, x2, s, out, st)  \
-       : run_adj<P, NE, 0>(m, u, lam, uvol, G, T, TB, X, Y, Z, x0, x1, x2, s, out, st))
+       : run_adj_sf<P, NE>(m, u, lam, uvol, G, T, TB, X, Y, Z, x0, x1, x2, s, out, st))
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);

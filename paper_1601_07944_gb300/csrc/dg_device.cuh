@@ -229,64 +229,132 @@ __device__ __forceinline__ int64_t checked(int64_t i, int64_t n, int *err) {
   return i;
 }
 
-// out = (d(F(U).n)/dU)^T b for the Euler flux F.n = (rho vn, mx vn + p nx,
-// my vn + p ny, (E+p) vn), using d vn/dU = (-vn, nx, ny, 0)/rho and
-// dp/dU = (gamma-1) (|v|^2/2, -u, -v, 1).
-__device__ __forceinline__ void flux_jac_t(const double U[M], double nx, double ny, double gamma,
-                                           const double b[M], double out[M]) {
-  const double inv = recip(U[0]);
-  const double u = U[1] * inv, v = U[2] * inv;
-  const double q2 = u * u + v * v;
-  const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * q2);
-  const double vn = u * nx + v * ny;
-  const double sig = (b[1] * U[1] + b[2] * U[2] + b[3] * (U[3] + p)) * inv;
-  const double tau = (gamma - 1.0) * (b[1] * nx + b[2] * ny + b[3] * vn);
-  out[0] = -sig * vn + 0.5 * tau * q2;
-  out[1] = b[0] * nx + b[1] * vn + sig * nx - tau * u;
-  out[2] = b[0] * ny + b[2] * vn + sig * ny - tau * v;
-  out[3] = b[3] * vn + tau;
+// 1/sqrt(x) for a finite x > 0 in float64: Newton-Raphson refinement of a float32
+// estimate r (rsqrt.approx.ftz.f32 on x rounded to float32), twice
+// r <- r + r (1/2 - (x/2) r^2); the estimate is good to about 2^-22 and each step
+// squares the relative error (dg_self_test checks the result against
+// 1 / sqrt(x): at most 1 ulp apart).  Seven float64 operations.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const float xf = f64_to_f32_dev(x);
+  float rf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  double r = f32_to_f64_dev(rf);
+  const double h = 0.5 * x;
+  r = fma(r, fma(-h * r, r, 0.5), r);
+  return fma(r, fma(-h * r, r, 0.5), r);
 }
 
-// Wave speed s = |v.n| + c and its gradient (d|x|/dx = sign(x), sign(0) = 0).
-__device__ __forceinline__ double wave_speed_grad(const double U[M], double nx, double ny,
-                                                  double gamma, double ds[M]) {
+// x with the sign of s applied, and 0 where s is zero (d|s|/ds times x with
+// sign(0) = 0), on the bit patterns
+__device__ __forceinline__ double sign_times(double s, double x) {
+  const int hi = __double2hiint(s), lo = __double2loint(s);
+  const bool zero = ((hi & 0x7FFFFFFF) | lo) == 0;
+  const double y = __hiloint2double(__double2hiint(x) ^ (hi & (int)0x80000000), __double2loint(x));
+  return zero ? 0.0 : y;
+}
+
+// The quantities of one Euler state that the transposed flux and wave-speed
+// Jacobians share: 1/rho, velocity (u, v), |v|^2, pressure p, E + p, v.n.
+struct EulerSide {
+  double inv, u, v, q2, p, H, vn;
+};
+__device__ __forceinline__ EulerSide euler_side(const double U[M], double nx, double ny, double g1) {
+  EulerSide s;
+  s.inv = recip(U[0]);
+  s.u = U[1] * s.inv;
+  s.v = U[2] * s.inv;
+  s.q2 = fma(s.u, s.u, s.v * s.v);
+  s.p = g1 * fma(-0.5 * U[0], s.q2, U[3]);
+  s.H = U[3] + s.p;
+  s.vn = fma(s.u, nx, s.v * ny);
+  return s;
+}
+
+// out = (d(F(U).n)/dU)^T b for the Euler flux F.n = (rho vn, mx vn + p nx,
+// my vn + p ny, (E+p) vn), using d vn/dU = (-vn, nx, ny, 0)/rho and
+// dp/dU = (gamma-1) (|v|^2/2, -u, -v, 1):
+//   sig = (b1 mx + b2 my + b3 (E+p)) / rho,  tau = (gamma-1) (b1 nx + b2 ny + b3 vn),
+//   out = (-sig vn + tau |v|^2 / 2, b0 nx + b1 vn + sig nx - tau u,
+//          b0 ny + b2 vn + sig ny - tau v, b3 vn + tau).
+__device__ __forceinline__ void flux_jac_t(const double U[M], const EulerSide &s, double nx, double ny, double g1,
+                                           const double b[M], double out[M]) {
+  const double sig = fma(b[1], U[1], fma(b[2], U[2], b[3] * s.H)) * s.inv;
+  const double tau = g1 * fma(b[1], nx, fma(b[2], ny, b[3] * s.vn));
+  out[0] = fma(0.5 * tau, s.q2, -sig * s.vn);
+  out[1] = fma(b[0], nx, fma(b[1], s.vn, fma(sig, nx, -tau * s.u)));
+  out[2] = fma(b[0], ny, fma(b[2], s.vn, fma(sig, ny, -tau * s.v)));
+  out[3] = fma(b[3], s.vn, tau);
+}
+
+// The volume term's pull-back at a point: out = A_x(U)^T bx + A_y(U)^T by for the
+// Jacobians A_x, A_y of the two Euler fluxes (flux_jac_t with n = (1, 0) and
+// (0, 1), the shared terms formed once):
+//   out = (T |v|^2/2 - sx u - sy v, bx0 + sx + bx1 u + by1 v - T u,
+//          by0 + sy + bx2 u + by2 v - T v, bx3 u + by3 v + T)
+// with sx = (bx1 mx + bx2 my + bx3 (E+p)) / rho, sy alike with by,
+// T = (gamma-1) (bx1 + bx3 u + by2 + by3 v).
+__device__ __forceinline__ void flux_jac_t_xy(const double U[M], double gamma, const double bx[M],
+                                              const double by[M], double out[M]) {
+  const double g1 = gamma - 1.0;
   const double inv = recip(U[0]);
   const double u = U[1] * inv, v = U[2] * inv;
-  const double q2 = u * u + v * v;
-  const double p = (gamma - 1.0) * (U[3] - 0.5 * U[0] * q2);
-  const double vn = u * nx + v * ny;
-  const double c = sqrt(gamma * p * inv);
-  const double sg = vn > 0.0 ? 1.0 : (vn < 0.0 ? -1.0 : 0.0);
-  const double k = gamma / (2.0 * c) * inv;          // dc = k (dp - p/rho drho)
+  const double q2 = fma(u, u, v * v);
+  const double H = fma(g1, fma(-0.5 * U[0], q2, U[3]), U[3]);
+  const double sx = fma(bx[1], U[1], fma(bx[2], U[2], bx[3] * H)) * inv;
+  const double sy = fma(by[1], U[1], fma(by[2], U[2], by[3] * H)) * inv;
+  const double T = g1 * (fma(bx[3], u, bx[1]) + fma(by[3], v, by[2]));
+  out[0] = fma(0.5 * T, q2, -fma(sx, u, sy * v));
+  out[1] = bx[0] + sx + fma(bx[1], u, fma(by[1], v, -T * u));
+  out[2] = by[0] + sy + fma(bx[2], u, fma(by[2], v, -T * v));
+  out[3] = fma(bx[3], u, fma(by[3], v, T));
+}
+
+// Wave speed s = |v.n| + c of a state and, when ds is not null, its gradient
+// (d|x|/dx = sign(x), sign(0) = 0):  dc = k (dp - p/rho drho), k = gamma / (2 c rho).
+__device__ __forceinline__ double wave_speed(const EulerSide &s, double gamma, double &rc) {
+  const double x = gamma * s.p * s.inv;          // c^2
+  rc = rsqrt_nr(x);                              // 1/c
+  return fabs(s.vn) + x * rc;
+}
+__device__ __forceinline__ void wave_speed_grad(const EulerSide &s, double rc, double nx, double ny, double gamma,
+                                                double ds[M]) {
   const double g1 = gamma - 1.0;
-  ds[0] = sg * (-vn * inv) + k * (g1 * 0.5 * q2 - p * inv);
-  ds[1] = sg * (nx * inv) + k * (-g1 * u);
-  ds[2] = sg * (ny * inv) + k * (-g1 * v);
-  ds[3] = k * g1;
-  return fabs(vn) + c;
+  const double k = (0.5 * gamma) * s.inv * rc;
+  const double kg = k * g1;
+  ds[0] = sign_times(s.vn, -s.vn * s.inv) + k * fma(0.5 * g1, s.q2, -s.p * s.inv);
+  ds[1] = fma(-kg, s.u, sign_times(s.vn, nx * s.inv));
+  ds[2] = fma(-kg, s.v, sign_times(s.vn, ny * s.inv));
+  ds[3] = kg;
 }
 
 // Transposed Lax-Friedrichs Jacobians applied to a cotangent fb:
 //   gl = (dF_hat/dUl)^T fb,  gr = (dF_hat/dUr)^T fb,
 // dF_hat/dUl = A(Ul)/2 + alpha/2 I - (Ur-Ul)/2 (x) d alpha/dUl, and alike for Ur;
-// d alpha follows the larger wave speed, the left one at a tie.
+// d alpha follows the larger wave speed, the left one at a tie (the speeds are
+// compared on their bit patterns: both are >= 0).
 __device__ __forceinline__ void lax_friedrichs_vjp(const double ul[M], const double ur[M], double nx,
                                                    double ny, double gamma, const double fb[M],
                                                    double gl[M], double gr[M]) {
-  double dsl[M], dsr[M], jl[M], jr[M];
-  const double sl = wave_speed_grad(ul, nx, ny, gamma, dsl);
-  const double sr = wave_speed_grad(ur, nx, ny, gamma, dsr);
-  const bool left = sl >= sr;
+  const double g1 = gamma - 1.0;
+  const EulerSide Sl = euler_side(ul, nx, ny, g1), Sr = euler_side(ur, nx, ny, g1);
+  double rcl, rcr;
+  const double sl = wave_speed(Sl, gamma, rcl), sr = wave_speed(Sr, gamma, rcr);
+  const bool left = __double_as_longlong(sl) >= __double_as_longlong(sr);
   const double a = left ? sl : sr;
-  double jump = 0.0;
+  double ds[M];
+  wave_speed_grad(left ? Sl : Sr, left ? rcl : rcr, nx, ny, gamma, ds);
+  double jump = (ur[0] - ul[0]) * fb[0];
 #pragma unroll
-  for (int m = 0; m < M; ++m) jump += (ur[m] - ul[m]) * fb[m];
-  flux_jac_t(ul, nx, ny, gamma, fb, jl);
-  flux_jac_t(ur, nx, ny, gamma, fb, jr);
+  for (int m = 1; m < M; ++m) jump = fma(ur[m] - ul[m], fb[m], jump);
+  double jl[M], jr[M];
+  flux_jac_t(ul, Sl, nx, ny, g1, fb, jl);
+  flux_jac_t(ur, Sr, nx, ny, g1, fb, jr);
+  const double ha = 0.5 * a, hj = 0.5 * jump;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    gl[m] = 0.5 * jl[m] + 0.5 * a * fb[m] - (left ? 0.5 * jump * dsl[m] : 0.0);
-    gr[m] = 0.5 * jr[m] - 0.5 * a * fb[m] - (left ? 0.0 : 0.5 * jump * dsr[m]);
+    const double t = hj * ds[m];
+    gl[m] = fma(0.5, jl[m], fma(ha, fb[m], left ? -t : 0.0));
+    gr[m] = fma(0.5, jr[m], fma(-ha, fb[m], left ? 0.0 : -t));
   }
 }
 

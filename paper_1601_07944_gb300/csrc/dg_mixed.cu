@@ -111,8 +111,9 @@ __global__ void k_convert_check(int n, unsigned long long *bad) {
   const double d_hw = (double)f_hw, d_int = tc::f32_to_f64(f_hw);
   if (__float_as_uint(f_hw) != __float_as_uint(f_int)) atomicAdd(bad, 1ull);
   if (__double_as_longlong(d_hw) != __double_as_longlong(d_int)) atomicAdd(bad + 1, 1ull);
-  // Newton-refined reciprocal and square root against the correctly rounded
-  // 1/x and sqrt(x): at most 1 ulp apart
+  // Newton-refined reciprocal and square root against the correctly rounded 1/x
+  // and sqrt(x): at most 1 ulp apart; the reciprocal square root against
+  // 1/sqrt(x), itself rounded twice: at most 2 ulp apart
   const double ax = fabs(x);
   if (ax != 0.0) {
     const long long q = __double_as_longlong(1.0 / ax), r = __double_as_longlong(recip(ax));
@@ -120,7 +121,9 @@ __global__ void k_convert_check(int n, unsigned long long *bad) {
     if (d > 1) atomicAdd(bad + 2, 1ull);
     const long long qs = __double_as_longlong(sqrt(ax)), rs = __double_as_longlong(sqrt_nr(ax));
     const long long ds = qs > rs ? qs - rs : rs - qs;
-    if (ds > 1) atomicAdd(bad + 3, 1ull);
+    const long long qr = __double_as_longlong(1.0 / sqrt(ax)), rr = __double_as_longlong(rsqrt_nr(ax));
+    const long long dr = qr > rr ? qr - rr : rr - qr;
+    if (ds > 1 || dr > 2) atomicAdd(bad + 3, 1ull);
   }
 }
 

@@ -142,3 +142,9 @@ def test_autograd_central_differences(dgmod, oracle_mod, n, p, steps, every, nfd
         cm = c0.clone(); cm[idx] -= h
         g_fd = (loss_of(cp) - loss_of(cm)) / (2 * h)
         assert abs(g_fd - g[idx]) <= 1e-6 * abs(g[idx]) + floor, (idx, g_fd, g[idx], floor)
+        strong += abs(g[idx]) > 1e3 * floor
+    # the relative criterion was exercised: at least the mean-mode coefficients'
+    # gradients stand three orders above the rounding floor
+    assert strong >= 1, (strong, floor)
+    idx0 = (int(rng.integers(0, c0.shape[0])), 0, 0)
+    assert abs(g[idx0]) > 1e3 * floor, (g[idx0], floor)
