@@ -208,6 +208,17 @@ __device__ __forceinline__ void ghost_state(int code, const double ul[M], double
   }
 }
 
+// The edge flux of one stage, float64: fhat[f][k][m] = l_f F_hat(U_l(r_{L,k}),
+// U_r(r_{R,NE-1-k}), n_f) for every (edge, point) item; block `block` of
+// `nblocks` takes the block-th equal slice of the items, so that a grid of what
+// is resident at once gives every SM the same share (k_face, and the edge phase
+// of the fused small-mesh stepper).
+template <int NE>
+__device__ __forceinline__ void face_flux_points(const double *__restrict__ trace, double *__restrict__ fhat,
+                                                 const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg,
+                                                 const double *__restrict__ bstate, int64_t N, int64_t F,
+                                                 double gamma, int *err, int block, int nblocks);
+
 // device error flag bits (read by dg_device_status)
 constexpr int kErrTimeout = 1;      // a bounded tensor-core wait expired
 constexpr int kErrNonPhysical = 2;  // rho <= 0 or p <= 0 met at a quadrature point
@@ -227,6 +238,42 @@ __device__ __forceinline__ int64_t checked(int64_t i, int64_t n, int *err) {
   (void)n; (void)err;
 #endif
   return i;
+}
+
+template <int NE>
+__device__ __forceinline__ void face_flux_points(const double *__restrict__ trace, double *__restrict__ fhat,
+                                                 const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg,
+                                                 const double *__restrict__ bstate, int64_t N, int64_t F,
+                                                 double gamma, int *err, int block, int nblocks) {
+  constexpr int NF = 3 * NE;
+  bool ok = true;
+  const int64_t n = F * NE;
+  const int64_t lo = n * block / nblocks, hi = n * (block + 1) / nblocks;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int64_t f = i / NE;
+    const int k = (int)(i - f * NE);
+    const FaceConn cn = conn[f];
+    const FaceGeo g = fg[f];
+    const double *pl = trace + ((size_t)checked(cn.l, N, err) * NF + checked(cn.L, 3, err) * NE + k) * M;
+    double ul[M], ur[M], Fh[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) ul[m] = pl[m];
+    if (cn.r < 0) {
+      // boundary face (the first faces of the list): the ghost state at the same point
+      ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
+    } else {
+      const double *pr =
+          trace + ((size_t)checked(cn.r, N, err) * NF + checked(cn.R, 3, err) * NE + (NE - 1 - k)) * M;
+#pragma unroll
+      for (int m = 0; m < M; ++m) ur[m] = pr[m];
+    }
+    // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
+    ok &= lax_friedrichs_edge(ul, ur, g, gamma, Fh);
+    double *dst = fhat + (size_t)i * M;
+#pragma unroll
+    for (int m = 0; m < M; ++m) dst[m] = Fh[m];
+  }
+  if (!ok) atomicOr(err, kErrNonPhysical);
 }
 
 // 1/sqrt(x) for a finite x > 0 in float64: Newton-Raphson refinement of a float32

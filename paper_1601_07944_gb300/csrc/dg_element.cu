@@ -41,12 +41,14 @@ namespace {
 // Q N_p products per variable for each; the lift, the stage update and the
 // traces are the same in both forms.
 // ---------------------------------------------------------------------------
-template <int P, int NE, int Q>
+// EBX > 0 overrides the elements per tile (the fused small-mesh stepper's small
+// tiles spread a small mesh over many SMs)
+template <int P, int NE, int Q, int EBX = 0>
 struct SfCfg {
   using C = Cfg<P, NE, Q>;
   static constexpr bool DIRECT = Q > 0;
   static constexpr int NP = C::NP, ND = C::ND, NQ = C::NQ, NF = C::NF;
-  static constexpr int EB = P <= 1 ? 64 : (P <= 3 ? 32 : 16);
+  static constexpr int EB = EBX > 0 ? EBX : (P <= 1 ? 64 : (P <= 3 ? 32 : 16));
   // per element and variable, the edge-flux buffer holds the NF gathered fluxes,
   // then (in place) the LW sums of the factorised lift
   static constexpr int LW = ND + 2 * NE;
@@ -94,15 +96,16 @@ __device__ __forceinline__ int mode_a_ge1(int r) {
   return d * (d + 1) / 2 + (r - d * (d - 1) / 2);
 }
 
-template <int P, int NE, int Q>
-__global__ void __launch_bounds__(kThreads, 2)
-k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
-             const double *__restrict__ fhat, const double *__restrict__ geo,
-             const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
-             double gamma, int *err) {
-  using S = SfCfg<P, NE, Q>;
+// The element stage on the tiles block, block + nblocks, ... (k_element_sf, and
+// the element phase of the fused small-mesh stepper); smem holds SfCfg::SMEM bytes.
+template <int P, int NE, int Q, int EBX = 0>
+__device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, const double *u0, double *out,
+                                                 double *__restrict__ trace_out, const double *__restrict__ fhat,
+                                                 const double *__restrict__ geo, const int32_t *__restrict__ elem_face,
+                                                 const DevTables &tab, int N, int64_t F, const StageUpdate &su,
+                                                 int mode, double gamma, int *err, int block, int nblocks) {
+  using S = SfCfg<P, NE, Q, EBX>;
   constexpr int NP = S::NP, ND = S::ND, NQ = S::NQ, NF = S::NF, EB = S::EB;
-  extern __shared__ double smem[];
   double *sPa = smem;                  // [ND][ND]   P_a(alpha_ia)
   double *sPaW = sPa + ND * ND;        // [ND][ND]   wa P_a
   double *sdPaW = sPaW + ND * ND;      // [ND][ND]   wa P_a'
@@ -143,7 +146,7 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   }
 
   const int ntiles = (N + EB - 1) / EB;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = block; tile < ntiles; tile += nblocks) {
     const int e0 = tile * EB;
     const int ecount = min(EB, N - e0);
     __syncthreads();
@@ -436,6 +439,17 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
   }
 }
 
+template <int P, int NE, int Q>
+__global__ void __launch_bounds__(kThreads, 2)
+k_element_sf(const double *c, const double *u0, double *out, double *__restrict__ trace_out,
+             const double *__restrict__ fhat, const double *__restrict__ geo,
+             const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
+             double gamma, int *err) {
+  extern __shared__ double smem[];
+  element_sf_tiles<P, NE, Q>(smem, c, u0, out, trace_out, fhat, geo, elem_face, tab, N, F, su, mode, gamma, err,
+                             blockIdx.x, gridDim.x);
+}
+
 
 template <int P, int NE, int Q>
 int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
@@ -460,7 +474,181 @@ int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *
   return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// fused small-mesh stepper
+//
+// On a mesh whose element tiles fit in one wave of the GPU, a stage's two
+// launches (edge flux, element) do a few microseconds of work each and the step
+// is bound by launch latency (the paper's Section 7.1 finds its small meshes
+// alike).  This kernel runs every stage of a whole call inside one cooperative
+// launch: the edge phase (face_flux_points) and the element phase
+// (element_sf_tiles) of the same code as k_face and k_element_sf, separated by a
+// barrier over the grid, so the results are bitwise those of the separate
+// launches.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kGridWaitNs = 2000000000ull;    // 2 s per barrier before giving up
+
+// All blocks of the (co-resident) grid meet here: one thread per block arrives on
+// a counter, the last one resets it and advances the generation the others
+// wait on.  The wait is bounded: after kGridWaitNs it records kErrTimeout and
+// returns false, and the caller leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();                                  // this block's writes before its arrival
+    int ok = 1;
+    if (atomicAdd(bar, 1u) + 1u == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = tc::global_ns();
+      while (*gen == g) {
+        if (tc::global_ns() - t0 > kGridWaitNs) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();                                  // the other blocks' writes after it
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+constexpr int kSmallThreads = 128;
+constexpr int kSmallTiles[2] = {4, 8};          // elements per tile of the two variants
+
+template <int P, int NE, int Q, int EBX>
+__global__ void __launch_bounds__(kSmallThreads, 4)
+k_rk_small(double *c, double *S, double *A, double *trace, double *fhat, const double *__restrict__ geo,
+           const int32_t *__restrict__ elem_face, const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg,
+           const double *__restrict__ bstate, DevTables tab, int N, int64_t F, double gamma, double dt, int nsteps,
+           int method, unsigned *bar, int *err) {
+  extern __shared__ double smem[];
+  const unsigned nb = gridDim.x;
+  const int ns = rk_num_stages(method);
+  for (int step = 0; step < nsteps; ++step)
+    for (int i = 0; i < ns; ++i) {
+      const RkStage st = rk_stage(method, i, dt, c, S, A);
+      face_flux_points<NE>(trace, fhat, conn, fg, bstate, N, F, gamma, err, blockIdx.x, nb);
+      if (!grid_barrier(bar, nb, err)) return;
+      element_sf_tiles<P, NE, Q, EBX>(smem, st.cin, st.u0, st.out, trace, fhat, geo, elem_face, tab, N, F, st.su, 1,
+                                      gamma, err, blockIdx.x, nb);
+      if (!grid_barrier(bar, nb, err)) return;
+    }
+}
+
+// Resident blocks per SM of the two variants on the mesh's device (0: not
+// launchable), asked once per device.
+template <int P, int NE, int Q>
+const int *small_per_sm(int dev) {
+  static PerDevice ready;
+  static int per_sm[64][2];
+  static int fallback[2];
+  int *r = dev >= 0 && dev < 64 ? per_sm[dev] : fallback;
+  if (dev >= 0 && dev < 64 && ready.test(dev)) return r;
+  auto k0 = k_rk_small<P, NE, Q, kSmallTiles[0]>;
+  auto k1 = k_rk_small<P, NE, Q, kSmallTiles[1]>;
+  const int s0 = SfCfg<P, NE, Q, kSmallTiles[0]>::SMEM, s1 = SfCfg<P, NE, Q, kSmallTiles[1]>::SMEM;
+  r[0] = r[1] = 0;
+  if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, s0) != cudaSuccess ||
+      cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, s1) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[0], k0, kSmallThreads, s0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[1], k1, kSmallThreads, s1) != cudaSuccess) {
+    cudaGetLastError();
+    r[0] = r[1] = 0;
+  }
+  if (dev >= 0 && dev < 64) ready.set(dev);
+  return r;
+}
+
+// the variant whose tiles of the mesh fit in one wave (its blocks all resident),
+// the smaller tiles first; -1 if neither
+template <int P, int NE, int Q>
+int small_variant(const dg_mesh *m) {
+  const int *per_sm = small_per_sm<P, NE, Q>(m->device);
+  for (int v = 0; v < 2; ++v) {
+    const int64_t nb = (m->N + kSmallTiles[v] - 1) / kSmallTiles[v];
+    if (per_sm[v] > 0 && nb <= (int64_t)m->num_sms * per_sm[v]) return v;
+  }
+  return -1;
+}
+
+template <int P, int NE, int Q, int EBX>
+int run_rk_small(dg_mesh *m, double *c, double dt, int nsteps, int method, cudaStream_t s) {
+  using Sc = SfCfg<P, NE, Q, EBX>;
+  auto kern = k_rk_small<P, NE, Q, EBX>;
+  // one tile per block (the variant was chosen so that they are all resident);
+  // the edge phase spreads its points over the same blocks
+  const int64_t nb = (m->N + EBX - 1) / EBX;
+  cudaError_t e = cudaMemsetAsync(m->gbar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return (int)e;
+  double *S = m->stage, *A = m->rk_acc, *tr = m->trace, *fh = m->fhat;
+  const double *geo = m->geo, *bst = m->bstate;
+  const int32_t *ef = m->elem_face;
+  const FaceConn *conn = m->face_conn;
+  const FaceGeo *fg = m->face_geo;
+  DevTables tab = m->tab;
+  int N = (int)m->N;
+  int64_t F = m->F;
+  double gamma = m->gamma;
+  unsigned *bar = m->gbar;
+  int *err = m->err_flag;
+  void *args[] = {&c, &S, &A, &tr, &fh, &geo, &ef, &conn, &fg, &bst, &tab, &N, &F, &gamma, &dt, &nsteps, &method,
+                  &bar, &err};
+  return (int)cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)nb), dim3(kSmallThreads), args,
+                                          Sc::SMEM, s);
+}
+
+template <int P, int NE, int Q>
+int run_small(dg_mesh *m, double *c, double dt, int nsteps, int method, cudaStream_t s) {
+  switch (small_variant<P, NE, Q>(m)) {
+    case 0: return run_rk_small<P, NE, Q, kSmallTiles[0]>(m, c, dt, nsteps, method, s);
+    case 1: return run_rk_small<P, NE, Q, kSmallTiles[1]>(m, c, dt, nsteps, method, s);
+    default: return (int)cudaErrorCooperativeLaunchTooLarge;
+  }
+}
+
+template <int P, int NE, int Q>
+bool fits_small(const dg_mesh *m) {
+  return small_variant<P, NE, Q>(m) >= 0;
+}
+
 }  // namespace
+
+bool small_rk_fits(const dg_mesh *m) {
+#define CALL(P, NE) (m->rule == DG_RULE_SYMMETRIC ? fits_small<P, NE, sym_points(P)>(m) : fits_small<P, NE, 0>(m))
+  if (m->p == 1 && m->ne == 2) return CALL(1, 2);
+  if (m->p == 2 && m->ne == 3) return CALL(2, 3);
+  if (m->p == 3 && m->ne == 4) return CALL(3, 4);
+  if (m->p == 3 && m->ne == 3) return CALL(3, 3);
+  if (m->p == 4 && m->ne == 5) return CALL(4, 5);
+  if (m->p == 5 && m->ne == 6) return CALL(5, 6);
+#undef CALL
+  return false;
+}
+
+int launch_rk_small(dg_mesh *m, double *c, double dt, int nsteps, int method, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+#define CALL(P, NE)                                                                        \
+  (m->rule == DG_RULE_SYMMETRIC ? run_small<P, NE, sym_points(P)>(m, c, dt, nsteps, method, s) \
+                                : run_small<P, NE, 0>(m, c, dt, nsteps, method, s))
+  if (m->p == 1 && m->ne == 2) return CALL(1, 2);
+  if (m->p == 2 && m->ne == 3) return CALL(2, 3);
+  if (m->p == 3 && m->ne == 4) return CALL(3, 4);
+  if (m->p == 3 && m->ne == 3) return CALL(3, 3);
+  if (m->p == 4 && m->ne == 5) return CALL(4, 5);
+  if (m->p == 5 && m->ne == 6) return CALL(5, 6);
+#undef CALL
+  return (int)cudaErrorInvalidValue;
+}
 
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
                    const double *fhat, const StageUpdate &su, int mode, void *stream) {

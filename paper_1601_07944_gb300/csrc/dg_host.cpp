@@ -411,6 +411,7 @@ void free_mesh(dg_mesh *m) {
   cudaFree(m->bstate); cudaFree(m->bxy);
   cudaFree(m->adj_buf);
   cudaFree(m->err_flag);
+  cudaFree(m->gbar);
   if (m->timing) {
     for (auto &r : m->timing->pool) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete m->timing;
@@ -757,6 +758,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
   DG_ALLOC(m->partial, sizeof(double) * m->totals_blocks * M, "totals partials");
   DG_ALLOC(m->totals_dev, sizeof(double) * M, "totals");
   DG_ALLOC(m->err_flag, sizeof(int), "error flag");
+  DG_ALLOC(m->gbar, 2 * sizeof(unsigned), "grid barrier");
+  m->small_stepper = 1;
   m->Fb = Fb;
   m->n_state_faces = n_state;
   m->bstate_set = n_state == 0;
@@ -952,17 +955,14 @@ static dg_status rk_step_one(dg_mesh *m, double *c, double dt, bool traces_valid
     return DG_OK;
   };
   // With the limiter on (Section 4.3.5, p = 1) every stage value and the new
-  // state are limited; the limiter, not the element kernel, then writes the
-  // traces the next stage reads.
+  // state are limited; the limiter reads the traces the element kernel wrote and
+  // rewrites those of the elements it limits, for the next stage.
   auto stage = [&](const double *cin, const double *u0, double *out, const StageUpdate &su,
                    const char *what) -> dg_status {
     dg_status st = face(what);
     if (st != DG_OK) return st;
-    if (!m->limiter) return elem(cin, u0, out, su, what);
-    DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-              return launch_elem(m, prec, cin, u0, out, false, su, 1, stream);
-            }), what);
-    DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return launch_limit(m, out, m->trace, stream); }),
+    if ((st = elem(cin, u0, out, su, what)) != DG_OK || !m->limiter) return st;
+    DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return launch_limit(m, out, m->trace, 1, stream); }),
             what);
     return DG_OK;
   };
@@ -972,37 +972,13 @@ static dg_status rk_step_one(dg_mesh *m, double *c, double dt, bool traces_valid
   if (!traces_valid)
     DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces_p(m, prec, c, stream); }),
             "rk traces");
-  double *S = m->stage;
-  switch (method) {
-    case DG_SSP_RK3:
-      // u1 = c + dt L(c);  u2 = 3/4 c + 1/4 (u1 + dt L(u1)), over u1;
-      // c <- 1/3 c + 2/3 (u2 + dt L(u2))
-      if ((st = stage(c, nullptr, S, shu_osher(dt, 0.0, 1.0), "ssp-rk3 stage 1")) != DG_OK) return st;
-      if ((st = stage(S, c, S, shu_osher(dt, 0.75, 0.25), "ssp-rk3 stage 2")) != DG_OK) return st;
-      return stage(S, c, c, shu_osher(dt, 1.0 / 3.0, 2.0 / 3.0), "ssp-rk3 stage 3");
-    case DG_RK2:
-      // Heun's method c + dt/2 (k1 + k2) in Shu-Osher form:
-      // u1 = c + dt L(c);  c <- 1/2 c + 1/2 (u1 + dt L(u1))
-      if ((st = stage(c, nullptr, S, shu_osher(dt, 0.0, 1.0), "rk2 stage 1")) != DG_OK) return st;
-      return stage(S, c, c, shu_osher(dt, 0.5, 0.5), "rk2 stage 2");
-    case DG_RK4: {
-      // classical RK4 with the running sum A of dt b_i k_i:
-      //   stage 1: S = c + dt/2 k1,  A = S - dt/3 k1   (= c + dt/6 k1)
-      //   stage 2: S = c + dt/2 k2,  A += dt/3 k2
-      //   stage 3: S = c + dt k3,    A += dt/3 k3
-      //   stage 4: c = A + dt/6 k4
-      double *A = m->rk_acc;
-      StageUpdate s1{dt, 0.0, 1.0, 0.5, nullptr, A, 0.0, 1.0, -1.0 / 3.0};
-      StageUpdate s2{dt, 1.0, 0.0, 0.5, A, A, 1.0, 0.0, 1.0 / 3.0};
-      StageUpdate s3{dt, 1.0, 0.0, 1.0, A, A, 1.0, 0.0, 1.0 / 3.0};
-      StageUpdate s4{dt, 1.0, 0.0, 1.0 / 6.0, nullptr, nullptr, 0.0, 0.0, 0.0};
-      if ((st = stage(c, nullptr, S, s1, "rk4 stage 1")) != DG_OK) return st;
-      if ((st = stage(S, c, S, s2, "rk4 stage 2")) != DG_OK) return st;
-      if ((st = stage(S, c, S, s3, "rk4 stage 3")) != DG_OK) return st;
-      return stage(S, A, c, s4, "rk4 stage 4");
-    }
+  if (method != DG_SSP_RK3 && method != DG_RK2 && method != DG_RK4) return fail(DG_EINVAL, "rk step: unknown method");
+  const int ns = rk_num_stages(method);
+  for (int i = 0; i < ns; ++i) {
+    const RkStage rs = rk_stage(method, i, dt, c, m->stage, m->rk_acc);
+    if ((st = stage(rs.cin, rs.u0, rs.out, rs.su, "rk stage")) != DG_OK) return st;
   }
-  return fail(DG_EINVAL, "rk step: unknown method");
+  return DG_OK;
 }
 
 // Steps per captured graph.  Replaying a graph runs its launches back to back,
@@ -1042,6 +1018,22 @@ static cudaGraphExec_t step_graph(dg_mesh *m, double *c, double dt, dg_rk_method
   return g->exec;
 }
 
+// whether the mesh's device runs cooperative launches (every block of the grid
+// resident at once), asked once per device
+static bool coop_capable(const dg_mesh *m) {
+  static dg::PerDevice asked, yes;
+  if (!asked.test(m->device)) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, m->device) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    if (v) yes.set(m->device);
+    asked.set(m->device);
+  }
+  return yes.test(m->device);
+}
+
 extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nsteps, dg_rk_method method,
                                        dg_precision prec, void *stream) {
   if (!m || !c) return fail(DG_EINVAL, "dg_rk_step: null argument");
@@ -1058,6 +1050,16 @@ extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nst
   if (method == DG_RK4 && !m->rk_acc && nsteps > 0) {
     cudaError_t e = cudaMalloc(&m->rk_acc, sizeof(double) * m->N * dg::M * m->np);
     if (e != cudaSuccess) { cudaGetLastError(); m->rk_acc = nullptr; return fail(DG_ENOMEM, "dg_rk_step: RK4 buffer"); }
+  }
+  // a small mesh in float64 without the limiter: the whole call in one launch of
+  // the fused stepper (after the traces of c)
+  if (nsteps > 0 && prec == DG_FP64 && !m->limiter && m->small_stepper && dg::small_rk_fits(m) && coop_capable(m)) {
+    DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return dg::launch_traces(m, c, m->trace, stream); }),
+            "dg_rk_step traces");
+    DG_CUDA((cudaError_t)timed(m, DG_K_STEPPER, stream,
+                               [&] { return dg::launch_rk_small(m, c, dt, nsteps, (int)method, stream); }),
+            "dg_rk_step fused small-mesh stepper");
+    return DG_OK;
   }
   int done = 0;
   if (nsteps > 0) {
@@ -1085,6 +1087,12 @@ extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nst
   return DG_OK;
 }
 
+extern "C" dg_status dg_set_small_mesh_stepper(dg_mesh *m, int enable) {
+  if (!m) return fail(DG_EINVAL, "dg_set_small_mesh_stepper: null mesh");
+  m->small_stepper = enable != 0;
+  return DG_OK;
+}
+
 extern "C" dg_status dg_set_limiter(dg_mesh *m, int enable) {
   if (!m) return fail(DG_EINVAL, "dg_set_limiter: null mesh");
   if (enable && m->p != 1) return fail(DG_EINVAL, "dg_set_limiter: the Barth-Jespersen limiter is for p = 1 (p = %d)", m->p);
@@ -1100,7 +1108,7 @@ extern "C" dg_status dg_limit(dg_mesh *m, double *c, void *stream) {
   if (!m || !c) return fail(DG_EINVAL, "dg_limit: null argument");
   if (dg_status dst = check_device(m, "dg_limit")) return dst;
   if (m->p != 1) return fail(DG_EINVAL, "dg_limit: the Barth-Jespersen limiter is for p = 1 (p = %d)", m->p);
-  DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return dg::launch_limit(m, c, nullptr, stream); }),
+  DG_CUDA((cudaError_t)timed(m, DG_K_OTHER, stream, [&] { return dg::launch_limit(m, c, nullptr, 0, stream); }),
           "dg_limit");
   return DG_OK;
 }

@@ -71,8 +71,45 @@ struct StageUpdate {
   double *out2;
   double x, y, w;
 };
-inline StageUpdate shu_osher(double dt, double a0, double b0) {
+__host__ __device__ inline StageUpdate shu_osher(double dt, double a0, double b0) {
   return StageUpdate{dt, a0, b0, b0, nullptr, nullptr, 0.0, 0.0, 0.0};
+}
+
+// Stage i (0-based) of one step of the Runge-Kutta method `method` (dg_rk_method)
+// on the state c, the stage buffer S and the classical RK4's running sum A: the
+// element stage reads cin (and u0) and writes out with the update su.
+//   SSP-RK3: u1 = c + dt L(c);  u2 = 3/4 c + 1/4 (u1 + dt L(u1)), over u1;
+//            c <- 1/3 c + 2/3 (u2 + dt L(u2))
+//   RK2 (Heun, Shu-Osher form): u1 = c + dt L(c);  c <- 1/2 c + 1/2 (u1 + dt L(u1))
+//   RK4 with the running sum A of dt b_i k_i:
+//     stage 1: S = c + dt/2 k1,  A = S - dt/3 k1   (= c + dt/6 k1)
+//     stage 2: S = c + dt/2 k2,  A += dt/3 k2
+//     stage 3: S = c + dt k3,    A += dt/3 k3
+//     stage 4: c = A + dt/6 k4
+// The host launches the stages one by one; the fused small-mesh stepper runs
+// them inside one kernel.
+struct RkStage {
+  const double *cin, *u0;
+  double *out;
+  StageUpdate su;
+};
+__host__ __device__ inline int rk_num_stages(int method) {
+  return method == DG_RK2 ? 2 : (method == DG_RK4 ? 4 : 3);
+}
+__host__ __device__ inline RkStage rk_stage(int method, int i, double dt, double *c, double *S, double *A) {
+  if (method == DG_RK4) {
+    if (i == 0) return RkStage{c, nullptr, S, StageUpdate{dt, 0.0, 1.0, 0.5, nullptr, A, 0.0, 1.0, -1.0 / 3.0}};
+    if (i == 1) return RkStage{S, c, S, StageUpdate{dt, 1.0, 0.0, 0.5, A, A, 1.0, 0.0, 1.0 / 3.0}};
+    if (i == 2) return RkStage{S, c, S, StageUpdate{dt, 1.0, 0.0, 1.0, A, A, 1.0, 0.0, 1.0 / 3.0}};
+    return RkStage{S, A, c, StageUpdate{dt, 1.0, 0.0, 1.0 / 6.0, nullptr, nullptr, 0.0, 0.0, 0.0}};
+  }
+  if (method == DG_RK2) {
+    if (i == 0) return RkStage{c, nullptr, S, shu_osher(dt, 0.0, 1.0)};
+    return RkStage{S, c, c, shu_osher(dt, 0.5, 0.5)};
+  }
+  if (i == 0) return RkStage{c, nullptr, S, shu_osher(dt, 0.0, 1.0)};
+  if (i == 1) return RkStage{S, c, S, shu_osher(dt, 0.75, 0.25)};
+  return RkStage{S, c, c, shu_osher(dt, 1.0 / 3.0, 2.0 / 3.0)};
 }
 
 // Which devices a one-time setting of a kernel (cudaFuncSetAttribute, a per-device
@@ -152,6 +189,8 @@ struct dg_mesh {
   size_t adj_doubles;
   dg::Timing *timing;
   dg::GraphCache *graph;
+  unsigned *gbar;              // [2] grid barrier of the fused small-mesh stepper (count, generation)
+  int small_stepper;           // dg_set_small_mesh_stepper (on by default)
 };
 
 namespace dg {
@@ -192,13 +231,20 @@ int launch_element_tc_sym(const dg_mesh *m, int split3, const double *c, const d
                           float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
                           int mode, void *stream);
 int launch_convert_check(int n, unsigned long long *bad, void *stream);
+// The fused small-mesh stepper (float64, no limiter): nsteps steps of `method` on
+// c in one cooperative launch, the traces of c already in m->trace.  Returns a
+// cudaError_t cast to int.  small_rk_fits: whether the mesh is small enough (its
+// element tiles fit in one wave of the GPU).
+bool small_rk_fits(const dg_mesh *m);
+int launch_rk_small(dg_mesh *m, double *c, double dt, int nsteps, int method, void *stream);
 int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
 int launch_eval_points(const dg_mesh *m, const double *c, const double *tab, int npts, double *out, void *stream);
 int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);
-// Barth-Jespersen limiter (p = 1) in place on c; traces of the limited state to
-// trace when not null
-int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream);
+// Barth-Jespersen limiter (p = 1) in place on c.  have_traces: trace holds the
+// traces of c on entry and holds those of the limited state on return; else the
+// traces of the limited state go to trace when it is not null.
+int launch_limit(const dg_mesh *m, double *c, double *trace, int have_traces, void *stream);
 // largest |v| + c over the volume points -> out_dev[0]
 int launch_wave_speed(const dg_mesh *m, const double *c, double *out_dev, void *stream);
 // (dR/du)^T lam combined as out = x0 X + x1 Y + x2 Z + s (dR/du)^T lam (X, Y, Z may

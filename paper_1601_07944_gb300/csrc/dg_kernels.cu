@@ -79,38 +79,7 @@ __global__ void __launch_bounds__(kThreads)
 k_face(const double *__restrict__ trace, double *__restrict__ fhat, const FaceConn *__restrict__ conn,
        const FaceGeo *__restrict__ fg, const double *__restrict__ bstate, int64_t N, int64_t F, double gamma,
        int *err) {
-  constexpr int NF = 3 * NE;
-  bool ok = true;
-  // The grid is what fits on the GPU at once; block b takes the b-th of gridDim.x
-  // equal slices of the (edge, point) items, so every SM gets the same share
-  // and there is no partial last wave.
-  const int64_t n = F * NE;
-  const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const int64_t f = i / NE;
-    const int k = (int)(i - f * NE);
-    const FaceConn cn = conn[f];
-    const FaceGeo g = fg[f];
-    const double *pl = trace + ((size_t)checked(cn.l, N, err) * NF + checked(cn.L, 3, err) * NE + k) * M;
-    double ul[M], ur[M], Fh[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) ul[m] = pl[m];
-    if (cn.r < 0) {
-      // boundary face (the first faces of the list): the ghost state at the same point
-      ghost_state(cn.r, ul, g.nx, g.ny, bstate + ((size_t)f * NE + k) * M, ur);
-    } else {
-      const double *pr =
-          trace + ((size_t)checked(cn.r, N, err) * NF + checked(cn.R, 3, err) * NE + (NE - 1 - k)) * M;
-#pragma unroll
-      for (int m = 0; m < M; ++m) ur[m] = pr[m];
-    }
-    // l * F_hat = (l/2) (F(Ul).n + F(Ur).n - alpha (Ur - Ul))
-    ok &= lax_friedrichs_edge(ul, ur, g, gamma, Fh);
-    double *dst = fhat + (size_t)i * M;
-#pragma unroll
-    for (int m = 0; m < M; ++m) dst[m] = Fh[m];
-  }
-  if (!ok) atomicOr(err, kErrNonPhysical);
+  face_flux_points<NE>(trace, fhat, conn, fg, bstate, N, F, gamma, err, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -302,8 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 
 // ---------------------------------------------------------------------------
 // Barth-Jespersen limiter for p = 1 (Section 4.3.5), one thread per element and
-// variable, in place on c; the traces of the limited state go to trace (when not
-// null).
+// variable, in place on c.
 // Per variable: Ubar = phi_1 c_1 is the centroid value (the linear modes vanish at
 // the centroid), U^max / U^min the extremes of the centroid values of the element
 // and its three neighbours; at each edge integration point, with
@@ -311,11 +279,20 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 // min(1, (U^min - Ubar)/d) for d < 0; the linear modes are scaled by min_k alpha_k.
 // Threads read only the constant mode of their neighbours and write only the
 // linear modes of their own element, so the in-place update has no race.
+//
+// have_traces: trace holds the edge traces of c on entry (the element kernel
+// wrote them, with the same per-point sums, edge_traces_sf); they are read
+// instead of recomputed, and rewritten, for the limited state, only where an
+// element is limited.  Otherwise the traces are formed here, and written to
+// trace when it is not null.
 // The float64 pipe is spared where the decisions allow it: extremes are found by
-// integer compares of order-preserving keys of the bit patterns, the smallest
-// ratio num_k/|d_k| (both non-negative) by comparing the cross products
-// num_k |d_best| and num_best |d_k| as unsigned integers, and the one division
-// happens only when the element is limited.
+// integer compares of order-preserving keys of the bit patterns; the smallest
+// ratio over the points is the smaller of (U^max - Ubar) / d+ and
+// (U^min - Ubar) / d- with d+ the largest positive and |d-| the largest negative
+// deviation (again integer compares, the deviations' magnitudes being
+// non-negative), compared by their cross products; a ratio limits only when its
+// numerator is below its denominator; the one division happens only when the
+// element is limited.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long order_key(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -326,7 +303,7 @@ __device__ __forceinline__ unsigned long long nonneg_bits(double x) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ elem_nbr,
+k_limit_p1(double *c, double *__restrict__ trace, int have_traces, const int32_t *__restrict__ elem_nbr,
            const double *__restrict__ EPa, const double *__restrict__ EChiM1, const double *__restrict__ EChi,
            double phi1, int64_t N, int *err) {
   constexpr int P = 1, NE = 2, ND = 2, NP = 3, NF = 6;
@@ -346,6 +323,16 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
     double *ce = c + (e * M + m) * NP;
     double cj[NP] = {ce[0], ce[1], ce[2]};
     const double cn[3] = {c[(nb0 * M + m) * NP], c[(nb1 * M + m) * NP], c[(nb2 * M + m) * NP]};
+    double *dst = trace ? trace + (size_t)e * NF * M + m : nullptr;
+    double t[NF], z[ND];
+    if (have_traces) {
+#pragma unroll
+      for (int x = 0; x < NF; ++x) t[x] = dst[x * M];
+    } else {
+      face0_z<P>(cj, sChiM1, z);
+#pragma unroll
+      for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
+    }
     // extremes of the constant modes (phi_1 > 0 keeps the order)
     double cmax = cj[0], cmin = cj[0];
 #pragma unroll
@@ -359,20 +346,26 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
     // of either sign, where the difference is 0; the comparisons below read
     // these as non-negative bit patterns)
     const double up = phi1 * (cmax - cj[0]), dn = phi1 * (cj[0] - cmin);
-    double t[NF], z[ND];
-    face0_z<P>(cj, sChiM1, z);
-#pragma unroll
-    for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
-    double nbest = 1.0, dbest = 1.0;                                  // ratio 1: no limiting
+    // the largest deviation above and below the centroid value, by magnitude
+    unsigned long long dpos = 0ull, dneg = 0ull;
 #pragma unroll
     for (int x = 0; x < NF; ++x) {
       const unsigned long long db = (unsigned long long)__double_as_longlong(t[x] - ub);
       const unsigned long long mag = db & 0x7FFFFFFFFFFFFFFFull;       // |d|
-      const double num = (db >> 63) ? dn : up;
-      const double den = __longlong_as_double((long long)mag);
-      if (mag != 0ull && nonneg_bits(num * dbest) < nonneg_bits(nbest * den)) { nbest = num; dbest = den; }
+      if (db >> 63) dneg = mag > dneg ? mag : dneg;
+      else dpos = mag > dpos ? mag : dpos;
     }
-    if (nonneg_bits(nbest) < nonneg_bits(dbest)) {
+    double nbest = 1.0, dbest = 1.0;                                    // ratio 1: no limiting
+    if (dpos != 0ull && nonneg_bits(up) < dpos) {
+      nbest = up;
+      dbest = __longlong_as_double((long long)dpos);
+    }
+    if (dneg != 0ull && nonneg_bits(dn) < dneg) {
+      const double dm = __longlong_as_double((long long)dneg);
+      if (nonneg_bits(dn * dbest) < nonneg_bits(nbest * dm)) { nbest = dn; dbest = dm; }
+    }
+    const bool limited = nonneg_bits(nbest) < nonneg_bits(dbest);
+    if (limited) {
       const double alpha = nbest / dbest;
       cj[1] *= alpha;
       cj[2] *= alpha;
@@ -382,8 +375,7 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
 #pragma unroll
       for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
     }
-    if (trace) {
-      double *dst = trace + (size_t)e * NF * M + m;
+    if (dst && (limited || !have_traces)) {
 #pragma unroll
       for (int x = 0; x < NF; ++x) dst[x * M] = t[x];
     }
@@ -433,12 +425,13 @@ int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, 
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
-int launch_limit(const dg_mesh *m, double *c, double *trace, void *stream) {
+int launch_limit(const dg_mesh *m, double *c, double *trace, int have_traces, void *stream) {
   if (m->p != 1 || m->ne != 2) return (int)cudaErrorInvalidValue;
+  if (have_traces && !trace) return (int)cudaErrorInvalidValue;
   static int per_sm = 0;
   k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N * M, &per_sm), kThreads, 0,
-               (cudaStream_t)stream>>>(c, trace, m->elem_nbr, m->tab.EPa, m->tab.EChiM1, m->tab.EChi, m->phi1,
-                                       m->N, m->err_flag);
+               (cudaStream_t)stream>>>(c, trace, have_traces, m->elem_nbr, m->tab.EPa, m->tab.EChiM1, m->tab.EChi,
+                                       m->phi1, m->N, m->err_flag);
   return (int)cudaGetLastError();
 }
 

@@ -29,8 +29,8 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_point
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
            "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt",
            "dg_rk_step_method", "dg_limit", "dg_set_limiter", "dg_boundary_points",
-           "dg_set_boundary_state", "dg_volume_rule")
-KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "unused")
+           "dg_set_boundary_state", "dg_volume_rule", "dg_set_small_mesh_stepper")
+KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "stepper")
 
 
 class DGError(RuntimeError):
@@ -81,6 +81,7 @@ def load(path: str = None):
         "dg_boundary_points": [P, P, P],
         "dg_set_boundary_state": [P, P, P],
         "dg_set_limiter": [P, I],
+        "dg_set_small_mesh_stepper": [P, I],
         "dg_rk_step_host": [P, P, D, I, I, P],
         "dg_adjoint_step": [P, P, D, P, P, P],
         "dg_conserved_totals": [P, P, P, P],
@@ -346,6 +347,11 @@ class Mesh:
         """Barth-Jespersen limiter (p = 1) in place on the device tensor c."""
         _check(load().dg_limit(self._h, _dev_ptr(c, "c", self.coef_shape), _stream_ptr(stream)))
         return c
+
+    def set_small_mesh_stepper(self, on: bool):
+        """Run rk_step on a small mesh (float64, no limiter) as one fused launch
+        per call (on by default) or as separate launches."""
+        _check(load().dg_set_small_mesh_stepper(self._h, 1 if on else 0))
 
     def set_limiter(self, on: bool):
         """Limit every stage value and new state of rk_step (p = 1, float64)."""
