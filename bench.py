@@ -13,6 +13,7 @@ between timed steps, outside the timed events.
   python bench.py --configs     the five stated workloads, one JSON line each
   python bench.py --sweep       mesh-size scaling (RK4, p = 1 and 4, 200 to 184,832 elements;
                                 p = 1 also with the limiter)
+  python bench.py --case NAME   a few untimed steps of one workload, for a profiler
 
 With N = 1 the line also carries the tensor-core modes on the same workload
 (throughput, speedup over float64 and state error against the float64 run) and
@@ -130,8 +131,8 @@ def _src_hash(*names) -> str:
 # aside) it was taken on, and the volume rule when it is not the collapsed grid;
 # a code change voids the entry.
 TRAFFIC = {
-    # k_element_sf<3,4,0>, stage-1 launch, 256x256 p=3 vortex (one ncu capture)
-    "fc0afafb13edafeb": 77147136 + 40573184,
+    # k_element_sf<3,4,0>, stage-2 launch (reads u^n), 256x256 p=3 vortex (one ncu capture)
+    "b7e59d9a2991de35": 119100160 + 43306496,
 }
 
 
@@ -660,6 +661,48 @@ def run_rules(n: int = 256, steps: int = 100):
                           "rel_l2_symmetric_vs_collapsed_fp64": d}), flush=True)
 
 
+def run_case(name: str):
+    """A few steps of one workload, untimed, for a profiler to capture: `mixed`
+    (3xTF32, 256x256, p=3, vortex), `mixed512` (3xTF32, 512x512, p=4, perturbed
+    vortex), `limiter` (float64 RK4 with every stage limited, 304x304, p=1,
+    perturbed vortex), `adjoint` (two dg_adjoint_step calls, 256x256, p=2)."""
+    import torch
+    from paper_1601_07944_gb300 import _build, dg, inputs as I
+    _build.build()
+    dg.load()
+    if name in ("mixed", "mixed512"):
+        n, p, ic = (256, 3, I.vortex) if name == "mixed" else (512, 4, I.perturbed_vortex)
+        mesh = I.periodic_mesh(n)
+        m = dg.Mesh.from_mesh(mesh, p)
+        c = m.project_function(ic)
+        dt = I.fixed_dt(mesh, ic, p)
+        for _ in range(2):
+            m.rk_step(c, dt, 1, precision="tf32x3")
+    elif name == "limiter":
+        mesh = I.periodic_mesh(304)
+        m = dg.Mesh.from_mesh(mesh, 1)
+        dt = I.fixed_dt(mesh, I.perturbed_vortex, 1)
+        c = m.project_function(I.perturbed_vortex)
+        m.set_limiter(True)
+        m.limit(c)
+        for _ in range(3):
+            m.rk_step(c, dt, 1, method="rk4")
+    elif name == "adjoint":
+        mesh = I.periodic_mesh(256)
+        m = dg.Mesh.from_mesh(mesh, 2)
+        dt = I.fixed_dt(mesh, I.perturbed_vortex, 2)
+        c = m.project_function(I.perturbed_vortex)
+        lam = m.project_function(lambda x, y: I.perturbed_vortex(x, y, seed=I.SEED_TARGET))
+        out = torch.empty_like(c)
+        for _ in range(2):
+            m.adjoint_step(c, dt, lam, out=out)
+    else:
+        raise SystemExit("unknown case %r" % name)
+    torch.cuda.synchronize()
+    m.device_status()
+    print(json.dumps({"case": name, "ok": True}), flush=True)
+
+
 def run_configs():
     """Every workload of the five configurations as stated, one JSON line each
     (device-timed full runs; parity with the oracle is the tests' job)."""
@@ -952,10 +995,16 @@ def main():
                     help="both volume rules at p=1..5 in every precision instead of the benchmark")
     ap.add_argument("--sweep", action="store_true",
                     help="mesh-size scaling runs (p=1 x 10000 and p=4 x 1000 RK4 steps) instead of the benchmark")
+    ap.add_argument("--case", choices=["mixed", "mixed512", "limiter", "adjoint"],
+                    help="a few untimed steps of one workload (for a profiler) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     world, rank, local = _dist()
+    if args.case:
+        if rank == 0:
+            run_case(args.case)
+        return
     if args.configs:
         if rank == 0:
             run_configs()

@@ -173,6 +173,28 @@ dg_status dg_volume_points(const dg_mesh *mesh, double *xy, void *stream);
 dg_status dg_eval_points(dg_mesh *mesh, int npts, const double *r, const double *s, const double *c,
                          double *out, void *stream);
 
+/* det J of every element (twice its area; the Jacobian of Eq. 2dmap):
+ * detj[N], DEVICE.  Asynchronous. */
+dg_status dg_det_j(const dg_mesh *mesh, double *detj, void *stream);
+
+/* Physical points of npts reference points (r[k], s[k]) in every element
+ * (Eq. 2dmap): xy[N][npts][2], DEVICE.  r, s: HOST (inside the reference
+ * triangle; DG_EINVAL otherwise).  Synchronous (a temporary device copy of the
+ * points is freed before returning). */
+dg_status dg_map_points(const dg_mesh *mesh, int npts, const double *r, const double *s, double *xy,
+                        void *stream);
+
+/* L2 error of variable var (0..3) of the solution U = sum_j c_j phi_j against
+ * given values on a reference rule (r[k], s[k], w[k]) whose weights sum to 1/2
+ * over the reference triangle:
+ *   err = sqrt( sum_e det J_e sum_k w_k (U_var(r_k) - exact[e][k][var])^2 ),
+ * the sum in a fixed order (bitwise repeatable).  r, s, w: HOST [npts];
+ * c: DEVICE [N][4][N_p]; exact: DEVICE [N][npts][4] (for example an exact
+ * solution evaluated at the points of dg_map_points); err: HOST double.
+ * Synchronous (temporary device buffers are freed before returning). */
+dg_status dg_l2_error(const dg_mesh *mesh, int npts, const double *r, const double *s, const double *w,
+                      const double *c, const double *exact, int var, double *err, void *stream);
+
 /* L2 projection of point values onto the orthonormal basis (Section 2, the
  * initial data u_0):  c[e][m][j] = sum_k w_k u[e][k][m] phi_j(r_k), with u the
  * conserved state at the points returned by dg_volume_points.

@@ -412,6 +412,7 @@ void free_mesh(dg_mesh *m) {
   cudaFree(m->adj_buf);
   cudaFree(m->err_flag);
   cudaFree(m->gbar);
+  cudaFree(m->tc_img[0]); cudaFree(m->tc_img[1]);
   if (m->timing) {
     for (auto &r : m->timing->pool) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete m->timing;
@@ -806,7 +807,8 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc *d, dg_mesh **out) {
       (ce = cudaMemcpy(m->face_conn, conn.data(), sizeof(FaceConn) * F, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->face_geo, fgeo.data(), sizeof(FaceGeo) * F, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(m->table_block, tb.data(), sizeof(double) * off, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (ce = cudaMemset(m->err_flag, 0, sizeof(int))) != cudaSuccess) {
+      (ce = cudaMemset(m->err_flag, 0, sizeof(int))) != cudaSuccess ||
+      (ce = (cudaError_t)dg::tc_tables(m)) != cudaSuccess) {
     free_mesh(m);
     return cuda_fail(ce, "dg_mesh_create: upload");
   }
@@ -875,6 +877,70 @@ extern "C" dg_status dg_eval_points(dg_mesh *m, int npts, const double *r, const
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dtab);
   if (e != cudaSuccess) return cuda_fail(e, "dg_eval_points");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_det_j(const dg_mesh *m, double *detj, void *stream) {
+  if (!m || !detj) return fail(DG_EINVAL, "dg_det_j: null argument");
+  if (dg_status dst = check_device(m, "dg_det_j")) return dst;
+  DG_CUDA((cudaError_t)dg::launch_det_j(m, detj, stream), "dg_det_j");
+  return DG_OK;
+}
+
+// the reference points (r[k], s[k]) checked and packed for the device
+static dg_status ref_points(const char *who, int npts, const double *r, const double *s, std::vector<double> &rs) {
+  if (npts < 1 || npts > 1 << 20) return fail(DG_EINVAL, "%s: npts=%d", who, npts);
+  rs.resize(2 * (size_t)npts);
+  for (int k = 0; k < npts; ++k) {
+    if (!(r[k] >= 0.0 && s[k] >= 0.0 && r[k] + s[k] < 1.0))
+      return fail(DG_EINVAL, "%s: point %d = (%g, %g) is not inside the reference triangle", who, k, r[k], s[k]);
+    rs[2 * k] = r[k];
+    rs[2 * k + 1] = s[k];
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_map_points(const dg_mesh *m, int npts, const double *r, const double *s, double *xy,
+                                   void *stream) {
+  if (!m || !r || !s || !xy) return fail(DG_EINVAL, "dg_map_points: null argument");
+  if (dg_status dst = check_device(m, "dg_map_points")) return dst;
+  std::vector<double> rs;
+  if (dg_status st = ref_points("dg_map_points", npts, r, s, rs)) return st;
+  double *drs = nullptr;
+  DG_CUDA(cudaMalloc(&drs, sizeof(double) * rs.size()), "dg_map_points alloc");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(drs, rs.data(), sizeof(double) * rs.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = (cudaError_t)dg::launch_map_points(m, drs, npts, xy, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(drs);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_map_points");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_l2_error(const dg_mesh *m, int npts, const double *r, const double *s, const double *w,
+                                 const double *c, const double *exact, int var, double *err_out, void *stream) {
+  if (!m || !r || !s || !w || !c || !exact || !err_out) return fail(DG_EINVAL, "dg_l2_error: null argument");
+  if (dg_status dst = check_device(m, "dg_l2_error")) return dst;
+  if (var < 0 || var >= dg::M) return fail(DG_EINVAL, "dg_l2_error: var=%d", var);
+  std::vector<double> rs;
+  if (dg_status st = ref_points("dg_l2_error", npts, r, s, rs)) return st;
+  // basis values at the points, the weights, block partials and the result in one buffer
+  const int nb = 256;
+  std::vector<double> host((size_t)npts * m->np + npts);
+  for (int k = 0; k < npts; ++k) {
+    dubiner(m->p, (real)r[k], (real)s[k], &host[(size_t)k * m->np], nullptr, nullptr);
+    host[(size_t)npts * m->np + k] = w[k];
+  }
+  double *buf = nullptr;
+  DG_CUDA(cudaMalloc(&buf, sizeof(double) * (host.size() + nb + 1)), "dg_l2_error alloc");
+  cudaStream_t st = (cudaStream_t)stream;
+  double *tab = buf, *dw = buf + (size_t)npts * m->np, *partial = dw + npts, *res = partial + nb;
+  cudaError_t e = cudaMemcpyAsync(buf, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = (cudaError_t)dg::launch_l2_error(m, c, exact, tab, dw, npts, var, partial, nb, res, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(err_out, res, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_l2_error");
   return DG_OK;
 }
 

@@ -190,6 +190,7 @@ struct dg_mesh {
   dg::Timing *timing;
   dg::GraphCache *graph;
   unsigned *gbar;              // [2] grid barrier of the fused small-mesh stepper (count, generation)
+  unsigned char *tc_img[2];    // B operand images of the tensor-core kernel (1xTF32, 3xTF32)
   int small_stepper;           // dg_set_small_mesh_stepper (on by default)
 };
 
@@ -226,6 +227,10 @@ inline int launch_element_tc(const dg_mesh *m, int split3, const double *c, cons
                              double b0, int mode, void *stream) {
   return launch_element_tc(m, split3, c, u0, out, trace_out, fhat, fmean, shu_osher(dt, a0, b0), mode, stream);
 }
+// Builds m->tc_img (synchronous; at mesh creation): the tensor-core kernel's B
+// operand images for the mesh's p, n_e and volume rule.  cudaError_t as int.
+int tc_tables(dg_mesh *m);
+int tc_tables_sym(dg_mesh *m);
 // launch_element_tc for a mesh on the symmetric volume rule (dg_mixed_sym.cu)
 int launch_element_tc_sym(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
                           float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
@@ -241,6 +246,14 @@ int launch_project(const dg_mesh *m, const double *u, double *c, void *stream);
 int launch_volume_points(const dg_mesh *m, double *xy, void *stream);
 int launch_eval_points(const dg_mesh *m, const double *c, const double *tab, int npts, double *out, void *stream);
 int launch_totals(const dg_mesh *m, const double *c, double *out_dev, void *stream);
+// det J per element -> out [N]; physical points of npts reference points (rs =
+// [npts][2], device) -> out [N][npts][2]; the L2 error of variable var against
+// exact [N][npts][4] on the rule (tab [npts][np] basis values, w [npts] weights,
+// device) through nb block partials -> out_dev[0]
+int launch_det_j(const dg_mesh *m, double *out, void *stream);
+int launch_map_points(const dg_mesh *m, const double *rs, int npts, double *out, void *stream);
+int launch_l2_error(const dg_mesh *m, const double *c, const double *exact, const double *tab, const double *w,
+                    int npts, int var, double *partial, int nb, double *out_dev, void *stream);
 // Barth-Jespersen limiter (p = 1) in place on c.  have_traces: trace holds the
 // traces of c on entry and holds those of the limited state on return; else the
 // traces of the limited state go to trace when it is not null.

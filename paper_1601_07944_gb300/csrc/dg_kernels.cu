@@ -198,6 +198,63 @@ k_totals_final(const double *__restrict__ partial, int nb, double *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// element geometry for callers: det J of every element, physical points of a
+// reference rule, and the L2 error of one variable against given point values
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_det_j(const double *__restrict__ geo, double *__restrict__ out, int64_t N) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < N) out[e] = geo[e * GEO + 5];
+}
+
+// x(r, s) = x1 (1 - r - s) + x2 r + x3 s (Eq. 2dmap) at npts points per element
+__global__ void __launch_bounds__(kThreads)
+k_map_points(const double *__restrict__ xy, const double *__restrict__ rs, double *__restrict__ out, int64_t N,
+             int npts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * npts) return;
+  const int64_t e = i / npts;
+  const int k = (int)(i - e * npts);
+  const double *v = xy + e * 6;
+  const double r = rs[2 * k], s = rs[2 * k + 1], l0 = 1.0 - r - s;
+  out[i * 2 + 0] = v[0] * l0 + v[2] * r + v[4] * s;
+  out[i * 2 + 1] = v[1] * l0 + v[3] * r + v[5] * s;
+}
+
+// per block: sum over its elements' points of det J w_k (U_h(r_k) - exact_k)^2 for
+// one variable; tab = [npts][np] basis values, w = [npts] weights (device)
+__global__ void __launch_bounds__(kThreads)
+k_l2_partial(const double *__restrict__ c, const double *__restrict__ exact, const double *__restrict__ tab,
+             const double *__restrict__ w, const double *__restrict__ geo, int64_t N, int np, int npts, int var,
+             double *__restrict__ partial) {
+  double acc[M] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t n = N * npts;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t beg = blockIdx.x * chunk;
+  const int64_t end = min(n, beg + chunk);
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const int64_t e = i / npts;
+    const int k = (int)(i - e * npts);
+    const double *ce = c + ((size_t)e * M + var) * np;
+    const double *t = tab + (size_t)k * np;
+    double u = 0.0;
+    for (int j = 0; j < np; ++j) u = fma(ce[j], t[j], u);
+    const double d = u - exact[(size_t)i * M + var];
+    acc[0] = fma(geo[e * GEO + 5] * w[k], d * d, acc[0]);
+  }
+  block_sum4(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_l2_final(const double *__restrict__ partial, int nb, double *__restrict__ out) {
+  double acc[M] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc[0] += partial[b];
+  block_sum4(acc);
+  if (threadIdx.x == 0) out[0] = sqrt(acc[0]);
+}
+
+// ---------------------------------------------------------------------------
 // largest wave speed |v| + c over the volume points (max is exact, so the result
 // does not depend on the order)
 // ---------------------------------------------------------------------------
@@ -291,8 +348,8 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 // (U^min - Ubar) / d- with d+ the largest positive and |d-| the largest negative
 // deviation (again integer compares, the deviations' magnitudes being
 // non-negative), compared by their cross products; a ratio limits only when its
-// numerator is below its denominator; the one division happens only when the
-// element is limited.
+// numerator is below its denominator; the one reciprocal is formed only when
+// the element is limited.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long order_key(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -346,15 +403,19 @@ k_limit_p1(double *c, double *__restrict__ trace, int have_traces, const int32_t
     // of either sign, where the difference is 0; the comparisons below read
     // these as non-negative bit patterns)
     const double up = phi1 * (cmax - cj[0]), dn = phi1 * (cj[0] - cmin);
-    // the largest deviation above and below the centroid value, by magnitude
-    unsigned long long dpos = 0ull, dneg = 0ull;
+    // the largest deviation above and below the centroid value: the extremes of
+    // the edge values, found by integer compares, less Ubar (a rounded
+    // subtraction of Ubar is monotone, so this is the largest of the rounded
+    // deviations t - Ubar); 0 where none lies on that side
+    double tmax = t[0], tmin = t[0];
 #pragma unroll
-    for (int x = 0; x < NF; ++x) {
-      const unsigned long long db = (unsigned long long)__double_as_longlong(t[x] - ub);
-      const unsigned long long mag = db & 0x7FFFFFFFFFFFFFFFull;       // |d|
-      if (db >> 63) dneg = mag > dneg ? mag : dneg;
-      else dpos = mag > dpos ? mag : dpos;
+    for (int x = 1; x < NF; ++x) {
+      if (order_key(t[x]) > order_key(tmax)) tmax = t[x];
+      if (order_key(t[x]) < order_key(tmin)) tmin = t[x];
     }
+    const unsigned long long bp = (unsigned long long)__double_as_longlong(tmax - ub);
+    const unsigned long long bn = (unsigned long long)__double_as_longlong(ub - tmin);
+    const unsigned long long dpos = (bp >> 63) ? 0ull : bp, dneg = (bn >> 63) ? 0ull : bn;
     double nbest = 1.0, dbest = 1.0;                                    // ratio 1: no limiting
     if (dpos != 0ull && nonneg_bits(up) < dpos) {
       nbest = up;
@@ -366,7 +427,10 @@ k_limit_p1(double *c, double *__restrict__ trace, int have_traces, const int32_t
     }
     const bool limited = nonneg_bits(nbest) < nonneg_bits(dbest);
     if (limited) {
-      const double alpha = nbest / dbest;
+      // alpha = nbest / dbest by the Newton-refined reciprocal (within 1.5 ulp of
+      // the quotient); the traces of the scaled coefficients by the same sums
+      // every kernel uses, so that they agree bit for bit with k_traces'
+      const double alpha = nbest * recip(dbest);
       cj[1] *= alpha;
       cj[2] *= alpha;
       ce[1] = cj[1];
@@ -517,6 +581,26 @@ int launch_wave_speed(const dg_mesh *m, const double *c, double *out_dev, void *
   }
 #undef WAVE
   k_wave_final<<<1, 32, 0, s>>>(m->partial, nb, out_dev);
+  return (int)cudaGetLastError();
+}
+
+int launch_det_j(const dg_mesh *m, double *out, void *stream) {
+  k_det_j<<<(int)((m->N + kThreads - 1) / kThreads), kThreads, 0, (cudaStream_t)stream>>>(m->geo, out, m->N);
+  return (int)cudaGetLastError();
+}
+
+int launch_map_points(const dg_mesh *m, const double *rs, int npts, double *out, void *stream) {
+  const int64_t n = m->N * npts;
+  k_map_points<<<(int)((n + kThreads - 1) / kThreads), kThreads, 0, (cudaStream_t)stream>>>(m->xy, rs, out, m->N,
+                                                                                           npts);
+  return (int)cudaGetLastError();
+}
+
+int launch_l2_error(const dg_mesh *m, const double *c, const double *exact, const double *tab, const double *w,
+                    int npts, int var, double *partial, int nb, double *out_dev, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  k_l2_partial<<<nb, kThreads, 0, s>>>(c, exact, tab, w, m->geo, m->N, m->np, npts, var, partial);
+  k_l2_final<<<1, kThreads, 0, s>>>(partial, nb, out_dev);
   return (int)cudaGetLastError();
 }
 

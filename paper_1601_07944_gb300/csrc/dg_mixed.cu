@@ -134,6 +134,10 @@ int launch_convert_check(int n, unsigned long long *bad, void *stream) {
   return (int)cudaGetLastError();
 }
 
+int tc_tables(dg_mesh *m) {
+  return m->rule == DG_RULE_SYMMETRIC ? tc_tables_sym(m) : tc_tables_rule<false>(m);
+}
+
 int launch_element_tc(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
                       float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
                       int mode, void *stream) {

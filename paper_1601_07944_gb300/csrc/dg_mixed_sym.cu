@@ -7,6 +7,8 @@
 
 namespace dg {
 
+int tc_tables_sym(dg_mesh *m) { return tc_tables_rule<true>(m); }
+
 int launch_element_tc_sym(const dg_mesh *m, int split3, const double *c, const double *u0, double *out,
                           float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
                           int mode, void *stream) {

@@ -182,8 +182,8 @@ template <int P, int NE, bool X3, bool OUT2, int Q>
 __global__ void __launch_bounds__(kTcThreads, Tc<P, NE, X3, Q>::CTAS)
 k_element_tc(const double *c, const double *u0, double *out, float *__restrict__ trace_out,
              const float *__restrict__ fhat, const double *__restrict__ fmean, const double *__restrict__ geo,
-             const int32_t *__restrict__ elem_face, DevTables tab, int N, int64_t F, StageUpdate su, int mode,
-             double gamma, int bulk, int *err) {
+             const int32_t *__restrict__ elem_face, const unsigned char *__restrict__ bimg, int N, int64_t F,
+             StageUpdate su, int mode, double gamma, int bulk, int *err) {
   using T = Tc<P, NE, X3, Q>;
   constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB, SE = T::SE, RG = T::RG;
   constexpr int K1 = T::K1, N1 = T::N1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
@@ -202,27 +202,9 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   const uint32_t mbar = tc::smem_u32(bar), mbar_in = tc::smem_u32(bar + 1);
   const bool pf = T::PF && bulk;
 
-  // ---- once per CTA: B operands (split), TMEM, mbarrier ----
-  for (int i = tid; i < T::N1 * K1; i += kTcThreads) {
-    const int n = i / K1, k = i - n * K1;
-    const double v = (n < NQ && k < NP) ? tab.BvT[k * NQ + n] : 0.0;
-    put<X3>(B1, T::B1P, n, k, K1, (float)v);
-  }
-  for (int i = tid; i < N2 * K2; i += kTcThreads) {
-    const int n = i / K2, k = i - n * K2;
-    double v = 0.0;
-    if (n < NP) {
-      if (k < NQ) v = tab.Dr[k * NP + n];
-      else if (k < 2 * NQ) v = tab.Ds[(k - NQ) * NP + n];
-      else if (k < 2 * NQ + NF) v = tab.Lf[(k - 2 * NQ) * NP + n];
-    }
-    put<X3>(B2, T::B2P, n, k, K2, (float)v);
-  }
-  for (int i = tid; i < N4 * K1; i += kTcThreads) {
-    const int n = i / K1, k = i - n * K1;
-    const double v = (n < NF && k < NP) ? tab.BfT[k * NF + n] : 0.0;
-    put<X3>(B4, T::B4P, n, k, K1, (float)v);
-  }
+  // ---- once per CTA: TMEM, mbarriers; the B operands (split, in their shared-
+  // memory layout: the mesh's image, k_tc_tables) arrive by a bulk copy, with
+  // the first tile's inputs ----
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(slot), T::COLS);
   if (tid == 0) {
     tc::mbar_init(mbar, 1);
@@ -241,7 +223,9 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   const int row = tid, rel = row >> 2, rm = row & 3;                 // accumulator row = 4 e + m
   const int le = rel & 7;                                            // element within the warp
   uint32_t phase = 0, phase_in = 0;
-  bool failed = false, copies = false;        // copies: a bulk copy is in flight
+  // failed: a bounded wait expired; mma_lost: it was an MMA batch's; copies: a
+  // bulk copy is in flight (its phase is phase_in)
+  bool failed = false, mma_lost = false, copies = false;
 
   // the rows' tcgen05.st complete and are ordered before the MMA issue
   auto sync_operands = [&]() {
@@ -257,6 +241,7 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     if (__syncthreads_or(!done)) {
       if (tid == 0) atomicOr(err, kErrTimeout);
       failed = true;
+      mma_lost = true;
       return false;
     }
     tc::fence_after_sync();
@@ -293,9 +278,29 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     if (need_u0) tc::bulk_g2s(tc::smem_u32(sPU), u0 + (size_t)e0 * M * NP, bc, mbar_in);
     if (mode != 2) tc::bulk_g2s(tc::smem_u32(sPG), geo + (size_t)e0 * GEO, bg, mbar_in);
   };
-  if (pf && blockIdx.x < ntiles) {
-    if (tid == 0) prefetch(blockIdx.x);
-    copies = true;
+  // the prologue's copies: the B image, and the first tile's inputs
+  if (tid == 0) {
+    const int e0 = blockIdx.x * EB, ec = min(EB, N - e0);
+    const uint32_t bc = (uint32_t)ec * M * NP * 8, bg = (uint32_t)ec * GEO * 8;
+    const bool first = pf && blockIdx.x < ntiles;
+    tc::mbar_arrive_expect_tx(mbar_in, (uint32_t)T::endB +
+                                           (first ? bc + (need_u0 ? bc : 0u) + (mode != 2 ? bg : 0u) : 0u));
+    tc::bulk_g2s(tc::smem_u32(sm), bimg, (uint32_t)T::endB, mbar_in);
+    if (first) {
+      tc::bulk_g2s(tc::smem_u32(sPC), c + (size_t)e0 * M * NP, bc, mbar_in);
+      if (need_u0) tc::bulk_g2s(tc::smem_u32(sPU), u0 + (size_t)e0 * M * NP, bc, mbar_in);
+      if (mode != 2) tc::bulk_g2s(tc::smem_u32(sPG), geo + (size_t)e0 * GEO, bg, mbar_in);
+    }
+  }
+  {
+    const bool ok = tc::mbar_wait_sleep(mbar_in, phase_in, kWaitNs, kSuspendNs);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(err, kErrTimeout);
+      failed = true;
+      copies = true;                    // the teardown waits on phase_in again
+    } else {
+      phase_in ^= 1u;
+    }
   }
   // the element's three edges (2 f + side), loaded one tile ahead
   auto load_ef = [&](int t, int *ef) {
@@ -305,7 +310,7 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   };
   int ef[3];
   load_ef(blockIdx.x, ef);
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = failed ? ntiles : blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int e0 = tile * EB;
     const int ecount = min(EB, N - e0);
     const bool live = rel < ecount;
@@ -331,16 +336,15 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
       }
       load_ef(tnext, ef);
     }
-    if (pf) {
+    if (pf && tile != (int)blockIdx.x) {
       const bool ok = tc::mbar_wait_sleep(mbar_in, phase_in, kWaitNs, kSuspendNs);
-      phase_in ^= 1u;
-      copies = false;
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(err, kErrTimeout);
-        failed = true;
-        copies = true;
+        failed = true;                  // copies stays true: the teardown waits on phase_in again
         break;
       }
+      phase_in ^= 1u;
+      copies = false;
     }
     // ---- the stage input: GEMM 1's operand (A columns [0, K1)) ----
     // (without the bulk copies: scalar loads of the caller's array, which then
@@ -547,13 +551,73 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
     // a bounded wait expired: wait (bounded again) for the MMAs of that batch, so
     // that the columns freed below are no longer written, and for a bulk copy
     // still in flight, so that no copy lands after the CTA has left
-    tc::mbar_wait_sleep(mbar, phase ^ 1u, kWaitNs, kSuspendNs);
+    if (mma_lost) tc::mbar_wait_sleep(mbar, phase ^ 1u, kWaitNs, kSuspendNs);
     if (copies) tc::mbar_wait_sleep(mbar_in, phase_in, kWaitNs, kSuspendNs);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem, T::COLS);
+}
+
+// The B operands of the three GEMMs, split into TF32 planes, in the byte layout
+// k_element_tc keeps them in shared memory: one image per mesh and precision
+// mode (T::endB bytes), which every CTA of every launch bulk-copies.
+template <int P, int NE, bool X3, int Q>
+__global__ void __launch_bounds__(kTcThreads) k_tc_tables(DevTables tab, unsigned char *img) {
+  using T = Tc<P, NE, X3, Q>;
+  constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, K1 = T::K1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
+  unsigned char *B1 = img + T::oB1, *B2 = img + T::oB2, *B4 = img + T::oB4;
+  for (int i = threadIdx.x; i < T::endB / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(img)[i] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < T::N1 * K1; i += blockDim.x) {
+    const int n = i / K1, k = i - n * K1;
+    const double v = (n < NQ && k < NP) ? tab.BvT[k * NQ + n] : 0.0;
+    put<X3>(B1, T::B1P, n, k, K1, (float)v);
+  }
+  for (int i = threadIdx.x; i < N2 * K2; i += blockDim.x) {
+    const int n = i / K2, k = i - n * K2;
+    double v = 0.0;
+    if (n < NP) {
+      if (k < NQ) v = tab.Dr[k * NP + n];
+      else if (k < 2 * NQ) v = tab.Ds[(k - NQ) * NP + n];
+      else if (k < 2 * NQ + NF) v = tab.Lf[(k - 2 * NQ) * NP + n];
+    }
+    put<X3>(B2, T::B2P, n, k, K2, (float)v);
+  }
+  for (int i = threadIdx.x; i < N4 * K1; i += blockDim.x) {
+    const int n = i / K1, k = i - n * K1;
+    const double v = (n < NF && k < NP) ? tab.BfT[k * NF + n] : 0.0;
+    put<X3>(B4, T::B4P, n, k, K1, (float)v);
+  }
+}
+
+// builds the mesh's two images (1xTF32, 3xTF32) for its p, n_e and volume rule
+template <int P, int NE, int Q>
+int tc_tables_pq(dg_mesh *m) {
+  const size_t bytes[2] = {(size_t)Tc<P, NE, false, Q>::endB, (size_t)Tc<P, NE, true, Q>::endB};
+  for (int x = 0; x < 2; ++x) {
+    cudaError_t e = cudaMalloc((void **)&m->tc_img[x], bytes[x]);
+    if (e != cudaSuccess) return (int)e;
+  }
+  k_tc_tables<P, NE, false, Q><<<1, kTcThreads>>>(m->tab, m->tc_img[0]);
+  k_tc_tables<P, NE, true, Q><<<1, kTcThreads>>>(m->tab, m->tc_img[1]);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return (int)e;
+}
+
+template <bool SYM>
+int tc_tables_rule(dg_mesh *m) {
+#define CALL(P, NE) tc_tables_pq<P, NE, SYM ? sym_points(P) : 0>(m)
+  if (m->p == 1 && m->ne == 2) return CALL(1, 2);
+  if (m->p == 2 && m->ne == 3) return CALL(2, 3);
+  if (m->p == 3 && m->ne == 4) return CALL(3, 4);
+  if (m->p == 3 && m->ne == 3) return CALL(3, 3);
+  if (m->p == 4 && m->ne == 5) return CALL(4, 5);
+  if (m->p == 5 && m->ne == 6) return CALL(5, 6);
+#undef CALL
+  return (int)cudaSuccess;           // no tensor-core kernel for this (p, n_e): nothing to build
 }
 
 template <int P, int NE, bool X3, bool OUT2, int Q>
@@ -606,8 +670,10 @@ int run_tc(const dg_mesh *m, const double *c, const double *u0, double *out, flo
   // caller's state arrays usually are, else the kernel loads them directly)
   const bool need_u0 = mode == 1 && su.a0 != 0.0;
   const int bulk = ((uintptr_t)c % 16 == 0 && (!need_u0 || (uintptr_t)u0 % 16 == 0)) ? 1 : 0;
-  kern<<<grid, kTcThreads, L.smem, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face, m->tab, (int)m->N,
-                                        m->F, su, mode, m->gamma, bulk, m->err_flag);
+  if (!m->tc_img[X3 ? 1 : 0]) return (int)cudaErrorNotReady;
+  kern<<<grid, kTcThreads, L.smem, s>>>(c, u0, out, trace_out, fhat, fmean, m->geo, m->elem_face,
+                                        m->tc_img[X3 ? 1 : 0], (int)m->N, m->F, su, mode, m->gamma, bulk,
+                                        m->err_flag);
   return (int)cudaGetLastError();
 }
 

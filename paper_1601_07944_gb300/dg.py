@@ -29,7 +29,8 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_point
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
            "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt",
            "dg_rk_step_method", "dg_limit", "dg_set_limiter", "dg_boundary_points",
-           "dg_set_boundary_state", "dg_volume_rule", "dg_set_small_mesh_stepper")
+           "dg_set_boundary_state", "dg_volume_rule", "dg_set_small_mesh_stepper", "dg_det_j",
+           "dg_map_points", "dg_l2_error")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "stepper")
 
 
@@ -82,6 +83,9 @@ def load(path: str = None):
         "dg_set_boundary_state": [P, P, P],
         "dg_set_limiter": [P, I],
         "dg_set_small_mesh_stepper": [P, I],
+        "dg_det_j": [P, P, P],
+        "dg_map_points": [P, I, P, P, P, P],
+        "dg_l2_error": [P, I, P, P, P, P, P, I, P, P],
         "dg_rk_step_host": [P, P, D, I, I, P],
         "dg_adjoint_step": [P, P, D, P, P, P],
         "dg_conserved_totals": [P, P, P, P],
@@ -233,13 +237,22 @@ class Mesh:
         except Exception:
             pass
 
-    def det_j(self, device="cuda"):
-        """det J of every element (twice its area), float64 tensor [N]."""
+    def det_j(self, stream=None):
+        """det J of every element (twice its area), a float64 device tensor [N] (dg_det_j)."""
         import torch
-        xy = self._xy
-        a = xy[:, 1] - xy[:, 0]
-        b = xy[:, 2] - xy[:, 0]
-        return torch.from_numpy(a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0]).to(device)
+        out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        _check(load().dg_det_j(self._h, _dev_ptr(out, "detj"), _stream_ptr(stream)))
+        return out
+
+    def map_points(self, r, s, stream=None):
+        """Physical points [N, npts, 2] (device) of reference points (r, s) of every element."""
+        import torch
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        out = torch.empty((self.N, r.size, 2), dtype=torch.float64, device="cuda")
+        _check(load().dg_map_points(self._h, r.size, _np_ptr(r), _np_ptr(s), _dev_ptr(out, "xy"),
+                                    _stream_ptr(stream)))
+        return out
 
     # -- diagnostics --------------------------------------------------------
     def set_timing(self, enable: bool):
@@ -272,23 +285,27 @@ class Mesh:
                                      _dev_ptr(out, "out"), _stream_ptr(stream)))
         return out
 
-    def l2_error(self, c, exact, var: int = 0, n_dir: int = 0, rule=None):
-        """sqrt(sum_e int_e (U_h - U_exact)^2) for one variable.  `rule` = (r, s, w) is
-        a reference-triangle rule (default: the library's collapsed rule with p+4
-        points per direction, exact to degree 2p+7); exact(x, y) -> [..., 4]."""
+    def l2_error(self, c, exact, var: int = 0, n_dir: int = 0, rule=None, stream=None):
+        """sqrt(sum_e int_e (U_h - U_exact)^2) for one variable (dg_l2_error).  `rule` =
+        (r, s, w) is a reference-triangle rule (default: the library's collapsed rule
+        with p+4 points per direction, exact to degree 2p+7); exact(x, y) -> [..., 4]
+        is evaluated on the host at the physical points (dg_map_points)."""
         import torch
         if rule is None:
             T = host_tables(n_dir - 1 if n_dir else self.p + 3)
             r, s, w = T["vol_r"], T["vol_s"], T["vol_w"]
         else:
             r, s, w = rule
-        vals = self.eval_points(c, r, s)[..., var].cpu().numpy()
-        xy = self._xy
-        x = xy[:, 0, 0][:, None] * (1 - r - s) + xy[:, 1, 0][:, None] * r + xy[:, 2, 0][:, None] * s
-        y = xy[:, 0, 1][:, None] * (1 - r - s) + xy[:, 1, 1][:, None] * r + xy[:, 2, 1][:, None] * s
-        ex = exact(x, y)[..., var]
-        dJ = self.det_j("cpu").numpy()
-        return float(np.sqrt(np.sum(dJ[:, None] * w[None, :] * (vals - ex) ** 2)))
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        xy = self.map_points(r, s, stream).cpu().numpy()
+        ex = torch.from_numpy(np.ascontiguousarray(exact(xy[..., 0], xy[..., 1]), dtype=np.float64)).cuda()
+        out = ctypes.c_double()
+        _check(load().dg_l2_error(self._h, r.size, _np_ptr(r), _np_ptr(s), _np_ptr(w),
+                                  _dev_ptr(c, "c", self.coef_shape), _dev_ptr(ex, "exact", (self.N, r.size, 4)),
+                                  int(var), ctypes.byref(out), _stream_ptr(stream)))
+        return out.value
 
     def project_ic(self, u, out=None, stream=None):
         import torch

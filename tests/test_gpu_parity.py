@@ -351,3 +351,21 @@ def test_non_physical_state_reported(dgmod, prec):
     assert ei.value.status == 5
     m.rhs(c, precision=prec)
     m.device_status()
+
+
+def test_det_j_and_map_points(dgmod, oracle_mod):
+    """dg_det_j and dg_map_points (Eq. 2dmap) against the oracle's geometry; the
+    library's L2 error is repeatable bit for bit (fixed-order reduction)."""
+    mesh = I.periodic_mesh(9)
+    m = dgmod.Mesh.from_mesh(mesh, 2)
+    o = oracle_mod.OracleDG.from_mesh(mesh, 2)
+    assert np.abs(_host(m.det_j()) - o.det_j()).max() <= 1e-15 * np.abs(o.det_j()).max()
+    rng = np.random.default_rng(5)
+    r = rng.uniform(0.01, 0.49, 7)
+    s = rng.uniform(0.01, 0.49, 7)
+    xy = _host(m.map_points(r, s))
+    ref = o.map_points(r, s)
+    assert np.abs(xy - np.asarray(ref).reshape(xy.shape)).max() < 1e-14
+    c = m.project_function(I.vortex)
+    e1 = m.l2_error(c, lambda x, y: I.vortex(x, y, 0.0))
+    assert e1 == m.l2_error(c, lambda x, y: I.vortex(x, y, 0.0)) and e1 > 0.0
