@@ -45,6 +45,7 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
   constexpr int NP = C::NP, ND = C::ND, NF = C::NF, EB = C::EB;
   __shared__ double sPa[ND * NE], sChiM1[NP], sChi[NP * NE];
   __shared__ double sC[EB * M * NP];
+  __shared__ double sZ[EB * M * ND];
   for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) sChi[i] = EChi[i];
   for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sPa[i] = EPa[i];
   for (int i = threadIdx.x; i < NP; i += blockDim.x) sChiM1[i] = EChiM1[i];
@@ -57,12 +58,19 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
     for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x)
       sC[i] = i < ecount * M * NP ? src[i] : 0.0;
     __syncthreads();
+    // Z_a of face 0, once per (element, variable), as the element kernel forms them
+    for (int i = threadIdx.x; i < ecount * M; i += blockDim.x) {
+      double z[ND];
+      face0_z<P>(sC + i * NP, sChiM1, z);
+#pragma unroll
+      for (int a = 0; a < ND; ++a) sZ[i * ND + a] = z[a];
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < ecount * M * NE; i += blockDim.x) {
       const int el = i / (M * NE), m = (i / NE) % M, k = i % NE;
       const double *cj = sC + (el * M + m) * NP;
-      double z[ND], t0, t1, t2;
-      face0_z<P>(cj, sChiM1, z);
-      edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t0, t1, t2);
+      double t0, t1, t2;
+      edge_traces_sf<P, NE>(cj, sZ + (el * M + m) * ND, sPa, sChi, k, t0, t1, t2);
       double *dst = trace + (size_t)(e0 + el) * NF * M + m;
       dst[k * M] = t0;
       dst[(NE + k) * M] = t1;

@@ -63,15 +63,24 @@ struct Tc {
   static constexpr int EB = 32, ROWS = 128;
   static constexpr int K1 = pad8(NP), N1 = pad16(NQ), K2 = pad8(2 * NQ + NF), N2 = pad16(NP), N4 = pad16(NF);
   static constexpr int NS = X3 ? 2 : 1;                     // TF32 planes: hi (, lo)
-  // TMEM columns: D [0, ND), A hi [ND, ND + K2), A lo [ND + K2, ND + 2 K2)
   static constexpr int ND = imax(imax(N1, N2), N4);
-  static constexpr int COLS = tmem_cols(ND + NS * K2);
+  // GEMM 2 as one batch over [G_r | G_s | lifted fluxes] (K2 columns of A), or,
+  // where that takes fewer TMEM columns (SPLIT: p = 4 in 3xTF32), as two batches
+  // into the same accumulator that reuse the operand columns: [G_r | lifted
+  // fluxes] (KG + KL columns, B = [Dr; Lf]), then G_s (KG columns, B = Ds)
+  static constexpr int KG = pad8(NQ), KL = pad8(NF);
+  static constexpr bool SPLIT = tmem_cols(ND + NS * (KG + KL)) < tmem_cols(ND + NS * K2);
+  static constexpr int KA = SPLIT ? KG + KL : K2;            // A columns per plane
+  // TMEM columns: D [0, ND), A hi [ND, ND + KA), A lo [ND + KA, ND + 2 KA)
+  static constexpr int COLS = tmem_cols(ND + NS * KA);
   static constexpr int PER_SM = 512 / COLS;                   // CTAs whose TMEM fits on one SM
   // shared memory: B operands (split), then per-warp staging
-  static constexpr int B1P = N1 * K1 * 4, B2P = N2 * K2 * 4, B4P = N4 * K1 * 4;
+  static constexpr int B1P = N1 * K1 * 4, B4P = N4 * K1 * 4;
+  static constexpr int B2P = N2 * (SPLIT ? KG + KL : K2) * 4, B2bP = SPLIT ? N2 * KG * 4 : 0;
   static constexpr int oB1 = 0;
   static constexpr int oB2 = align1k(oB1 + B1P * NS);
-  static constexpr int oB4 = align1k(oB2 + B2P * NS);
+  static constexpr int oB2b = align1k(oB2 + B2P * NS);
+  static constexpr int oB4 = align1k(oB2b + B2bP * NS);
   static constexpr int endB = align1k(oB4 + B4P * NS);
   // U staging [EB][SE] floats, point k of element e at e SE + 4 k (its four
   // variables); SE / 4 is odd, so the row threads' scalar writes hit 32 banks.
@@ -96,9 +105,9 @@ struct Tc {
   static constexpr int CTAS = PER_SM < 4 ? PER_SM : 4;              // the launch bound
   static constexpr bool PF = SMEM_PF + 1024 <= 233472 / CTAS;
   static constexpr int SMEM = PF ? SMEM_PF : SMEM_NOPF;
-  static_assert(K1 <= K2, "GEMM 1's operand shares GEMM 2's columns");
+  static_assert(K1 <= KA, "GEMM 1's operand shares GEMM 2's columns");
   static_assert(N1 <= 256 && N2 <= 256 && N4 <= 256, "MMA N");
-  static_assert(ND + NS * K2 <= 512, "TMEM columns");
+  static_assert(ND + NS * KA <= 512, "TMEM columns");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -133,18 +142,20 @@ __device__ __forceinline__ void st_split(uint32_t tHi, uint32_t tLo, const float
 
 // D (TMEM) = sum over k-steps of A B^T with A in TMEM (columns aHi, aLo) and B in
 // shared memory; split products a_lo b_hi + a_hi b_lo + a_hi b_hi when X3
-template <bool X3, int KT>
+// ACC: accumulate onto D from the first k-step on (the second batch of a split GEMM 2)
+template <bool X3, int KT, bool ACC = false>
 __device__ __forceinline__ void gemm_ts(uint32_t d, uint32_t aHi, uint32_t aLo, uint32_t b, int b_plane,
                                         uint32_t idesc) {
 #pragma unroll
   for (int s = 0; s < KT / 8; ++s) {
     const uint32_t off = (uint32_t)s * 256u, ac = (uint32_t)s * 8u;
+    const uint32_t first = (ACC || s > 0) ? 1u : 0u;
     if (X3) {
-      tc::mma_tf32_ts(d, aLo + ac, tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
+      tc::mma_tf32_ts(d, aLo + ac, tc::desc(b + off, KT), idesc, first);
       tc::mma_tf32_ts(d, aHi + ac, tc::desc(b + b_plane + off, KT), idesc, 1u);
       tc::mma_tf32_ts(d, aHi + ac, tc::desc(b + off, KT), idesc, 1u);
     } else {
-      tc::mma_tf32_ts(d, aHi + ac, tc::desc(b + off, KT), idesc, s > 0 ? 1u : 0u);
+      tc::mma_tf32_ts(d, aHi + ac, tc::desc(b + off, KT), idesc, first);
     }
   }
 }
@@ -188,7 +199,7 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, EB = T::EB, SE = T::SE, RG = T::RG;
   constexpr int K1 = T::K1, N1 = T::N1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char *B1 = sm + T::oB1, *B2 = sm + T::oB2, *B4 = sm + T::oB4;
+  unsigned char *B1 = sm + T::oB1, *B2 = sm + T::oB2, *B2b = sm + T::oB2b, *B4 = sm + T::oB4;
   // this warp's staging region: element e (its e & 7) at sU + (e & 7) SE, sG + (e & 7) M RG
   float *sU = reinterpret_cast<float *>(sm + T::oW) + (threadIdx.x >> 5) * T::WS;
   float *sG = sU;
@@ -216,9 +227,9 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
   const uint32_t tD = tmem + ((uint32_t)(warp * 32) << 16);          // this warp's 32 lanes
-  const uint32_t tHi = tD + (uint32_t)T::ND, tLo = tHi + (uint32_t)K2;
-  const uint32_t aHi = tmem + (uint32_t)T::ND, aLo = aHi + (uint32_t)K2;
-  const uint32_t uB1 = tc::smem_u32(B1), uB2 = tc::smem_u32(B2), uB4 = tc::smem_u32(B4);
+  const uint32_t tHi = tD + (uint32_t)T::ND, tLo = tHi + (uint32_t)T::KA;
+  const uint32_t aHi = tmem + (uint32_t)T::ND, aLo = aHi + (uint32_t)T::KA;
+  const uint32_t uB1 = tc::smem_u32(B1), uB2 = tc::smem_u32(B2), uB2b = tc::smem_u32(B2b), uB4 = tc::smem_u32(B4);
   const float g32 = (float)gamma;
   const int row = tid, rel = row >> 2, rm = row & 3;                 // accumulator row = 4 e + m
   const int le = rel & 7;                                            // element within the warp
@@ -475,9 +486,9 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
       if (!phys) atomicOr(err, kErrNonPhysical);
     }
     __syncwarp();
-    // ---- GEMM 2's operand: [G_r | G_s | lifted fluxes | 0] in A columns [0, K2) ----
-    {
-      const float *g = sG + (row & 31) * RG;
+    const float *g = sG + (row & 31) * RG;
+    if constexpr (!T::SPLIT) {
+      // ---- GEMM 2's operand: [G_r | G_s | lifted fluxes | 0] in A columns [0, K2) ----
 #pragma unroll
       for (int c0 = 0; c0 < K2; c0 += 8) {
         float v[8];
@@ -490,14 +501,49 @@ k_element_tc(const double *c, const double *u0, double *out, float *__restrict__
         }
         st_split<X3, 8>(tHi + (uint32_t)c0, tLo + (uint32_t)c0, v);
       }
+      sync_operands();
+      // ---- GEMM 2: volume projection + lift ----
+      if (tid == 0) {
+        gemm_ts<X3, K2>(tmem, aHi, aLo, uB2, T::B2P, tc::idesc_tf32(128, N2));
+        tc::commit(mbar);
+      }
+      if (!mma_done()) break;
+    } else {
+      // ---- GEMM 2 in two batches: [G_r | 0 | lifted fluxes | 0] in A columns
+      // [0, KG + KL) against [Dr; Lf], then G_s in columns [0, KG) against Ds ----
+      constexpr int KG = T::KG, KL = T::KL;
+#pragma unroll
+      for (int c0 = 0; c0 < KG + KL; c0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int col = c0 + i;
+          const int li = col - KG >= 0 && col - KG < NF ? col - KG : 0;
+          v[i] = col < KG ? (col < NQ ? g[col] : 0.0f)
+                          : (col - KG < NF ? __uint_as_float(__float_as_uint(fl[li]) ^ sgn[li / NE]) : 0.0f);
+        }
+        st_split<X3, 8>(tHi + (uint32_t)c0, tLo + (uint32_t)c0, v);
+      }
+      sync_operands();
+      if (tid == 0) {
+        gemm_ts<X3, KG + KL>(tmem, aHi, aLo, uB2, T::B2P, tc::idesc_tf32(128, N2));
+        tc::commit(mbar);
+      }
+      if (!mma_done()) break;
+#pragma unroll
+      for (int c0 = 0; c0 < KG; c0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = c0 + i < NQ ? g[NQ + c0 + i] : 0.0f;
+        st_split<X3, 8>(tHi + (uint32_t)c0, tLo + (uint32_t)c0, v);
+      }
+      sync_operands();
+      if (tid == 0) {
+        gemm_ts<X3, KG, true>(tmem, aHi, aLo, uB2b, T::B2bP, tc::idesc_tf32(128, N2));
+        tc::commit(mbar);
+      }
+      if (!mma_done()) break;
     }
-    sync_operands();
-    // ---- GEMM 2: volume projection + lift ----
-    if (tid == 0) {
-      gemm_ts<X3, K2>(tmem, aHi, aLo, uB2, T::B2P, tc::idesc_tf32(128, N2));
-      tc::commit(mbar);
-    }
-    if (!mma_done()) break;
     double cr[NP];
     {
       // the mean mode's lift: the three edges' float64 integrals, signed by the
@@ -567,7 +613,7 @@ template <int P, int NE, bool X3, int Q>
 __global__ void __launch_bounds__(kTcThreads) k_tc_tables(DevTables tab, unsigned char *img) {
   using T = Tc<P, NE, X3, Q>;
   constexpr int NP = T::NP, NQ = T::NQ, NF = T::NF, K1 = T::K1, K2 = T::K2, N2 = T::N2, N4 = T::N4;
-  unsigned char *B1 = img + T::oB1, *B2 = img + T::oB2, *B4 = img + T::oB4;
+  unsigned char *B1 = img + T::oB1, *B2 = img + T::oB2, *B2b = img + T::oB2b, *B4 = img + T::oB4;
   for (int i = threadIdx.x; i < T::endB / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(img)[i] = 0u;
   __syncthreads();
   for (int i = threadIdx.x; i < T::N1 * K1; i += blockDim.x) {
@@ -575,15 +621,33 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_tables(DevTables tab, unsigne
     const double v = (n < NQ && k < NP) ? tab.BvT[k * NQ + n] : 0.0;
     put<X3>(B1, T::B1P, n, k, K1, (float)v);
   }
-  for (int i = threadIdx.x; i < N2 * K2; i += blockDim.x) {
-    const int n = i / K2, k = i - n * K2;
-    double v = 0.0;
-    if (n < NP) {
-      if (k < NQ) v = tab.Dr[k * NP + n];
-      else if (k < 2 * NQ) v = tab.Ds[(k - NQ) * NP + n];
-      else if (k < 2 * NQ + NF) v = tab.Lf[(k - 2 * NQ) * NP + n];
+  if constexpr (!T::SPLIT) {
+    for (int i = threadIdx.x; i < N2 * K2; i += blockDim.x) {
+      const int n = i / K2, k = i - n * K2;
+      double v = 0.0;
+      if (n < NP) {
+        if (k < NQ) v = tab.Dr[k * NP + n];
+        else if (k < 2 * NQ) v = tab.Ds[(k - NQ) * NP + n];
+        else if (k < 2 * NQ + NF) v = tab.Lf[(k - 2 * NQ) * NP + n];
+      }
+      put<X3>(B2, T::B2P, n, k, K2, (float)v);
     }
-    put<X3>(B2, T::B2P, n, k, K2, (float)v);
+  } else {
+    constexpr int KG = T::KG, KA = T::KG + T::KL;
+    for (int i = threadIdx.x; i < N2 * KA; i += blockDim.x) {   // [Dr; Lf]
+      const int n = i / KA, k = i - n * KA;
+      double v = 0.0;
+      if (n < NP) {
+        if (k < NQ) v = tab.Dr[k * NP + n];
+        else if (k >= KG && k < KG + NF) v = tab.Lf[(k - KG) * NP + n];
+      }
+      put<X3>(B2, T::B2P, n, k, KA, (float)v);
+    }
+    for (int i = threadIdx.x; i < N2 * KG; i += blockDim.x) {   // Ds
+      const int n = i / KG, k = i - n * KG;
+      const double v = (n < NP && k < NQ) ? tab.Ds[k * NP + n] : 0.0;
+      put<X3>(B2b, T::B2bP, n, k, KG, (float)v);
+    }
   }
   for (int i = threadIdx.x; i < N4 * K1; i += blockDim.x) {
     const int n = i / K1, k = i - n * K1;
