@@ -13,6 +13,7 @@
 
 #include "dg_device.cuh"
 #include "dg_internal.h"
+#include "dg_limiter.cuh"
 
 namespace dg {
 namespace {
@@ -529,8 +530,8 @@ template <int P, int NE, int Q, int EBX>
 __global__ void __launch_bounds__(kSmallThreads, 4)
 k_rk_small(double *c, double *S, double *A, double *trace, double *fhat, const double *__restrict__ geo,
            const int32_t *__restrict__ elem_face, const FaceConn *__restrict__ conn, const FaceGeo *__restrict__ fg,
-           const double *__restrict__ bstate, DevTables tab, int N, int64_t F, double gamma, double dt, int nsteps,
-           int method, unsigned *bar, int *err) {
+           const double *__restrict__ bstate, const int32_t *__restrict__ elem_nbr, DevTables tab, int N, int64_t F,
+           double gamma, double phi1, double dt, int nsteps, int method, int limit, unsigned *bar, int *err) {
   extern __shared__ double smem[];
   const unsigned nb = gridDim.x;
   const int ns = rk_num_stages(method);
@@ -542,6 +543,14 @@ k_rk_small(double *c, double *S, double *A, double *trace, double *fhat, const d
       element_sf_tiles<P, NE, Q, EBX>(smem, st.cin, st.u0, st.out, trace, fhat, geo, elem_face, tab, N, F, st.su, 1,
                                       gamma, err, blockIdx.x, nb);
       if (!grid_barrier(bar, nb, err)) return;
+      if constexpr (P == 1) {
+        // with the limiter on, every stage value is limited in place (and the
+        // traces of the elements it limits rewritten) before the next stage
+        if (limit) {
+          limit_p1_items<true>(st.out, trace, elem_nbr, tab.EPa, tab.EChiM1, tab.EChi, phi1, N, err, blockIdx.x, nb);
+          if (!grid_barrier(bar, nb, err)) return;
+        }
+      }
     }
 }
 
@@ -601,8 +610,11 @@ int run_rk_small(dg_mesh *m, double *c, double dt, int nsteps, int method, cudaS
   double gamma = m->gamma;
   unsigned *bar = m->gbar;
   int *err = m->err_flag;
-  void *args[] = {&c, &S, &A, &tr, &fh, &geo, &ef, &conn, &fg, &bst, &tab, &N, &F, &gamma, &dt, &nsteps, &method,
-                  &bar, &err};
+  const int32_t *nbr = m->elem_nbr;
+  double phi1 = m->phi1;
+  int limit = m->limiter ? 1 : 0;
+  void *args[] = {&c,   &S, &A, &tr,    &fh,   &geo, &ef,     &conn,  &fg,   &bst, &nbr, &tab,
+                  &N,   &F, &gamma, &phi1, &dt,   &nsteps, &method, &limit, &bar, &err};
   return (int)cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)nb), dim3(kSmallThreads), args,
                                           Sc::SMEM, s);
 }

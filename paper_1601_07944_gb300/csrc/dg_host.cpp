@@ -1117,9 +1117,9 @@ extern "C" dg_status dg_rk_step_method(dg_mesh *m, double *c, double dt, int nst
     cudaError_t e = cudaMalloc(&m->rk_acc, sizeof(double) * m->N * dg::M * m->np);
     if (e != cudaSuccess) { cudaGetLastError(); m->rk_acc = nullptr; return fail(DG_ENOMEM, "dg_rk_step: RK4 buffer"); }
   }
-  // a small mesh in float64 without the limiter: the whole call in one launch of
-  // the fused stepper (after the traces of c)
-  if (nsteps > 0 && prec == DG_FP64 && !m->limiter && m->small_stepper && dg::small_rk_fits(m) && coop_capable(m)) {
+  // a small mesh in float64: the whole call in one launch of the fused stepper
+  // (after the traces of c), the limiter included when it is on
+  if (nsteps > 0 && prec == DG_FP64 && m->small_stepper && dg::small_rk_fits(m) && coop_capable(m)) {
     DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return dg::launch_traces(m, c, m->trace, stream); }),
             "dg_rk_step traces");
     DG_CUDA((cudaError_t)timed(m, DG_K_STEPPER, stream,

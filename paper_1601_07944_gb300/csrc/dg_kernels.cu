@@ -29,6 +29,7 @@
 
 #include "dg_device.cuh"
 #include "dg_internal.h"
+#include "dg_limiter.cuh"
 
 namespace dg {
 namespace {
@@ -335,123 +336,15 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, double *out) 
 }
 
 // ---------------------------------------------------------------------------
-// Barth-Jespersen limiter for p = 1 (Section 4.3.5), one thread per element and
-// variable, in place on c.
-// Per variable: Ubar = phi_1 c_1 is the centroid value (the linear modes vanish at
-// the centroid), U^max / U^min the extremes of the centroid values of the element
-// and its three neighbours; at each edge integration point, with
-// d = U(r_qk) - Ubar, alpha_k = min(1, (U^max - Ubar)/d) for d > 0 and
-// min(1, (U^min - Ubar)/d) for d < 0; the linear modes are scaled by min_k alpha_k.
-// Threads read only the constant mode of their neighbours and write only the
-// linear modes of their own element, so the in-place update has no race.
-//
-// have_traces: trace holds the edge traces of c on entry (the element kernel
-// wrote them, with the same per-point sums, edge_traces_sf); they are read
-// instead of recomputed, and rewritten, for the limited state, only where an
-// element is limited.  Otherwise the traces are formed here, and written to
-// trace when it is not null.
-// The float64 pipe is spared where the decisions allow it: extremes are found by
-// integer compares of order-preserving keys of the bit patterns; the smallest
-// ratio over the points is the smaller of (U^max - Ubar) / d+ and
-// (U^min - Ubar) / d- with d+ the largest positive and |d-| the largest negative
-// deviation (again integer compares, the deviations' magnitudes being
-// non-negative), compared by their cross products; a ratio limits only when its
-// numerator is below its denominator; the one reciprocal is formed only when
-// the element is limited.
+// Barth-Jespersen limiter for p = 1 (Section 4.3.5), in place on c: the items of
+// limit_p1_items (dg_limiter.cuh) over the grid.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long order_key(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ unsigned long long nonneg_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x);   // x >= 0: bits order like values
-}
-
+template <bool HAVE_TRACES>
 __global__ void __launch_bounds__(kThreads)
-k_limit_p1(double *c, double *__restrict__ trace, int have_traces, const int32_t *__restrict__ elem_nbr,
+k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ elem_nbr,
            const double *__restrict__ EPa, const double *__restrict__ EChiM1, const double *__restrict__ EChi,
            double phi1, int64_t N, int *err) {
-  constexpr int P = 1, NE = 2, ND = 2, NP = 3, NF = 6;
-  __shared__ double sPa[ND * NE], sChiM1[NP], sChi[NP * NE];
-  if (threadIdx.x < NP * NE) sChi[threadIdx.x] = EChi[threadIdx.x];
-  if (threadIdx.x < ND * NE) sPa[threadIdx.x] = EPa[threadIdx.x];
-  if (threadIdx.x < NP) sChiM1[threadIdx.x] = EChiM1[threadIdx.x];
-  __syncthreads();
-  // one item per (element, variable): four independent chains per element, and
-  // a warp's loads and trace stores cover contiguous runs
-  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < N * M;
-       it += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = it >> 2;
-    const int m = (int)(it & 3);
-    const int64_t nb0 = checked(elem_nbr[e * 3], N, err), nb1 = checked(elem_nbr[e * 3 + 1], N, err),
-                  nb2 = checked(elem_nbr[e * 3 + 2], N, err);
-    double *ce = c + (e * M + m) * NP;
-    double cj[NP] = {ce[0], ce[1], ce[2]};
-    const double cn[3] = {c[(nb0 * M + m) * NP], c[(nb1 * M + m) * NP], c[(nb2 * M + m) * NP]};
-    double *dst = trace ? trace + (size_t)e * NF * M + m : nullptr;
-    double t[NF], z[ND];
-    if (have_traces) {
-#pragma unroll
-      for (int x = 0; x < NF; ++x) t[x] = dst[x * M];
-    } else {
-      face0_z<P>(cj, sChiM1, z);
-#pragma unroll
-      for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
-    }
-    // extremes of the constant modes (phi_1 > 0 keeps the order)
-    double cmax = cj[0], cmin = cj[0];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (order_key(cn[q]) > order_key(cmax)) cmax = cn[q];
-      if (order_key(cn[q]) < order_key(cmin)) cmin = cn[q];
-    }
-    const double ub = phi1 * cj[0];
-    // U^max - Ubar and Ubar - U^min, formed so that they are exactly >= 0 (an
-    // FMA-contracted phi1 cmax - ub would leave the product's rounding error,
-    // of either sign, where the difference is 0; the comparisons below read
-    // these as non-negative bit patterns)
-    const double up = phi1 * (cmax - cj[0]), dn = phi1 * (cj[0] - cmin);
-    // the largest deviation above and below the centroid value: the extremes of
-    // the edge values, found by integer compares, less Ubar (a rounded
-    // subtraction of Ubar is monotone, so this is the largest of the rounded
-    // deviations t - Ubar); 0 where none lies on that side
-    double tmax = t[0], tmin = t[0];
-#pragma unroll
-    for (int x = 1; x < NF; ++x) {
-      if (order_key(t[x]) > order_key(tmax)) tmax = t[x];
-      if (order_key(t[x]) < order_key(tmin)) tmin = t[x];
-    }
-    const unsigned long long bp = (unsigned long long)__double_as_longlong(tmax - ub);
-    const unsigned long long bn = (unsigned long long)__double_as_longlong(ub - tmin);
-    const unsigned long long dpos = (bp >> 63) ? 0ull : bp, dneg = (bn >> 63) ? 0ull : bn;
-    double nbest = 1.0, dbest = 1.0;                                    // ratio 1: no limiting
-    if (dpos != 0ull && nonneg_bits(up) < dpos) {
-      nbest = up;
-      dbest = __longlong_as_double((long long)dpos);
-    }
-    if (dneg != 0ull && nonneg_bits(dn) < dneg) {
-      const double dm = __longlong_as_double((long long)dneg);
-      if (nonneg_bits(dn * dbest) < nonneg_bits(nbest * dm)) { nbest = dn; dbest = dm; }
-    }
-    const bool limited = nonneg_bits(nbest) < nonneg_bits(dbest);
-    if (limited) {
-      // alpha = nbest / dbest by the Newton-refined reciprocal (within 1.5 ulp of
-      // the quotient); the traces of the scaled coefficients by the same sums
-      // every kernel uses, so that they agree bit for bit with k_traces'
-      const double alpha = nbest * recip(dbest);
-      cj[1] *= alpha;
-      cj[2] *= alpha;
-      ce[1] = cj[1];
-      ce[2] = cj[2];
-      face0_z<P>(cj, sChiM1, z);
-#pragma unroll
-      for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
-    }
-    if (dst && (limited || !have_traces)) {
-#pragma unroll
-      for (int x = 0; x < NF; ++x) dst[x * M] = t[x];
-    }
-  }
+  limit_p1_items<HAVE_TRACES>(c, trace, elem_nbr, EPa, EChiM1, EChi, phi1, N, err, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -500,10 +393,16 @@ int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, 
 int launch_limit(const dg_mesh *m, double *c, double *trace, int have_traces, void *stream) {
   if (m->p != 1 || m->ne != 2) return (int)cudaErrorInvalidValue;
   if (have_traces && !trace) return (int)cudaErrorInvalidValue;
-  static int per_sm = 0;
-  k_limit_p1<<<resident_grid(m, (const void *)k_limit_p1, kThreads, m->N * M, &per_sm), kThreads, 0,
-               (cudaStream_t)stream>>>(c, trace, have_traces, m->elem_nbr, m->tab.EPa, m->tab.EChiM1, m->tab.EChi,
-                                       m->phi1, m->N, m->err_flag);
+  static int per_sm[2] = {0, 0};
+  cudaStream_t s = (cudaStream_t)stream;
+  if (have_traces)
+    k_limit_p1<true><<<resident_grid(m, (const void *)k_limit_p1<true>, kThreads, m->N * M, &per_sm[1]), kThreads,
+                        0, s>>>(c, trace, m->elem_nbr, m->tab.EPa, m->tab.EChiM1, m->tab.EChi, m->phi1, m->N,
+                                m->err_flag);
+  else
+    k_limit_p1<false><<<resident_grid(m, (const void *)k_limit_p1<false>, kThreads, m->N * M, &per_sm[0]), kThreads,
+                         0, s>>>(c, trace, m->elem_nbr, m->tab.EPa, m->tab.EChiM1, m->tab.EChi, m->phi1, m->N,
+                                 m->err_flag);
   return (int)cudaGetLastError();
 }
 

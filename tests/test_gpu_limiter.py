@@ -64,13 +64,17 @@ def test_limit_parity(dgmod, oracle_mod, kind, n):
     assert not np.array_equal(ref, c0)                        # the limiter acted
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("method", ["ssp_rk3", "rk2", "rk4"])
 @pytest.mark.parametrize("kind", ["steps", "random_slopes"])
-def test_limited_stepping_parity(dgmod, oracle_mod, method, kind):
-    """20 steps (one plain step, then a replayed 16-step graph and three more)."""
+def test_limited_stepping_parity(dgmod, oracle_mod, method, kind, fused):
+    """20 steps: in one launch of the fused small-mesh stepper (its limiter phase),
+    or as separate launches (one plain step, then a replayed 16-step graph and
+    three more)."""
     mesh = I.periodic_mesh(16)
     o = oracle_mod.OracleDG.from_mesh(mesh, 1)
     m = dgmod.Mesh.from_mesh(mesh, 1)
+    m.set_small_mesh_stepper(fused)
     c0 = o.limit(_state(o, kind))
     dt = I.fixed_dt(mesh, I.density_steps, 1)
     o.set_limiter(True)
@@ -93,6 +97,7 @@ def test_limited_graph_replay_matches_plain_launches(dgmod, oracle_mod):
     m = dgmod.Mesh.from_mesh(mesh, 1)
     c0 = o.limit(o.project_ic(I.density_steps))
     dt = I.fixed_dt(mesh, I.density_steps, 1)
+    m.set_small_mesh_stepper(False)        # the separate launches and their graph
     m.set_limiter(True)
     a = _dev(c0); b = _dev(c0)
     m.rk_step(a, dt, 40)

@@ -1,9 +1,9 @@
 """The fused small-mesh stepper (dg_set_small_mesh_stepper): on a mesh whose
-element tiles fit in one wave of the GPU, a float64 Runge-Kutta call without the
-limiter runs every stage in one cooperative launch, the edge and element phases
-separated by a barrier over the grid.  It runs the same code as the separate
-launches, so the states agree bit for bit; every small-mesh parity test of the
-suite (against the oracle) goes through it by default."""
+element tiles fit in one wave of the GPU, a float64 Runge-Kutta call runs every
+stage in one cooperative launch, the edge, element and (with the limiter on)
+limiter phases separated by a barrier over the grid.  It runs the same code as
+the separate launches, so the states agree bit for bit; every small-mesh parity
+test of the suite (against the oracle) goes through it by default."""
 import numpy as np
 import pytest
 
@@ -77,6 +77,30 @@ def test_fused_with_boundary_faces(dgmod, rule):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("method", ["ssp_rk3", "rk2", "rk4"])
+@pytest.mark.parametrize("n", [10, 16])
+def test_fused_with_limiter(dgmod, n, method):
+    """p = 1 with every stage limited (density steps: the limiter acts on most
+    elements); 200 and 512 elements, ragged last tiles; no limiter launch on the
+    fused side."""
+    mesh = I.periodic_mesh(n)
+    m = dgmod.Mesh.from_mesh(mesh, 1)
+    c0 = m.limit(m.project_function(I.density_steps))
+    dt = I.fixed_dt(mesh, I.density_steps, 1)
+    m.set_limiter(True)
+    a, kta = _run(m, c0, dt, 20, method, True)
+    b, ktb = _run(m, c0, dt, 20, method, False)
+    m.set_limiter(False)
+    assert "stepper" in kta and "other" not in kta and "element" not in kta
+    assert "stepper" not in ktb and "other" in ktb
+    assert np.array_equal(a, b)
+    try:
+        free, _ = _run(m, c0, dt, 20, method, True)
+        assert not np.array_equal(free, a)        # limiting changed the run
+    except dgmod.DGError as e:
+        assert dgmod.STATUS[e.status] == "DG_ENONPHYS"   # or, without it, the run broke down
+
+
 def test_fused_matches_oracle(dgmod, oracle_mod):
     """The fused path against the oracle's SSP-RK3 run (relative L2 <= 1e-12)."""
     mesh = I.periodic_mesh(12)
@@ -95,13 +119,14 @@ def test_fused_matches_oracle(dgmod, oracle_mod):
 
 
 def test_large_mesh_keeps_separate_launches(dgmod):
-    """p = 3 tiles hold 32 elements; 9,800 elements are 307 tiles, more than one
-    wave (2 per SM on 152 SMs): the separate launches run."""
+    """The fused stepper's tiles hold 4 or 8 elements, at most 4 blocks per SM;
+    9,800 elements at p = 3 need 1,225 blocks of 8, more than one wave on 152 SMs:
+    the separate launches run."""
     import torch
     mesh = I.periodic_mesh(70)
     m = dgmod.Mesh.from_mesh(mesh, 3)
     props = torch.cuda.get_device_properties(0)
-    assert (m.N + 31) // 32 > 2 * props.multi_processor_count
+    assert (m.N + 7) // 8 > 4 * props.multi_processor_count
     c = m.project_function(I.vortex)
     m.set_timing(True)
     m.rk_step(c, I.fixed_dt(mesh, I.vortex, 3), 2)
