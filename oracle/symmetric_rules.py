@@ -29,8 +29,9 @@ float64 once at the end.
 The solution is not unique for every structure (at p = 3 there are at least
 two rules with positive weights and interior points).  The rule used is the
 one this iteration reaches from START; among the positive-interior solutions
-that a seeded multi-start search found, it is the one whose points lie
-farthest from the edges (largest smallest barycentric coordinate).
+that the seeded multi-start search of search_symmetric_rules.py finds, it is
+the one whose points lie farthest from the edges (largest smallest barycentric
+coordinate), and START is that rule to three significant digits.
 
 Point order within the rule: the orbits in START's order; an S21 orbit as
 (r, s) = (a, a), (a, 1-2a), (1-2a, a); an S111 orbit, with c = 1-a-b, as

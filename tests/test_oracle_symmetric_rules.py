@@ -12,7 +12,11 @@ Facts checked, none of them a re-run of the derivation:
     (1/6, 2/3) with weights 1/6 (closed form);
   * the basis is orthonormal under the rule (Gram = I, degree 2p products);
   * the DG solver on the rule: free-stream preservation, exact discrete
-    conservation, and order p+1 on the exact density wave.
+    conservation, and order p+1 on the exact density wave;
+  * provenance: the seeded multi-start search (oracle/search_symmetric_rules.py,
+    float64 Levenberg-Marquardt on orthogonal-basis moments from random orbit
+    parameters) finds, as the rule farthest from the edges, the one the start
+    values lead to, and it agrees with the 50-digit solution.
 """
 import math
 
@@ -139,3 +143,27 @@ def test_rules_differ_from_collapsed_grid(oracle_mod):
     kw = dict(rho0=1.0, rx=0.02, ry=-0.015, u=0.4, v=-0.3, p0=1.0, px=0.03, py=0.05)
     cl = a.project_ic(lambda x, y: I.linear_state(x, y, **kw))
     assert np.abs(a.rhs(cl) - b.rhs(cl)).max() < 1e-13
+
+
+@pytest.mark.parametrize("p", sorted(COUNTS))
+def test_start_values_come_from_the_search(rules, p):
+    """START (three significant digits) is the search's chosen rule rounded, and
+    that rule is the 50-digit rule to float64 search accuracy."""
+    from oracle import search_symmetric_rules as S
+    found = S.search(p)
+    assert found, "no positive-interior rule found"
+    can, mb = found[0]
+    assert S.as_start(can) == [(k, tuple(v)) for k, v in S.START[p]]
+    # the chosen rule's points and weights against the oracle's rule (same orbit
+    # order as START after canonical sorting: compare as sets of weighted points)
+    x = []
+    for o in can:
+        x += list(o[1:])
+    bary, w = S._points([o[0] for o in can], np.array(x))
+    r, s_, wr = rules[p]
+    assert len(w) == len(wr)
+    for k in range(len(wr)):        # every point of the oracle's rule, found with its weight
+        d = np.hypot(bary[:, 1] - r[k], bary[:, 2] - s_[k])
+        j = int(np.argmin(d))
+        assert d[j] < 1e-9 and abs(w[j] - wr[k]) < 1e-9
+
