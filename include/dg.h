@@ -254,16 +254,16 @@ dg_status dg_rk_step_method(dg_mesh *mesh, double *c, double dt, int nsteps, dg_
                             dg_precision prec, void *stream);
 
 /* The fused small-mesh stepper (Section 7.1 finds small meshes bound by kernel
- * launches): on a mesh whose element tiles fit in one wave of the GPU (at most
- * 2 x SMs tiles of 64 / 32 / 16 elements for p = 1 / 2-3 / 4-5), a float64
- * dg_rk_step or dg_rk_step_method call without the limiter runs the traces of
- * the state and then every stage of all nsteps steps in one cooperative launch,
- * the edge and element phases of each stage separated by a barrier over the grid
- * (bounded: a wait longer than 2 s records DG_ETIMEOUT for dg_device_status).
- * The phases run the same code as the separate launches, so the results are
- * bitwise equal.  enable = 0 makes such calls use the separate launches (and
- * CUDA graphs) as on larger meshes; on by default.  Errors: DG_EINVAL (null
- * mesh). */
+ * launches): on a mesh whose elements fit, in tiles of 4 or 8, in the blocks
+ * of one wave of the GPU (at most 4 per SM), a float64 dg_rk_step or
+ * dg_rk_step_method call runs the traces of the state and then every stage of
+ * all nsteps steps in one cooperative launch, the edge, element and (with
+ * dg_set_limiter on) limiter phases of each stage separated by a barrier over
+ * the grid (bounded: a wait longer than 2 s records DG_ETIMEOUT for
+ * dg_device_status).  The phases run the same code as the separate launches,
+ * so the results are bitwise equal.  enable = 0 makes such calls use the
+ * separate launches (and CUDA graphs) as on larger meshes; on by default.
+ * Errors: DG_EINVAL (null mesh). */
 dg_status dg_set_small_mesh_stepper(dg_mesh *mesh, int enable);
 
 /* Barth-Jespersen limiter for p = 1 (Section 4.3.5, Eqs. limit, limitmax,

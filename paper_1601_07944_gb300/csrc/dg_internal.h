@@ -198,7 +198,6 @@ namespace dg {
 
 // Kernel launchers (dg_kernels.cu).  All return a cudaError_t cast to int.
 int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream);
-// fast_alpha: the dissipation coefficient in float32 (mixed-precision modes only)
 int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream);
 int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, int *per_sm);
 // out = mode==0 ? R(c) : the stage update su (and su.out2);  trace_out may be null.
@@ -236,8 +235,9 @@ int launch_element_tc_sym(const dg_mesh *m, int split3, const double *c, const d
                           float *trace_out, const float *fhat, const double *fmean, const StageUpdate &su,
                           int mode, void *stream);
 int launch_convert_check(int n, unsigned long long *bad, void *stream);
-// The fused small-mesh stepper (float64, no limiter): nsteps steps of `method` on
-// c in one cooperative launch, the traces of c already in m->trace.  Returns a
+// The fused small-mesh stepper (float64; the limiter a phase of it when on):
+// nsteps steps of `method` on c in one cooperative launch, the traces of c
+// already in m->trace.  Returns a
 // cudaError_t cast to int.  small_rk_fits: whether the mesh is small enough (its
 // element tiles fit in one wave of the GPU).
 bool small_rk_fits(const dg_mesh *m);

@@ -366,8 +366,8 @@ class Mesh:
         return c
 
     def set_small_mesh_stepper(self, on: bool):
-        """Run rk_step on a small mesh (float64, no limiter) as one fused launch
-        per call (on by default) or as separate launches."""
+        """Run rk_step on a small mesh (float64) as one fused launch per call (on
+        by default) or as separate launches."""
         _check(load().dg_set_small_mesh_stepper(self._h, 1 if on else 0))
 
     def set_limiter(self, on: bool):
