@@ -46,8 +46,10 @@ constexpr int kThreads = 256;
 // face0_z forms the Z_a of a coefficient set (they do not depend on k);
 // edge_traces_sf takes them with cj, the N_p coefficients; ePa = P_a(xi_k)
 // [ND][NE], eChi = chi_j(xi_k) [N_p][NE], eChiM1 = chi_j(-1) [N_p].  Every kernel
-// that writes traces goes through these two, in this order of operations, so
-// traces of the same state agree bit for bit whichever kernel wrote them.
+// that writes traces goes through these two (or through face_sums and
+// edge_traces_unit below, which give the same values), in this order of
+// operations, so traces of the same state agree bit for bit whichever kernel
+// wrote them.
 template <int P>
 __device__ __forceinline__ void face0_z(const double *cj, const double *eChiM1, double z[P + 1]) {
 #pragma unroll
@@ -70,6 +72,39 @@ __device__ __forceinline__ void edge_traces_sf(const double *cj, const double *z
   for (int a = 0; a <= P; ++a) t0 = fma(ePa[a * NE + k], z[a], t0);
 #pragma unroll
   for (int d = 0; d <= P; ++d)
+#pragma unroll
+    for (int b = 0; b <= d; ++b) {
+      const int j = d * (d + 1) / 2 + b;
+      const double cv = cj[j];
+      if ((d - b) & 1) od = fma(eChi[j * NE + k], cv, od);
+      else ev = fma(eChi[j * NE + k], cv, ev);
+    }
+  t1 = ev + od;
+  t2 = ev - od;
+}
+
+// The same traces from the unweighted tables, in 2 n_e - 1 fewer float64
+// operations per (element, variable): P_0 = 1, so T0_k starts from Z_0; and
+// chi_00 does not depend on the edge point, so the constant mode's term
+// chi_00 c_00 of faces 1 and 2 is formed once (face_sums puts it in z[P+1]).
+// The values are those of edge_traces_sf on the same tables: fma(1, Z_0, 0) is
+// Z_0, and chi_00 c_00 is the same rounded product.  (The weighted tables of the
+// adjoint's transposed lift have neither property: edge_traces_sf serves them.)
+template <int P>
+__device__ __forceinline__ void face_sums(const double *cj, const double *eChiM1, double chi00, double z[P + 2]) {
+  face0_z<P>(cj, eChiM1, z);
+  z[P + 1] = chi00 * cj[0];
+}
+
+template <int P, int NE>
+__device__ __forceinline__ void edge_traces_unit(const double *cj, const double *z, const double *ePa,
+                                                 const double *eChi, int k, double &t0, double &t1, double &t2) {
+  double ev = z[P + 1], od = 0.0;
+  t0 = z[0];
+#pragma unroll
+  for (int a = 1; a <= P; ++a) t0 = fma(ePa[a * NE + k], z[a], t0);
+#pragma unroll
+  for (int d = 1; d <= P; ++d)
 #pragma unroll
     for (int b = 0; b <= d; ++b) {
       const int j = d * (d + 1) / 2 + b;

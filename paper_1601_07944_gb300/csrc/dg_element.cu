@@ -66,20 +66,25 @@ struct SfCfg {
 // Reference fluxes at one volume point: G_r = J^tau row 0 . (F1, F2), G_s = row 1
 // . (F1, F2).  The Euler flux along a direction d is (rho v_d, rho u v_d + p d_x,
 // rho v v_d + p d_y, (E + p) v_d) with v_d = (rho u d_x + rho v d_y) / rho.
-__device__ __forceinline__ void ref_flux(const double U[M], const double *g, double gamma, int *err, double Gr[M],
-                                         double Gs[M]) {
+// The Euler flux of U along two directions a and b (Fa = F1 a_x + F2 a_y, ...).
+__device__ __forceinline__ void flux_two_dirs(const double U[M], double ax, double ay, double bx, double by,
+                                              double gamma, int *err, double Fa[M], double Fb[M]) {
   const double inv = recip(U[0]);
   const double p = (gamma - 1.0) * fma(fma(U[1], U[1], U[2] * U[2]), -0.5 * inv, U[3]);
   if (!(positive_finite(U[0]) & positive_finite(p))) atomicOr(err, kErrNonPhysical);
   const double Ep = U[3] + p;
   {
-    const double mn = fma(U[1], g[0], U[2] * g[1]), vd = mn * inv;
-    Gr[0] = mn; Gr[1] = fma(U[1], vd, p * g[0]); Gr[2] = fma(U[2], vd, p * g[1]); Gr[3] = Ep * vd;
+    const double mn = fma(U[1], ax, U[2] * ay), vd = mn * inv;
+    Fa[0] = mn; Fa[1] = fma(U[1], vd, p * ax); Fa[2] = fma(U[2], vd, p * ay); Fa[3] = Ep * vd;
   }
   {
-    const double mn = fma(U[1], g[2], U[2] * g[3]), vd = mn * inv;
-    Gs[0] = mn; Gs[1] = fma(U[1], vd, p * g[2]); Gs[2] = fma(U[2], vd, p * g[3]); Gs[3] = Ep * vd;
+    const double mn = fma(U[1], bx, U[2] * by), vd = mn * inv;
+    Fb[0] = mn; Fb[1] = fma(U[1], vd, p * bx); Fb[2] = fma(U[2], vd, p * by); Fb[3] = Ep * vd;
   }
+}
+__device__ __forceinline__ void ref_flux(const double U[M], const double *g, double gamma, int *err, double Gr[M],
+                                         double Gs[M]) {
+  flux_two_dirs(U, g[0], g[1], g[2], g[3], gamma, err, Gr, Gs);
 }
 
 // mode j -> a (first Dubiner index); modes are ordered by degree d = a+b, then b
@@ -250,14 +255,11 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
         }
         double Ha[M], Hb[M];
         if (el < ecount) {
-          double Gr[M], Gs[M];
-          ref_flux(U, geo + (size_t)(e0 + el) * GEO, gamma, err, Gr, Gs);
+          // the flux is linear in its direction: Ha = G_r + half G_s is the flux
+          // along J^tau row 0 + half row 1, Hb = G_s the flux along row 1
+          const double *g = geo + (size_t)(e0 + el) * GEO;
           const double half = sHalf[ia];
-#pragma unroll
-          for (int m = 0; m < M; ++m) {
-            Ha[m] = fma(half, Gs[m], Gr[m]);
-            Hb[m] = Gs[m];
-          }
+          flux_two_dirs(U, fma(half, g[2], g[0]), fma(half, g[3], g[1]), g[2], g[3], gamma, err, Ha, Hb);
         } else {
 #pragma unroll
           for (int m = 0; m < M; ++m) { Ha[m] = 0.0; Hb[m] = 0.0; }
@@ -416,10 +418,10 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
       // variable), in the buffer the modes have finished reading (sX; direct: sH)
       double *sZ = S::DIRECT ? sH : sX;
       for (int i = threadIdx.x; i < ecount * M; i += blockDim.x) {
-        double z[ND];
-        face0_z<P>(sO + i * NP, sEChiM1, z);
+        double z[ND + 1];
+        face_sums<P>(sO + i * NP, sEChiM1, sEChi[0], z);
 #pragma unroll
-        for (int a = 0; a < ND; ++a) sZ[i * ND + a] = z[a];
+        for (int a = 0; a <= ND; ++a) sZ[i * (ND + 1) + a] = z[a];
       }
       __syncthreads();
       // edge traces of the new state, one item per (element, variable, edge point k):
@@ -431,7 +433,7 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
         const double *cj = sO + (el * M + m) * NP;
         double *dst = trace_out + (size_t)(e0 + el) * NF * M + m;
         double t0, t1, t2;
-        edge_traces_sf<P, NE>(cj, sZ + (el * M + m) * ND, sEPa, sEChi, k, t0, t1, t2);
+        edge_traces_unit<P, NE>(cj, sZ + (el * M + m) * (ND + 1), sEPa, sEChi, k, t0, t1, t2);
         dst[k * M] = t0;
         dst[(NE + k) * M] = t1;
         dst[(3 * NE - 1 - k) * M] = t2;

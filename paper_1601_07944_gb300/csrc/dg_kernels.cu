@@ -36,7 +36,7 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // edge traces of a coefficient array: trace[e][q*NE+k][m] = sum_j c[e][m][j] phi_j(r_{q,k}),
-// by the same factorised sums (edge_traces_sf) as the element kernel's epilogue
+// by the same factorised sums (face_sums, edge_traces_unit) as the element kernel's epilogue
 // ---------------------------------------------------------------------------
 template <int P, int NE>
 __global__ void __launch_bounds__(kThreads)
@@ -46,7 +46,7 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
   constexpr int NP = C::NP, ND = C::ND, NF = C::NF, EB = C::EB;
   __shared__ double sPa[ND * NE], sChiM1[NP], sChi[NP * NE];
   __shared__ double sC[EB * M * NP];
-  __shared__ double sZ[EB * M * ND];
+  __shared__ double sZ[EB * M * (ND + 1)];
   for (int i = threadIdx.x; i < NP * NE; i += blockDim.x) sChi[i] = EChi[i];
   for (int i = threadIdx.x; i < ND * NE; i += blockDim.x) sPa[i] = EPa[i];
   for (int i = threadIdx.x; i < NP; i += blockDim.x) sChiM1[i] = EChiM1[i];
@@ -61,17 +61,17 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
     __syncthreads();
     // Z_a of face 0, once per (element, variable), as the element kernel forms them
     for (int i = threadIdx.x; i < ecount * M; i += blockDim.x) {
-      double z[ND];
-      face0_z<P>(sC + i * NP, sChiM1, z);
+      double z[ND + 1];
+      face_sums<P>(sC + i * NP, sChiM1, sChi[0], z);
 #pragma unroll
-      for (int a = 0; a < ND; ++a) sZ[i * ND + a] = z[a];
+      for (int a = 0; a <= ND; ++a) sZ[i * (ND + 1) + a] = z[a];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ecount * M * NE; i += blockDim.x) {
       const int el = i / (M * NE), m = (i / NE) % M, k = i % NE;
       const double *cj = sC + (el * M + m) * NP;
       double t0, t1, t2;
-      edge_traces_sf<P, NE>(cj, sZ + (el * M + m) * ND, sPa, sChi, k, t0, t1, t2);
+      edge_traces_unit<P, NE>(cj, sZ + (el * M + m) * (ND + 1), sPa, sChi, k, t0, t1, t2);
       double *dst = trace + (size_t)(e0 + el) * NF * M + m;
       dst[k * M] = t0;
       dst[(NE + k) * M] = t1;

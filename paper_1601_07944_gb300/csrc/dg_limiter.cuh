@@ -27,7 +27,7 @@ namespace {
 // linear modes of their own element, so the in-place update has no race.
 //
 // HAVE_TRACES: trace holds the edge traces of c on entry (the element kernel
-// wrote them, with the same per-point sums, edge_traces_sf); they are read
+// wrote them, with the same per-point sums, edge_traces_unit); they are read
 // instead of recomputed, and rewritten, for the limited state, only where an
 // element is limited.  Otherwise the traces are formed here, and written to
 // trace when it is not null.
@@ -80,14 +80,14 @@ __device__ __forceinline__ void limit_p1_items(double *c, double *__restrict__ t
     double cj[NP] = {ce[0], ce[1], ce[2]};
     const double cn[3] = {c[(nb0 * M + m) * NP], c[(nb1 * M + m) * NP], c[(nb2 * M + m) * NP]};
     double *dst = trace ? trace + (size_t)e * NF * M + m : nullptr;
-    double t[NF], z[ND];
+    double t[NF], z[ND + 1];
     if (HAVE_TRACES) {
 #pragma unroll
       for (int x = 0; x < NF; ++x) t[x] = dst[x * M];
     } else {
-      face0_z<P>(cj, sChiM1, z);
+      face_sums<P>(cj, sChiM1, sChi[0], z);
 #pragma unroll
-      for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
+      for (int k = 0; k < NE; ++k) edge_traces_unit<P, NE>(cj, z, sPa, sChi, k, t[k], t[NE + k], t[3 * NE - 1 - k]);
     }
     // extremes of the constant modes (phi_1 > 0 keeps the order)
     unsigned long long kmax = order_key(cj[0]), kmin = kmax;
@@ -137,9 +137,9 @@ __device__ __forceinline__ void limit_p1_items(double *c, double *__restrict__ t
       ce[2] = cj[2];
       if (dst) {
         double u[NF];
-        face0_z<P>(cj, sChiM1, z);
+        face_sums<P>(cj, sChiM1, sChi[0], z);
 #pragma unroll
-        for (int k = 0; k < NE; ++k) edge_traces_sf<P, NE>(cj, z, sPa, sChi, k, u[k], u[NE + k], u[3 * NE - 1 - k]);
+        for (int k = 0; k < NE; ++k) edge_traces_unit<P, NE>(cj, z, sPa, sChi, k, u[k], u[NE + k], u[3 * NE - 1 - k]);
 #pragma unroll
         for (int x = 0; x < NF; ++x) dst[x * M] = u[x];
       }
