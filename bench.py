@@ -576,8 +576,10 @@ def vortex_error(steps: int = 200):
 
 def adjoint_ratio(steps: int = 20, every: int = 10):
     """Cost of the discrete adjoint relative to the forward pass on the 256x256,
-    p=2 differentiation workload: one dg_adjoint_step against one dg_rk_step, and
-    the checkpointed backward (recomputation included) against its forward."""
+    p=2 differentiation workload: one dg_adjoint_step (stages recomputed) and one
+    dg_adjoint_step_stages (stages given) against one dg_rk_step, and the
+    checkpointed backward (recomputation included, stage values kept, the
+    default) against its forward, and the same backward recomputing the stages."""
     import torch
     from paper_1601_07944_gb300 import autograd as AG, dg, inputs as I
     mesh = I.periodic_mesh(256)
@@ -590,26 +592,37 @@ def adjoint_ratio(steps: int = 20, every: int = 10):
     c = c0.clone()
     m.rk_step(c, dt, 2); m.adjoint_step(c0, dt, lam, out=out)
     torch.cuda.synchronize()
+    u1, u2 = torch.empty_like(c0), torch.empty_like(c0)
+    m.rk_step_stages(c0.clone(), dt, u1, u2)
+    m.adjoint_step_stages(c0, u1, u2, dt, lam, out=out)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     e[0].record(); m.rk_step(c, dt, steps); e[1].record()
     for _ in range(steps):
         m.adjoint_step(c0, dt, lam, out=out)
-    e[2].record(); torch.cuda.synchronize()
-    fwd, adj = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    e[2].record()
+    for _ in range(steps):
+        m.adjoint_step_stages(c0, u1, u2, dt, lam, out=out)
+    e[3].record(); torch.cuda.synchronize()
+    fwd, adj, adj_s = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])
     dJ = m.det_j()
     tgt = c0.clone()
-    for rep in range(2):                   # the first pass warms up torch's autograd path
-        x = c0.clone().requires_grad_(True)
-        torch.cuda.synchronize(); t0 = time.perf_counter()
-        cT = AG.solve(m, x, dt, steps, every)
-        loss = AG.density_misfit(dJ, cT, tgt)
-        torch.cuda.synchronize(); t1 = time.perf_counter()
-        loss.backward()
-        torch.cuda.synchronize(); t2 = time.perf_counter()
+    ratio = {}
+    for keep in (True, False):
+        for rep in range(2):                   # the first pass warms up torch's autograd path
+            x = c0.clone().requires_grad_(True)
+            torch.cuda.synchronize(); t0 = time.perf_counter()
+            cT = AG.solve(m, x, dt, steps, every, keep_stages=keep)
+            loss = AG.density_misfit(dJ, cT, tgt)
+            torch.cuda.synchronize(); t1 = time.perf_counter()
+            loss.backward()
+            torch.cuda.synchronize(); t2 = time.perf_counter()
+        ratio[keep] = (t2 - t1) / (t1 - t0)
     return {"workload": "perturbed vortex, 256x256 mesh, p=2, %d steps, checkpoint every %d" % (steps, every),
             "adjoint_step_over_rk_step": adj / fwd,
-            "backward_over_forward_with_recompute": (t2 - t1) / (t1 - t0),
-            "rk_step_ms": fwd / steps, "adjoint_step_ms": adj / steps}
+            "adjoint_step_stages_given_over_rk_step": adj_s / fwd,
+            "backward_over_forward_with_recompute": ratio[True],
+            "backward_over_forward_recomputing_stages": ratio[False],
+            "rk_step_ms": fwd / steps, "adjoint_step_ms": adj / steps, "adjoint_step_stages_given_ms": adj_s / steps}
 
 
 def run_rules(n: int = 256, steps: int = 100):

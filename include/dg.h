@@ -311,6 +311,24 @@ dg_status dg_rhs_adjoint(dg_mesh *mesh, const double *c, const double *lam, doub
 dg_status dg_adjoint_step(dg_mesh *mesh, const double *c_n, double dt, const double *lam_np1,
                           double *lam_n, void *stream);
 
+/* One float64 SSP-RK3 step of dg_rk_step on c (DEVICE [N][4][N_p], in place)
+ * that also writes its two stage values, u1 = c + dt R(c) and
+ * u2 = 3/4 c + 1/4 (u1 + dt R(u1)) (Section 4.3.1's stages in Shu-Osher form),
+ * into u1 and u2 (DEVICE [N][4][N_p], caller-owned, distinct from c and from each
+ * other): the same launches as dg_rk_step, so c comes out with the same bits,
+ * and the stage values are those dg_adjoint_step would recompute.  For a
+ * backward pass that keeps them (dg_adjoint_step_stages).  Errors: DG_EINVAL
+ * (null or aliased buffers, dt not finite, boundary state missing), DG_ENOTIMPL
+ * with the limiter on.  Asynchronous. */
+dg_status dg_rk_step_stages(dg_mesh *mesh, double *c, double dt, double *u1, double *u2, void *stream);
+
+/* dg_adjoint_step with the step's stage values given (as dg_rk_step_stages
+ * writes them) instead of recomputed: the reverse sweep alone, three transposed
+ * RHS applications.  The same result, bit for bit, as dg_adjoint_step on c_n.
+ * lam_n must not alias the inputs.  Errors as dg_adjoint_step.  Asynchronous. */
+dg_status dg_adjoint_step_stages(dg_mesh *mesh, const double *c_n, const double *u1, const double *u2,
+                                 double dt, const double *lam_np1, double *lam_n, void *stream);
+
 /* A stable time step (the paper gives none; Section 4.3.1 computes one with a
  * reduction): dt = cfl * r_min / ((2p+1) * s_max), with r_min the smallest
  * inscribed radius (twice the area over the perimeter) of the mesh and s_max the

@@ -1246,34 +1246,16 @@ extern "C" dg_status dg_rhs_adjoint(dg_mesh *m, const double *c, const double *l
   return DG_OK;
 }
 
-extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, const double *lam_np1,
-                                     double *lam_n, void *stream) {
+// The reverse sweep of one SSP-RK3 step from c_n, given its stage values u1, u2:
+// c_{n+1} = 1/3 c_n + 2/3 (u2 + dt R(u2)), u2 = 3/4 c_n + 1/4 (u1 + dt R(u1)),
+// u1 = c_n + dt R(c_n), transposed stage by stage.
+static dg_status adjoint_sweep(dg_mesh *m, const double *c_n, const double *u1, const double *u2, double dt,
+                               const double *lam_np1, double *lam_n, void *stream) {
   using namespace dg;
-  if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "dg_adjoint_step: null argument");
-  if (dg_status dst = check_device(m, "dg_adjoint_step")) return dst;
-  if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "dg_adjoint_step: lam_n aliases an input");
-  if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_adjoint_step: dt is not finite");
-  if (m->limiter) return fail(DG_ENOTIMPL, "dg_adjoint_step: the limited step has no adjoint here (the limiter is off by default)");
-  dg_status ast = adjoint_buffers(m, "dg_adjoint_step");
-  if (ast != DG_OK) return ast;
   const size_t S = (size_t)m->N * M * m->np;           // one state
   const size_t TR = (size_t)m->N * 3 * m->ne * M;       // one trace block
-  double *u1 = m->adj_buf, *u2 = u1 + S, *b1 = u2 + S, *b2 = b1 + S, *uvol = b2 + S;
+  double *b1 = m->adj_buf + 2 * S, *b2 = b1 + S, *uvol = b2 + S;
   double *G = uvol + S, *TB = G + TR;
-  // forward stages from c_n: u1 = c_n + dt R(c_n), u2 = 3/4 c_n + 1/4 (u1 + dt R(u1))
-  DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces(m, c_n, m->trace, stream); }),
-          "adjoint traces");
-  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
-          "adjoint stage 1 flux");
-  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-            return launch_element(m, c_n, nullptr, u1, m->trace, m->fhat, dt, 0.0, 1.0, 1, stream);
-          }), "adjoint stage 1");
-  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
-          "adjoint stage 2 flux");
-  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
-            return launch_element(m, u1, c_n, u2, nullptr, m->fhat, dt, 0.75, 0.25, 1, stream);
-          }), "adjoint stage 2");
-  // reverse sweep of c_{n+1} = 1/3 c_n + 2/3 (u2 + dt R(u2))
   auto vjp = [&](const double *u, const double *lam, const double *X, const double *Y, const double *Z,
                  double x0, double x1, double x2, double s, double *out, const char *what) -> dg_status {
     DG_CUDA((cudaError_t)timed(m, DG_K_ADJOINT, stream, [&] {
@@ -1290,6 +1272,75 @@ extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, c
   // lam_n = 1/3 lam + 3/4 b2 + b1 + dt R'(c_n)^T b1
   if ((st = vjp(c_n, b1, lam_np1, b2, b1, 1.0 / 3.0, 0.75, 1.0, dt, lam_n, "adjoint c_n")) != DG_OK) return st;
   return DG_OK;
+}
+
+// The forward stages of one SSP-RK3 step from c: u1 = c + dt R(c) and
+// u2 = 3/4 c + 1/4 (u1 + dt R(u1)); with cnew, also cnew = 1/3 c + 2/3 (u2 + dt R(u2))
+// (cnew may be c).  The same launches, in the same order, as a float64 dg_rk_step
+// step, so the values are the same bits.
+static dg_status forward_stages(dg_mesh *m, const double *c, double dt, double *u1, double *u2, double *cnew,
+                                void *stream) {
+  using namespace dg;
+  DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] { return launch_traces(m, c, m->trace, stream); }),
+          "stages traces");
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
+          "stage 1 flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+            return launch_element(m, c, nullptr, u1, m->trace, m->fhat, dt, 0.0, 1.0, 1, stream);
+          }), "stage 1");
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
+          "stage 2 flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+            return launch_element(m, u1, c, u2, cnew ? m->trace : nullptr, m->fhat, dt, 0.75, 0.25, 1, stream);
+          }), "stage 2");
+  if (!cnew) return DG_OK;
+  DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
+          "stage 3 flux");
+  DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+            return launch_element(m, u2, c, cnew, m->trace, m->fhat, dt, 1.0 / 3.0, 2.0 / 3.0, 1, stream);
+          }), "stage 3");
+  return DG_OK;
+}
+
+static dg_status adjoint_checks(dg_mesh *m, const void *c_n, double dt, const void *lam_np1, const void *lam_n,
+                                const char *who) {
+  if (!m || !c_n || !lam_np1 || !lam_n) return fail(DG_EINVAL, "%s: null argument", who);
+  if (dg_status dst = check_device(m, who)) return dst;
+  if (lam_n == lam_np1 || lam_n == c_n) return fail(DG_EINVAL, "%s: lam_n aliases an input", who);
+  if (!std::isfinite(dt)) return fail(DG_EINVAL, "%s: dt is not finite", who);
+  if (m->limiter) return fail(DG_ENOTIMPL, "%s: the limited step has no adjoint here (the limiter is off by default)", who);
+  return adjoint_buffers(m, who);
+}
+
+extern "C" dg_status dg_adjoint_step(dg_mesh *m, const double *c_n, double dt, const double *lam_np1,
+                                     double *lam_n, void *stream) {
+  dg_status st = adjoint_checks(m, c_n, dt, lam_np1, lam_n, "dg_adjoint_step");
+  if (st != DG_OK) return st;
+  const size_t S = (size_t)m->N * dg::M * m->np;
+  double *u1 = m->adj_buf, *u2 = u1 + S;
+  // the forward stages from c_n, then the reverse sweep
+  if ((st = forward_stages(m, c_n, dt, u1, u2, nullptr, stream)) != DG_OK) return st;
+  return adjoint_sweep(m, c_n, u1, u2, dt, lam_np1, lam_n, stream);
+}
+
+extern "C" dg_status dg_rk_step_stages(dg_mesh *m, double *c, double dt, double *u1, double *u2, void *stream) {
+  if (!m || !c || !u1 || !u2) return fail(DG_EINVAL, "dg_rk_step_stages: null argument");
+  if (dg_status dst = check_device(m, "dg_rk_step_stages")) return dst;
+  if (u1 == u2 || u1 == c || u2 == c) return fail(DG_EINVAL, "dg_rk_step_stages: c, u1 and u2 must be distinct");
+  if (!std::isfinite(dt)) return fail(DG_EINVAL, "dg_rk_step_stages: dt is not finite");
+  if (!m->bstate_set)
+    return fail(DG_EINVAL, "dg_rk_step_stages: the mesh has DG_BC_STATE faces and no boundary state was set");
+  if (m->limiter) return fail(DG_ENOTIMPL, "dg_rk_step_stages: not with the limiter on");
+  return forward_stages(m, c, dt, u1, u2, c, stream);
+}
+
+extern "C" dg_status dg_adjoint_step_stages(dg_mesh *m, const double *c_n, const double *u1, const double *u2,
+                                            double dt, const double *lam_np1, double *lam_n, void *stream) {
+  dg_status st = adjoint_checks(m, c_n, dt, lam_np1, lam_n, "dg_adjoint_step_stages");
+  if (st != DG_OK) return st;
+  if (!u1 || !u2) return fail(DG_EINVAL, "dg_adjoint_step_stages: null argument");
+  if (lam_n == u1 || lam_n == u2) return fail(DG_EINVAL, "dg_adjoint_step_stages: lam_n aliases an input");
+  return adjoint_sweep(m, c_n, u1, u2, dt, lam_np1, lam_n, stream);
 }
 
 extern "C" dg_status dg_set_timing(dg_mesh *m, int enable) {

@@ -29,7 +29,7 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_volume_point
            "dg_conserved_totals", "dg_last_error", "dg_host_tables", "dg_set_timing",
            "dg_kernel_times", "dg_probe_fma_rate", "dg_device_status", "dg_rhs_noalloc", "dg_self_test", "dg_eval_points", "dg_rhs_adjoint", "dg_stable_dt",
            "dg_rk_step_method", "dg_limit", "dg_set_limiter", "dg_boundary_points",
-           "dg_set_boundary_state", "dg_volume_rule", "dg_set_small_mesh_stepper", "dg_det_j",
+           "dg_set_boundary_state", "dg_volume_rule", "dg_set_small_mesh_stepper", "dg_rk_step_stages", "dg_adjoint_step_stages", "dg_det_j",
            "dg_map_points", "dg_l2_error")
 KERNEL_KINDS = ("traces", "face", "element", "project", "totals", "adjoint", "other", "stepper")
 
@@ -83,6 +83,8 @@ def load(path: str = None):
         "dg_set_boundary_state": [P, P, P],
         "dg_set_limiter": [P, I],
         "dg_set_small_mesh_stepper": [P, I],
+        "dg_rk_step_stages": [P, P, D, P, P, P],
+        "dg_adjoint_step_stages": [P, P, P, P, D, P, P, P],
         "dg_det_j": [P, P, P],
         "dg_map_points": [P, I, P, P, P, P],
         "dg_l2_error": [P, I, P, P, P, P, P, I, P, P],
@@ -405,6 +407,24 @@ class Mesh:
         _check(load().dg_adjoint_step(self._h, _dev_ptr(c_n, "c_n", self.coef_shape), float(dt),
                                       _dev_ptr(lam_np1, "lam_np1", self.coef_shape),
                                       _dev_ptr(lam, "lam_n", self.coef_shape), _stream_ptr(stream)))
+        return lam
+
+    def rk_step_stages(self, c, dt: float, u1, u2, stream=None):
+        """One float64 SSP-RK3 step on c in place (the same bits as rk_step) that
+        also writes its stage values into u1 and u2."""
+        _check(load().dg_rk_step_stages(self._h, _dev_ptr(c, "c", self.coef_shape), float(dt),
+                                        _dev_ptr(u1, "u1", self.coef_shape), _dev_ptr(u2, "u2", self.coef_shape),
+                                        _stream_ptr(stream)))
+        return c
+
+    def adjoint_step_stages(self, c_n, u1, u2, dt: float, lam_np1, out=None, stream=None):
+        """adjoint_step with the step's stage values given (rk_step_stages)."""
+        import torch
+        lam = out if out is not None else torch.empty(self.coef_shape, dtype=torch.float64, device="cuda")
+        _check(load().dg_adjoint_step_stages(self._h, _dev_ptr(c_n, "c_n", self.coef_shape),
+                                             _dev_ptr(u1, "u1", self.coef_shape), _dev_ptr(u2, "u2", self.coef_shape),
+                                             float(dt), _dev_ptr(lam_np1, "lam_np1", self.coef_shape),
+                                             _dev_ptr(lam, "lam_n", self.coef_shape), _stream_ptr(stream)))
         return lam
 
     def stable_dt(self, c, cfl: float = 0.3, stream=None) -> float:

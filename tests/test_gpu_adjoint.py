@@ -63,6 +63,49 @@ def test_rhs_adjoint_parity(dgmod, oracle_mod, p, ne, n):
     assert rel_l2(got, o.rhs_vjp(c, lam)) < 1e-12
 
 
+@pytest.mark.parametrize("n", [6, 16, 128])
+@pytest.mark.parametrize("p,ne", [(1, 0), (2, 0), (3, 0), (5, 0)])
+def test_stored_stages_bitwise(dgmod, p, ne, n):
+    """dg_rk_step_stages gives dg_rk_step's new state bit for bit, and
+    dg_adjoint_step_stages on its stage values gives dg_adjoint_step's lam_n bit
+    for bit (6 x 6 and 16 x 16 run the fused small-mesh stepper in dg_rk_step,
+    128 x 128 the separate launches)."""
+    import torch
+    mesh = I.periodic_mesh(n)
+    m = dgmod.Mesh.from_mesh(mesh, p, n_edge_pts=ne)
+    rng = np.random.default_rng(7 * n + p)
+    c = m.project_function(I.perturbed_vortex)
+    lam = _dev(rng.standard_normal(tuple(c.shape)))
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    a, b = c.clone(), c.clone()
+    u1, u2 = torch.empty_like(c), torch.empty_like(c)
+    m.rk_step(a, dt, 1)
+    m.rk_step_stages(b, dt, u1, u2)
+    assert np.array_equal(_host(a), _host(b))
+    ref = _host(m.adjoint_step(c, dt, lam))
+    got = _host(m.adjoint_step_stages(c, u1, u2, dt, lam))
+    m.device_status()
+    assert np.array_equal(got, ref)
+
+
+def test_stored_stages_errors(dgmod):
+    import torch
+    mesh = I.periodic_mesh(6)
+    m = dgmod.Mesh.from_mesh(mesh, 1)
+    c = m.project_function(I.vortex)
+    u = torch.empty_like(c)
+    with pytest.raises(dgmod.DGError):
+        m.rk_step_stages(c, 1e-3, u, u)              # u1 and u2 the same buffer
+    with pytest.raises(dgmod.DGError):
+        m.rk_step_stages(c, 1e-3, c, u)              # u1 aliases c
+    with pytest.raises(dgmod.DGError):
+        m.adjoint_step_stages(c, u, u, 1e-3, c, out=u)   # lam_n aliases a stage
+    m.set_limiter(True)
+    with pytest.raises(dgmod.DGError):
+        m.rk_step_stages(c, 1e-3, u, torch.empty_like(c))
+    m.set_limiter(False)
+
+
 def _loss_setup(dgmod, oracle_mod, n, p):
     mesh = I.periodic_mesh(n)
     m = dgmod.Mesh.from_mesh(mesh, p)
@@ -72,9 +115,11 @@ def _loss_setup(dgmod, oracle_mod, n, p):
     return mesh, m, dt, c0, tgt0
 
 
-def test_autograd_matches_oracle_reverse_sweep(dgmod, oracle_mod):
+@pytest.mark.parametrize("keep_stages", [True, False])
+def test_autograd_matches_oracle_reverse_sweep(dgmod, oracle_mod, keep_stages):
     """40 steps, checkpoints every 8: the gradient of the density misfit with
-    respect to c0 equals the oracle's step-by-step reverse sweep."""
+    respect to c0 equals the oracle's step-by-step reverse sweep, with the stage
+    values kept by the recomputation or recomputed by each transposed step."""
     import torch
     from paper_1601_07944_gb300 import autograd as AG
     n, p, steps, every = 16, 2, 40, 8
@@ -83,7 +128,7 @@ def test_autograd_matches_oracle_reverse_sweep(dgmod, oracle_mod):
     m.rk_step(target, dt, steps)
     dJ = m.det_j()
     x = c0.clone().requires_grad_(True)
-    loss = AG.density_misfit(dJ, AG.solve(m, x, dt, steps, every), target)
+    loss = AG.density_misfit(dJ, AG.solve(m, x, dt, steps, every, keep_stages=keep_stages), target)
     loss.backward()
     g = _host(x.grad)
     # oracle reverse sweep from the same c0 and target
