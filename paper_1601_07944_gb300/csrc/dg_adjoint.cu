@@ -382,14 +382,16 @@ k_adj_element_sf(const double *__restrict__ u, const double *__restrict__ lam, d
       }
       double ub[M] = {0.0, 0.0, 0.0, 0.0};
       if (el < ecount) {
+        // the cotangents of G_r = ha and G_s = half ha + hb pulled back through
+        // J^tau: bx = g0 ha + g2 (half ha + hb) = (g0 + half g2) ha + g2 hb, by alike
         const double *g = geo + (size_t)(e0 + el) * GEO;
         const double half = sHalf[ia];
+        const double dax = fma(half, g[2], g[0]), day = fma(half, g[3], g[1]);
         double bx[M], by[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          const double ar = ha[m], as = fma(half, ha[m], hb[m]);
-          bx[m] = fma(ar, g[0], as * g[2]);
-          by[m] = fma(ar, g[1], as * g[3]);
+          bx[m] = fma(dax, ha[m], g[2] * hb[m]);
+          by[m] = fma(day, ha[m], g[3] * hb[m]);
         }
         flux_jac_t_xy(U, gamma, bx, by, ub);
       }

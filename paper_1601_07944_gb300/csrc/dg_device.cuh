@@ -371,23 +371,23 @@ __device__ __forceinline__ void flux_jac_t(const double U[M], const EulerSide &s
 // The volume term's pull-back at a point: out = A_x(U)^T bx + A_y(U)^T by for the
 // Jacobians A_x, A_y of the two Euler fluxes (flux_jac_t with n = (1, 0) and
 // (0, 1), the shared terms formed once):
-//   out = (T |v|^2/2 - sx u - sy v, bx0 + sx + bx1 u + by1 v - T u,
-//          by0 + sy + bx2 u + by2 v - T v, bx3 u + by3 v + T)
-// with sx = (bx1 mx + bx2 my + bx3 (E+p)) / rho, sy alike with by,
-// T = (gamma-1) (bx1 + bx3 u + by2 + by3 v).
+//   out = (T |v|^2/2 - sx u - sy v, bx0 + sx + (bx1 - T) u + by1 v,
+//          by0 + sy + bx2 u + (by2 - T) v, bx3 u + by3 v + T)
+// with sx = bx1 u + bx2 v + bx3 h, sy alike with by, h = (E+p) / rho the
+// enthalpy, T = (gamma-1) (bx1 + bx3 u + by2 + by3 v).
 __device__ __forceinline__ void flux_jac_t_xy(const double U[M], double gamma, const double bx[M],
                                               const double by[M], double out[M]) {
   const double g1 = gamma - 1.0;
   const double inv = recip(U[0]);
   const double u = U[1] * inv, v = U[2] * inv;
   const double q2 = fma(u, u, v * v);
-  const double H = fma(g1, fma(-0.5 * U[0], q2, U[3]), U[3]);
-  const double sx = fma(bx[1], U[1], fma(bx[2], U[2], bx[3] * H)) * inv;
-  const double sy = fma(by[1], U[1], fma(by[2], U[2], by[3] * H)) * inv;
+  const double h = fma(g1, fma(-0.5 * U[0], q2, U[3]), U[3]) * inv;
+  const double sx = fma(bx[1], u, fma(bx[2], v, bx[3] * h));
+  const double sy = fma(by[1], u, fma(by[2], v, by[3] * h));
   const double T = g1 * (fma(bx[3], u, bx[1]) + fma(by[3], v, by[2]));
   out[0] = fma(0.5 * T, q2, -fma(sx, u, sy * v));
-  out[1] = bx[0] + sx + fma(bx[1], u, fma(by[1], v, -T * u));
-  out[2] = by[0] + sy + fma(bx[2], u, fma(by[2], v, -T * v));
+  out[1] = fma(bx[1] - T, u, fma(by[1], v, bx[0] + sx));
+  out[2] = fma(by[2] - T, v, fma(bx[2], u, by[0] + sy));
   out[3] = fma(bx[3], u, fma(by[3], v, T));
 }
 
