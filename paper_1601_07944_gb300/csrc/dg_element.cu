@@ -63,10 +63,9 @@ struct SfCfg {
   static_assert(DIRECT || 8 * NQ >= M * NP, "the new state reuses the point buffer");
 };
 
-// Reference fluxes at one volume point: G_r = J^tau row 0 . (F1, F2), G_s = row 1
-// . (F1, F2).  The Euler flux along a direction d is (rho v_d, rho u v_d + p d_x,
-// rho v v_d + p d_y, (E + p) v_d) with v_d = (rho u d_x + rho v d_y) / rho.
 // The Euler flux of U along two directions a and b (Fa = F1 a_x + F2 a_y, ...).
+// The Euler flux along a direction d is (rho v_d, rho u v_d + p d_x,
+// rho v v_d + p d_y, (E + p) v_d) with v_d = (rho u d_x + rho v d_y) / rho.
 __device__ __forceinline__ void flux_two_dirs(const double U[M], double ax, double ay, double bx, double by,
                                               double gamma, int *err, double Fa[M], double Fb[M]) {
   const double inv = recip(U[0]);
@@ -82,6 +81,8 @@ __device__ __forceinline__ void flux_two_dirs(const double U[M], double ax, doub
     Fb[0] = mn; Fb[1] = fma(U[1], vd, p * bx); Fb[2] = fma(U[2], vd, p * by); Fb[3] = Ep * vd;
   }
 }
+// Reference fluxes at one volume point: G_r = J^tau row 0 . (F1, F2), G_s = row 1
+// . (F1, F2).
 __device__ __forceinline__ void ref_flux(const double U[M], const double *g, double gamma, int *err, double Gr[M],
                                          double Gs[M]) {
   flux_two_dirs(U, g[0], g[1], g[2], g[3], gamma, err, Gr, Gs);
