@@ -286,8 +286,12 @@ dg_status dg_set_limiter(dg_mesh *mesh, int enable);
 
 /* Same as dg_rk_step (Section 4.3.1) with c in HOST memory (pinned memory gives
  * the fastest copies): copies c to the device, takes nsteps steps and copies the
- * result back into c.  Errors as dg_rk_step, and DG_ENOMEM if the device copy of
- * the state cannot be allocated (first call on the handle).  Synchronous. */
+ * result back into c.  When c is page-locked memory the device can reach
+ * (cudaPointerGetAttributes: cudaMemoryTypeHost) and the call is float64
+ * without the limiter on a mesh the fused small-mesh stepper does not take, the
+ * first kernel reads c in place and makes the device copy itself (the same
+ * results).  Errors as dg_rk_step, and DG_ENOMEM if the device copy of the state
+ * cannot be allocated (first call on the handle).  Synchronous. */
 dg_status dg_rk_step_host(dg_mesh *mesh, double *c_host, double dt, int nsteps,
                           dg_precision prec, void *stream);
 

@@ -1194,6 +1194,35 @@ extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int 
     if (e != cudaSuccess) { cudaGetLastError(); m->host_state = nullptr; return fail(DG_ENOMEM, "dg_rk_step_host: cudaMalloc"); }
   }
   cudaStream_t s = (cudaStream_t)stream;
+  // c_host in page-locked memory the device reaches (NVLink-C2C on this part):
+  // the first kernel (the traces of c) reads it in place and writes the device
+  // copy the steps run on, so the copy in travels while the traces are formed.
+  // The same launches as below, so the same results.  (Float64 without the
+  // limiter, on meshes the fused small-mesh stepper does not take.  Writing
+  // the new state from the last stage straight into host memory measured
+  // slower than the copy out.)
+  if (nsteps >= 1 && prec == DG_FP64 && !m->limiter && m->bstate_set &&
+      !(m->small_stepper && dg::small_rk_fits(m))) {
+    cudaPointerAttributes pa;
+    double *dev = nullptr;
+    if (cudaPointerGetAttributes(&pa, c_host) == cudaSuccess) {
+      if (pa.type == cudaMemoryTypeHost && pa.devicePointer) dev = static_cast<double *>(pa.devicePointer);
+    } else {
+      cudaGetLastError();
+    }
+    if (dev && std::isfinite(dt)) {
+      DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] {
+                return dg::launch_traces(m, dev, m->trace, stream, m->host_state);
+              }), "dg_rk_step_host traces");
+      for (int i = 0; i < nsteps; ++i) {
+        dg_status st = rk_step_one(m, m->host_state, dt, true, DG_SSP_RK3, prec, stream);
+        if (st != DG_OK) return st;
+      }
+      DG_CUDA(cudaMemcpyAsync(c_host, m->host_state, bytes, cudaMemcpyDeviceToHost, s), "dg_rk_step_host D2H");
+      DG_CUDA(cudaStreamSynchronize(s), "dg_rk_step_host sync");
+      return DG_OK;
+    }
+  }
   DG_CUDA(cudaMemcpyAsync(m->host_state, c_host, bytes, cudaMemcpyHostToDevice, s), "dg_rk_step_host H2D");
   dg_status st = dg_rk_step(m, m->host_state, dt, nsteps, prec, stream);
   if (st != DG_OK) return st;

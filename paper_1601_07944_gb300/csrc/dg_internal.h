@@ -197,7 +197,8 @@ struct dg_mesh {
 namespace dg {
 
 // Kernel launchers (dg_kernels.cu).  All return a cudaError_t cast to int.
-int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream);
+// copy (optional): also writes c to copy (c may be host memory the device reaches)
+int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream, double *copy = nullptr);
 int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream);
 int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, int *per_sm);
 // out = mode==0 ? R(c) : the stage update su (and su.out2);  trace_out may be null.

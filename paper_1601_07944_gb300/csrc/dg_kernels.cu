@@ -41,7 +41,7 @@ namespace {
 template <int P, int NE>
 __global__ void __launch_bounds__(kThreads)
 k_traces(const double *__restrict__ c, double *__restrict__ trace, const double *__restrict__ EPa,
-         const double *__restrict__ EChiM1, const double *__restrict__ EChi, int N) {
+         const double *__restrict__ EChiM1, const double *__restrict__ EChi, int N, double *__restrict__ copy) {
   using C = Cfg<P, NE>;
   constexpr int NP = C::NP, ND = C::ND, NF = C::NF, EB = C::EB;
   __shared__ double sPa[ND * NE], sChiM1[NP], sChi[NP * NE];
@@ -59,6 +59,9 @@ k_traces(const double *__restrict__ c, double *__restrict__ trace, const double 
     for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x)
       sC[i] = i < ecount * M * NP ? src[i] : 0.0;
     __syncthreads();
+    // (c in host memory the device can reach: the device copy the steps run on)
+    if (copy)
+      for (int i = threadIdx.x; i < ecount * M * NP; i += blockDim.x) copy[(size_t)e0 * M * NP + i] = sC[i];
     // Z_a of face 0, once per (element, variable), as the element kernel forms them
     for (int i = threadIdx.x; i < ecount * M; i += blockDim.x) {
       double z[ND + 1];
@@ -351,19 +354,19 @@ k_limit_p1(double *c, double *__restrict__ trace, const int32_t *__restrict__ el
 // dispatch
 // ---------------------------------------------------------------------------
 template <int P, int NE>
-int run_traces(const dg_mesh *m, const double *c, double *trace, cudaStream_t s) {
+int run_traces(const dg_mesh *m, const double *c, double *trace, double *copy, cudaStream_t s) {
   using C = Cfg<P, NE>;
   const int ntiles = (int)((m->N + C::EB - 1) / C::EB);
   const int grid = ntiles < m->num_sms * 4 ? ntiles : m->num_sms * 4;
-  k_traces<P, NE><<<grid, kThreads, 0, s>>>(c, trace, m->tab.EPa, m->tab.EChiM1, m->tab.EChi, (int)m->N);
+  k_traces<P, NE><<<grid, kThreads, 0, s>>>(c, trace, m->tab.EPa, m->tab.EChiM1, m->tab.EChi, (int)m->N, copy);
   return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream) {
+int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream, double *copy) {
   cudaStream_t s = (cudaStream_t)stream;
-#define CALL(P, NE) run_traces<P, NE>(m, c, trace, s)
+#define CALL(P, NE) run_traces<P, NE>(m, c, trace, copy, s)
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);

@@ -134,6 +134,29 @@ def test_host_entry_matches_device_entry(dgmod):
     assert np.array_equal(_host(c), h.numpy())
 
 
+@pytest.mark.parametrize("p,steps", [(1, 1), (3, 1), (3, 3)])
+def test_host_entry_in_place_on_pinned_memory(dgmod, p, steps):
+    """On a mesh the fused small-mesh stepper does not take (9,800 elements), a
+    page-locked host state is read in place by the first kernel (the traces
+    kernel makes the device copy); a pageable one is copied in.  Both give
+    dg_rk_step's bits."""
+    import torch
+    mesh = I.periodic_mesh(70)
+    m = dgmod.Mesh.from_mesh(mesh, p)
+    c = m.project_function(I.perturbed_vortex)
+    dt = I.fixed_dt(mesh, I.perturbed_vortex, p)
+    pinned = torch.empty(c.shape, dtype=torch.float64).pin_memory()
+    pinned.copy_(c.cpu())
+    pageable = c.cpu().clone()
+    m.rk_step(c, dt, steps)
+    m.rk_step_host(pinned, dt, steps)
+    m.rk_step_host(pageable, dt, steps)
+    m.device_status()
+    ref = _host(c)
+    assert np.array_equal(pinned.numpy(), ref)
+    assert np.array_equal(pageable.numpy(), ref)
+
+
 def test_free_stream_full_size(dgmod):
     """A uniform state is an exact steady solution on the full 1024^2 p=5 mesh:
     the RHS vanishes up to the rounding of its two terms, each of size about
