@@ -455,9 +455,9 @@ k_element_sf(const double *c, const double *u0, double *out, double *__restrict_
 }
 
 
+// CTAs of k_element_sf per SM (the kernel's shared memory attribute set first)
 template <int P, int NE, int Q>
-int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
-                   const double *fhat, const StageUpdate &su, int mode, cudaStream_t s) {
+int element_sf_per_sm(const dg_mesh *m, int *per_sm) {
   using S = SfCfg<P, NE, Q>;
   static PerDevice attr_set;
   if (!attr_set.test(m->device)) {
@@ -467,14 +467,37 @@ int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *
     if (e != cudaSuccess) return (int)e;
     attr_set.set(m->device);
   }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_element_sf<P, NE, Q>, kThreads, S::SMEM);
+  *per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_element_sf<P, NE, Q>, kThreads, S::SMEM);
   if (e != cudaSuccess) return (int)e;
-  if (per_sm < 1) per_sm = 1;
-  const int ntiles = (int)((m->N + S::EB - 1) / S::EB);
+  if (*per_sm < 1) *per_sm = 1;
+  return (int)cudaSuccess;
+}
+
+// Elements [e0, e1) of the mesh (e1 < 0: all): the kernel runs on the views of
+// the arrays that start at element e0.  Each element's arithmetic does not
+// depend on the tile it falls in, so a range launch gives the same bits.
+template <int P, int NE, int Q>
+int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
+                   const double *fhat, const StageUpdate &su0, int mode, cudaStream_t s, int64_t e0 = 0,
+                   int64_t e1 = -1) {
+  using S = SfCfg<P, NE, Q>;
+  int per_sm = 0;
+  int err = element_sf_per_sm<P, NE, Q>(m, &per_sm);
+  if (err != (int)cudaSuccess) return err;
+  if (e1 < 0) e1 = m->N;
+  const int64_t n = e1 - e0;
+  if (n <= 0) return (int)cudaSuccess;
+  const size_t so = (size_t)e0 * M * S::NP;           // state rows of the range
+  StageUpdate su = su0;
+  if (su.acc) su.acc += so;
+  if (su.out2) su.out2 += so;
+  const int ntiles = (int)((n + S::EB - 1) / S::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_element_sf<P, NE, Q><<<grid, kThreads, S::SMEM, s>>>(c, u0, out, trace_out, fhat, m->geo, m->elem_face, m->tab,
-                                                      (int)m->N, m->F, su, mode, m->gamma, m->err_flag);
+  k_element_sf<P, NE, Q><<<grid, kThreads, S::SMEM, s>>>(
+      c + so, u0 ? u0 + so : nullptr, out + so, trace_out ? trace_out + (size_t)e0 * S::NF * M : nullptr, fhat,
+      m->geo + (size_t)e0 * GEO, m->elem_face + (size_t)e0 * 3, m->tab, (int)n, m->F, su, mode, m->gamma,
+      m->err_flag);
   return (int)cudaGetLastError();
 }
 
@@ -665,12 +688,30 @@ int launch_rk_small(dg_mesh *m, double *c, double dt, int nsteps, int method, vo
   return (int)cudaErrorInvalidValue;
 }
 
+int element_wave(const dg_mesh *m, int *tiles, int *elems_per_tile) {
+#define CALL(P, NE)                                                                                 \
+  (m->rule == DG_RULE_SYMMETRIC                                                                     \
+       ? (*elems_per_tile = SfCfg<P, NE, sym_points(P)>::EB, element_sf_per_sm<P, NE, sym_points(P)>(m, tiles)) \
+       : (*elems_per_tile = SfCfg<P, NE, 0>::EB, element_sf_per_sm<P, NE, 0>(m, tiles)))
+  int e = (int)cudaErrorInvalidValue;
+  if (m->p == 1 && m->ne == 2) e = CALL(1, 2);
+  else if (m->p == 2 && m->ne == 3) e = CALL(2, 3);
+  else if (m->p == 3 && m->ne == 4) e = CALL(3, 4);
+  else if (m->p == 3 && m->ne == 3) e = CALL(3, 3);
+  else if (m->p == 4 && m->ne == 5) e = CALL(4, 5);
+  else if (m->p == 5 && m->ne == 6) e = CALL(5, 6);
+#undef CALL
+  if (e == (int)cudaSuccess) *tiles *= m->num_sms;
+  return e;
+}
+
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out, double *trace_out,
-                   const double *fhat, const StageUpdate &su, int mode, void *stream) {
+                   const double *fhat, const StageUpdate &su, int mode, void *stream, int64_t e0, int64_t e1) {
   cudaStream_t s = (cudaStream_t)stream;
-#define CALL(P, NE)                                                                       \
-  (m->rule == DG_RULE_SYMMETRIC ? run_element_sf<P, NE, sym_points(P)>(m, c, u0, out, trace_out, fhat, su, mode, s) \
-                                : run_element_sf<P, NE, 0>(m, c, u0, out, trace_out, fhat, su, mode, s))
+#define CALL(P, NE)                                                                                        \
+  (m->rule == DG_RULE_SYMMETRIC                                                                            \
+       ? run_element_sf<P, NE, sym_points(P)>(m, c, u0, out, trace_out, fhat, su, mode, s, e0, e1)        \
+       : run_element_sf<P, NE, 0>(m, c, u0, out, trace_out, fhat, su, mode, s, e0, e1))
   if (m->p == 1 && m->ne == 2) return CALL(1, 2);
   if (m->p == 2 && m->ne == 3) return CALL(2, 3);
   if (m->p == 3 && m->ne == 4) return CALL(3, 4);

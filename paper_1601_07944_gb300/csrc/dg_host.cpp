@@ -413,6 +413,9 @@ void free_mesh(dg_mesh *m) {
   cudaFree(m->err_flag);
   cudaFree(m->gbar);
   cudaFree(m->tc_img[0]); cudaFree(m->tc_img[1]);
+  if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
+  for (auto &e : m->copy_ev)
+    if (e) cudaEventDestroy(e);
   if (m->timing) {
     for (auto &r : m->timing->pool) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete m->timing;
@@ -1184,6 +1187,58 @@ extern "C" dg_status dg_rk_step(dg_mesh *m, double *c, double dt, int nsteps, dg
   return dg_rk_step_method(m, c, dt, nsteps, DG_SSP_RK3, prec, stream);
 }
 
+// One float64 SSP-RK3 step on the device state c whose new state is also copied
+// into c_host: the last stage's element launch is split into chunks of whole
+// waves of the element kernel, and each chunk's rows travel to the host on
+// m->copy_stream while the next chunk computes (the same launches otherwise,
+// and the same bits: an element's arithmetic does not depend on its tile).
+static dg_status ssp_step_copy_out(dg_mesh *m, double *c, double dt, double *c_host, void *stream) {
+  using namespace dg;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!m->copy_stream) {
+    if (cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->copy_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->copy_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DG_ECUDA, "dg_rk_step_host: copy stream");
+    }
+  }
+  auto face = [&]() -> dg_status {
+    DG_CUDA((cudaError_t)timed(m, DG_K_FACE, stream, [&] { return launch_face_flux(m, m->trace, m->fhat, stream); }),
+            "dg_rk_step_host flux");
+    return DG_OK;
+  };
+  dg_status st;
+  for (int i = 0; i < 2; ++i) {
+    const RkStage rs = rk_stage(DG_SSP_RK3, i, dt, c, m->stage, m->rk_acc);
+    if ((st = face()) != DG_OK) return st;
+    DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+              return launch_element(m, rs.cin, rs.u0, rs.out, m->trace, m->fhat, rs.su, 1, stream);
+            }), "dg_rk_step_host stage");
+  }
+  if ((st = face()) != DG_OK) return st;
+  const RkStage rs = rk_stage(DG_SSP_RK3, 2, dt, c, m->stage, m->rk_acc);
+  int wave_tiles = 0, eb = 0;
+  DG_CUDA((cudaError_t)element_wave(m, &wave_tiles, &eb), "dg_rk_step_host wave");
+  const int64_t wave = (int64_t)wave_tiles * eb;
+  const int64_t waves = (m->N + wave - 1) / wave;
+  const int64_t chunk = std::max<int64_t>(1, waves / 4) * wave;
+  const size_t row = (size_t)M * m->np;
+  for (int64_t e0 = 0; e0 < m->N; e0 += chunk) {
+    const int64_t e1 = std::min<int64_t>(m->N, e0 + chunk);
+    DG_CUDA((cudaError_t)timed(m, DG_K_ELEMENT, stream, [&] {
+              return launch_element(m, rs.cin, rs.u0, rs.out, m->trace, m->fhat, rs.su, 1, stream, e0, e1);
+            }), "dg_rk_step_host last stage");
+    DG_CUDA(cudaEventRecord(m->copy_ev[0], s), "dg_rk_step_host order");
+    DG_CUDA(cudaStreamWaitEvent(m->copy_stream, m->copy_ev[0], 0), "dg_rk_step_host order");
+    DG_CUDA(cudaMemcpyAsync(c_host + e0 * row, c + e0 * row, sizeof(double) * (e1 - e0) * row,
+                            cudaMemcpyDeviceToHost, m->copy_stream), "dg_rk_step_host D2H");
+  }
+  DG_CUDA(cudaEventRecord(m->copy_ev[1], m->copy_stream), "dg_rk_step_host order");
+  DG_CUDA(cudaStreamWaitEvent(s, m->copy_ev[1], 0), "dg_rk_step_host order");
+  return DG_OK;
+}
+
 extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int nsteps,
                                      dg_precision prec, void *stream) {
   if (!m || !c_host) return fail(DG_EINVAL, "dg_rk_step_host: null argument");
@@ -1197,10 +1252,11 @@ extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int 
   // c_host in page-locked memory the device reaches (NVLink-C2C on this part):
   // the first kernel (the traces of c) reads it in place and writes the device
   // copy the steps run on, so the copy in travels while the traces are formed.
-  // The same launches as below, so the same results.  (Float64 without the
-  // limiter, on meshes the fused small-mesh stepper does not take.  Writing
-  // the new state from the last stage straight into host memory measured
-  // slower than the copy out.)
+  // The copy out of the new state runs in chunks behind the last stage
+  // (ssp_step_copy_out).  The same arithmetic as below, so the same results.
+  // (Float64 without the limiter, on meshes the fused small-mesh stepper does
+  // not take.  Writing the new state from the last stage straight into host
+  // memory measured slower than copies.)
   if (nsteps >= 1 && prec == DG_FP64 && !m->limiter && m->bstate_set &&
       !(m->small_stepper && dg::small_rk_fits(m))) {
     cudaPointerAttributes pa;
@@ -1214,11 +1270,12 @@ extern "C" dg_status dg_rk_step_host(dg_mesh *m, double *c_host, double dt, int 
       DG_CUDA((cudaError_t)timed(m, DG_K_TRACES, stream, [&] {
                 return dg::launch_traces(m, dev, m->trace, stream, m->host_state);
               }), "dg_rk_step_host traces");
-      for (int i = 0; i < nsteps; ++i) {
+      for (int i = 0; i + 1 < nsteps; ++i) {
         dg_status st = rk_step_one(m, m->host_state, dt, true, DG_SSP_RK3, prec, stream);
         if (st != DG_OK) return st;
       }
-      DG_CUDA(cudaMemcpyAsync(c_host, m->host_state, bytes, cudaMemcpyDeviceToHost, s), "dg_rk_step_host D2H");
+      dg_status st = ssp_step_copy_out(m, m->host_state, dt, c_host, stream);
+      if (st != DG_OK) return st;
       DG_CUDA(cudaStreamSynchronize(s), "dg_rk_step_host sync");
       return DG_OK;
     }

@@ -192,6 +192,8 @@ struct dg_mesh {
   unsigned *gbar;              // [2] grid barrier of the fused small-mesh stepper (count, generation)
   unsigned char *tc_img[2];    // B operand images of the tensor-core kernel (1xTF32, 3xTF32)
   int small_stepper;           // dg_set_small_mesh_stepper (on by default)
+  cudaStream_t copy_stream;    // dg_rk_step_host's copies out (created on first use)
+  cudaEvent_t copy_ev[2];
 };
 
 namespace dg {
@@ -202,8 +204,12 @@ int launch_traces(const dg_mesh *m, const double *c, double *trace, void *stream
 int launch_face_flux(const dg_mesh *m, const double *trace, double *fhat, void *stream);
 int resident_grid(const dg_mesh *m, const void *kernel, int threads, int64_t n, int *per_sm);
 // out = mode==0 ? R(c) : the stage update su (and su.out2);  trace_out may be null.
+// Elements [e0, e1) only (e1 < 0: all; the same bits per element either way).
 int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
-                   double *trace_out, const double *fhat, const StageUpdate &su, int mode, void *stream);
+                   double *trace_out, const double *fhat, const StageUpdate &su, int mode, void *stream,
+                   int64_t e0 = 0, int64_t e1 = -1);
+// The float64 element kernel's resident wave: tiles (all SMs) and elements per tile.
+int element_wave(const dg_mesh *m, int *tiles, int *elems_per_tile);
 // out = mode==0 ? R(c) : a0*u0 + b0*(c + dt*R(c))
 inline int launch_element(const dg_mesh *m, const double *c, const double *u0, double *out,
                           double *trace_out, const double *fhat, double dt, double a0, double b0,
