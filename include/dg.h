@@ -289,9 +289,10 @@ dg_status dg_set_limiter(dg_mesh *mesh, int enable);
  * result back into c.  When c is page-locked memory the device can reach
  * (cudaPointerGetAttributes: cudaMemoryTypeHost) and the call is float64
  * without the limiter on a mesh the fused small-mesh stepper does not take, the
- * first kernel reads c in place and makes the device copy itself (the same
- * results).  Errors as dg_rk_step, and DG_ENOMEM if the device copy of the state
- * cannot be allocated (first call on the handle).  Synchronous. */
+ * first kernel reads c in place and makes the device copy itself, and the copy
+ * back runs in chunks behind the last stage on a second stream of the handle
+ * (the same results).  Errors as dg_rk_step, and DG_ENOMEM if the device copy of
+ * the state cannot be allocated (first call on the handle).  Synchronous. */
 dg_status dg_rk_step_host(dg_mesh *mesh, double *c_host, double dt, int nsteps,
                           dg_precision prec, void *stream);
 
