@@ -49,7 +49,10 @@ struct SfCfg {
   using C = Cfg<P, NE, Q>;
   static constexpr bool DIRECT = Q > 0;
   static constexpr int NP = C::NP, ND = C::ND, NQ = C::NQ, NF = C::NF;
-  static constexpr int EB = EBX > 0 ? EBX : (P <= 1 ? 64 : (P <= 3 ? 32 : 16));
+  // tiles of 32 elements on 128 threads at p = 1 (64 on 256 measured 2.5 %
+  // slower there), 32 / 16 elements on 256 threads above
+  static constexpr int EB = EBX > 0 ? EBX : (P <= 3 ? 32 : 16);
+  static constexpr int THREADS = P <= 1 ? 128 : kThreads;
   // per element and variable, the edge-flux buffer holds the NF gathered fluxes,
   // then (in place) the LW sums of the factorised lift
   static constexpr int LW = ND + 2 * NE;
@@ -468,7 +471,7 @@ int element_sf_per_sm(const dg_mesh *m, int *per_sm) {
     attr_set.set(m->device);
   }
   *per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_element_sf<P, NE, Q>, kThreads, S::SMEM);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_element_sf<P, NE, Q>, S::THREADS, S::SMEM);
   if (e != cudaSuccess) return (int)e;
   if (*per_sm < 1) *per_sm = 1;
   return (int)cudaSuccess;
@@ -494,7 +497,7 @@ int run_element_sf(const dg_mesh *m, const double *c, const double *u0, double *
   if (su.out2) su.out2 += so;
   const int ntiles = (int)((n + S::EB - 1) / S::EB);
   const int grid = ntiles < m->num_sms * per_sm ? ntiles : m->num_sms * per_sm;
-  k_element_sf<P, NE, Q><<<grid, kThreads, S::SMEM, s>>>(
+  k_element_sf<P, NE, Q><<<grid, S::THREADS, S::SMEM, s>>>(
       c + so, u0 ? u0 + so : nullptr, out + so, trace_out ? trace_out + (size_t)e0 * S::NF * M : nullptr, fhat,
       m->geo + (size_t)e0 * GEO, m->elem_face + (size_t)e0 * 3, m->tab, (int)n, m->F, su, mode, m->gamma,
       m->err_flag);
