@@ -680,7 +680,9 @@ def run_case(name: str):
     """A few steps of one workload, untimed, for a profiler to capture: `mixed`
     (3xTF32, 256x256, p=3, vortex), `mixed512` (3xTF32, 512x512, p=4, perturbed
     vortex), `limiter` (float64 RK4 with every stage limited, 304x304, p=1,
-    perturbed vortex), `adjoint` (two dg_adjoint_step calls, 256x256, p=2)."""
+    perturbed vortex), `adjoint` (two dg_adjoint_step calls, 256x256, p=2), `small`
+    (the fused small-mesh stepper: two float64 RK4 calls of 100 steps each,
+    10x10 (200 elements), p=1, perturbed vortex)."""
     import torch
     from paper_1601_07944_gb300 import _build, dg, inputs as I
     _build.build()
@@ -711,6 +713,13 @@ def run_case(name: str):
         out = torch.empty_like(c)
         for _ in range(2):
             m.adjoint_step(c, dt, lam, out=out)
+    elif name == "small":
+        mesh = I.periodic_mesh(10)
+        m = dg.Mesh.from_mesh(mesh, 1)
+        dt = I.fixed_dt(mesh, I.perturbed_vortex, 1)
+        c = m.project_function(I.perturbed_vortex)
+        for _ in range(2):
+            m.rk_step(c, dt, 100, method="rk4")
     else:
         raise SystemExit("unknown case %r" % name)
     torch.cuda.synchronize()
@@ -1010,7 +1019,7 @@ def main():
                     help="both volume rules at p=1..5 in every precision instead of the benchmark")
     ap.add_argument("--sweep", action="store_true",
                     help="mesh-size scaling runs (p=1 x 10000 and p=4 x 1000 RK4 steps) instead of the benchmark")
-    ap.add_argument("--case", choices=["mixed", "mixed512", "limiter", "adjoint"],
+    ap.add_argument("--case", choices=["mixed", "mixed512", "limiter", "adjoint", "small"],
                     help="a few untimed steps of one workload (for a profiler) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
