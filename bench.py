@@ -59,12 +59,22 @@ def flops_element_per_elem(p: int, ne: int) -> float:
     the edges), counting an FMA as 2 flops and a multiply or add as 1:
       W = chi c                          2 N_p (p+1) 4
       U = P W (the a = 0 term, P_0 = 1, is a copy)
-                                         2 (p+1)^2 p 4
+                                         2 (p+1)^2 p 4;
+        p = 3, 5: on the mirror pairs of the Gauss-Legendre nodes, the sums
+        over the even and the odd a and their sum and difference
+                                         (p+1) h 4 (2 p + 2)
       per volume point: 1/rho (4 FMA Newton steps), pressure, the Euler flux
       along row 1 of J^tau (H_beta = G_s) and along row 0 + (1+alpha)/2 row 1
-      (H_alpha = G_r + (1+alpha)/2 G_s; 2 FMAs for the direction)      42
-      Xa, Xb (p <= 4: Xa(0, .) = 0 without arithmetic, P_0' = 0)
-                                         2 (p+1)^2 (2p+1) 4; p = 5: 4 (p+1)^3 4
+      (H_alpha = G_r + (1+alpha)/2 G_s)  38
+      the directions of H_alpha (2 FMAs each): once per alpha node and element
+      for p >= 3                         4 (p+1); p <= 2: 4 per point
+      Xa, Xb (Xa(0, .) = 0 without arithmetic, P_0' = 0); at p = 2-4 folded on
+      the mirror pairs of the Gauss-Legendre nodes: per (ib, variable) 4 h
+      additions (h = floor((p+1)/2) pairs; at p = 3 formed in the point phase)
+      and T = (2p+1) h (+ p+1 for p even, the middle node) products
+                                         (p+1) 4 (2 T + 4 h);
+      p = 1: 2 (p+1)^2 (2p+1) 4; p = 5 (every a, on the pair sums and
+      differences): 4 (p+1)^2 h 4 + 16 h (p+1)
       V = chiA Xa + dchiB Xb (modes with a = 0: the Xb term only)
                                          (4 (N_p - p - 1) + 2 (p+1)) (p+1) 4
       lift sums per variable (face 0: omega P_a; faces 1, 2: F1 +/- F2)
@@ -77,8 +87,17 @@ def flops_element_per_elem(p: int, ne: int) -> float:
                                          (2 N_p + 1 + n_e (2 p + 2 N_p)) 4"""
     NP = (p + 1) * (p + 2) // 2
     ND = p + 1
-    x_phase = 2 * ND * ND * (2 * ND - 1) * 4 if p <= 4 else 4 * ND ** 3 * 4
-    return (2 * NP * ND * 4 + 2 * ND * ND * p * 4 + 42 * ND * ND + x_phase + (4 * (NP - ND) + 2 * ND) * ND * 4
+    h = ND // 2
+    if 2 <= p <= 4:
+        T = (2 * ND - 1) * h + (ND if ND % 2 else 0)
+        x_phase = ND * 4 * (2 * T + 4 * h)
+    elif p == 1:
+        x_phase = 2 * ND * ND * (2 * ND - 1) * 4
+    else:
+        x_phase = 4 * ND * ND * h * 4 + 16 * h * ND
+    u_phase = ND * h * 4 * (2 * p + 2) if p in (3, 5) else 2 * ND * ND * p * 4
+    dirs = 4 * ND if p >= 3 else 4 * ND * ND
+    return (2 * NP * ND * 4 + u_phase + 38 * ND * ND + dirs + x_phase + (4 * (NP - ND) + 2 * ND) * ND * 4
             + (2 * ND * ne + 2 * ne) * 4 + 2 * (1 + ne) * NP * 4 + 5 * NP * 4 + (2 * NP + 1 + ne * (2 * p + 2 * NP)) * 4)
 
 
@@ -135,6 +154,16 @@ def _src_hash(*names) -> str:
 TRAFFIC = {
     # k_element_sf<3,4,0>, stage-2 launch (reads u^n), 256x256 p=3 vortex (one ncu capture)
     "448baf8993eb4ed8": 119190000 + 42630000,
+}
+
+
+# Float64 thread instructions per element of one element-kernel launch
+# (DFMA + DMUL + DADD: sm__sass_thread_inst_executed_op_d{fma,mul,add}_pred_on.sum
+# over the elements) from one ncu capture, keyed like TRAFFIC.  The float64 pipe
+# takes an FMA, a multiply or an add in the same issue slot, so these against
+# the pipe's FMA rate (half the flop peak) tell how full the kernel keeps the
+# pipe, whatever its mix of FMAs and single operations.
+FP64_INST = {
 }
 
 
@@ -943,6 +972,13 @@ def run_ours(args, world, rank, local):
                         "frac": achieved / fp64_peak if fp64_peak else None, "traffic": TRAFFIC.get(khash),
                         "peak_source": "measured live: dg_probe_fma_rate float64 FMA chain",
                         "flops_per_launch": flops, "avg_launch_ms": avg_el_ms}
+            ipe = FP64_INST.get(khash)
+            if ipe is not None and fp64_peak:
+                ach_i = ipe * m.N / (avg_el_ms * 1e-3) / 1e12
+                roofline["fp64_issue"] = {"inst_per_elem": ipe, "achieved": ach_i, "peak": fp64_peak / 2,
+                                          "unit": "T float64 instructions/s", "frac": ach_i / (fp64_peak / 2)}
+            else:
+                roofline["fp64_issue"] = None
         else:
             nbytes = bytes_element_tc_per_elem(p, ne) * m.N
             achieved = nbytes / (avg_el_ms * 1e-3) / 1e9

@@ -49,6 +49,9 @@ struct SfCfg {
   using C = Cfg<P, NE, Q>;
   static constexpr bool DIRECT = Q > 0;
   static constexpr int NP = C::NP, ND = C::ND, NQ = C::NQ, NF = C::NF;
+  // the volume points in mirror pairs of the Gauss-Legendre nodes (p + 1 even,
+  // p >= 3; at p = 1 the pairing saves nothing)
+  static constexpr bool PAIRS = !DIRECT && ND % 2 == 0 && P >= 3;
   // tiles of 32 elements on 128 threads at p = 1 (64 on 256 measured 2.5 %
   // slower there), 32 / 16 elements on 256 threads above
   static constexpr int EB = EBX > 0 ? EBX : (P <= 3 ? 32 : 16);
@@ -61,7 +64,13 @@ struct SfCfg {
   // per element: the sum-factorisation buffer (8 ND^2), or for the direct form
   // the new state (its point buffer is read until the last mode is done)
   static constexpr int XS = DIRECT ? M * NP : 8 * ND * ND;
-  static constexpr int TILE = EB * (M * NP + XS + 8 * NQ + RS * M);
+  // per element (collapsed grid, p >= 3): the flux directions of H_alpha at the
+  // ND alpha nodes and of H_beta, [ND + 1][2], formed once per tile (at p <= 2
+  // the few points' FMAs are not worth the registers: at p = 2 they cost a
+  // third resident CTA per SM)
+  static constexpr bool PREDIR = !DIRECT && P >= 3;
+  static constexpr int DS = PREDIR ? 2 * (ND + 1) : 0;
+  static constexpr int TILE = EB * (M * NP + XS + 8 * NQ + RS * M + DS);
   static constexpr int SMEM = (TAB + TILE) * 8;
   static_assert(DIRECT || 8 * NQ >= M * NP, "the new state reuses the point buffer");
 };
@@ -135,6 +144,7 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
   double *sX = sC + EB * M * NP;       // [EB][ND][ND][8]    W (first 4), then Xa, Xb (direct: the new state)
   double *sH = sX + EB * S::XS;        // [EB][NQ][8]        Ha, Hb (direct: G_r, G_s); later the new state
   double *sF = sH + EB * NQ * 8;       // [EB][RS][M]        -F_hat_out * l, then the lift sums
+  double *sDir = sF + EB * S::RS * M;  // [EB][ND+1][2]      J^tau row 0 + half_ia row 1 (ia < ND), row 1
   double *sO = S::DIRECT ? sX : sH;
   constexpr int RS = S::RS;
 
@@ -163,6 +173,27 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
     const double *src = c + (size_t)e0 * M * NP;
     for (int i = threadIdx.x; i < EB * M * NP; i += blockDim.x)
       sC[i] = i < ecount * M * NP ? src[i] : 0.0;
+    if constexpr (S::PREDIR) {
+      // the flux is linear in its direction: H_alpha = G_r + half G_s is the flux
+      // along J^tau row 0 + half row 1, H_beta = G_s the flux along row 1
+      for (int i = threadIdx.x; i < EB * (ND + 1); i += blockDim.x) {
+        const int el = i / (ND + 1), ia = i - el * (ND + 1);
+        double dx = 0.0, dy = 0.0;
+        if (el < ecount) {
+          const double *g = geo + (size_t)(e0 + el) * GEO;
+          if (ia < ND) {
+            const double half = sHalf[ia];
+            dx = fma(half, g[2], g[0]);
+            dy = fma(half, g[3], g[1]);
+          } else {
+            dx = g[2];
+            dy = g[3];
+          }
+        }
+        sDir[2 * i] = dx;
+        sDir[2 * i + 1] = dy;
+      }
+    }
     for (int i = threadIdx.x; i < EB * NF; i += blockDim.x) {
       const int el = i / NF, qk = i - el * NF;
       double v[M] = {0.0, 0.0, 0.0, 0.0};
@@ -244,40 +275,146 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
       }
       __syncthreads();
 
-      // volume points: U = sum_a P_a W; Euler flux; Ha, Hb
-      for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
-        const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
-        // P_0 = 1: the a = 0 term is W(0, ib) itself
-        const double *w0 = sX + ((el * ND) * ND + ib) * 8;
-        double U[M] = {w0[0], w0[1], w0[2], w0[3]};
+      // volume points: U = sum_a P_a W; Euler flux; Ha, Hb.
+      // PAIRS (p + 1 even, p >= 3): one item per (element, ib, mirror pair ia,
+      // ia' = ND-1-ia of the Gauss-Legendre nodes).  With P_a(alpha_ia') =
+      // (-1)^a P_a(alpha_ia) the pair's states are E +/- O, E = sum_{a even} P_a W,
+      // O = sum_{a odd} P_a W, and the point slots of the pair receive the sums
+      // and differences the folded projection takes: slot ia (Ha + Ha', Hb + Hb'),
+      // slot ia' (Ha - Ha', Hb - Hb').
+      if constexpr (S::PAIRS) {
+        constexpr int NH = ND / 2;
+        for (int i = threadIdx.x; i < EB * ND * NH; i += blockDim.x) {
+          const int el = i / (ND * NH), r = i - el * (ND * NH), ib = r / NH, ia = r - ib * NH;
+          const int ia2 = ND - 1 - ia;
+          const double *w0 = sX + ((el * ND) * ND + ib) * 8;
+          double E[M] = {w0[0], w0[1], w0[2], w0[3]}, O[M];
 #pragma unroll
-        for (int a = 1; a < ND; ++a) {
-          const double pa = sPa[a * ND + ia];
-          const double *w = sX + ((el * ND + a) * ND + ib) * 8;
+          for (int a = 1; a < ND; ++a) {
+            const double pa = sPa[a * ND + ia];
+            const double *w = sX + ((el * ND + a) * ND + ib) * 8;
 #pragma unroll
-          for (int m = 0; m < M; ++m) U[m] += pa * w[m];
+            for (int m = 0; m < M; ++m) {
+              if (a == 1) O[m] = pa * w[m];
+              else if (a & 1) O[m] = fma(pa, w[m], O[m]);
+              else E[m] = fma(pa, w[m], E[m]);
+            }
+          }
+          double S1[M], D1[M], S2[M], D2[M];
+          if (el < ecount) {
+            const double *dir = sDir + el * 2 * (ND + 1);
+            const double bx = dir[2 * ND], by = dir[2 * ND + 1];
+            double U[M], Ha[M], Hb[M], Ha2[M], Hb2[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) U[m] = E[m] + O[m];
+            flux_two_dirs(U, dir[2 * ia], dir[2 * ia + 1], bx, by, gamma, err, Ha, Hb);
+#pragma unroll
+            for (int m = 0; m < M; ++m) U[m] = E[m] - O[m];
+            flux_two_dirs(U, dir[2 * ia2], dir[2 * ia2 + 1], bx, by, gamma, err, Ha2, Hb2);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              S1[m] = Ha[m] + Ha2[m]; D1[m] = Ha[m] - Ha2[m];
+              S2[m] = Hb[m] + Hb2[m]; D2[m] = Hb[m] - Hb2[m];
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < M; ++m) { S1[m] = 0.0; D1[m] = 0.0; S2[m] = 0.0; D2[m] = 0.0; }
+          }
+          double *h1 = sH + ((size_t)el * NQ + ib * ND + ia) * 8, *h2 = sH + ((size_t)el * NQ + ib * ND + ia2) * 8;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            h1[m] = S1[m]; h1[4 + m] = S2[m];
+            h2[m] = D1[m]; h2[4 + m] = D2[m];
+          }
         }
-        double Ha[M], Hb[M];
-        if (el < ecount) {
-          // the flux is linear in its direction: Ha = G_r + half G_s is the flux
-          // along J^tau row 0 + half row 1, Hb = G_s the flux along row 1
-          const double *g = geo + (size_t)(e0 + el) * GEO;
-          const double half = sHalf[ia];
-          flux_two_dirs(U, fma(half, g[2], g[0]), fma(half, g[3], g[1]), g[2], g[3], gamma, err, Ha, Hb);
-        } else {
+      } else {
+        for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
+          const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
+          // P_0 = 1: the a = 0 term is W(0, ib) itself
+          const double *w0 = sX + ((el * ND) * ND + ib) * 8;
+          double U[M] = {w0[0], w0[1], w0[2], w0[3]};
 #pragma unroll
-          for (int m = 0; m < M; ++m) { Ha[m] = 0.0; Hb[m] = 0.0; }
+          for (int a = 1; a < ND; ++a) {
+            const double pa = sPa[a * ND + ia];
+            const double *w = sX + ((el * ND + a) * ND + ib) * 8;
+#pragma unroll
+            for (int m = 0; m < M; ++m) U[m] += pa * w[m];
+          }
+          double Ha[M], Hb[M];
+          if (el < ecount) {
+            if constexpr (S::PREDIR) {
+              const double *dir = sDir + el * 2 * (ND + 1);
+              flux_two_dirs(U, dir[2 * ia], dir[2 * ia + 1], dir[2 * ND], dir[2 * ND + 1], gamma, err, Ha, Hb);
+            } else {
+              // the flux along J^tau row 0 + half row 1 and along row 1
+              const double *g = geo + (size_t)(e0 + el) * GEO;
+              const double half = sHalf[ia];
+              flux_two_dirs(U, fma(half, g[2], g[0]), fma(half, g[3], g[1]), g[2], g[3], gamma, err, Ha, Hb);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < M; ++m) { Ha[m] = 0.0; Hb[m] = 0.0; }
+          }
+          double *h = sH + (size_t)i * 8;
+#pragma unroll
+          for (int m = 0; m < M; ++m) { h[m] = Ha[m]; h[4 + m] = Hb[m]; }
         }
-        double *h = sH + (size_t)i * 8;
-#pragma unroll
-        for (int m = 0; m < M; ++m) { h[m] = Ha[m]; h[4 + m] = Hb[m]; }
       }
       __syncthreads();
 
-      if constexpr (P <= 4) {
-        // Xa(a, ib) = sum_ia Ha wa P_a', Xb(a, ib) = sum_ia Hb wa P_a; one item per
-        // (element, ib, variable) runs over every a, so that Xa(0, ib) = 0 (P_0' = 0)
-        // costs no arithmetic
+      if constexpr (P >= 2 && P <= 4) {
+        // Xa(a, ib) = sum_ia Ha wa P_a', Xb(a, ib) = sum_ia Hb wa P_a, one item per
+        // (element, ib, variable) over every a, folded on the mirror pairs of the
+        // Gauss-Legendre nodes (alpha_{ND-1-ia} = -alpha_ia, the same weight):
+        // P_a(-x) = (-1)^a P_a(x) and P_a'(-x) = (-1)^(a+1) P_a'(x), so
+        //   Xb(a) = sum_{ia < ND/2} wa P_a(alpha_ia) (Hb_ia +/- Hb_ia'),  + for a even
+        //   Xa(a) = sum_{ia < ND/2} wa P_a'(alpha_ia) (Ha_ia -/+ Ha_ia'), - for a even,
+        // and for ND odd the middle node alpha = 0 enters Xb of the even a and Xa
+        // of the odd a only (P_a(0) = 0 for a odd, P_a'(0) = 0 for a even).  Per item
+        // that is 4 (ND / 2) additions (already formed by the point phase when
+        // PAIRS) and about half the products of the plain sums; Xa(0, ib) = 0
+        // (P_0' = 0) costs no arithmetic.
+        constexpr int NH = ND / 2, MID = ND / 2;
+        for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
+          const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
+          const double *hrow = sH + ((el * NQ) + ib * ND) * 8;
+          double ea[NH], oa[NH], eb[NH], ob[NH];
+#pragma unroll
+          for (int ia = 0; ia < NH; ++ia) {
+            const double *h1 = hrow + ia * 8, *h2 = hrow + (ND - 1 - ia) * 8;
+            const double a1 = h1[m], a2 = h2[m], b1 = h1[4 + m], b2 = h2[4 + m];
+            if constexpr (S::PAIRS) {
+              ea[ia] = a1; oa[ia] = a2;
+              eb[ia] = b1; ob[ia] = b2;
+            } else {
+              ea[ia] = a1 + a2; oa[ia] = a1 - a2;
+              eb[ia] = b1 + b2; ob[ia] = b1 - b2;
+            }
+          }
+          double xa[ND], xb[ND];
+#pragma unroll
+          for (int a = 0; a < ND; ++a) {
+            const double *fb = (a & 1) ? ob : eb, *fa = (a & 1) ? ea : oa;
+            double sb = 0.0, sa = 0.0;
+            if ((ND & 1) && !(a & 1)) sb = hrow[MID * 8 + 4 + m] * sPaW[a * ND + MID];
+            if ((ND & 1) && (a & 1)) sa = hrow[MID * 8 + m] * sdPaW[a * ND + MID];
+#pragma unroll
+            for (int ia = 0; ia < NH; ++ia) {
+              sb = fma(fb[ia], sPaW[a * ND + ia], sb);
+              if (a > 0) sa = fma(fa[ia], sdPaW[a * ND + ia], sa);
+            }
+            xa[a] = sa;
+            xb[a] = sb;
+          }
+#pragma unroll
+          for (int a = 0; a < ND; ++a) {
+            double *x = sX + ((el * ND + a) * ND + ib) * 8;
+            x[m] = xa[a];
+            x[4 + m] = xb[a];
+          }
+        }
+      } else if constexpr (P <= 4) {
+        // p = 1: the plain sums (the folding would add more than it saves)
         for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
           const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
           double xa[ND], xb[ND];
@@ -301,16 +438,22 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
         }
       } else {
         // p = 5: one item per (element, a, ib) for all four variables (the
-        // per-variable form above would spill at this size)
+        // per-variable form above would spill at this size), on the pair sums and
+        // differences of the point phase (PAIRS): Xa(a) takes the sums of Ha for
+        // a odd and the differences for a even, Xb(a) the sums of Hb for a even
+        // and the differences for a odd, over the ND / 2 pairs
+        static_assert(S::PAIRS && S::PREDIR, "p = 5 has mirror pairs");
+        constexpr int NH = ND / 2;
         for (int i = threadIdx.x; i < EB * ND * ND; i += blockDim.x) {
           const int el = i / (ND * ND), a = (i / ND) % ND, ib = i % ND;
           double xa[M] = {0.0, 0.0, 0.0, 0.0}, xb[M] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-          for (int ia = 0; ia < ND; ++ia) {
+          for (int ia = 0; ia < NH; ++ia) {
             const double dp = sdPaW[a * ND + ia], pa = sPaW[a * ND + ia];
-            const double *h = sH + ((el * NQ) + ib * ND + ia) * 8;
+            const double *hs = sH + ((el * NQ) + ib * ND + ia) * 8, *hd = sH + ((el * NQ) + ib * ND + ND - 1 - ia) * 8;
+            const double *fa = (a & 1) ? hs : hd, *fb = (a & 1) ? hd : hs;
 #pragma unroll
-            for (int m = 0; m < M; ++m) { xa[m] += h[m] * dp; xb[m] += h[4 + m] * pa; }
+            for (int m = 0; m < M; ++m) { xa[m] = fma(fa[m], dp, xa[m]); xb[m] = fma(fb[4 + m], pa, xb[m]); }
           }
           double *x = sX + (size_t)i * 8;
 #pragma unroll
