@@ -153,7 +153,7 @@ def _src_hash(*names) -> str:
 # a code change voids the entry.
 TRAFFIC = {
     # k_element_sf<3,4,0>, stage-2 launch (reads u^n), 256x256 p=3 vortex (one ncu capture)
-    "448baf8993eb4ed8": 119190000 + 42630000,
+    "2589403be7b65c72": 119270912 + 42965760,
 }
 
 
@@ -164,6 +164,9 @@ TRAFFIC = {
 # the pipe's FMA rate (half the flop peak) tell how full the kernel keeps the
 # pipe, whatever its mix of FMAs and single operations.
 FP64_INST = {
+    # k_element_sf<3,4,0>, stage-2 launch, 256x256 p=3 vortex: 1,512 DFMA + 289.2 DMUL
+    # + 240.6 DADD per element (the stage-1 launch, without u^n, has 40 fewer)
+    "2589403be7b65c72": 1512.0 + 289.1875 + 240.59375,
 }
 
 
