@@ -60,9 +60,10 @@ def flops_element_per_elem(p: int, ne: int) -> float:
       W = chi c                          2 N_p (p+1) 4
       U = P W (the a = 0 term, P_0 = 1, is a copy)
                                          2 (p+1)^2 p 4;
-        p = 3, 5: on the mirror pairs of the Gauss-Legendre nodes, the sums
-        over the even and the odd a and their sum and difference
-                                         (p+1) h 4 (2 p + 2)
+        p >= 3: on the mirror pairs of the Gauss-Legendre nodes, the sums
+        over the even and the odd a and their sum and difference, and for p
+        even the middle node alpha = 0 (P_a(0) = 0 for odd a)
+                                         (p+1) h 4 (2 p + 2) [+ (p+1) 4 p]
       per volume point: 1/rho (4 FMA Newton steps), pressure, the Euler flux
       along row 1 of J^tau (H_beta = G_s) and along row 0 + (1+alpha)/2 row 1
       (H_alpha = G_r + (1+alpha)/2 G_s)  38
@@ -70,7 +71,7 @@ def flops_element_per_elem(p: int, ne: int) -> float:
       for p >= 3                         4 (p+1); p <= 2: 4 per point
       Xa, Xb (Xa(0, .) = 0 without arithmetic, P_0' = 0); at p = 2-4 folded on
       the mirror pairs of the Gauss-Legendre nodes: per (ib, variable) 4 h
-      additions (h = floor((p+1)/2) pairs; at p = 3 formed in the point phase)
+      additions (h = floor((p+1)/2) pairs; at p >= 3 formed in the point phase)
       and T = (2p+1) h (+ p+1 for p even, the middle node) products
                                          (p+1) 4 (2 T + 4 h);
       p = 1: 2 (p+1)^2 (2p+1) 4; p = 5 (every a, on the pair sums and
@@ -95,7 +96,10 @@ def flops_element_per_elem(p: int, ne: int) -> float:
         x_phase = 2 * ND * ND * (2 * ND - 1) * 4
     else:
         x_phase = 4 * ND * ND * h * 4 + 16 * h * ND
-    u_phase = ND * h * 4 * (2 * p + 2) if p in (3, 5) else 2 * ND * ND * p * 4
+    if p >= 3:
+        u_phase = ND * h * 4 * (2 * p + 2) + (ND * 4 * 2 * (p // 2) if ND % 2 else 0)
+    else:
+        u_phase = 2 * ND * ND * p * 4
     dirs = 4 * ND if p >= 3 else 4 * ND * ND
     return (2 * NP * ND * 4 + u_phase + 38 * ND * ND + dirs + x_phase + (4 * (NP - ND) + 2 * ND) * ND * 4
             + (2 * ND * ne + 2 * ne) * 4 + 2 * (1 + ne) * NP * 4 + 5 * NP * 4 + (2 * NP + 1 + ne * (2 * p + 2 * NP)) * 4)

@@ -49,9 +49,11 @@ struct SfCfg {
   using C = Cfg<P, NE, Q>;
   static constexpr bool DIRECT = Q > 0;
   static constexpr int NP = C::NP, ND = C::ND, NQ = C::NQ, NF = C::NF;
-  // the volume points in mirror pairs of the Gauss-Legendre nodes (p + 1 even,
-  // p >= 3; at p = 1 the pairing saves nothing)
-  static constexpr bool PAIRS = !DIRECT && ND % 2 == 0 && P >= 3;
+  // the volume points in mirror pairs of the Gauss-Legendre nodes (p >= 3; at
+  // p = 1 the pairing saves nothing, at p = 2 its registers would cost the
+  // third resident CTA per SM).  The small-mesh stepper's tiles take the same
+  // arithmetic, so that its results stay bitwise those of k_element_sf.
+  static constexpr bool PAIRS = !DIRECT && P >= 3;
   // tiles of 32 elements on 128 threads at p = 1 (64 on 256 measured 2.5 %
   // slower there), 32 / 16 elements on 256 threads above
   static constexpr int EB = EBX > 0 ? EBX : (P <= 3 ? 32 : 16);
@@ -276,15 +278,43 @@ __device__ __forceinline__ void element_sf_tiles(double *smem, const double *c, 
       __syncthreads();
 
       // volume points: U = sum_a P_a W; Euler flux; Ha, Hb.
-      // PAIRS (p + 1 even, p >= 3): one item per (element, ib, mirror pair ia,
-      // ia' = ND-1-ia of the Gauss-Legendre nodes).  With P_a(alpha_ia') =
-      // (-1)^a P_a(alpha_ia) the pair's states are E +/- O, E = sum_{a even} P_a W,
-      // O = sum_{a odd} P_a W, and the point slots of the pair receive the sums
-      // and differences the folded projection takes: slot ia (Ha + Ha', Hb + Hb'),
-      // slot ia' (Ha - Ha', Hb - Hb').
+      // PAIRS (p >= 3): one item per (element, ib, mirror pair ia, ia' = ND-1-ia
+      // of the Gauss-Legendre nodes), then (p + 1 odd) one per (element, ib) for
+      // the middle node.  With P_a(alpha_ia') = (-1)^a P_a(alpha_ia) the pair's
+      // states are E +/- O, E = sum_{a even} P_a W, O = sum_{a odd} P_a W, and the
+      // point slots of the pair receive the sums and differences the folded
+      // projection takes: slot ia (Ha + Ha', Hb + Hb'), slot ia' (Ha - Ha',
+      // Hb - Hb'); the middle slot keeps (Ha, Hb).
       if constexpr (S::PAIRS) {
-        constexpr int NH = ND / 2;
-        for (int i = threadIdx.x; i < EB * ND * NH; i += blockDim.x) {
+        constexpr int NH = ND / 2, NPAIR = EB * ND * NH, NMID = (ND & 1) ? EB * ND : 0;
+        for (int i = threadIdx.x; i < NPAIR + NMID; i += blockDim.x) {
+          if ((ND & 1) && i >= NPAIR) {
+            // the middle node alpha = 0 (p + 1 odd), after all the pairs so that
+            // warps stay uniform: P_a(0) = 0 for odd a
+            const int el = (i - NPAIR) / ND, ib = (i - NPAIR) - el * ND;
+            constexpr int MID = ND / 2;
+            const double *w0 = sX + ((el * ND) * ND + ib) * 8;
+            double U[M] = {w0[0], w0[1], w0[2], w0[3]};
+#pragma unroll
+            for (int a = 2; a < ND; a += 2) {
+              const double pa = sPa[a * ND + MID];
+              const double *w = sX + ((el * ND + a) * ND + ib) * 8;
+#pragma unroll
+              for (int m = 0; m < M; ++m) U[m] = fma(pa, w[m], U[m]);
+            }
+            double Ha[M], Hb[M];
+            if (el < ecount) {
+              const double *dir = sDir + el * 2 * (ND + 1);
+              flux_two_dirs(U, dir[2 * MID], dir[2 * MID + 1], dir[2 * ND], dir[2 * ND + 1], gamma, err, Ha, Hb);
+            } else {
+#pragma unroll
+              for (int m = 0; m < M; ++m) { Ha[m] = 0.0; Hb[m] = 0.0; }
+            }
+            double *h = sH + ((size_t)el * NQ + ib * ND + MID) * 8;
+#pragma unroll
+            for (int m = 0; m < M; ++m) { h[m] = Ha[m]; h[4 + m] = Hb[m]; }
+            continue;
+          }
           const int el = i / (ND * NH), r = i - el * (ND * NH), ib = r / NH, ia = r - ib * NH;
           const int ia2 = ND - 1 - ia;
           const double *w0 = sX + ((el * ND) * ND + ib) * 8;
