@@ -273,6 +273,9 @@ struct AdjSf {
   // (W, Xa~, Xb~ at (a, ib), later U~ with stride 4); ub at the points [NQ][4];
   // Z_a of u and of lb [M][ND] each
   static constexpr int XS = 12 * ND * ND;
+  // p >= 2: the volume points in mirror pairs of the Gauss-Legendre nodes, the
+  // transpose of the forward kernel's folding (at p = 1 it saves nothing)
+  static constexpr bool PAIRS = P >= 2;
   static constexpr int TILE = EB * (2 * M * NP + XS + 4 * NQ + 2 * M * ND);
   static constexpr int SMEM = (TAB + TILE) * 8;
 };
@@ -357,62 +360,163 @@ k_adj_element_sf(const double *__restrict__ u, const double *__restrict__ lam, d
     __syncthreads();
 
     // points: U, the cotangents of G_r and G_s, through J^tau and the flux
-    // Jacobians to ub; one item per (element, point)
-    for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
-      const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
-      const double *x0 = sX + ((el * ND) * ND + ib) * 12;
-      double U[M], ha[M], hb[M];
-      const double pw0 = sPaW[ia];
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        U[m] = x0[m];                                   // P_0 = 1
-        ha[m] = 0.0;
-        hb[m] = pw0 * x0[8 + m];
-      }
-#pragma unroll
-      for (int a = 1; a < ND; ++a) {
-        const double pa = sPa[a * ND + ia], dpw = sdPaW[a * ND + ia], pw = sPaW[a * ND + ia];
-        const double *x = sX + ((el * ND + a) * ND + ib) * 12;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          U[m] = fma(pa, x[m], U[m]);
-          ha[m] = fma(dpw, x[4 + m], ha[m]);
-          hb[m] = fma(pw, x[8 + m], hb[m]);
-        }
-      }
-      double ub[M] = {0.0, 0.0, 0.0, 0.0};
-      if (el < ecount) {
-        // the cotangents of G_r = ha and G_s = half ha + hb pulled back through
-        // J^tau: bx = g0 ha + g2 (half ha + hb) = (g0 + half g2) ha + g2 hb, by alike
-        const double *g = geo + (size_t)(e0 + el) * GEO;
-        const double half = sHalf[ia];
-        const double dax = fma(half, g[2], g[0]), day = fma(half, g[3], g[1]);
-        double bx[M], by[M];
+    // Jacobians to ub; one item per (element, point), or (PAIRS) one per
+    // (element, ib, mirror pair ia, ia' = ND-1-ia) and then one per (element, ib)
+    // for the middle node of an odd p + 1.  With P_a(-x) = (-1)^a P_a(x),
+    // P_a'(-x) = (-1)^(a+1) P_a'(x) and equal weights, each of U, ha, hb at the
+    // pair is S +/- A from its sums over the terms that keep (S) and flip (A)
+    // their sign; the pair's slots get ub + ub' (ia) and ub - ub' (ia'), which
+    // the transposed interpolation below takes.
+    if constexpr (A::PAIRS) {
+      constexpr int NH = ND / 2, NPAIR = EB * ND * NH, NMID = (ND & 1) ? EB * ND : 0, MID = ND / 2;
+      for (int i = threadIdx.x; i < NPAIR + NMID; i += blockDim.x) {
+        const bool mid = (ND & 1) && i >= NPAIR;
+        const int el = mid ? (i - NPAIR) / ND : i / (ND * NH);
+        const int ib = mid ? (i - NPAIR) - el * ND : (i - el * (ND * NH)) / NH;
+        const int ia = mid ? MID : (i - el * (ND * NH)) - ib * NH, ia2 = ND - 1 - ia;
+        const double *x0 = sX + ((el * ND) * ND + ib) * 12;
+        const double pw0 = sPaW[ia];
+        // S: the terms of the same sign at ia and ia' (U, hb: even a; ha: odd a)
+        double SU[M], AU[M], Sa[M], Aa[M], Sb[M], Ab[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          bx[m] = fma(dax, ha[m], g[2] * hb[m]);
-          by[m] = fma(day, ha[m], g[3] * hb[m]);
+          SU[m] = x0[m];                                // P_0 = 1
+          Sb[m] = pw0 * x0[8 + m];
+          AU[m] = 0.0; Sa[m] = 0.0; Aa[m] = 0.0; Ab[m] = 0.0;
         }
-        flux_jac_t_xy(U, gamma, bx, by, ub);
-      }
-      double *b = sB + (size_t)i * 4;
 #pragma unroll
-      for (int m = 0; m < M; ++m) b[m] = ub[m];
+        for (int a = 1; a < ND; ++a) {
+          if (mid && (a & 1)) {
+            // at alpha = 0 only the terms of P_a' (odd a) remain
+            const double dpw = sdPaW[a * ND + ia];
+            const double *x = sX + ((el * ND + a) * ND + ib) * 12;
+#pragma unroll
+            for (int m = 0; m < M; ++m) Sa[m] = a == 1 ? dpw * x[4 + m] : fma(dpw, x[4 + m], Sa[m]);
+            continue;
+          }
+          const double pa = sPa[a * ND + ia], dpw = sdPaW[a * ND + ia], pw = sPaW[a * ND + ia];
+          const double *x = sX + ((el * ND + a) * ND + ib) * 12;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            if (a & 1) {
+              AU[m] = a == 1 ? pa * x[m] : fma(pa, x[m], AU[m]);
+              Sa[m] = a == 1 ? dpw * x[4 + m] : fma(dpw, x[4 + m], Sa[m]);
+              Ab[m] = a == 1 ? pw * x[8 + m] : fma(pw, x[8 + m], Ab[m]);
+            } else {
+              SU[m] = fma(pa, x[m], SU[m]);
+              if (!mid) Aa[m] = a == 2 ? dpw * x[4 + m] : fma(dpw, x[4 + m], Aa[m]);
+              Sb[m] = fma(pw, x[8 + m], Sb[m]);
+            }
+          }
+        }
+        double ub1[M] = {0.0, 0.0, 0.0, 0.0}, ub2[M] = {0.0, 0.0, 0.0, 0.0};
+        if (el < ecount) {
+          const double *g = geo + (size_t)(e0 + el) * GEO;
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            if (mid && side == 1) break;
+            const double sg = side ? -1.0 : 1.0;
+            double U[M], bx[M], by[M];
+            const double half = sHalf[side ? ia2 : ia];
+            const double dax = fma(half, g[2], g[0]), day = fma(half, g[3], g[1]);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              U[m] = mid ? SU[m] : fma(sg, AU[m], SU[m]);
+              const double ha = mid ? Sa[m] : fma(sg, Aa[m], Sa[m]);
+              const double hb = mid ? Sb[m] : fma(sg, Ab[m], Sb[m]);
+              bx[m] = fma(dax, ha, g[2] * hb);
+              by[m] = fma(day, ha, g[3] * hb);
+            }
+            flux_jac_t_xy(U, gamma, bx, by, side ? ub2 : ub1);
+          }
+        }
+        double *b1 = sB + ((size_t)el * NQ + ib * ND + ia) * 4;
+        if (mid) {
+#pragma unroll
+          for (int m = 0; m < M; ++m) b1[m] = ub1[m];
+        } else {
+          double *b2 = sB + ((size_t)el * NQ + ib * ND + ia2) * 4;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            b1[m] = ub1[m] + ub2[m];
+            b2[m] = ub1[m] - ub2[m];
+          }
+        }
+      }
+    } else {
+      for (int i = threadIdx.x; i < EB * NQ; i += blockDim.x) {
+        const int el = i / NQ, k = i - el * NQ, ib = k / ND, ia = k - ib * ND;
+        const double *x0 = sX + ((el * ND) * ND + ib) * 12;
+        double U[M], ha[M], hb[M];
+        const double pw0 = sPaW[ia];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          U[m] = x0[m];                                   // P_0 = 1
+          ha[m] = 0.0;
+          hb[m] = pw0 * x0[8 + m];
+        }
+#pragma unroll
+        for (int a = 1; a < ND; ++a) {
+          const double pa = sPa[a * ND + ia], dpw = sdPaW[a * ND + ia], pw = sPaW[a * ND + ia];
+          const double *x = sX + ((el * ND + a) * ND + ib) * 12;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            U[m] = fma(pa, x[m], U[m]);
+            ha[m] = fma(dpw, x[4 + m], ha[m]);
+            hb[m] = fma(pw, x[8 + m], hb[m]);
+          }
+        }
+        double ub[M] = {0.0, 0.0, 0.0, 0.0};
+        if (el < ecount) {
+          // the cotangents of G_r = ha and G_s = half ha + hb pulled back through
+          // J^tau: bx = g0 ha + g2 (half ha + hb) = (g0 + half g2) ha + g2 hb, by alike
+          const double *g = geo + (size_t)(e0 + el) * GEO;
+          const double half = sHalf[ia];
+          const double dax = fma(half, g[2], g[0]), day = fma(half, g[3], g[1]);
+          double bx[M], by[M];
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            bx[m] = fma(dax, ha[m], g[2] * hb[m]);
+            by[m] = fma(day, ha[m], g[3] * hb[m]);
+          }
+          flux_jac_t_xy(U, gamma, bx, by, ub);
+        }
+        double *b = sB + (size_t)i * 4;
+#pragma unroll
+        for (int m = 0; m < M; ++m) b[m] = ub[m];
+      }
     }
     __syncthreads();
 
-    // U~(a, ib) = sum_ia P_a(ia) ub(ia, ib); one item per (element, ib, variable)
+    // U~(a, ib) = sum_ia P_a(ia) ub(ia, ib); one item per (element, ib, variable).
+    // PAIRS: over the pairs' sums (even a) and differences (odd a), and the
+    // middle node (even a only; P_0 = 1 makes the a = 0 sum additions)
     for (int i = threadIdx.x; i < EB * ND * M; i += blockDim.x) {
       const int el = i / (ND * M), ib = (i / M) % ND, m = i % M;
       double ut[ND];
+      const double *brow = sB + ((el * NQ) + ib * ND) * 4 + m;
+      if constexpr (A::PAIRS) {
+        constexpr int NH = ND / 2, MID = ND / 2;
 #pragma unroll
-      for (int a = 0; a < ND; ++a) ut[a] = 0.0;
+        for (int a = 0; a < ND; ++a) {
+          double t = ((ND & 1) && !(a & 1)) ? (a == 0 ? brow[MID * 4] : sPa[a * ND + MID] * brow[MID * 4]) : 0.0;
 #pragma unroll
-      for (int ia = 0; ia < ND; ++ia) {
-        const double b = sB[((el * NQ) + ib * ND + ia) * 4 + m];
-        ut[0] += b;
+          for (int ia = 0; ia < NH; ++ia) {
+            const double v = brow[((a & 1) ? ND - 1 - ia : ia) * 4];
+            t = a == 0 ? t + v : fma(sPa[a * ND + ia], v, t);
+          }
+          ut[a] = t;
+        }
+      } else {
 #pragma unroll
-        for (int a = 1; a < ND; ++a) ut[a] = fma(sPa[a * ND + ia], b, ut[a]);
+        for (int a = 0; a < ND; ++a) ut[a] = 0.0;
+#pragma unroll
+        for (int ia = 0; ia < ND; ++ia) {
+          const double b = brow[ia * 4];
+          ut[0] += b;
+#pragma unroll
+          for (int a = 1; a < ND; ++a) ut[a] = fma(sPa[a * ND + ia], b, ut[a]);
+        }
       }
 #pragma unroll
       for (int a = 0; a < ND; ++a) sX[((el * ND + a) * ND + ib) * 4 + m] = ut[a];
