@@ -55,9 +55,13 @@ struct SfCfg {
   // arithmetic, so that its results stay bitwise those of k_element_sf.
   static constexpr bool PAIRS = !DIRECT && P >= 3;
   // tiles of 32 elements on 128 threads at p = 1 (64 on 256 measured 2.5 %
-  // slower there), 32 / 16 elements on 256 threads above
-  static constexpr int EB = EBX > 0 ? EBX : (P <= 3 ? 32 : 16);
-  static constexpr int THREADS = P <= 1 ? 128 : kThreads;
+  // slower there), 32 on 256 threads at p = 2 (16 on 128: 6 % slower), 16 on
+  // 128 at p = 3 (four CTAs per SM instead of two with 32 on 256: 8 % faster;
+  // 8 on 64: 8 % slower), 16 on 256 at p = 4-5 (8 on 128: 7 % slower at p = 4,
+  // and at p = 5 no faster on the collapsed grid, 6 % slower on the symmetric
+  // rule)
+  static constexpr int EB = EBX > 0 ? EBX : (P <= 2 ? 32 : 16);
+  static constexpr int THREADS = (P <= 1 || P == 3) ? 128 : kThreads;
   // per element and variable, the edge-flux buffer holds the NF gathered fluxes,
   // then (in place) the LW sums of the factorised lift
   static constexpr int LW = ND + 2 * NE;
