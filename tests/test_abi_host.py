@@ -62,6 +62,28 @@ def test_host_tables_match_oracle(lib, oracle_mod, p):
         assert rel(T["phi_face"][q], pf) < 4e-16
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_collapsed_grid_alpha_nodes_are_mirror_pairs(lib, p):
+    """The float64 element kernels fold their alpha sums on mirror pairs of
+    nodes (P_a(-x) = (-1)^a P_a(x)); that needs the library's alpha nodes to be
+    symmetric about 0 with equal weights, and the middle node of an odd count at
+    0, to rounding."""
+    T = dg.host_tables(p)
+    nd = p + 1
+    r = T["vol_r"].reshape(nd, nd)          # point index ib * nd + ia
+    s = T["vol_s"].reshape(nd, nd)
+    w = T["vol_w"].reshape(nd, nd)
+    beta = 2.0 * s - 1.0
+    alpha = 4.0 * r / (1.0 - beta) - 1.0
+    # alpha recovered from the rounded points: the rounding of r grows by 4 / (1 - beta)
+    tol = 8 * np.finfo(float).eps / (1.0 - beta).min()
+    assert np.abs(alpha - alpha[:1, :]).max() < tol           # the same alpha nodes on every beta line
+    assert np.abs(alpha + alpha[:, ::-1]).max() < tol         # alpha_{nd-1-ia} = -alpha_ia
+    assert np.abs(w - w[:, ::-1]).max() <= 4 * np.finfo(float).eps * np.abs(w).max()
+    if nd % 2:
+        assert np.abs(alpha[:, nd // 2]).max() < tol
+
+
 def test_host_tables_p3_three_edge_points(lib, oracle_mod):
     T = dg.host_tables(3, 3)
     x, w = oracle_mod.gauss_legendre(3)
