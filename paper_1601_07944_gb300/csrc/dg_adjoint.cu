@@ -417,6 +417,8 @@ k_adj_element_sf(const double *__restrict__ u, const double *__restrict__ lam, d
             if (mid && side == 1) break;
             const double sg = side ? -1.0 : 1.0;
             double U[M], bx[M], by[M];
+            // the cotangents of G_r = ha and G_s = half ha + hb pulled back
+            // through J^tau, as for a single point
             const double half = sHalf[side ? ia2 : ia];
             const double dax = fma(half, g[2], g[0]), day = fma(half, g[3], g[1]);
 #pragma unroll
